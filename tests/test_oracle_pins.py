@@ -1,0 +1,398 @@
+"""Pins of the FP64 oracle against closed forms, invariants, hand-worked examples and brute force.
+
+Each check is chosen so that a plausible slip in the oracle (a dropped term, a wrong sign, a wrong
+index, a transposed operand) fails at least one of them. None re-types an oracle formula.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.special import erfc, j0
+
+from conftest import golden_lines
+from oracle import phy_oracle as O
+from paper_2510_07843_gb300 import synth as S
+
+
+def crandn(rng, *shape):
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / math.sqrt(2.0)
+
+
+# ------------------------------------------------------------------ constellation
+
+@pytest.mark.parametrize("qm", [2, 4, 6, 8])
+def test_constellation_unit_energy_and_grid(qm):
+    pts = O.qam_points(qm)
+    assert len(np.unique(np.round(pts, 12))) == 1 << qm
+    assert abs(np.mean(np.abs(pts) ** 2) - 1.0) < 1e-12
+    # square grid of odd integers scaled by the NR normalisation
+    h = qm // 2
+    nrm = math.sqrt(2.0 * (4 ** h - 1) / 3.0)
+    lv = np.arange(-(2 ** h) + 1, 2 ** h, 2)
+    assert set(np.round(pts.real * nrm).astype(int)) == set(lv)
+    assert set(np.round(pts.imag * nrm).astype(int)) == set(lv)
+
+
+@pytest.mark.parametrize("qm", [2, 4, 6, 8])
+def test_constellation_gray_neighbours(qm):
+    """Horizontally or vertically adjacent points differ in exactly one bit; I bits are even."""
+    pts = O.qam_points(qm)
+    bt = O.point_bits(qm)
+    dmin = 2.0 / math.sqrt(2.0 * (4 ** (qm // 2) - 1) / 3.0)
+    for a in range(len(pts)):
+        for b in range(len(pts)):
+            if abs(abs(pts[a] - pts[b]) - dmin) < 1e-9:
+                diff = np.nonzero(bt[a] != bt[b])[0]
+                assert len(diff) == 1
+                # a horizontal step flips an even (in-phase) bit, a vertical one an odd bit
+                horiz = abs(pts[a].imag - pts[b].imag) < 1e-9
+                assert (diff[0] % 2 == 0) == horiz
+
+
+def test_constellation_first_bit_is_sign():
+    for qm in (2, 4, 6, 8):
+        pts = O.qam_points(qm)
+        bt = O.point_bits(qm)
+        assert np.all((pts.real > 0) == (bt[:, 0] == 0))
+        assert np.all((pts.imag > 0) == (bt[:, 1] == 0))
+
+
+@pytest.mark.parametrize("qm", [2, 4, 6, 8])
+def test_generator_mapper_agrees_with_oracle_slicer(qm):
+    """Two independent writings of the NR mapper: the transmitter's and the oracle's."""
+    rng = np.random.default_rng(qm)
+    bits = rng.integers(0, 2, size=(500, qm), dtype=np.uint8)
+    x = S.gray_qam_modulate(bits, qm)
+    np.testing.assert_array_equal(O.slice_bits(x, qm), bits)
+
+
+# ------------------------------------------------------------------ detection
+
+def _golden_lmmse():
+    cases, cur = [], None
+    for tok in golden_lines("lmmse_handworked.txt"):
+        if tok[0] == "case":
+            cur = {"s2": float(tok[2])}
+            cases.append(cur)
+        else:
+            cur[tok[0]] = np.array([float(v) for v in tok[1:]])
+    return cases
+
+
+def test_lmmse_handworked():
+    for c in _golden_lmmse():
+        H = (c["H"][0::2] + 1j * c["H"][1::2]).reshape(2, 2)
+        y = c["y"][0::2] + 1j * c["y"][1::2]
+        x_ref = c["x"][0::2] + 1j * c["x"][1::2]
+        x, d = O.lmmse_gram(H, y, c["s2"])
+        np.testing.assert_allclose(x, x_ref, atol=1e-14)
+        np.testing.assert_allclose(d, c["d"], atol=1e-14)
+        sinr, _, _ = O.sinr_unbias(x, d, c["s2"])
+        np.testing.assert_allclose(sinr, c["sinr"], rtol=1e-13)
+        xc, _ = O.lmmse_covariance_lu(H, y, c["s2"])
+        np.testing.assert_allclose(xc, x_ref, atol=1e-14)
+
+
+@pytest.mark.parametrize("nr,nl", [(2, 2), (4, 2), (16, 4), (64, 16)])
+def test_zero_forcing_recovers_symbols(nr, nl):
+    """Noise-free, s2 = 0: the Gram form is zero forcing and returns x exactly."""
+    rng = np.random.default_rng(nr * 100 + nl)
+    H = crandn(rng, 50, nr, nl)
+    x = crandn(rng, 50, nl)
+    y = np.einsum("brl,bl->br", H, x)
+    xh, _ = O.lmmse_gram(H, y, 0.0)
+    np.testing.assert_allclose(xh, x, atol=1e-10)
+
+
+@pytest.mark.parametrize("nr,nl,s2", [(2, 2, 0.1), (4, 2, 0.01), (16, 4, 0.5), (8, 8, 1e-3)])
+def test_push_through_identity(nr, nl, s2):
+    """The paper's covariance form (LU on H H^H + s2 I) equals the Gram form."""
+    rng = np.random.default_rng(7 + nr)
+    for _ in range(10):
+        H = crandn(rng, nr, nl)
+        y = crandn(rng, nr)
+        xc, W = O.lmmse_covariance_lu(H, y, s2)
+        xg, _ = O.lmmse_gram(H, y, s2)
+        Wg = np.linalg.inv(O.gram(H, s2)) @ np.conj(H.T)
+        np.testing.assert_allclose(W, Wg, rtol=1e-10, atol=1e-12)
+        np.testing.assert_allclose(xc, xg, rtol=1e-10, atol=1e-12)
+
+
+def test_orthogonal_channel_closed_form():
+    """H^H H = c I  =>  x_hat = H^H y / (c + s2), (A^-1)_kk = 1/(c + s2)."""
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(crandn(rng, 16, 16))
+    c, s2 = 2.5, 0.3
+    H = math.sqrt(c) * Q[:, :4]
+    y = crandn(rng, 16)
+    x, d = O.lmmse_gram(H, y, s2)
+    np.testing.assert_allclose(x, np.conj(H.T) @ y / (c + s2), atol=1e-13)
+    np.testing.assert_allclose(d, np.full(4, 1.0 / (c + s2)), atol=1e-13)
+
+
+def test_single_layer_mrc_closed_form():
+    """One layer: x_hat = h^H y / (|h|^2 + s2), SINR = |h|^2 / s2."""
+    rng = np.random.default_rng(4)
+    h = crandn(rng, 8, 1)
+    y = crandn(rng, 8)
+    s2 = 0.2
+    x, d = O.lmmse_gram(h, y, s2)
+    nh = float(np.sum(np.abs(h) ** 2))
+    np.testing.assert_allclose(x[0], np.vdot(h[:, 0], y) / (nh + s2), rtol=1e-13)
+    sinr, _, _ = O.sinr_unbias(x, d, s2)
+    np.testing.assert_allclose(sinr[0], nh / s2, rtol=1e-12)
+
+
+def test_unbiased_error_times_sinr_is_one():
+    """E|x~ - x|^2 SINR = 1 per layer for the unbiased LMMSE output (genie channel)."""
+    rng = np.random.default_rng(5)
+    nb, nr, nl, s2 = 40000, 4, 3, 0.3
+    H = crandn(rng, nb, nr, nl)
+    bits = rng.integers(0, 2, size=(nb, nl, 4), dtype=np.uint8)
+    x = S.gray_qam_modulate(bits, 4)
+    y = np.einsum("brl,bl->br", H, x) + math.sqrt(s2) * crandn(rng, nb, nr)
+    xh, d = O.lmmse_gram(H, y, s2)
+    sinr, xt, _ = O.sinr_unbias(xh, d, s2)
+    v = np.abs(xt - x) ** 2 * sinr
+    # mean of nb*nl samples of an O(1)-variance variable: 5 sigma ~ 0.02
+    assert abs(v.mean() - 1.0) < 0.03, v.mean()
+
+
+def test_pivot_ratio_closed_forms():
+    A = np.diag([4.0, 1.0, 0.5]).astype(np.complex128)
+    assert abs(O.pivot_ratio(A) - 0.5 / 4.0) < 1e-15
+    a, b, c = 2.0, 1.0 + 1.0j, 3.0
+    A2 = np.array([[a, np.conj(b)], [b, c]])
+    p1 = c - abs(b) ** 2 / a  # second pivot of [[a, b*], [b, c]]
+    assert abs(O.pivot_ratio(A2) - min(a, p1) / max(a, p1)) < 1e-14
+    assert O.pivot_ratio(np.array([[1.0, 2.0], [2.0, 1.0]], dtype=np.complex128)) == 0.0
+
+
+def test_ml_bruteforce_vs_mmse_2x2_qpsk():
+    """Exact ML over 16 hypotheses: never more bit errors than MMSE on average, agrees at high SNR."""
+    rng = np.random.default_rng(6)
+    nb = 4000
+    for snr_db, agree_min in ((5.0, 0.5), (25.0, 0.98)):
+        s2 = 10 ** (-snr_db / 10)
+        H = crandn(rng, nb, 2, 2)
+        bits = rng.integers(0, 2, size=(nb, 2, 2), dtype=np.uint8)
+        x = S.gray_qam_modulate(bits, 2)
+        y = np.einsum("brl,bl->br", H, x) + math.sqrt(s2) * crandn(rng, nb, 2)
+        ml = O.ml_detect_bruteforce(H, y, 2)
+        ml_bits = O.point_bits(2)[ml]
+        xh, d = O.lmmse_gram(H, y, s2)
+        _, xt, _ = O.sinr_unbias(xh, d, s2)
+        mm_bits = O.slice_bits(xt, 2)
+        e_ml = np.mean(ml_bits != bits)
+        e_mm = np.mean(mm_bits != bits)
+        assert e_ml <= e_mm + 0.005, (snr_db, e_ml, e_mm)
+        assert np.mean(np.all(ml_bits == mm_bits, axis=(-1, -2))) >= agree_min
+
+
+def test_siso_awgn_qpsk_ber_matches_q_function():
+    """Flat unit channel, genie detection: QPSK bit error rate equals Q(sqrt(SNR))."""
+    rng = np.random.default_rng(8)
+    nb = 200000
+    snr_db = 6.0
+    s2 = 10 ** (-snr_db / 10)
+    bits = rng.integers(0, 2, size=(nb, 1, 2), dtype=np.uint8)
+    x = S.gray_qam_modulate(bits, 2)
+    H = np.ones((nb, 1, 1), dtype=np.complex128)
+    y = x + math.sqrt(s2) * crandn(rng, nb, 1)
+    xh, d = O.lmmse_gram(H, y, s2)
+    sinr, xt, s2e = O.sinr_unbias(xh, d, s2)
+    llr = O.llr_maxlog(xt, s2e, 2)
+    ber = np.mean((llr < 0).astype(np.uint8) != bits)
+    p = 0.5 * erfc(math.sqrt(1.0 / s2) / math.sqrt(2.0))
+    sd = math.sqrt(p * (1 - p) / (2 * nb))
+    assert abs(ber - p) < 5 * sd, (ber, p)
+
+
+# ------------------------------------------------------------------ LLR
+
+def test_llr_handworked_16qam():
+    for tok in golden_lines("llr_handworked.txt"):
+        qm = int(tok[0])
+        xt = float(tok[1]) + 1j * float(tok[2])
+        s2e = float(tok[3])
+        ref = np.array([float(v) for v in tok[4:]])
+        np.testing.assert_allclose(O.llr_maxlog(np.array([xt]), np.array([s2e]), qm)[0], ref,
+                                   atol=1e-12)
+
+
+def test_llr_qpsk_closed_form():
+    rng = np.random.default_rng(9)
+    xt = crandn(rng, 200) * 2
+    s2e = rng.uniform(0.05, 2.0, 200)
+    llr = O.llr_maxlog(xt, s2e, 2)
+    np.testing.assert_allclose(llr[:, 0], 2 * math.sqrt(2) * xt.real / s2e, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(llr[:, 1], 2 * math.sqrt(2) * xt.imag / s2e, rtol=1e-12, atol=1e-12)
+
+
+def test_llr_16qam_inner_outer_closed_form():
+    """b2 of 16-QAM (inner/outer level): LLR = 4 (2 - |u|) / (10 s2eff), u = sqrt(10) Re x~."""
+    rng = np.random.default_rng(10)
+    xt = crandn(rng, 300) * 1.5
+    s2e = rng.uniform(0.05, 1.0, 300)
+    llr = O.llr_maxlog(xt, s2e, 4)
+    u = np.abs(xt.real) * math.sqrt(10)
+    np.testing.assert_allclose(llr[:, 2], 4 * (2 - u) / (10 * s2e), rtol=1e-10, atol=1e-10)
+
+
+@pytest.mark.parametrize("qm", [2, 4, 6, 8])
+def test_llr_sign_equals_slicer(qm):
+    rng = np.random.default_rng(11 + qm)
+    xt = crandn(rng, 2000) * 1.3
+    llr = O.llr_maxlog(xt, np.full(2000, 0.3), qm)
+    hard = (llr < 0).astype(np.uint8)
+    np.testing.assert_array_equal(hard, O.slice_bits(xt, qm))
+
+
+@pytest.mark.parametrize("qm", [4, 6, 8])
+def test_llr_separable_equals_bruteforce(qm):
+    """Max-log over the 2-D grid equals two 1-D PAM searches (even bits I, odd bits Q)."""
+    rng = np.random.default_rng(12 + qm)
+    xt = crandn(rng, 500) * 1.3
+    s2e = rng.uniform(0.1, 1.0, 500)
+    llr = O.llr_maxlog(xt, s2e, qm)
+    pts = O.qam_points(qm)
+    bt = O.point_bits(qm)
+    for i in range(qm):
+        comp = pts.real if i % 2 == 0 else pts.imag
+        v = xt.real if i % 2 == 0 else xt.imag
+        lv1 = np.unique(comp[bt[:, i] == 1])
+        lv0 = np.unique(comp[bt[:, i] == 0])
+        d1 = np.min((v[:, None] - lv1) ** 2, axis=1)
+        d0 = np.min((v[:, None] - lv0) ** 2, axis=1)
+        np.testing.assert_allclose(llr[:, i], (d1 - d0) / s2e, rtol=1e-10, atol=1e-10)
+
+
+# ------------------------------------------------------------------ LS estimation
+
+@pytest.mark.parametrize("n_prb,nl", [(1, 2), (3, 4), (5, 8), (7, 16), (51, 2), (2, 16)])
+def test_ls_exact_on_constant_channel(n_prb, nl):
+    """Noise-free, frequency-flat channel: every anchor equals the channel (Walsh orthogonality),
+    including ragged PRB counts where the last group overlaps its neighbour."""
+    rng = np.random.default_rng(n_prb * 31 + nl)
+    nr = 3
+    Hc = crandn(rng, nr, nl)
+    L = O.occ_length(nl)
+    if 6 * n_prb < L:
+        pytest.skip("cover longer than the comb")
+    spec = S.SlotSpec(n_prb=n_prb, n_rx=nr, n_layers=nl, qm=2, dmrs_sym=(2, 11), snr_db=100.0)
+    ch = np.broadcast_to(Hc, (1, 14, spec.n_sc, nr, nl))
+    sl = S.make_slot(spec, 1, noise=False, channel=ch)
+    A = O.ls_anchors(sl.Y, sl.pilots, spec.dmrs_sym, nl, L)
+    G = A.shape[2]
+    want = np.broadcast_to(Hc.T, (1, 2, G, nl, nr))
+    np.testing.assert_allclose(A, want, atol=1e-6)  # complex64 grid
+
+
+def test_ls_anchor_sits_at_group_mean():
+    """One layer, cover length 4 forced, channel linear in k: the LS anchor is the channel at the
+    group's mean subcarrier."""
+    nr, n_prb, L = 2, 3, 4
+    spec = S.SlotSpec(n_prb=n_prb, n_rx=nr, n_layers=1, qm=2, dmrs_sym=(3,), occ_len=L,
+                      snr_db=100.0)
+    K = spec.n_sc
+    a = np.array([1.0 + 0.5j, -0.3 + 0.2j])
+    slope = np.array([0.01 - 0.02j, 0.03 + 0.01j])
+    k = np.arange(K)
+    Hk = (a[None, :] + slope[None, :] * k[:, None])[:, :, None]  # [sc][rx][1]
+    ch = np.broadcast_to(Hk, (1, 14, K, nr, 1))
+    sl = S.make_slot(spec, 2, noise=False, channel=ch)
+    A = O.ls_anchors(sl.Y, sl.pilots, spec.dmrs_sym, 1, L)
+    s, pos = O.ls_groups(K, L)
+    for g in range(len(s)):
+        want = a + slope * pos[0][g]
+        np.testing.assert_allclose(A[0, 0, g, 0], want, atol=2e-6)
+
+
+def test_ls_groups_overlap_rule():
+    s, pos = O.ls_groups(3276, 8)  # 1638 comb subcarriers, 204.75 groups of 8
+    assert len(s) == 205
+    assert s[-1] == 1638 - 8 and s[-2] == 8 * 203
+    assert pos[0][0] == 7 and pos[1][0] == 8
+    s1, _ = O.ls_groups(24, 4)
+    np.testing.assert_array_equal(s1, [0, 4, 8])
+
+
+# ------------------------------------------------------------------ interpolation
+
+def test_interp_handworked():
+    rows = list(golden_lines("interp_handworked.txt"))
+    anc = np.array([float(v) for v in rows[0][1:]])
+    anc = anc[0::2] + 1j * anc[1::2]
+    A = anc.reshape(1, 3, 1, 1)  # [dmrs][group][layer][rx]
+    want = {int(r[0]): float(r[1]) + 1j * float(r[2]) for r in rows[1:] if r[0] != "time"}
+    H = O.interp_channel(A, (2,), 12, 2, 5, np.arange(12))
+    for k, v in want.items():
+        assert abs(H[k, 0, 0] - v) < 1e-14, (k, H[k, 0, 0], v)
+    for r in rows:
+        if r[0] == "time":
+            assert abs(O.time_weight((2, 11), int(r[1])) - float(r[2])) < 1e-15
+
+
+def test_interp_exact_for_linear_time_variation():
+    """Anchors that are the channel at the DMRS symbols of a channel linear in t reproduce it
+    inside [d0, d1] and hold it outside."""
+    rng = np.random.default_rng(13)
+    nr, nl, K = 2, 2, 24
+    H2, H11 = crandn(rng, nr, nl), crandn(rng, nr, nl)
+    L = 1
+    s, pos = O.ls_groups(K, L)
+    G = len(s)
+    A = np.zeros((2, G, nl, nr), dtype=np.complex128)
+    A[0] = H2.T[None]
+    A[1] = H11.T[None]
+    for t in range(14):
+        H = O.interp_channel(A, (2, 11), K, L, t, np.arange(K))
+        a = min(max((t - 2) / 9, 0.0), 1.0)
+        np.testing.assert_allclose(H, np.broadcast_to((1 - a) * H2 + a * H11, H.shape), atol=1e-14)
+
+
+def test_interp_exact_for_linear_frequency_variation():
+    """Single layer, L = 1 (an anchor on every comb subcarrier), channel linear in k: the
+    interpolation is exact at every subcarrier between the first and last anchors."""
+    rng = np.random.default_rng(14)
+    nr, K = 3, 36
+    a, slope = crandn(rng, nr), crandn(rng, nr) * 0.05
+    s, pos = O.ls_groups(K, 1)
+    A = np.zeros((1, len(s), 1, nr), dtype=np.complex128)
+    for g in range(len(s)):
+        A[0, g, 0] = a + slope * pos[0][g]
+    k = np.arange(K)
+    H = O.interp_channel(A, (2,), K, 1, 4, k)
+    inside = (k >= pos[0][0]) & (k <= pos[0][-1])
+    want = a[None, :] + slope[None, :] * k[:, None]
+    np.testing.assert_allclose(H[inside, :, 0], want[inside], atol=1e-13)
+    np.testing.assert_allclose(H[k > pos[0][-1], :, 0], np.broadcast_to(A[0, -1, 0], (1, nr)),
+                               atol=1e-14)
+
+
+# ------------------------------------------------------------------ whole slot
+
+def test_slot_noise_free_recovers_bits():
+    """Noise-free flat channel, full pipeline: LS + interpolation + LMMSE + LLR signs give back
+    the transmitted bits on every data RE (tiny s2 keeps the LLR scale finite)."""
+    spec = S.SlotSpec(n_prb=4, n_rx=4, n_layers=4, qm=6, dmrs_sym=(2, 11), snr_db=100.0)
+    rng = np.random.default_rng(15)
+    Hc = crandn(rng, 4, 4)
+    ch = np.broadcast_to(Hc, (1, 14, spec.n_sc, 4, 4))
+    sl = S.make_slot(spec, 3, noise=False, channel=ch)
+    out = O.run_slot(sl.Y, sl.pilots, np.array([1e-10]), spec.dmrs_sym, 4, 6)
+    hard = (out["llr"] < 0).astype(np.uint8)
+    np.testing.assert_array_equal(hard, sl.bits)
+    np.testing.assert_allclose(out["x_hat"], sl.x, atol=1e-4)
+
+
+def test_slot_sampled_matches_dense():
+    spec = S.spec_small_51prb(n_prb=5)
+    sl = S.make_slot(spec, 16)
+    dense = O.run_slot(sl.Y, sl.pilots, sl.sigma2, spec.dmrs_sym, 2, 4)
+    rng = np.random.default_rng(0)
+    jj = rng.integers(0, 13, 40)
+    kk = rng.integers(0, spec.n_sc, 40)
+    samp = O.run_slot(sl.Y, sl.pilots, sl.sigma2, spec.dmrs_sym, 2, 4, res={0: (jj, kk)})
+    np.testing.assert_allclose(samp["x_hat_0"], dense["x_hat"][0, jj, kk], rtol=1e-13)
+    np.testing.assert_allclose(samp["llr_0"], dense["llr"][0, jj, kk], rtol=1e-12, atol=1e-12)

@@ -1,0 +1,74 @@
+"""Statistical checks of the seeded input generator (channel, pilots, noise)."""
+import math
+
+import numpy as np
+import pytest
+from scipy.special import j0
+
+from paper_2510_07843_gb300 import synth as S
+
+
+def test_pdp_rms_delay_spread_and_power():
+    for n, ds in ((6, 100e-9), (23, 300e-9)):
+        tau, p = S.exp_pdp(n, ds)
+        assert abs(p.sum() - 1) < 1e-12
+        assert abs(S.rms_delay_spread(tau, p) - ds) < 1e-15
+        assert np.all(np.diff(p) < 0)
+
+
+def test_channel_power_is_unit():
+    spec = S.spec_carrier_273prb(n_rx=4, n_layers=2, n_prb=20, doppler_hz=0.0)
+    rng = np.random.default_rng(0)
+    pw = []
+    for _ in range(200):
+        H = S.tdl_channel(rng, spec)
+        pw.append(np.mean(np.abs(H[0]) ** 2))
+    assert abs(np.mean(pw) - 1.0) < 0.05
+
+
+def test_kronecker_rx_correlation():
+    spec = S.SlotSpec(n_prb=1, n_rx=6, n_layers=1, n_taps=1, rho_rx=0.7)
+    rng = np.random.default_rng(1)
+    hs = np.stack([S.tdl_channel(rng, spec)[0, 0, :, 0] for _ in range(20000)])
+    R = hs.T @ hs.conj() / len(hs)
+    i = np.arange(6)
+    np.testing.assert_allclose(R, 0.7 ** np.abs(i[:, None] - i[None, :]), atol=0.04)
+
+
+def test_jakes_autocorrelation_is_bessel():
+    rng = np.random.default_rng(2)
+    fd = 100.0
+    t = np.linspace(0, 5e-3, 51)
+    g = S.jakes_sos(rng, (4000,), t, fd)
+    assert abs(np.mean(np.abs(g) ** 2) - 1.0) < 0.03
+    for lag in (5, 10, 20, 40):
+        r = np.mean(g[:, lag:] * np.conj(g[:, :-lag])).real
+        assert abs(r - j0(2 * math.pi * fd * t[lag])) < 0.05, (lag, r)
+
+
+def test_noise_variance():
+    spec = S.SlotSpec(n_prb=10, n_rx=2, n_layers=1, qm=2, snr_db=10.0)
+    ch = np.zeros((1, 14, spec.n_sc, 2, 1), dtype=np.complex128)
+    sl = S.make_slot(spec, 5, channel=ch)
+    v = np.mean(np.abs(sl.Y.astype(np.complex128)) ** 2)
+    assert abs(v / spec.sigma2 - 1) < 0.05
+
+
+def test_pilot_structure():
+    rng = np.random.default_rng(3)
+    P = S.dmrs_pilots(rng, 48, 6, 2, 4)
+    for l in range(6):
+        c = l % 2
+        on = P[:, l, c::2]
+        off = P[:, l, 1 - c::2]
+        assert np.allclose(np.abs(on), 1.0) and np.all(off == 0)
+    # layers sharing a comb share the base sequence up to the Walsh sign
+    ratio = P[0, 2, 0::2] / P[0, 0, 0::2]
+    assert np.allclose(np.abs(ratio), 1) and np.allclose(ratio.imag, 0)
+
+
+def test_seeded_reproducible():
+    spec = S.spec_small_51prb(n_prb=3)
+    a = S.make_slot(spec, 42)
+    b = S.make_slot(spec, 42)
+    assert np.array_equal(a.Y, b.Y) and np.array_equal(a.bits, b.bits)
