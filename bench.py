@@ -1,0 +1,422 @@
+#!/usr/bin/env python3
+"""Throughput of the uplink receiver hot path on GB300: MMSE-detected REs/s.
+
+One step = one pass of the whole path over one batch: DMRS LS estimation (phy_chest) then the
+fused interpolation + LMMSE + SINR + LLR kernel (phy_detect_anchors) for 8 cells x 273 PRB x
+14 symbols, 64 Rx x 16 layers, 256-QAM (the massive-MIMO workload). Inputs are seeded synthetic
+slots resident in HBM. Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import dataclasses
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+# The oracle baseline runs single-threaded numpy; pin BLAS before numpy loads.
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2510_07843_gb300 import synth as S  # noqa: E402
+
+METRIC = "MMSE-detected REs/s (64Rx×16L, 273 PRB) & p99 slot latency vs plain FP32"
+N_SM = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ_NOMINAL = 2070.0
+
+
+def workload(name: str) -> S.SlotSpec:
+    if name == "massive":
+        return S.spec_massive_mimo()
+    if name == "carrier":
+        return S.spec_carrier_273prb(n_cells=8)
+    if name == "small":
+        return S.spec_small_51prb(n_cells=8)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def n_data_res(spec: S.SlotSpec) -> int:
+    return spec.n_cells * spec.n_sc * len(spec.data_sym)
+
+
+def algorithmic_bytes(spec: S.SlotSpec) -> dict:
+    """Bytes the path must move once per step: the grid and pilots in, every output out."""
+    C, K, R, L, qm = spec.n_cells, spec.n_sc, spec.n_rx, spec.n_layers, spec.qm
+    J, nd = len(spec.data_sym), len(spec.dmrs_sym)
+    y_data = C * J * R * K * 8
+    y_dmrs = C * nd * R * K * 8
+    pilots = C * nd * L * K * 8
+    n_re = C * J * K
+    outs = n_re * (L * 8 + L * 4 + L * qm * 4 + 1)
+    return dict(y_data=y_data, y_dmrs=y_dmrs, pilots=pilots, outputs=outs,
+                step=y_data + y_dmrs + pilots + outs)
+
+
+def detect_flops(spec: S.SlotSpec) -> float:
+    """Floating-point operations of the segment-factored LMMSE per launch (FMA = 2).
+
+    Counts what the method needs, not what the kernel issues: Hermitian halves only, no layer
+    padding. Per segment: corner cross-Gram X = C^H C (NX = 2 n_dmrs n_layers, Hermitian);
+    per segment and data symbol: the three time-folded blocks and H_g(t); per RE: two matched
+    filters against H_0(t), H_1(t), the frequency-weighted Gram, Cholesky (n^3/6 complex MACs),
+    forward and backward solves (n^2), the diagonal of the inverse (n^3/6 + n^2/2), SINR and the
+    max-log demapper (2^(qm/2) levels per axis).
+    """
+    nr, nl, qm = spec.n_rx, spec.n_layers, spec.qm
+    nd = len(spec.dmrs_sym)
+    L = spec.occ
+    n_comb = spec.n_sc // 2
+    G = -(-n_comb // L)
+    n_seg = max(G - 1, 1)
+    J = len(spec.data_sym)
+    cm = 8.0  # flops per complex multiply-add
+    nx = 2 * nd * nl
+    per_seg = nx * (nx + 1) / 2 * nr * cm
+    per_seg_sym = (2 * nl * (nl + 1) / 2 + nl * nl) * (4 if nd == 2 else 1) * 4 + \
+        (2 * nl * nr * 6 if nd == 2 else 0)
+    per_re = (2 * nl * nr * cm + nl * 6 + nl * (nl + 1) / 2 * 4 * 6
+              + (nl ** 3 / 6) * cm + nl ** 2 * cm + (nl ** 3 / 6 + nl ** 2 / 2) * cm
+              + nl * 10 + nl * 2 * (2 ** (qm // 2)) * 3)
+    return spec.n_cells * (n_seg * per_seg + n_seg * J * per_seg_sym) + n_data_res(spec) * per_re
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+# profiles: DRAM traffic of the dominant kernel from a committed ncu summary
+# ---------------------------------------------------------------------------------------------
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2510_07843_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel: str, workload_name: str):
+    """Per-launch DRAM bytes from profiles/traffic.txt if recorded for the current sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    for line in open(path):
+        p = line.split()
+        if len(p) >= 4 and not line.startswith("#") and p[0] == kernel and p[1] == workload_name \
+                and p[3] == src:
+            return float(p[2])
+    return None
+
+
+# ---------------------------------------------------------------------------------------------
+# oracle baseline
+# ---------------------------------------------------------------------------------------------
+
+def oracle_sample_rate(spec: S.SlotSpec, slot, budget_s: float) -> dict:
+    """Time the FP64 oracle on a bounded sample of the workload: LS estimation of cell 0, then
+    detection of whole data symbols of cell 0, 256 subcarriers at a time, until budget_s."""
+    from oracle import phy_oracle as O
+    t0 = time.perf_counter()
+    anchors = O.ls_anchors(slot.Y[:1], slot.pilots[:1], spec.dmrs_sym, spec.n_layers, spec.occ)
+    n = 0
+    chunks = 0
+    data = spec.data_sym
+    while True:
+        j = chunks % len(data)
+        k0 = (chunks // len(data)) * 256 % spec.n_sc
+        ks = np.arange(k0, min(k0 + 256, spec.n_sc))
+        O.detect_res(anchors[0], slot.Y[0], spec.dmrs_sym, spec.n_layers, spec.occ, spec.qm,
+                     float(slot.sigma2[0]), data[j], ks)
+        n += ks.size
+        chunks += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "res": n, "seconds": dt}
+
+
+# ---------------------------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="massive", choices=["massive", "carrier", "small"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32"])
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle timing")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    spec = workload(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, spec, rank, world)
+    return run_ours(args, spec, rank, world, local)
+
+
+def run_reference(args, spec, rank, world):
+    """The oracle (the FP64 CPU definition of the method) timed on this host's cores."""
+    if rank != 0:
+        return 0
+    slot = S.make_slot(dataclasses.replace(spec, n_cells=1), 3000, keep_h=False)
+    per_step = max(args.cpu_budget / max(args.steps + args.warmup, 1), 0.5)
+    for _ in range(args.warmup):
+        oracle_sample_rate(spec, slot, per_step)
+    vals, secs = [], 0.0
+    for _ in range(args.steps):
+        r = oracle_sample_rate(spec, slot, per_step)
+        vals.append(r["value"])
+        secs += r["seconds"]
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "REs/s", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(spec, args, world),
+        "cpu_baseline": {"value": value, "unit": "REs/s", "cores": 1, "kind": "oracle",
+                         "sample": f"cell 0 of the workload: LS on the whole cell, then whole "
+                                   f"data symbols 256 subcarriers at a time, {per_step:.1f} s "
+                                   f"per step"},
+        "e2e": {"value": value, "unit": "REs/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def config_dict(spec, args, world):
+    return {"workload": f"{args.workload}: {spec.n_cells} cells x {spec.n_prb} PRB x "
+                        f"{spec.n_sym} sym, {spec.n_rx} Rx x {spec.n_layers} layers, "
+                        f"{2 ** spec.qm}-QAM, DMRS {list(spec.dmrs_sym)}",
+            "n_cells_per_gpu": spec.n_cells, "n_prb": spec.n_prb, "n_rx": spec.n_rx,
+            "n_layers": spec.n_layers, "qm": spec.qm, "snr_db": spec.snr_db,
+            "precision": args.precision, "parallelism": f"replicas x{world} (cells per rank)",
+            "l2": "working set per step larger than the 129 MB L2 (no flush needed)"}
+
+
+def run_ours(args, spec, rank, world, local):
+    import torch
+    from paper_2510_07843_gb300 import build, phy
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    phy.load()
+    cfg = phy.SlotConfig.from_spec(spec, precision=args.precision)
+    slot = S.make_slot(spec, 3000 + 1000 * rank, keep_h=False)
+    buf = phy.SlotBuffers(cfg, device=dev)
+    buf.Y.copy_(torch.from_numpy(slot.Y))
+    buf.pilots.copy_(torch.from_numpy(slot.pilots))
+    buf.sigma2.copy_(torch.from_numpy(slot.sigma2))
+    st = torch.cuda.Stream(device=dev)
+    n_re = n_data_res(spec)
+
+    def step(e_mid=None):
+        phy.chest(cfg, buf.Y, buf.pilots, buf.anchors, stream=st)
+        if e_mid is not None:
+            e_mid.record(st)
+        phy.detect_anchors(cfg, buf.anchors, buf.Y, buf.sigma2, buf.x_hat, buf.sinr, buf.llr,
+                           buf.flags, stream=st)
+
+    with torch.cuda.stream(st):
+        for _ in range(max(args.warmup, 3)):
+            step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(st)
+    for i in range(args.steps):
+        ev[i][0].record(st)
+        step(ev[i][1])
+        ev[i][2].record(st)
+    t_end.record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    chest_ms = [a.elapsed_time(b) for a, b, c in ev]
+    det_ms = [b.elapsed_time(c) for a, b, c in ev]
+    t_max = torch.tensor([total_ms], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t_max.item())
+
+    # e2e through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        Yh = torch.from_numpy(slot.Y).pin_memory()
+        Ph = torch.from_numpy(slot.pilots).pin_memory()
+        sh = torch.from_numpy(slot.sigma2).pin_memory()
+        lh = torch.empty(buf.llr.shape, dtype=torch.float32).pin_memory()
+        fh = torch.empty(buf.flags.shape, dtype=torch.uint8).pin_memory()
+
+        def e2e_step():
+            phy.slot_run_host(cfg, Yh, Ph, sh, lh, fh, buf.Y, buf.pilots, buf.sigma2, buf.x_hat,
+                              buf.sinr, buf.llr, buf.flags, buf.workspace, stream=st)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        k2 = max(min(args.steps, 20), 3)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(k2):
+            e2e_step()
+        b.record(st)
+        torch.cuda.synchronize()
+        e_ms = torch.tensor([a.elapsed_time(b)], device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(e_ms, op=torch.distributed.ReduceOp.MAX)
+        h2d = Yh.numel() * 8 + Ph.numel() * 8 + sh.numel() * 4
+        d2h = lh.numel() * 4 + fh.numel()
+        e2e = {"value": world * n_re * k2 / (float(e_ms.item()) / 1e3), "unit": "REs/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "api": "phy_slot_run_host (pinned host buffers)"}
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        r = oracle_sample_rate(spec, S.make_slot(dataclasses.replace(spec, n_cells=1),
+                                                 3000, keep_h=False), args.cpu_budget)
+        cpu = {"value": r["value"], "unit": "REs/s", "cores": 1, "kind": "oracle",
+               "sample": f"cell 0 of the workload: LS on the whole cell, then {r['res']} data "
+                         f"REs (whole symbols, 256 subcarriers at a time) in {r['seconds']:.1f} s, "
+                         f"numpy float64 single thread"}
+
+    det_avg = statistics.mean(det_ms)
+    flops = detect_flops(spec)
+    sm_max = clk.get("sm_max_mhz") or SM_MAX_MHZ_NOMINAL
+    peak_tf = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    achieved_tf = flops / (det_avg * 1e-3) / 1e12
+    ab = algorithmic_bytes(spec)
+    det_bytes = ab["y_data"] + ab["outputs"]
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    value = world * n_re * args.steps / (total_ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "REs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_dict(spec, args, world),
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                       "p99": float(np.percentile(step_ms, 99)), "deadline_ms": 0.5,
+                       "what": "one step (8-cell batch) on an idle GPU, CUDA events"},
+        "stages_ms": {"chest": statistics.mean(chest_ms), "detect": det_avg},
+        "roofline": {"bound": "alu", "kernel": "detect_fp32_kernel<16>",
+                     "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                     "frac": achieved_tf / peak_tf,
+                     "peak_source": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
+                                    f"x {SM_MAX_MHZ_NOMINAL:.0f} MHz",
+                     "flops_per_launch": flops,
+                     "traffic": committed_traffic("detect_fp32_kernel", args.workload),
+                     "hbm_view": {"algorithmic_bytes": det_bytes,
+                                  "achieved_gbs": det_bytes / (det_avg * 1e-3) / 1e9,
+                                  "peak_gbs": hbm_peak,
+                                  "frac": det_bytes / (det_avg * 1e-3) / 1e9 / hbm_peak}},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,168 @@
+/*
+ * phy.h - C ABI of the GB300 uplink receiver library (libphy.so).
+ *
+ * The library runs the uplink PUSCH receiver inner loop that the paper accelerates with CPU SIMD:
+ * DMRS least-squares channel estimation with linear frequency/time interpolation, per-resource-
+ * element (RE) LMMSE MIMO detection (Gram matrix H^H H + s2 I, Cholesky, triangular solves,
+ * equalisation W y, per-layer post-equalisation SINR), and max-log QAM LLR demapping over the NR
+ * Gray constellations. The paper's LMMSE block is Sec. IV and Fig. 3 (covariance inversion by
+ * LU with forward/backward substitution); its covariance-by-FMA step is Fig. 2(b); it names
+ * channel estimation as a SIMD target in Sec. III-B. The estimation, interpolation and demapping
+ * rules below are this library's readings where the paper gives no method.
+ *
+ * Conventions for every entry point:
+ *  - All array arguments are DEVICE pointers owned by the caller, except where a name ends in
+ *    _host. The library never allocates device memory; scratch space is a caller-provided
+ *    workspace of phy_workspace_size() bytes (256-byte aligned).
+ *  - Work is enqueued on `stream` (a cudaStream_t passed as void*, NULL = legacy default stream)
+ *    and the call returns without synchronising. Results are valid once the stream reaches
+ *    the point after the call.
+ *  - Arguments are validated on the host before anything is enqueued. A failed validation
+ *    returns PHY_ERR_INVALID_ARG (bad sizes or pointers) or PHY_ERR_UNSUPPORTED (a valid but
+ *    unimplemented shape) and enqueues nothing. A CUDA launch error returns PHY_ERR_CUDA.
+ *  - Numerical trouble is data, not an error: it is reported per RE in `flags`
+ *    (bit 0: ill-conditioned Gram matrix, Cholesky pivot ratio below cfg.pivot_ratio_min or a
+ *    non-positive pivot; bit 1: RE re-computed in FP64; bit 2: non-finite input). An RE whose
+ *    factorisation fails in FP32 and is not re-computed gets zero x_hat, SINR and LLRs.
+ *
+ * Layouts (complex values are interleaved float pairs, phy_c32):
+ *  Y        [cell][sym][rx][sc]                     received grid, all n_sym symbols
+ *  pilots   [cell][dmrs][layer][sc]                 DMRS values; 0 off the layer's comb
+ *  anchors  [cell][dmrs][group][layer][rx]          LS channel estimates
+ *  H        [cell][dsym][sc][rx][layer]             full channel (phy_mmse_detect only)
+ *  x_hat    [cell][dsym][sc][layer]                 biased LMMSE output W y
+ *  sinr     [cell][dsym][sc][layer]      float      post-equalisation SINR
+ *  llr      [cell][dsym][sc][layer][qm]  float      max-log LLRs, positive = bit 0
+ *  flags    [cell][dsym][sc]             uint8      see above
+ *  sigma2   [cell]                       float      noise variance per Rx per RE (known)
+ * `dsym` counts data symbols only: the symbols 0..n_sym-1 that are not DMRS symbols, in order.
+ *
+ * DMRS and estimation rules: layer l uses comb c = l % 2 (subcarriers k = 2m + c) and Walsh row
+ * o = l / 2 of length L = occ_len (0 selects the smallest power of two >= ceil(n_layers/2)).
+ * LS group g covers comb indices m = s_g .. s_g + L - 1, s_g = min(L g, n_sc/2 - L) (the last
+ * group overlaps its neighbour), with the estimate (1/L) sum Y conj(pilot) placed at subcarrier
+ * 2 s_g + L - 1 + c. Frequency interpolation is linear between a layer's neighbouring anchors and
+ * holds the end values; time interpolation with two DMRS symbols d0 < d1 is linear with weight
+ * clamp((t - d0)/(d1 - d0), 0, 1) on d1, and holds with one DMRS symbol.
+ *
+ * Per-layer outputs: with e_k = s2 (A^-1)_kk clamped to [1e-30, 1 - 1e-7], mu_k = 1 - e_k,
+ * SINR_k = mu_k / e_k; the LLRs use x~_k = x_hat_k / mu_k and noise e_k / mu_k.
+ */
+#ifndef PHY_H
+#define PHY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  float re;
+  float im;
+} phy_c32;
+
+typedef enum {
+  PHY_OK = 0,
+  PHY_ERR_INVALID_ARG = 1,
+  PHY_ERR_UNSUPPORTED = 2,
+  PHY_ERR_NO_MEMORY = 3, /* workspace smaller than phy_workspace_size() */
+  PHY_ERR_CUDA = 4,
+  PHY_ERR_TIMEOUT = 5
+} phy_status;
+
+typedef enum {
+  PHY_PREC_FP32 = 0,    /* every product on FP32 CUDA cores */
+  PHY_PREC_TC_TF32 = 1, /* Gram and H^H y products on tcgen05 tensor cores, TF32 in, FP32 acc */
+  PHY_PREC_TC_BF16 = 2, /* same with BF16 operands */
+  PHY_PREC_TC_FP16 = 3  /* same with FP16 operands */
+} phy_precision;
+
+typedef struct {
+  int32_t n_cells;        /* independent cells (slots) in one call, >= 1 */
+  int32_t n_prb;          /* physical resource blocks; n_sc = 12 n_prb, 1..275 */
+  int32_t n_sym;          /* OFDM symbols in the slot, 1..14 */
+  int32_t n_rx;           /* receive antennas, 1..64 */
+  int32_t n_layers;       /* spatial layers, 1..16, <= n_rx */
+  int32_t qm;             /* bits per QAM symbol: 2, 4, 6 or 8 */
+  int32_t n_dmrs;         /* DMRS symbols, 1 or 2 */
+  int32_t dmrs_sym[2];    /* their indices, increasing */
+  int32_t occ_len;        /* Walsh cover length L (power of two) or 0 for automatic */
+  int32_t precision;      /* phy_precision */
+  float pivot_ratio_min;  /* flag bit 0 threshold on min L_kk^2 / max L_kk^2, e.g. 1e-6 */
+  int32_t fp64_refactor;  /* 1: re-compute flagged REs in FP64 (sets flag bit 1) */
+} phy_slot_cfg;
+
+/* Human-readable name of a status code (static string). */
+const char* phy_status_str(phy_status s);
+
+/* Number of LS groups (anchors per DMRS symbol, layer and Rx) for cfg, or -1 if cfg is invalid. */
+int32_t phy_n_groups(const phy_slot_cfg* cfg);
+
+/* Number of data symbols for cfg (n_sym minus DMRS symbols), or -1 if cfg is invalid. */
+int32_t phy_n_data_symbols(const phy_slot_cfg* cfg);
+
+/* Workspace bytes phy_slot_run() needs for cfg; 0 if cfg is invalid. */
+size_t phy_workspace_size(const phy_slot_cfg* cfg);
+
+/*
+ * DMRS least-squares estimation (the channel-estimation block of Sec. III-B): writes
+ * anchors[cell][dmrs][group][layer][rx] from the DMRS symbols of Y and the pilots.
+ */
+phy_status phy_chest(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32* pilots,
+                     phy_c32* anchors, void* stream);
+
+/*
+ * LMMSE detection on a given full channel H[cell][dsym][sc][rx][layer] (Sec. IV): per data RE
+ * x_hat = (H^H H + s2 I)^-1 H^H y, SINR and flags. sigma2 may be 0 (zero forcing); the SINR is
+ * then clamped large. Used for genie-channel checks; the fused path is phy_slot_run().
+ */
+phy_status phy_mmse_detect(const phy_slot_cfg* cfg, const phy_c32* H, const phy_c32* Y,
+                           const float* sigma2, phy_c32* x_hat, float* sinr, uint8_t* flags,
+                           void* stream);
+
+/*
+ * Interpolation, LMMSE detection, SINR and LLRs from given LS anchors (as written by phy_chest,
+ * or any estimate in that layout): the second half of phy_slot_run. Same outputs and rules.
+ */
+phy_status phy_detect_anchors(const phy_slot_cfg* cfg, const phy_c32* anchors, const phy_c32* Y,
+                              const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
+                              uint8_t* flags, void* stream);
+
+/*
+ * Max-log LLR demapping of equalised symbols: from x_hat and SINR (as written by
+ * phy_slot_run or phy_mmse_detect) computes llr[cell][dsym][sc][layer][qm].
+ * REs whose SINR is not positive get zero LLRs.
+ */
+phy_status phy_llr_demap(const phy_slot_cfg* cfg, const phy_c32* x_hat, const float* sinr,
+                         float* llr, void* stream);
+
+/*
+ * The whole receiver for one slot per cell: LS estimation, interpolation, LMMSE detection,
+ * SINR and LLRs. Requires sigma2 > 0 for every cell. Any of x_hat, sinr, llr may be NULL to
+ * skip writing that output; flags may not be NULL.
+ */
+phy_status phy_slot_run(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32* pilots,
+                        const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
+                        uint8_t* flags, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * phy_slot_run() with HOST inputs and outputs: copies Y_host, pilots_host and sigma2_host into
+ * the caller's device staging buffers (Y, pilots, sigma2, same layouts), runs the receiver into
+ * the device outputs, and copies llr and flags back into llr_host and flags_host, all on
+ * `stream`. Host buffers should be page-locked for the copies to be asynchronous. x_hat and
+ * sinr stay on the device (may be NULL).
+ */
+phy_status phy_slot_run_host(const phy_slot_cfg* cfg, const phy_c32* Y_host,
+                             const phy_c32* pilots_host, const float* sigma2_host,
+                             float* llr_host, uint8_t* flags_host, phy_c32* Y, phy_c32* pilots,
+                             float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
+                             uint8_t* flags, void* workspace, size_t workspace_bytes,
+                             void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PHY_H */

@@ -131,12 +131,9 @@ def ls_anchors(Y: np.ndarray, pilots: np.ndarray, dmrs_sym: Sequence[int], n_lay
         for d, t in enumerate(dmrs_sym):
             for l in range(n_layers):
                 c = l % 2
-                for g in range(G):
-                    ks = 2 * np.arange(s[g], s[g] + L) + c
-                    acc = np.zeros(n_rx, dtype=np.complex128)
-                    for k in ks:
-                        acc += Y[cell, t, :, k] * np.conj(P[cell, d, l, k])
-                    out[cell, d, g, l, :] = acc / L
+                ks = 2 * (s[:, None] + np.arange(L)[None, :]) + c  # [group][i]
+                prod = Y[cell, t][:, ks] * np.conj(P[cell, d, l, ks])[None]  # [rx][group][i]
+                out[cell, d, :, l, :] = (prod.sum(axis=-1) / L).T
     return out
 
 

@@ -1,0 +1,221 @@
+// C ABI of libphy.so: argument validation, slot geometry, workspace carving, stream enqueue.
+#include <cstdint>
+#include <cstring>
+
+#include "../../include/phy.h"
+#include "launch.h"
+
+using phy::Geo;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+
+bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int auto_occ(int n_layers) {
+  int half = (n_layers + 1) / 2, L = 1;
+  while (L < half) L *= 2;
+  return L;
+}
+
+// Validates cfg and fills g. Returns PHY_OK, PHY_ERR_INVALID_ARG or PHY_ERR_UNSUPPORTED.
+phy_status make_geo(const phy_slot_cfg* c, Geo* g) {
+  if (!c) return PHY_ERR_INVALID_ARG;
+  if (c->n_cells < 1 || c->n_cells > 65535) return PHY_ERR_INVALID_ARG;
+  if (c->n_prb < 1 || c->n_prb > 275) return PHY_ERR_INVALID_ARG;
+  if (c->n_sym < 1 || c->n_sym > phy::kMaxSym) return PHY_ERR_INVALID_ARG;
+  if (c->n_rx < 1 || c->n_rx > phy::kMaxRx) return PHY_ERR_INVALID_ARG;
+  if (c->n_layers < 1 || c->n_layers > phy::kMaxLayers || c->n_layers > c->n_rx)
+    return PHY_ERR_INVALID_ARG;
+  if (c->qm != 2 && c->qm != 4 && c->qm != 6 && c->qm != 8) return PHY_ERR_INVALID_ARG;
+  if (c->n_dmrs != 1 && c->n_dmrs != 2) return PHY_ERR_INVALID_ARG;
+  for (int d = 0; d < c->n_dmrs; ++d)
+    if (c->dmrs_sym[d] < 0 || c->dmrs_sym[d] >= c->n_sym) return PHY_ERR_INVALID_ARG;
+  if (c->n_dmrs == 2 && c->dmrs_sym[1] <= c->dmrs_sym[0]) return PHY_ERR_INVALID_ARG;
+  if (c->precision < PHY_PREC_FP32 || c->precision > PHY_PREC_TC_FP16) return PHY_ERR_INVALID_ARG;
+  if (!(c->pivot_ratio_min >= 0.f) || c->pivot_ratio_min > 1.f) return PHY_ERR_INVALID_ARG;
+  const int need = auto_occ(c->n_layers);
+  const int L = c->occ_len == 0 ? need : c->occ_len;
+  if (!pow2(L) || L < need || L > 64) return PHY_ERR_INVALID_ARG;
+  const int n_sc = 12 * c->n_prb;
+  const int n_comb = n_sc / 2;
+  if (n_comb < L) return PHY_ERR_INVALID_ARG;
+  Geo t;
+  std::memset(&t, 0, sizeof(t));
+  t.n_cells = c->n_cells;
+  t.n_sc = n_sc;
+  t.n_sym = c->n_sym;
+  t.n_rx = c->n_rx;
+  t.n_layers = c->n_layers;
+  t.qm = c->qm;
+  t.n_dmrs = c->n_dmrs;
+  t.dmrs0 = c->dmrs_sym[0];
+  t.dmrs1 = c->n_dmrs == 2 ? c->dmrs_sym[1] : c->dmrs_sym[0];
+  t.L = L;
+  t.n_comb = n_comb;
+  t.G = (n_comb + L - 1) / L;
+  t.n_seg = t.G > 1 ? t.G - 1 : 1;
+  t.pivot_min = c->pivot_ratio_min;
+  int nd = 0;
+  for (int s = 0; s < c->n_sym; ++s) {
+    bool is_dmrs = false;
+    for (int d = 0; d < c->n_dmrs; ++d) is_dmrs |= (c->dmrs_sym[d] == s);
+    if (is_dmrs) continue;
+    t.dsym[nd] = s;
+    if (c->n_dmrs == 2) {
+      double a = (double)(s - t.dmrs0) / (double)(t.dmrs1 - t.dmrs0);
+      a = a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
+      t.tw[nd] = (float)a;
+    } else {
+      t.tw[nd] = 0.f;
+    }
+    ++nd;
+  }
+  t.n_dsym = nd;
+  if (nd < 1) return PHY_ERR_INVALID_ARG;
+  *g = t;
+  return PHY_OK;
+}
+
+size_t anchor_bytes(const Geo& g) {
+  return (size_t)g.n_cells * g.n_dmrs * g.G * g.n_layers * g.n_rx * sizeof(phy_c32);
+}
+
+phy_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PHY_OK : PHY_ERR_CUDA; }
+
+phy_status check_precision(const phy_slot_cfg* cfg, const Geo& g) {
+  if (cfg->precision != PHY_PREC_FP32) return PHY_ERR_UNSUPPORTED;
+  if (phy::fused_fp32_smem_bytes(g) > 227 * 1024) return PHY_ERR_UNSUPPORTED;
+  return PHY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* phy_status_str(phy_status s) {
+  switch (s) {
+    case PHY_OK: return "ok";
+    case PHY_ERR_INVALID_ARG: return "invalid argument";
+    case PHY_ERR_UNSUPPORTED: return "unsupported configuration";
+    case PHY_ERR_NO_MEMORY: return "workspace too small";
+    case PHY_ERR_CUDA: return "CUDA error";
+    case PHY_ERR_TIMEOUT: return "timeout";
+  }
+  return "unknown status";
+}
+
+int32_t phy_n_groups(const phy_slot_cfg* cfg) {
+  Geo g;
+  return make_geo(cfg, &g) == PHY_OK ? g.G : -1;
+}
+
+int32_t phy_n_data_symbols(const phy_slot_cfg* cfg) {
+  Geo g;
+  return make_geo(cfg, &g) == PHY_OK ? g.n_dsym : -1;
+}
+
+size_t phy_workspace_size(const phy_slot_cfg* cfg) {
+  Geo g;
+  if (make_geo(cfg, &g) != PHY_OK) return 0;
+  return align_up(anchor_bytes(g));
+}
+
+phy_status phy_chest(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32* pilots,
+                     phy_c32* anchors, void* stream) {
+  Geo g;
+  phy_status s = make_geo(cfg, &g);
+  if (s != PHY_OK) return s;
+  if (!Y || !pilots || !anchors) return PHY_ERR_INVALID_ARG;
+  return cuda_status(phy::launch_chest(g, Y, pilots, anchors, (cudaStream_t)stream));
+}
+
+phy_status phy_mmse_detect(const phy_slot_cfg* cfg, const phy_c32* H, const phy_c32* Y,
+                           const float* sigma2, phy_c32* x_hat, float* sinr, uint8_t* flags,
+                           void* stream) {
+  Geo g;
+  phy_status s = make_geo(cfg, &g);
+  if (s != PHY_OK) return s;
+  if (!H || !Y || !sigma2 || !x_hat || !sinr || !flags) return PHY_ERR_INVALID_ARG;
+  return cuda_status(
+      phy::launch_detect_h(g, H, Y, sigma2, x_hat, sinr, flags, (cudaStream_t)stream));
+}
+
+phy_status phy_llr_demap(const phy_slot_cfg* cfg, const phy_c32* x_hat, const float* sinr,
+                         float* llr, void* stream) {
+  Geo g;
+  phy_status s = make_geo(cfg, &g);
+  if (s != PHY_OK) return s;
+  if (!x_hat || !sinr || !llr) return PHY_ERR_INVALID_ARG;
+  return cuda_status(phy::launch_llr(g, x_hat, sinr, llr, (cudaStream_t)stream));
+}
+
+phy_status phy_detect_anchors(const phy_slot_cfg* cfg, const phy_c32* anchors, const phy_c32* Y,
+                              const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
+                              uint8_t* flags, void* stream) {
+  Geo g;
+  phy_status s = make_geo(cfg, &g);
+  if (s != PHY_OK) return s;
+  if (!anchors || !Y || !sigma2 || !flags) return PHY_ERR_INVALID_ARG;
+  s = check_precision(cfg, g);
+  if (s != PHY_OK) return s;
+  return cuda_status(phy::launch_detect_fp32(g, anchors, Y, sigma2, x_hat, sinr, llr, flags,
+                                             (cudaStream_t)stream));
+}
+
+phy_status phy_slot_run(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32* pilots,
+                        const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
+                        uint8_t* flags, void* workspace, size_t workspace_bytes, void* stream) {
+  Geo g;
+  phy_status s = make_geo(cfg, &g);
+  if (s != PHY_OK) return s;
+  if (!Y || !pilots || !sigma2 || !flags || !workspace) return PHY_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace) % kAlign) return PHY_ERR_INVALID_ARG;
+  if (workspace_bytes < phy_workspace_size(cfg)) return PHY_ERR_NO_MEMORY;
+  s = check_precision(cfg, g);
+  if (s != PHY_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  phy_c32* anchors = (phy_c32*)workspace;
+  cudaError_t e = phy::launch_chest(g, Y, pilots, anchors, st);
+  if (e != cudaSuccess) return PHY_ERR_CUDA;
+  e = phy::launch_detect_fp32(g, anchors, Y, sigma2, x_hat, sinr, llr, flags, st);
+  return cuda_status(e);
+}
+
+phy_status phy_slot_run_host(const phy_slot_cfg* cfg, const phy_c32* Y_host,
+                             const phy_c32* pilots_host, const float* sigma2_host,
+                             float* llr_host, uint8_t* flags_host, phy_c32* Y, phy_c32* pilots,
+                             float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
+                             uint8_t* flags, void* workspace, size_t workspace_bytes,
+                             void* stream) {
+  Geo g;
+  phy_status s = make_geo(cfg, &g);
+  if (s != PHY_OK) return s;
+  if (!Y_host || !pilots_host || !sigma2_host || !llr_host || !flags_host || !Y || !pilots ||
+      !sigma2 || !llr || !flags)
+    return PHY_ERR_INVALID_ARG;
+  if (workspace_bytes < phy_workspace_size(cfg)) return PHY_ERR_NO_MEMORY;
+  s = check_precision(cfg, g);
+  if (s != PHY_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t y_bytes = (size_t)g.n_cells * g.n_sym * g.n_rx * g.n_sc * sizeof(phy_c32);
+  const size_t p_bytes = (size_t)g.n_cells * g.n_dmrs * g.n_layers * g.n_sc * sizeof(phy_c32);
+  const size_t n_re = (size_t)g.n_cells * g.n_dsym * g.n_sc;
+  const size_t l_bytes = n_re * g.n_layers * g.qm * sizeof(float);
+  if (cudaMemcpyAsync(Y, Y_host, y_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(pilots, pilots_host, p_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(sigma2, sigma2_host, g.n_cells * sizeof(float), cudaMemcpyHostToDevice,
+                      st) != cudaSuccess)
+    return PHY_ERR_CUDA;
+  s = phy_slot_run(cfg, Y, pilots, sigma2, x_hat, sinr, llr, flags, workspace, workspace_bytes,
+                   stream);
+  if (s != PHY_OK) return s;
+  if (cudaMemcpyAsync(llr_host, llr, l_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(flags_host, flags, n_re, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return PHY_ERR_CUDA;
+  return PHY_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,267 @@
+// Per-RE FP32 LMMSE solve, one thread per resource element.
+//
+// Given the Gram matrix A = H^H H + s2 I (Hermitian positive definite, supplied entry by entry
+// through a functor so that callers can build it on the fly) and the matched filter b = H^H y,
+// computes x = A^-1 b and d_k = (A^-1)_kk. The paper's LMMSE block (Sec. IV, Fig. 3) factors
+// the matrix to invert and runs forward/backward substitution; here A is factored by Cholesky
+// A = L L^H (it is Hermitian positive definite), x by the two triangular solves, and the diagonal
+// of the inverse by the column norms of L^-1, since (A^-1)_kk = sum_i |(L^-1)_ik|^2.
+//
+// Up to 8 layers the packed lower triangle lives in registers. For 9..16 layers the matrix is
+// split into 8x8 blocks, A = [A11 A12; A21 A22]:
+//   L11 = chol(A11), M = L11^-1, L21 = A21 M^H, S = A22 - L21 L21^H, L22 = chol(S), N = L22^-1,
+//   L^-1 = [M 0; -N L21 M  N],
+// so z = L^-1 b = [M b1; N (b2 - L21 z1)], x = L^-H z = [M^H (z1 - L21^H x2); N^H z2], and the
+// column norms of L^-1 give d. M, S/N and the vectors stay in registers; L21 goes to a
+// thread-private scratch (shared memory in the fused kernel).
+#pragma once
+
+#include "common.cuh"
+
+namespace phy {
+
+__device__ __forceinline__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }
+
+// Cholesky in place on a packed lower triangle (left-looking). rinv[j] = 1 / L_jj; the diagonal
+// entries of `a` are left holding the pivots L_jj^2. Returns false on a non-positive or
+// non-finite pivot.
+template <int N>
+__device__ __forceinline__ bool chol_packed(cf (&a)[N * (N + 1) / 2], float (&rinv)[N],
+                                            float& pmin, float& pmax, bool& fin) {
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    float d = a[tri(j, j)].x;
+#pragma unroll
+    for (int k = 0; k < j; ++k) d -= cabs2(a[tri(j, k)]);
+    fin = fin && isfinite(d);
+    ok = ok && (d > 0.f) && (d < 3.0e38f);
+    pmin = fminf(pmin, d);
+    pmax = fmaxf(pmax, d);
+    a[tri(j, j)] = mk(d, 0.f);
+    const float r = rsqrtf(d);
+    rinv[j] = r;
+#pragma unroll
+    for (int i = j + 1; i < N; ++i) {
+      cf s = a[tri(i, j)];
+#pragma unroll
+      for (int k = 0; k < j; ++k) s = cfms_cjb(a[tri(i, k)], a[tri(j, k)], s);
+      a[tri(i, j)] = r * s;
+    }
+  }
+  return ok;
+}
+
+// z = L^-1 b (forward substitution) for the factor produced by chol_packed.
+template <int N>
+__device__ __forceinline__ void fwd_packed(const cf (&a)[N * (N + 1) / 2], const float (&rinv)[N],
+                                           const cf (&b)[N], cf (&z)[N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    cf s = b[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) s = cfms(a[tri(i, k)], z[k], s);
+    z[i] = rinv[i] * s;
+  }
+}
+
+// x = L^-H z (backward substitution).
+template <int N>
+__device__ __forceinline__ void bwd_packed(const cf (&a)[N * (N + 1) / 2], const float (&rinv)[N],
+                                           const cf (&z)[N], cf (&x)[N]) {
+#pragma unroll
+  for (int i = N - 1; i >= 0; --i) {
+    cf s = z[i];
+#pragma unroll
+    for (int k = i + 1; k < N; ++k) {
+      // s -= conj(L_ki) x_k
+      const cf l = a[tri(k, i)];
+      s.x = fmaf(-l.x, x[k].x, s.x);
+      s.x = fmaf(-l.y, x[k].y, s.x);
+      s.y = fmaf(-l.x, x[k].y, s.y);
+      s.y = fmaf(l.y, x[k].x, s.y);
+    }
+    x[i] = rinv[i] * s;
+  }
+}
+
+// Overwrite the strictly-lower part of the factor with that of L^-1 and return its diagonal in
+// rinv (unchanged: (L^-1)_jj = 1/L_jj). Columns left to right, rows top to bottom: entry (i, c)
+// of the inverse needs row i of L at columns >= c (still intact) and rows < i of the inverse's
+// column c (already written).
+template <int N>
+__device__ __forceinline__ void inv_packed(cf (&a)[N * (N + 1) / 2], const float (&rinv)[N]) {
+#pragma unroll
+  for (int c = 0; c < N; ++c) {
+#pragma unroll
+    for (int i = c + 1; i < N; ++i) {
+      // (L^-1)_ic = -(L_ic (L^-1)_cc + sum_{c<m<i} L_im (L^-1)_mc) / L_ii
+      cf s = rinv[c] * a[tri(i, c)];
+#pragma unroll
+      for (int m = c + 1; m < i; ++m) s = cfma(a[tri(i, m)], a[tri(m, c)], s);
+      a[tri(i, c)] = (-rinv[i]) * s;
+    }
+  }
+}
+
+// Column norms of the lower-triangular inverse stored by inv_packed.
+template <int N>
+__device__ __forceinline__ void colnorm_inv(const cf (&a)[N * (N + 1) / 2], const float (&rinv)[N],
+                                            float (&d)[N]) {
+#pragma unroll
+  for (int c = 0; c < N; ++c) {
+    float s = rinv[c] * rinv[c];
+#pragma unroll
+    for (int i = c + 1; i < N; ++i) s += cabs2(a[tri(i, c)]);
+    d[c] = s;
+  }
+}
+
+struct SolveInfo {
+  bool ok;    // every pivot positive and finite
+  bool fin;   // every pivot finite (false points at non-finite input)
+  float pmin, pmax;
+};
+
+// Up to 8 layers: everything in registers.
+template <int N, class GetA>
+__device__ __forceinline__ SolveInfo solve_small(GetA getA, const cf (&b)[N], cf (&x)[N],
+                                                 float (&d)[N]) {
+  cf a[N * (N + 1) / 2];
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) a[tri(i, j)] = getA(i, j);
+  float rinv[N];
+  SolveInfo si{true, true, 3.0e38f, 0.f};
+  si.ok = chol_packed<N>(a, rinv, si.pmin, si.pmax, si.fin);
+  cf z[N];
+  fwd_packed<N>(a, rinv, b, z);
+  bwd_packed<N>(a, rinv, z, x);
+  inv_packed<N>(a, rinv);
+  colnorm_inv<N>(a, rinv, d);
+  return si;
+}
+
+// 9..16 layers: two 8x8 blocks; Scr provides ld(i, j) / st(i, j, v) for the 8x8 block L21.
+template <class GetA, class Scr>
+__device__ __forceinline__ SolveInfo solve16(GetA getA, Scr scr, const cf (&b)[16], cf (&x)[16],
+                                             float (&d)[16]) {
+  constexpr int B = 8;
+  SolveInfo si{true, true, 3.0e38f, 0.f};
+  // ---- block 1: L11, z1 = L11^-1 b1, M = L11^-1
+  cf m[B * (B + 1) / 2];
+#pragma unroll
+  for (int i = 0; i < B; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) m[tri(i, j)] = getA(i, j);
+  float r1[B];
+  si.ok = chol_packed<B>(m, r1, si.pmin, si.pmax, si.fin);
+  cf b1[B], z1[B];
+#pragma unroll
+  for (int i = 0; i < B; ++i) b1[i] = b[i];
+  fwd_packed<B>(m, r1, b1, z1);
+  inv_packed<B>(m, r1);
+  // M as a full lower triangle accessor: (i, j) with j <= i
+  auto M = [&](int i, int j) -> cf { return (i == j) ? mk(r1[i], 0.f) : m[tri(i, j)]; };
+  // ---- L21 = A21 M^H row by row; v = b2 - L21 z1
+  cf v[B];
+#pragma unroll
+  for (int i = 0; i < B; ++i) {
+    cf row[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) row[k] = getA(B + i, k);
+    cf acc = b[B + i];
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      cf l = mk(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k <= j; ++k) l = cfma_cj(M(j, k), row[k], l);  // row[k] conj(M[j][k])
+      scr.st(i, j, l);
+      acc = cfms(l, z1[j], acc);
+    }
+    v[i] = acc;
+  }
+  // ---- S = A22 - L21 L21^H
+  cf s[B * (B + 1) / 2];
+#pragma unroll
+  for (int i = 0; i < B; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) s[tri(i, j)] = getA(B + i, B + j);
+#pragma unroll
+  for (int c = 0; c < B; ++c) {
+    cf col[B];
+#pragma unroll
+    for (int i = 0; i < B; ++i) col[i] = scr.ld(i, c);
+#pragma unroll
+    for (int i = 0; i < B; ++i)
+#pragma unroll
+      for (int j = 0; j <= i; ++j) s[tri(i, j)] = cfms_cjb(col[i], col[j], s[tri(i, j)]);
+  }
+  float r2[B];
+  si.ok = chol_packed<B>(s, r2, si.pmin, si.pmax, si.fin) && si.ok;
+  cf z2[B], x2[B];
+  fwd_packed<B>(s, r2, v, z2);
+  bwd_packed<B>(s, r2, z2, x2);
+  inv_packed<B>(s, r2);
+  auto Nn = [&](int i, int j) -> cf { return (i == j) ? mk(r2[i], 0.f) : s[tri(i, j)]; };
+  // ---- x1 = M^H (z1 - L21^H x2)
+  cf u[B];
+#pragma unroll
+  for (int j = 0; j < B; ++j) u[j] = z1[j];
+#pragma unroll
+  for (int i = 0; i < B; ++i) {
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      // u_j -= conj(L21_ij) x2_i
+      const cf l = scr.ld(i, j);
+      u[j].x = fmaf(-l.x, x2[i].x, u[j].x);
+      u[j].x = fmaf(-l.y, x2[i].y, u[j].x);
+      u[j].y = fmaf(-l.x, x2[i].y, u[j].y);
+      u[j].y = fmaf(l.y, x2[i].x, u[j].y);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < B; ++i) {
+    cf acc = mk(0.f, 0.f);
+#pragma unroll
+    for (int k = i; k < B; ++k) acc = cfma_cj(M(k, i), u[k], acc);
+    x[i] = acc;
+    x[B + i] = x2[i];
+  }
+  // ---- diagonal of A^-1: block 2 from N, block 1 from M and N L21 M
+#pragma unroll
+  for (int c = 0; c < B; ++c) {
+    float s2 = 0.f;
+#pragma unroll
+    for (int i = c; i < B; ++i) s2 += cabs2(Nn(i, c));
+    d[B + c] = s2;
+  }
+#pragma unroll
+  for (int c = 0; c < B; ++c) {
+    float s1 = 0.f;
+#pragma unroll
+    for (int i = c; i < B; ++i) s1 += cabs2(M(i, c));
+    // w = L21 M[:, c]
+    cf w[B];
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+      cf acc = mk(0.f, 0.f);
+#pragma unroll
+      for (int mm = c; mm < B; ++mm) acc = cfma(scr.ld(i, mm), M(mm, c), acc);
+      w[i] = acc;
+    }
+    // p = N w, add |p|^2
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+      cf acc = mk(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k <= i; ++k) acc = cfma(Nn(i, k), w[k], acc);
+      s1 += cabs2(acc);
+    }
+    d[c] = s1;
+  }
+  return si;
+}
+
+}  // namespace phy

@@ -1,0 +1,199 @@
+"""Thin ctypes binding of libphy.so: argument marshalling only.
+
+Tensors are torch CUDA tensors (PyTorch supplies device memory and streams); every step of the
+receiver runs in the library's CUDA kernels. The library must be built (build.build()) before
+use; loading fails loudly when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libphy.so")
+
+PHY_OK = 0
+PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "fp16": 3}
+STATUS = {0: "PHY_OK", 1: "PHY_ERR_INVALID_ARG", 2: "PHY_ERR_UNSUPPORTED",
+          3: "PHY_ERR_NO_MEMORY", 4: "PHY_ERR_CUDA", 5: "PHY_ERR_TIMEOUT"}
+
+
+class CSlotCfg(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_int32), ("n_prb", ctypes.c_int32),
+                ("n_sym", ctypes.c_int32), ("n_rx", ctypes.c_int32),
+                ("n_layers", ctypes.c_int32), ("qm", ctypes.c_int32),
+                ("n_dmrs", ctypes.c_int32), ("dmrs_sym", ctypes.c_int32 * 2),
+                ("occ_len", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("pivot_ratio_min", ctypes.c_float), ("fp64_refactor", ctypes.c_int32)]
+
+
+# Every entry point declared in include/phy.h, with its ctypes signature.
+_P = ctypes.c_void_p
+_SIGS = {
+    "phy_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "phy_n_groups": (ctypes.c_int32, [_P]),
+    "phy_n_data_symbols": (ctypes.c_int32, [_P]),
+    "phy_workspace_size": (ctypes.c_size_t, [_P]),
+    "phy_chest": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "phy_mmse_detect": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "phy_detect_anchors": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "phy_llr_demap": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "phy_slot_run": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "phy_slot_run_host": (ctypes.c_int, [_P] * 14 + [ctypes.c_size_t, _P]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libphy.so not built at {path}; run paper_2510_07843_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class PhyError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        super().__init__(f"{fn} returned {STATUS.get(code, code)}")
+        self.code = code
+
+
+@dataclass
+class SlotConfig:
+    n_cells: int
+    n_prb: int
+    n_rx: int
+    n_layers: int
+    qm: int
+    dmrs_sym: Sequence[int] = (2,)
+    n_sym: int = 14
+    occ_len: int = 0
+    precision: str = "fp32"
+    pivot_ratio_min: float = 1e-6
+    fp64_refactor: bool = False
+
+    def c(self) -> CSlotCfg:
+        ds = list(self.dmrs_sym) + [0] * (2 - len(self.dmrs_sym))
+        return CSlotCfg(self.n_cells, self.n_prb, self.n_sym, self.n_rx, self.n_layers, self.qm,
+                        len(self.dmrs_sym), (ctypes.c_int32 * 2)(*ds), self.occ_len,
+                        PREC[self.precision], self.pivot_ratio_min, int(self.fp64_refactor))
+
+    @property
+    def n_sc(self) -> int:
+        return 12 * self.n_prb
+
+    @property
+    def n_dsym(self) -> int:
+        return self.n_sym - len(self.dmrs_sym)
+
+    @staticmethod
+    def from_spec(spec, **kw) -> "SlotConfig":
+        return SlotConfig(n_cells=spec.n_cells, n_prb=spec.n_prb, n_rx=spec.n_rx,
+                          n_layers=spec.n_layers, qm=spec.qm, dmrs_sym=tuple(spec.dmrs_sym),
+                          n_sym=spec.n_sym, occ_len=spec.occ_len, **kw)
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _check(fn: str, code: int):
+    if code != PHY_OK:
+        raise PhyError(fn, code)
+
+
+def n_groups(cfg: SlotConfig) -> int:
+    c = cfg.c()
+    return load().phy_n_groups(ctypes.byref(c))
+
+
+def workspace_size(cfg: SlotConfig) -> int:
+    c = cfg.c()
+    return load().phy_workspace_size(ctypes.byref(c))
+
+
+def chest(cfg: SlotConfig, Y, pilots, anchors, stream=None):
+    c = cfg.c()
+    _check("phy_chest", load().phy_chest(ctypes.byref(c), _ptr(Y), _ptr(pilots), _ptr(anchors),
+                                         _stream(stream)))
+
+
+def mmse_detect(cfg: SlotConfig, H, Y, sigma2, x_hat, sinr, flags, stream=None):
+    c = cfg.c()
+    _check("phy_mmse_detect",
+           load().phy_mmse_detect(ctypes.byref(c), _ptr(H), _ptr(Y), _ptr(sigma2), _ptr(x_hat),
+                                  _ptr(sinr), _ptr(flags), _stream(stream)))
+
+
+def detect_anchors(cfg: SlotConfig, anchors, Y, sigma2, x_hat, sinr, llr, flags, stream=None):
+    c = cfg.c()
+    _check("phy_detect_anchors",
+           load().phy_detect_anchors(ctypes.byref(c), _ptr(anchors), _ptr(Y), _ptr(sigma2),
+                                     _ptr(x_hat), _ptr(sinr), _ptr(llr), _ptr(flags),
+                                     _stream(stream)))
+
+
+def llr_demap(cfg: SlotConfig, x_hat, sinr, llr, stream=None):
+    c = cfg.c()
+    _check("phy_llr_demap", load().phy_llr_demap(ctypes.byref(c), _ptr(x_hat), _ptr(sinr),
+                                                 _ptr(llr), _stream(stream)))
+
+
+def slot_run(cfg: SlotConfig, Y, pilots, sigma2, x_hat, sinr, llr, flags, workspace,
+             stream=None):
+    c = cfg.c()
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check("phy_slot_run",
+           load().phy_slot_run(ctypes.byref(c), _ptr(Y), _ptr(pilots), _ptr(sigma2), _ptr(x_hat),
+                               _ptr(sinr), _ptr(llr), _ptr(flags), _ptr(workspace), ws_bytes,
+                               _stream(stream)))
+
+
+def slot_run_host(cfg: SlotConfig, Y_h, pilots_h, sigma2_h, llr_h, flags_h, Y, pilots, sigma2,
+                  x_hat, sinr, llr, flags, workspace, stream=None):
+    c = cfg.c()
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check("phy_slot_run_host",
+           load().phy_slot_run_host(ctypes.byref(c), _ptr(Y_h), _ptr(pilots_h), _ptr(sigma2_h),
+                                    _ptr(llr_h), _ptr(flags_h), _ptr(Y), _ptr(pilots),
+                                    _ptr(sigma2), _ptr(x_hat), _ptr(sinr), _ptr(llr),
+                                    _ptr(flags), _ptr(workspace), ws_bytes, _stream(stream)))
+
+
+class SlotBuffers:
+    """Device buffers for one phy_slot_run call (torch tensors, caller-owned)."""
+
+    def __init__(self, cfg: SlotConfig, device="cuda", with_inputs=True):
+        import torch
+        C, K, nl, nds = cfg.n_cells, cfg.n_sc, cfg.n_layers, cfg.n_dsym
+        f32, c64 = torch.float32, torch.complex64
+        if with_inputs:
+            self.Y = torch.empty((C, cfg.n_sym, cfg.n_rx, K), dtype=c64, device=device)
+            self.pilots = torch.empty((C, len(cfg.dmrs_sym), nl, K), dtype=c64, device=device)
+            self.sigma2 = torch.empty((C,), dtype=f32, device=device)
+        self.x_hat = torch.empty((C, nds, K, nl), dtype=c64, device=device)
+        self.sinr = torch.empty((C, nds, K, nl), dtype=f32, device=device)
+        self.llr = torch.empty((C, nds, K, nl, cfg.qm), dtype=f32, device=device)
+        self.flags = torch.empty((C, nds, K), dtype=torch.uint8, device=device)
+        self.anchors = torch.empty((C, len(cfg.dmrs_sym), n_groups(cfg), nl, cfg.n_rx),
+                                   dtype=c64, device=device)
+        ws = workspace_size(cfg)
+        if ws == 0:
+            raise PhyError("phy_workspace_size", 1)
+        self.workspace = torch.empty((ws,), dtype=torch.uint8, device=device)

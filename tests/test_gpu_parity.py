@@ -1,0 +1,230 @@
+"""CUDA path vs the FP64 oracle, element by element on identical seeded inputs.
+
+Small cases run the oracle on every RE (several segments, ragged PRB counts, every layer class
+and modulation); the full-size 8-cell 273-PRB 64x16 workload (the benchmark's launch) is checked
+on sampled REs that include the first and last frequency segments.
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+from oracle import phy_oracle as O
+from paper_2510_07843_gb300 import synth as S
+from parity import assert_parity, compare_res, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_07843_gb300 import build, phy
+    build.build()
+    phy.load()
+    return torch.device("cuda:0")
+
+
+def T(a, dev):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+
+def gpu_slot(spec, sl, dev, **kw):
+    import torch
+    from paper_2510_07843_gb300 import phy
+    cfg = phy.SlotConfig.from_spec(spec, **kw)
+    buf = phy.SlotBuffers(cfg, with_inputs=False)
+    Y, P, s2 = T(sl.Y, dev), T(sl.pilots, dev), T(sl.sigma2, dev)
+    phy.slot_run(cfg, Y, P, s2, buf.x_hat, buf.sinr, buf.llr, buf.flags, buf.workspace)
+    G = phy.n_groups(cfg)
+    anchors = torch.empty((spec.n_cells, len(spec.dmrs_sym), G, spec.n_layers, spec.n_rx),
+                          dtype=torch.complex64, device=dev)
+    phy.chest(cfg, Y, P, anchors)
+    torch.cuda.synchronize()
+    return dict(x_hat=buf.x_hat.cpu().numpy(), sinr=buf.sinr.cpu().numpy(),
+                llr=buf.llr.cpu().numpy(), flags=buf.flags.cpu().numpy(),
+                anchors=anchors.cpu().numpy(), cfg=cfg, buf=buf, Y=Y, P=P, s2=s2)
+
+
+def oracle_dense(spec, sl):
+    ref = O.run_slot(sl.Y, sl.pilots, sl.sigma2, spec.dmrs_sym, spec.n_layers, spec.qm,
+                     spec.occ_len)
+    sinr = ref["sinr"]
+    ref["s2eff"] = 1.0 / sinr
+    mu = sinr / (1.0 + sinr)
+    ref["x_t"] = ref["x_hat"] / mu
+    return ref
+
+
+CASES = {
+    "small_51prb_4x2_16qam": (S.spec_small_51prb(), 1001),
+    "carrier_25prb_16x4_64qam_jakes": (S.spec_carrier_273prb(n_prb=25), 2000),
+    "ragged_7prb_6x3_64qam": (S.SlotSpec(n_prb=7, n_rx=6, n_layers=3, qm=6, dmrs_sym=(2, 11),
+                                         snr_db=25.0, n_taps=6, doppler_hz=300.0), 11),
+    "one_layer_3prb_qpsk": (S.SlotSpec(n_prb=3, n_rx=2, n_layers=1, qm=2, dmrs_sym=(3,),
+                                       snr_db=10.0), 12),
+    "five_layers_5prb_8rx_256qam": (S.SlotSpec(n_prb=5, n_rx=8, n_layers=5, qm=8,
+                                               dmrs_sym=(2, 11), snr_db=35.0), 13),
+    "nine_layers_4prb_12rx": (S.SlotSpec(n_prb=4, n_rx=12, n_layers=9, qm=4, dmrs_sym=(2, 11),
+                                         snr_db=25.0, n_taps=4), 14),
+    "massive_6prb_64x16_256qam_2cells": (S.spec_massive_mimo(n_cells=2, n_prb=6), 3000),
+    "massive_one_dmrs_5prb_32x16": (S.spec_massive_mimo(n_cells=1, n_prb=5, n_rx=32,
+                                                        dmrs_sym=(2,)), 15),
+    "one_prb_4x2": (S.SlotSpec(n_prb=1, n_rx=4, n_layers=2, qm=4, dmrs_sym=(2,)), 16),
+    "forced_cover_4_single_layer": (S.SlotSpec(n_prb=4, n_rx=4, n_layers=1, qm=4,
+                                               dmrs_sym=(2, 11), occ_len=4), 17),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_slot_parity_dense(dev, name):
+    spec, seed = CASES[name]
+    sl = S.make_slot(spec, seed, keep_h=False)
+    got = gpu_slot(spec, sl, dev)
+    ref = oracle_dense(spec, sl)
+    # LS anchors
+    a_rel = rel_fro(got["anchors"], ref["anchors"])
+    print(name, "anchors rel", a_rel)
+    assert a_rel < 2e-7
+    # detection outputs over every data RE, flattened to [re][layer]
+    nl, qm = spec.n_layers, spec.qm
+    flat = lambda a, tail: a.reshape((-1,) + tail)
+    fl_ref = ref["flags"].reshape(-1)
+    fl_got = got["flags"].reshape(-1)
+    mask = (fl_ref == 0) & (fl_got == 0)
+    m = compare_res(name,
+                    dict(x_hat=flat(got["x_hat"], (nl,)), sinr=flat(got["sinr"], (nl,)),
+                         llr=flat(got["llr"], (nl, qm))),
+                    dict(x_hat=flat(ref["x_hat"], (nl,)), sinr=flat(ref["sinr"], (nl,)),
+                         llr=flat(ref["llr"], (nl, qm))),
+                    qm, flat(ref["s2eff"], (nl,)), flat(ref["x_t"], (nl,)), mask)
+    assert_parity(m)
+    assert np.array_equal(fl_got & 4, np.zeros_like(fl_got))
+    assert mask.mean() > 0.99
+
+
+def test_slot_parity_full_size_sampled(dev):
+    """The benchmark's launch: 8 cells x 273 PRB x 64 Rx x 16 layers, 256-QAM; sampled REs."""
+    spec = S.spec_massive_mimo()
+    sl = S.make_slot(spec, 3000, keep_h=False)
+    got = gpu_slot(spec, sl, dev)
+    rng = np.random.default_rng(0)
+    K, J = spec.n_sc, len(spec.data_sym)
+    res = {}
+    for c in range(spec.n_cells):
+        kk = np.concatenate([np.arange(0, 30), np.arange(K - 30, K), rng.integers(0, K, 60)])
+        jj = rng.integers(0, J, kk.size)
+        res[c] = (jj, kk)
+    ref = O.run_slot(sl.Y, sl.pilots, sl.sigma2, spec.dmrs_sym, spec.n_layers, spec.qm, res=res)
+    assert rel_fro(got["anchors"], ref["anchors"]) < 2e-7
+    gx, rx, gs, rs, gl, rl, gf, rf = [], [], [], [], [], [], [], []
+    for c, (jj, kk) in res.items():
+        gx.append(got["x_hat"][c, jj, kk]); rx.append(ref[f"x_hat_{c}"])
+        gs.append(got["sinr"][c, jj, kk]); rs.append(ref[f"sinr_{c}"])
+        gl.append(got["llr"][c, jj, kk]); rl.append(ref[f"llr_{c}"])
+        gf.append(got["flags"][c, jj, kk]); rf.append(ref[f"flags_{c}"])
+    gx, rx, gs, rs = map(np.concatenate, (gx, rx, gs, rs))
+    gl, rl, gf, rf = map(np.concatenate, (gl, rl, gf, rf))
+    s2eff = 1.0 / rs
+    x_t = rx / (rs / (1 + rs))
+    mask = (gf == 0) & (rf == 0)
+    m = compare_res("full_size_sampled", dict(x_hat=gx, sinr=gs, llr=gl),
+                    dict(x_hat=rx, sinr=rs, llr=rl), spec.qm, s2eff, x_t, mask)
+    assert_parity(m)
+
+
+def test_mmse_detect_genie_and_zero_forcing(dev):
+    import torch
+    from paper_2510_07843_gb300 import phy
+    spec = S.SlotSpec(n_prb=4, n_rx=8, n_layers=4, qm=4, dmrs_sym=(2, 11), snr_db=20.0)
+    for noise, s2 in ((True, spec.sigma2), (False, 0.0)):
+        sl = S.make_slot(spec, 21, keep_h=True, noise=noise)
+        dsym = list(spec.data_sym)
+        H = np.stack([sl.H[0][dsym]])  # [cell][dsym][sc][rx][layer]
+        cfg = phy.SlotConfig.from_spec(spec)
+        C, J, K, nl = 1, len(dsym), spec.n_sc, spec.n_layers
+        x = torch.empty((C, J, K, nl), dtype=torch.complex64, device=dev)
+        sn = torch.empty((C, J, K, nl), dtype=torch.float32, device=dev)
+        fl = torch.empty((C, J, K), dtype=torch.uint8, device=dev)
+        s2t = T(np.array([s2], dtype=np.float32), dev)
+        phy.mmse_detect(cfg, T(H.astype(np.complex64), dev), T(sl.Y, dev), s2t, x, sn, fl)
+        torch.cuda.synchronize()
+        Hc = H.astype(np.complex64).astype(np.complex128)
+        y = np.stack([sl.Y[0, t].T for t in dsym])[None].astype(np.complex128)  # [1][J][K][rx]
+        xr, d = O.lmmse_gram(Hc, y, s2)
+        got = x.cpu().numpy()
+        err = rel_fro(got, xr)
+        print("mmse_detect noise" if noise else "zero forcing", err)
+        assert err < 1e-5
+        if not noise:
+            assert rel_fro(got, sl.x) < 1e-5  # ZF recovers the transmitted symbols
+        else:
+            sr, _, _ = O.sinr_unbias(xr, d, s2)
+            assert np.max(np.abs(sn.cpu().numpy() - sr) / sr) < 1e-4
+        assert not fl.cpu().numpy().any()
+
+
+def test_llr_demap_standalone_matches_fused_and_oracle(dev):
+    import torch
+    from paper_2510_07843_gb300 import phy
+    spec = S.spec_carrier_273prb(n_prb=10)
+    sl = S.make_slot(spec, 31, keep_h=False)
+    got = gpu_slot(spec, sl, dev)
+    buf = got["buf"]
+    llr2 = torch.empty_like(buf.llr)
+    phy.llr_demap(got["cfg"], buf.x_hat, buf.sinr, llr2)
+    torch.cuda.synchronize()
+    l2 = llr2.cpu().numpy()
+    sinr = got["sinr"].astype(np.float64)
+    s2eff = 1.0 / sinr
+    x_t = got["x_hat"].astype(np.complex128) / (sinr / (1 + sinr))
+    ref = O.llr_maxlog(x_t, s2eff, spec.qm)
+    assert np.max(np.abs(l2 - ref) * s2eff[..., None]) < 1e-4
+    assert np.max(np.abs(l2 - got["llr"]) * s2eff[..., None]) < 1e-4
+
+
+def test_non_finite_input_is_flagged(dev):
+    spec = S.SlotSpec(n_prb=3, n_rx=4, n_layers=2, qm=4, dmrs_sym=(2,))
+    sl = S.make_slot(spec, 41, keep_h=False)
+    clean = gpu_slot(spec, sl, dev)
+    Y = sl.Y.copy()
+    Y[0, 5, 1, 17] = np.nan  # data symbol 5 (data index 4), subcarrier 17
+    sl.Y = Y
+    got = gpu_slot(spec, sl, dev)
+    j = spec.data_sym.index(5)
+    assert got["flags"][0, j, 17] & 4
+    assert np.all(np.isfinite(got["llr"])) and np.all(np.isfinite(got["x_hat"]))
+    assert np.all(got["llr"][0, j, 17] == 0)
+    other = np.ones(got["flags"].shape, dtype=bool)
+    other[0, j, 17] = False
+    assert np.array_equal(got["llr"][other], clean["llr"][other])
+
+
+def test_repeatable_bitwise(dev):
+    spec = S.spec_massive_mimo(n_cells=1, n_prb=4)
+    sl = S.make_slot(spec, 51, keep_h=False)
+    a = gpu_slot(spec, sl, dev)
+    b = gpu_slot(spec, sl, dev)
+    assert np.array_equal(a["llr"], b["llr"]) and np.array_equal(a["x_hat"], b["x_hat"])
+
+
+def test_errors_enqueue_nothing(dev):
+    import torch
+    from paper_2510_07843_gb300 import phy
+    spec = S.spec_small_51prb(n_prb=4)
+    cfg = phy.SlotConfig.from_spec(spec)
+    buf = phy.SlotBuffers(cfg)
+    small = torch.empty((16,), dtype=torch.uint8, device=dev)
+    with pytest.raises(phy.PhyError) as e:
+        phy.slot_run(cfg, buf.Y, buf.pilots, buf.sigma2, buf.x_hat, buf.sinr, buf.llr, buf.flags,
+                     small)
+    assert e.value.code == 3
+    bad = dataclasses.replace(cfg, occ_len=3)
+    with pytest.raises(phy.PhyError) as e:
+        phy.slot_run(bad, buf.Y, buf.pilots, buf.sigma2, buf.x_hat, buf.sinr, buf.llr, buf.flags,
+                     buf.workspace)
+    assert e.value.code == 1
