@@ -161,6 +161,33 @@ phy_status phy_slot_run_host(const phy_slot_cfg* cfg, const phy_c32* Y_host,
                              uint8_t* flags, void* workspace, size_t workspace_bytes,
                              void* stream);
 
+/*
+ * phy_slot_run() for callers that cannot allocate device memory. It has no counterpart in the
+ * paper; it exists for hosts of this library that are not allowed to call cudaMalloc, for
+ * example a real-time slot loop where an allocation could stall past the slot deadline (it may
+ * synchronise the device), or a plugin whose host framework owns all device memory and hands
+ * out only input and output buffers.
+ *
+ * The caller passes inputs and outputs only (same layouts and rules as phy_slot_run()). The
+ * scratch space lives in one fixed array of PHY_NOALLOC_SCRATCH_BYTES in the library's device
+ * memory: every GPU that loads libphy.so holds that array until the process exits, and the
+ * call itself allocates nothing (no cudaMalloc, no cudaFree, no allocating library routine).
+ *  - Limit: a configuration whose phy_workspace_size() exceeds PHY_NOALLOC_SCRATCH_BYTES is
+ *    rejected with PHY_ERR_NO_MEMORY before anything is enqueued (32 MiB covers 8 cells of
+ *    273 PRB with 64 Rx and 16 layers and two DMRS symbols).
+ *  - The first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ *    with that device current and caches it; make that first call before any stream capture.
+ *  - All calls on a device share the one array and it keeps the previous call's contents (every
+ *    value a call reads is written earlier in the same call, so nothing needs clearing). Calls
+ *    whose work overlaps on the GPU (different streams, or different host threads) race on it:
+ *    serialise them, e.g. on one stream.
+ */
+#define PHY_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+
+phy_status phy_slot_run_noalloc(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32* pilots,
+                                const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
+                                uint8_t* flags, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,61 @@
+// phy_slot_run_noalloc: the whole receiver with its scratch in a fixed device array.
+//
+// phy_slot_run keeps the LS anchors between its two kernels in a caller-provided workspace.
+// This variant keeps them in the file-scope array below instead, so the caller passes only
+// inputs and outputs and nothing is allocated, ever.
+#include <mutex>
+
+#include "../../include/phy.h"
+#include "launch.h"
+
+namespace {
+
+constexpr size_t kScratchBytes = PHY_NOALLOC_SCRATCH_BYTES;
+constexpr int kMaxDevices = 64;
+
+}  // namespace
+
+// One copy per device that loads the library, held until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+namespace {
+
+std::mutex g_mu;
+void* g_addr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device. The host-side name of the array
+// is a stand-in, not a device address, so it is resolved once per device (with that device
+// current) and cached.
+cudaError_t scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_addr[dev] = p;
+  }
+  *out = g_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" phy_status phy_slot_run_noalloc(const phy_slot_cfg* cfg, const phy_c32* Y,
+                                           const phy_c32* pilots, const float* sigma2,
+                                           phy_c32* x_hat, float* sinr, float* llr,
+                                           uint8_t* flags, void* stream) {
+  const size_t need = phy_workspace_size(cfg);
+  if (need == 0) return PHY_ERR_INVALID_ARG;
+  if (need > kScratchBytes) return PHY_ERR_NO_MEMORY;
+  if (!Y || !pilots || !sigma2 || !flags) return PHY_ERR_INVALID_ARG;
+  void* scratch = nullptr;
+  if (scratch_address(&scratch) != cudaSuccess) return PHY_ERR_CUDA;
+  // phy_slot_run validates the rest and runs both kernels; the chest kernel overwrites every
+  // anchor the detection kernel reads, so nothing in the array needs clearing between calls.
+  return phy_slot_run(cfg, Y, pilots, sigma2, x_hat, sinr, llr, flags, scratch, kScratchBytes,
+                      stream);
+}

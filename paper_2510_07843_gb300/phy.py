@@ -42,7 +42,11 @@ _SIGS = {
     "phy_llr_demap": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "phy_slot_run": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "phy_slot_run_host": (ctypes.c_int, [_P] * 14 + [ctypes.c_size_t, _P]),
+    "phy_slot_run_noalloc": (ctypes.c_int, [_P] * 9),
 }
+
+# Bytes of the fixed scratch array behind phy_slot_run_noalloc (PHY_NOALLOC_SCRATCH_BYTES).
+NOALLOC_SCRATCH_BYTES = 32 << 20
 
 _lib = None
 
@@ -163,6 +167,16 @@ def slot_run(cfg: SlotConfig, Y, pilots, sigma2, x_hat, sinr, llr, flags, worksp
            load().phy_slot_run(ctypes.byref(c), _ptr(Y), _ptr(pilots), _ptr(sigma2), _ptr(x_hat),
                                _ptr(sinr), _ptr(llr), _ptr(flags), _ptr(workspace), ws_bytes,
                                _stream(stream)))
+
+
+def slot_run_noalloc(cfg: SlotConfig, Y, pilots, sigma2, x_hat, sinr, llr, flags, stream=None):
+    """phy_slot_run without a workspace argument, for callers that may not allocate device
+    memory: the library keeps its scratch in a fixed device array (see include/phy.h)."""
+    c = cfg.c()
+    _check("phy_slot_run_noalloc",
+           load().phy_slot_run_noalloc(ctypes.byref(c), _ptr(Y), _ptr(pilots), _ptr(sigma2),
+                                       _ptr(x_hat), _ptr(sinr), _ptr(llr), _ptr(flags),
+                                       _stream(stream)))
 
 
 def slot_run_host(cfg: SlotConfig, Y_h, pilots_h, sigma2_h, llr_h, flags_h, Y, pilots, sigma2,
