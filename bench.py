@@ -291,7 +291,7 @@ def run_ours(args, spec, rank, world, local):
         if e_mid is not None:
             e_mid.record(st)
         phy.detect_anchors(cfg, buf.anchors, buf.Y, buf.sigma2, buf.x_hat, buf.sinr, buf.llr,
-                           buf.flags, stream=st)
+                           buf.flags, buf.workspace, stream=st)
 
     with torch.cuda.stream(st):
         for _ in range(max(args.warmup, 3)):

@@ -124,11 +124,13 @@ phy_status phy_mmse_detect(const phy_slot_cfg* cfg, const phy_c32* H, const phy_
 
 /*
  * Interpolation, LMMSE detection, SINR and LLRs from given LS anchors (as written by phy_chest,
- * or any estimate in that layout): the second half of phy_slot_run. Same outputs and rules.
+ * or any estimate in that layout): the second half of phy_slot_run, with the same outputs,
+ * rules and workspace (its first bytes, where phy_slot_run keeps the anchors, are unused).
  */
 phy_status phy_detect_anchors(const phy_slot_cfg* cfg, const phy_c32* anchors, const phy_c32* Y,
                               const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
-                              uint8_t* flags, void* stream);
+                              uint8_t* flags, void* workspace, size_t workspace_bytes,
+                              void* stream);
 
 /*
  * Max-log LLR demapping of equalised symbols: from x_hat and SINR (as written by
@@ -173,7 +175,7 @@ phy_status phy_slot_run_host(const phy_slot_cfg* cfg, const phy_c32* Y_host,
  * memory: every GPU that loads libphy.so holds that array until the process exits, and the
  * call itself allocates nothing (no cudaMalloc, no cudaFree, no allocating library routine).
  *  - Limit: a configuration whose phy_workspace_size() exceeds PHY_NOALLOC_SCRATCH_BYTES is
- *    rejected with PHY_ERR_NO_MEMORY before anything is enqueued (32 MiB covers 8 cells of
+ *    rejected with PHY_ERR_NO_MEMORY before anything is enqueued (64 MiB covers 8 cells of
  *    273 PRB with 64 Rx and 16 layers and two DMRS symbols).
  *  - The first call on each device looks up the array's device address (cudaGetSymbolAddress)
  *    with that device current and caches it; make that first call before any stream capture.
@@ -182,7 +184,7 @@ phy_status phy_slot_run_host(const phy_slot_cfg* cfg, const phy_c32* Y_host,
  *    whose work overlaps on the GPU (different streams, or different host threads) race on it:
  *    serialise them, e.g. on one stream.
  */
-#define PHY_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+#define PHY_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 
 phy_status phy_slot_run_noalloc(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32* pilots,
                                 const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,

@@ -15,7 +15,7 @@ LIB = os.path.join(PKG, "libphy.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-         "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
+         "--expt-relaxed-constexpr", "--extended-lambda", "-I", os.path.join(ROOT, "include")]
 
 
 def nvcc() -> str:

@@ -120,7 +120,7 @@ int32_t phy_n_data_symbols(const phy_slot_cfg* cfg) {
 size_t phy_workspace_size(const phy_slot_cfg* cfg) {
   Geo g;
   if (make_geo(cfg, &g) != PHY_OK) return 0;
-  return align_up(anchor_bytes(g));
+  return align_up(anchor_bytes(g)) + align_up(phy::detect_fp32_scratch_bytes(g));
 }
 
 phy_status phy_chest(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32* pilots,
@@ -154,15 +154,19 @@ phy_status phy_llr_demap(const phy_slot_cfg* cfg, const phy_c32* x_hat, const fl
 
 phy_status phy_detect_anchors(const phy_slot_cfg* cfg, const phy_c32* anchors, const phy_c32* Y,
                               const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
-                              uint8_t* flags, void* stream) {
+                              uint8_t* flags, void* workspace, size_t workspace_bytes,
+                              void* stream) {
   Geo g;
   phy_status s = make_geo(cfg, &g);
   if (s != PHY_OK) return s;
-  if (!anchors || !Y || !sigma2 || !flags) return PHY_ERR_INVALID_ARG;
+  if (!anchors || !Y || !sigma2 || !flags || !workspace) return PHY_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace) % kAlign) return PHY_ERR_INVALID_ARG;
+  if (workspace_bytes < phy_workspace_size(cfg)) return PHY_ERR_NO_MEMORY;
   s = check_precision(cfg, g);
   if (s != PHY_OK) return s;
+  void* scratch = static_cast<char*>(workspace) + align_up(anchor_bytes(g));
   return cuda_status(phy::launch_detect_fp32(g, anchors, Y, sigma2, x_hat, sinr, llr, flags,
-                                             (cudaStream_t)stream));
+                                             scratch, (cudaStream_t)stream));
 }
 
 phy_status phy_slot_run(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32* pilots,
@@ -180,7 +184,8 @@ phy_status phy_slot_run(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32
   phy_c32* anchors = (phy_c32*)workspace;
   cudaError_t e = phy::launch_chest(g, Y, pilots, anchors, st);
   if (e != cudaSuccess) return PHY_ERR_CUDA;
-  e = phy::launch_detect_fp32(g, anchors, Y, sigma2, x_hat, sinr, llr, flags, st);
+  void* scratch = static_cast<char*>(workspace) + align_up(anchor_bytes(g));
+  e = phy::launch_detect_fp32(g, anchors, Y, sigma2, x_hat, sinr, llr, flags, scratch, st);
   return cuda_status(e);
 }
 

@@ -114,45 +114,40 @@ __device__ __forceinline__ float seg_beta(const Geo& g, int j, int k, int c) {
 __device__ __forceinline__ int seg_g1(const Geo& g, int j) { return g.G == 1 ? 0 : j + 1; }
 
 // ---------------------------------------------------------------- max-log demapper
-// PAM level (in units of the unnormalised odd-integer grid) of the axis bits e_0..e_{H-1}, where
-// e_0 = bits & (1 << (H-1)) ... following the NR nesting
-// (1-2e0)(2^(H-1) - (1-2e1)(2^(H-2) - ... (2 - (1-2e_{H-1})))).
-template <int H>
-__device__ __forceinline__ float pam_level(int bits) {
-  float inner = 1.f;
-#pragma unroll
-  for (int i = H - 1; i >= 1; --i) {
-    int e = (bits >> (H - 1 - i)) & 1;
-    inner = (float)(1 << (H - i)) - (1 - 2 * e) * inner;
-  }
-  int e0 = (bits >> (H - 1)) & 1;
-  return (1 - 2 * e0) * inner;
+// NR Gray QAM: bits b0, b2, ... (e_0, e_1, ... of the in-phase axis) and b1, b3, ... (the
+// quadrature axis) each pick a PAM level (1-2e0)(2^(H-1) - (1-2e1)(2^(H-2) - ... (2 - (1-2e_{H-1}))))
+// on the odd-integer grid, scaled by 1/sqrt(2 (4^H - 1) / 3).
+
+// Nearest odd integer to x, clamped to the odd interval [a, b].
+__device__ __forceinline__ float nearest_odd(float x, float a, float b) {
+  return fminf(fmaxf(fmaf(2.f, floorf(0.5f * x), 1.f), a), b);
 }
 
 // Max-log LLRs of the H axis bits for axis value v (already scaled to the odd-integer grid),
-// out[i] = (min_{e_i=1} (v-s)^2 - min_{e_i=0} (v-s)^2) * scale.
+// out[i] = (min_{e_i=1} (v-s)^2 - min_{e_i=0} (v-s)^2) * scale, without visiting every level.
+// Bit e_0 is the sign: the nearest level of each set is a clamped nearest odd integer. For
+// i >= 1 the nesting |s| = 2^(H-1) - s_1 (2^(H-2) - s_2 (...)) means the level set of e_i is
+// symmetric under the reflections v -> |v| and u -> |u - 2^(H-j)| (j < i), so its distance to v
+// equals the distance of the folded value u_i to {1, 3, ..., 2^(H-i) - 1} (e_i = 0) or to
+// {2^(H-i) + 1, ..., 2^(H-i+1) - 1} (e_i = 1). Equal to the exhaustive search up to rounding.
 template <int H>
 __device__ __forceinline__ void pam_llr(float v, float scale, float* out) {
-  float m0[H], m1[H];
-#pragma unroll
-  for (int i = 0; i < H; ++i) {
-    m0[i] = 3.0e38f;
-    m1[i] = 3.0e38f;
+  constexpr float M = (float)((1 << H) - 1);
+  {
+    const float n0 = nearest_odd(v, 1.f, M), n1 = nearest_odd(v, -M, -1.f);
+    const float d0 = v - n0, d1 = v - n1;
+    out[0] = fmaf(d1, d1, -d0 * d0) * scale;
   }
+  float u = fabsf(v);
 #pragma unroll
-  for (int b = 0; b < (1 << H); ++b) {
-    float d = v - pam_level<H>(b);
-    d = d * d;
-#pragma unroll
-    for (int i = 0; i < H; ++i) {
-      if ((b >> (H - 1 - i)) & 1)
-        m1[i] = fminf(m1[i], d);
-      else
-        m0[i] = fminf(m0[i], d);
-    }
+  for (int i = 1; i < H; ++i) {
+    const float half = (float)(1 << (H - i));
+    const float n0 = nearest_odd(u, 1.f, half - 1.f);
+    const float n1 = nearest_odd(u, half + 1.f, 2.f * half - 1.f);
+    const float d0 = u - n0, d1 = u - n1;
+    out[i] = fmaf(d1, d1, -d0 * d0) * scale;
+    u = fabsf(u - half);
   }
-#pragma unroll
-  for (int i = 0; i < H; ++i) out[i] = (m1[i] - m0[i]) * scale;
 }
 
 // LLRs of one layer's QM bits (b0, b1, ... interleaving I and Q) from the unbiased symbol x~ and

@@ -1,21 +1,22 @@
-// Fused LMMSE detection on FP32 CUDA cores: interpolation, Gram, matched filter, Cholesky,
-// solves, SINR and max-log LLRs for one frequency segment of one cell per CTA.
+// LMMSE detection on FP32 CUDA cores in two kernels: per-segment Gram blocks and matched filter,
+// then a flat one-thread-per-RE solve.
 //
 // With linear interpolation every RE's channel is a weighted sum of the four "corner" anchor
-// matrices of its segment (anchors j and j+1 of both DMRS symbols): column l of H(k, t) is
-//   sum_{d,g} tau_d(t) w_g(k, comb(l)) C_{d,g}[:, l].
-// So the Gram matrix of every RE of the segment is a quadratic form in the same corner
-// cross-Gram X = C^H C (C = [C_00 C_01 C_10 C_11], n_rx x 4 n_layers), computed once per CTA.
-// That is the paper's covariance-by-FMA step (Fig. 2(b)) done once per segment instead of once
-// per RE, exact up to rounding. Per data symbol the time weights fold X into three blocks
-// Y_gg'(t) = H_g(t)^H H_g'(t); per RE A = sum_{g,g'} D_g Y_gg' D_g' + s2 I with diagonal D_g of
-// the frequency weights. The matched filter uses the time-interpolated anchors H_g(t) directly:
-// b = D_0 H_0(t)^H y + D_1 H_1(t)^H y.
+// matrices of its frequency segment (anchors j and j+1 of both DMRS symbols): column l of
+// H(k, t) is sum_{d,g} tau_d(t) w_g(k, comb(l)) C_{d,g}[:, l]. The Gram matrix of every RE of a
+// segment is therefore a quadratic form in one corner cross-Gram X = C^H C
+// (C = [C_00 C_01 C_10 C_11], n_rx x 4 n_layers) computed once per segment: the paper's
+// covariance-by-FMA step (Fig. 2(b)) done once per segment instead of once per RE, exact up to
+// rounding. Per data symbol the time weights fold X into Y_gg'(t) = H_g(t)^H H_g'(t),
+// g, g' in {0, 1}; per RE, A = sum_{g,g'} D_g Y_gg' D_g' + s2 I with D_g diagonal frequency
+// weights. The matched filter uses the time-interpolated anchors: b = D_0 H_0^H y + D_1 H_1^H y.
 //
-// Phases (one CTA, all data symbols of the segment):
-//   A0 corners -> smem (layout [r][corner*NL + l])        A1 X = C^H C (4x4 register tiles)
-//   A2 Y_gg'(t) for every data symbol                     A3 per symbol: H_g(t), matched filter
-//   B  one thread per RE: build A, solve (solver.cuh), SINR, unbias, LLR, store.
+//  seg_prep_fp32_kernel: one CTA per (segment, cell). Corners to shared memory, X (lower 4x4
+//    tiles), the four Y_gg' blocks per data symbol (lower triangle, 4-tuples) to the workspace,
+//    and the matched filter per symbol from a shared-memory Y tile (cp.async double buffer).
+//  re_solve_fp32_kernel: one thread per data RE, no barriers. Builds A from the 4-tuples,
+//    solves (solver.cuh), SINR, unbiasing, max-log LLRs, stores.
+// The two kernels run per chunk of cells so that the intermediates stay small (L2-sized).
 #include <algorithm>
 
 #include "launch.h"
@@ -25,89 +26,91 @@ namespace phy {
 
 namespace {
 
-template <int NL>
-struct FusedTraits {
-  static constexpr int NT = (NL == 16) ? 192 : 128;
+constexpr int kPrepThreads = 256;
+constexpr int kSolveThreads = 128;
+constexpr size_t kChunkBudget = 32ull << 20;  // bytes of intermediates per chunk of cells
+
+int nl_class(int nl) { return nl <= 2 ? 2 : nl <= 4 ? 4 : nl <= 8 ? 8 : 16; }
+
+struct PrepLayout {
+  int NC, NX, xs, hs, yw;
+  int off_C, off_X, off_Hg, off_Y, total;  // cf units
 };
 
-struct FusedLayout {
-  int NC, NX, xs, hs;
-  int off_ygg, off_b, off_C, off_X, off_Hg, off_scr;  // in cf units
-  int total;                                         // cf units
-};
-
-__host__ __device__ inline FusedLayout fused_layout(int NL, int NT, int n_dmrs, int n_rx,
-                                                   int n_dsym, int wmax) {
-  FusedLayout f;
+__host__ __device__ inline PrepLayout prep_layout(int NL, int n_dmrs, int n_rx, int wmax) {
+  PrepLayout f;
   f.NC = 2 * n_dmrs;
   f.NX = f.NC * NL;
-  f.xs = f.NX + 2;  // row stride keeps 16-byte alignment and spreads banks
-  f.hs = 2 * NL + 2;
-  f.off_ygg = 0;
-  int ygg = n_dsym * 3 * NL * NL;
-  f.off_b = f.off_ygg + ygg;
-  int bv = wmax * n_dsym * NL;
-  bv = (bv + 1) & ~1;
-  int u0 = f.off_b + bv;
-  f.off_C = u0;
+  f.xs = f.NX + 2;           // keeps 16-byte row alignment, spreads banks
+  f.hs = 2 * NL + 1;         // odd stride: conflict-free column reads
+  f.yw = wmax + 1;
+  f.off_C = 0;
   f.off_X = f.off_C + n_rx * f.xs;
   f.off_Hg = f.off_X + f.NX * f.xs;
-  int endA = f.off_Hg + n_rx * f.hs;
-  f.off_scr = u0;
-  int endB = (NL == 16) ? u0 + 64 * NT : u0;
-  f.total = endA > endB ? endA : endB;
+  f.off_Y = f.off_Hg + n_rx * f.hs;
+  f.total = f.off_Y + 2 * n_rx * f.yw;
   return f;
 }
 
-struct SmemScratch {
-  cf* base;  // points at this thread's first element
-  int stride;
-  __device__ __forceinline__ void st(int i, int j, cf v) const { base[(i * 8 + j) * stride] = v; }
-  __device__ __forceinline__ cf ld(int i, int j) const { return base[(i * 8 + j) * stride]; }
-};
-
-template <int QM>
-__device__ __forceinline__ void store_llr(float* dst, cf xt, float s2eff) {
-  float l[QM];
-  qam_llr<QM>(xt, s2eff, l);
-#pragma unroll
-  for (int q = 0; q < QM; q += 2) *reinterpret_cast<float2*>(dst + q) = make_float2(l[q], l[q + 1]);
+// Row l (l >= m) of the packed lower triangle from its index.
+__device__ __forceinline__ void tri_decode(int e, int& l, int& m) {
+  int r = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+  while (r * (r + 1) / 2 > e) --r;
+  while ((r + 1) * (r + 2) / 2 <= e) ++r;
+  l = r;
+  m = e - r * (r + 1) / 2;
 }
 
-__device__ __forceinline__ void store_llr_rt(int qm, float* dst, cf xt, float s2eff) {
-  switch (qm) {
-    case 2: store_llr<2>(dst, xt, s2eff); break;
-    case 4: store_llr<4>(dst, xt, s2eff); break;
-    case 6: store_llr<6>(dst, xt, s2eff); break;
-    default: store_llr<8>(dst, xt, s2eff); break;
-  }
+__device__ __forceinline__ int seg_of(const Geo& g, int k) {
+  if (g.G == 1) return 0;
+  int j = (k - g.L) / (2 * g.L);
+  if (k < g.L) j = 0;
+  return j < g.n_seg - 1 ? j : g.n_seg - 1;
+}
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
 template <int NL>
-__global__ void __launch_bounds__(FusedTraits<NL>::NT, 1)
-    detect_fp32_kernel(Geo g, int wmax, const phy_c32* __restrict__ anchors,
-                       const phy_c32* __restrict__ Y, const float* __restrict__ sigma2,
-                       phy_c32* __restrict__ x_hat, float* __restrict__ sinr_out,
-                       float* __restrict__ llr_out, uint8_t* __restrict__ flags_out) {
-  constexpr int NT = FusedTraits<NL>::NT;
+__global__ void __launch_bounds__(kPrepThreads)
+    seg_prep_fp32_kernel(Geo g, int wmax, int cell0, const phy_c32* __restrict__ anchors,
+                         const phy_c32* __restrict__ Y, float4* __restrict__ ygg,
+                         cf* __restrict__ bvec) {
+  constexpr int NT = kPrepThreads;
+  constexpr int NTRI = NL * (NL + 1) / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cf* sm = reinterpret_cast<cf*>(smem_raw);
   const int tid = threadIdx.x;
-  const int j = blockIdx.x, cell = blockIdx.y;
+  const int j = blockIdx.x, lc = blockIdx.y, cell = cell0 + lc;
   const int nr = g.n_rx, nl = g.n_layers, nds = g.n_dsym;
-  const FusedLayout f = fused_layout(NL, NT, g.n_dmrs, nr, nds, wmax);
-  cf* Ygg = sm + f.off_ygg;
-  cf* bvec = sm + f.off_b;
+  const PrepLayout f = prep_layout(NL, g.n_dmrs, nr, wmax);
   cf* Cs = sm + f.off_C;
   cf* Xs = sm + f.off_X;
   cf* Hg = sm + f.off_Hg;
+  cf* Yt = sm + f.off_Y;
   int lo, hi;
   segment_range(g, j, lo, hi);
   const int W = hi - lo;
-  const int nre = W * nds;
-  const float s2 = sigma2[cell];
 
-  // ---- A0: corner anchors
+  auto load_tile = [&](int jj, int buf) {
+    const phy_c32* ysym = Y + ((size_t)cell * g.n_sym + g.dsym[jj]) * nr * g.n_sc + lo;
+    cf* dst = Yt + buf * nr * f.yw;
+    for (int e = tid; e < nr * W; e += NT) {
+      const int r = e / W, kk = e % W;
+      cp_async8(dst + r * f.yw + kk, ysym + (size_t)r * g.n_sc + kk);
+    }
+    cp_async_commit();
+  };
+  load_tile(0, 0);  // overlaps the Gram work below
+
+  // ---- corners
   {
     const int total = f.NC * NL * nr;
     const int g1 = seg_g1(g, j);
@@ -125,11 +128,13 @@ __global__ void __launch_bounds__(FusedTraits<NL>::NT, 1)
     }
   }
   __syncthreads();
-  // ---- A1: X = C^H C, full NX x NX in 4x4 tiles
+  // ---- X = C^H C, lower 4x4 tiles
   {
     const int nt4 = f.NX / 4;
-    for (int tile = tid; tile < nt4 * nt4; tile += NT) {
-      const int ti = tile / nt4, tj = tile % nt4;
+    const int n_lt = nt4 * (nt4 + 1) / 2;
+    for (int t = tid; t < n_lt; t += NT) {
+      int ti, tj;
+      tri_decode(t, ti, tj);
       cf acc[4][4];
 #pragma unroll
       for (int p = 0; p < 4; ++p)
@@ -153,34 +158,44 @@ __global__ void __launch_bounds__(FusedTraits<NL>::NT, 1)
     }
   }
   __syncthreads();
-  // ---- A2: Y_gg'(t) = sum_{d,d'} tau_d tau_d' X[(d,g)][(d',g')] for (g,g') in 00, 10, 11
+  // ---- Y_gg'(t), lower triangle, as 4-tuples (Y00, Y01, Y10, Y11) per (l, m)
   {
-    const int per = 3 * NL * NL;
-    for (int e = tid; e < nds * per; e += NT) {
-      const int m = e % NL;
-      const int l = (e / NL) % NL;
-      const int blk = (e / (NL * NL)) % 3;
-      const int jj = e / per;
-      const int gg = blk == 0 ? 0 : 1;
-      const int gp = blk == 2 ? 1 : 0;
-      cf v;
-      if (g.n_dmrs == 2) {
-        const float t1 = g.tw[jj], t0 = 1.f - t1;
-        const cf x00 = Xs[(gg * NL + l) * f.xs + gp * NL + m];
-        const cf x01 = Xs[(gg * NL + l) * f.xs + (2 + gp) * NL + m];
-        const cf x10 = Xs[((2 + gg) * NL + l) * f.xs + gp * NL + m];
-        const cf x11 = Xs[((2 + gg) * NL + l) * f.xs + (2 + gp) * NL + m];
-        v = (t0 * t0) * x00 + (t0 * t1) * x01 + (t1 * t0) * x10 + (t1 * t1) * x11;
-      } else {
-        v = Xs[(gg * NL + l) * f.xs + gp * NL + m];
-      }
-      Ygg[e] = v;
+    auto Xget = [&](int i, int k) -> cf {
+      if ((i >> 2) >= (k >> 2)) return Xs[i * f.xs + k];
+      const cf v = Xs[k * f.xs + i];
+      return mk(v.x, -v.y);
+    };
+    float4* out = ygg + (((size_t)lc * g.n_seg + j) * nds) * NTRI * 2;
+    for (int e = tid; e < nds * NTRI; e += NT) {
+      const int jj = e / NTRI, te = e % NTRI;
+      int l, m;
+      tri_decode(te, l, m);
+      cf y[4];
+#pragma unroll
+      for (int gg = 0; gg < 2; ++gg)
+#pragma unroll
+        for (int gp = 0; gp < 2; ++gp) {
+          cf v;
+          if (g.n_dmrs == 2) {
+            const float t1 = g.tw[jj], t0 = 1.f - t1;
+            v = (t0 * t0) * Xget(gg * NL + l, gp * NL + m) +
+                (t0 * t1) * Xget(gg * NL + l, (2 + gp) * NL + m) +
+                (t1 * t0) * Xget((2 + gg) * NL + l, gp * NL + m) +
+                (t1 * t1) * Xget((2 + gg) * NL + l, (2 + gp) * NL + m);
+          } else {
+            v = Xget(gg * NL + l, gp * NL + m);
+          }
+          y[gg * 2 + gp] = v;
+        }
+      out[(size_t)e * 2] = make_float4(y[0].x, y[0].y, y[1].x, y[1].y);
+      out[(size_t)e * 2 + 1] = make_float4(y[2].x, y[2].y, y[3].x, y[3].y);
     }
   }
-  // ---- A3: per data symbol, time-interpolated anchors and the matched filter
+  // ---- matched filter per data symbol
   for (int jj = 0; jj < nds; ++jj) {
     const float t1 = g.tw[jj], t0 = 1.f - t1;
-    __syncthreads();  // previous symbol's readers of Hg are done (and A2 done reading X)
+    __syncthreads();  // Hg and the other tile buffer are free
+    if (jj + 1 < nds) load_tile(jj + 1, (jj + 1) & 1);
     for (int e = tid; e < nr * 2 * NL; e += NT) {
       const int col = e % (2 * NL);
       const int r = e / (2 * NL);
@@ -189,116 +204,188 @@ __global__ void __launch_bounds__(FusedTraits<NL>::NT, 1)
       if (g.n_dmrs == 2) v = t0 * v + t1 * Cs[r * f.xs + (2 + gg) * NL + l];
       Hg[r * f.hs + col] = v;
     }
+    if (jj + 1 < nds)
+      cp_async_wait<1>();
+    else
+      cp_async_wait<0>();
     __syncthreads();
-    const int t = g.dsym[jj];
-    const phy_c32* ysym = Y + ((size_t)cell * g.n_sym + t) * nr * g.n_sc;
+    const cf* yt = Yt + (jj & 1) * nr * f.yw;
+    cf* bout = bvec + ((size_t)(lc * nds + jj) * g.n_sc + lo) * NL;
     for (int e = tid; e < W * NL; e += NT) {
       const int l = e % NL, kk = e / NL;
-      const int k = lo + kk;
       cf z0 = mk(0.f, 0.f), z1 = mk(0.f, 0.f);
       if (l < nl) {
-        const phy_c32* yp = ysym + k;
-#pragma unroll 8
+#pragma unroll 4
         for (int r = 0; r < nr; ++r) {
-          const cf y = ld(yp + (size_t)r * g.n_sc);
+          const cf y = yt[r * f.yw + kk];
           z0 = cfma_cj(Hg[r * f.hs + l], y, z0);
           z1 = cfma_cj(Hg[r * f.hs + NL + l], y, z1);
         }
       }
-      const float be = seg_beta(g, j, k, l & 1);
-      bvec[(jj * W + kk) * NL + l] = (1.f - be) * z0 + be * z1;
-    }
-  }
-  __syncthreads();
-  // ---- B: one thread per RE
-  for (int re = tid; re < nre; re += NT) {
-    const int jj = re / W, kk = re % W;
-    const int k = lo + kk;
-    const float be0 = seg_beta(g, j, k, 0), be1 = seg_beta(g, j, k, 1);
-    const cf* Yj = Ygg + jj * 3 * NL * NL;
-    auto getA = [&](int l, int m) -> cf {
-      if (l >= nl || m >= nl) return (l == m) ? mk(1.f, 0.f) : mk(0.f, 0.f);
-      const float bl = (l & 1) ? be1 : be0, bm = (m & 1) ? be1 : be0;
-      const float wl0 = 1.f - bl, wm0 = 1.f - bm;
-      const cf y00 = Yj[l * NL + m];
-      const cf y10 = Yj[NL * NL + l * NL + m];
-      const cf y10t = Yj[NL * NL + m * NL + l];  // Y01[l][m] = conj(Y10[m][l])
-      const cf y11 = Yj[2 * NL * NL + l * NL + m];
-      cf a;
-      a.x = wl0 * wm0 * y00.x + wl0 * bm * y10t.x + bl * wm0 * y10.x + bl * bm * y11.x;
-      a.y = wl0 * wm0 * y00.y - wl0 * bm * y10t.y + bl * wm0 * y10.y + bl * bm * y11.y;
-      if (l == m) {
-        a.x += s2;
-        a.y = 0.f;
-      }
-      return a;
-    };
-    cf b[NL], x[NL];
-    float dd[NL];
-    bool fin = true;
-#pragma unroll
-    for (int l = 0; l < NL; ++l) {
-      b[l] = (l < nl) ? bvec[re * NL + l] : mk(0.f, 0.f);
-      fin = fin && finite_cf(b[l]);
-    }
-    SolveInfo si;
-    if constexpr (NL == 16) {
-      SmemScratch scr{sm + f.off_scr + tid, NT};
-      si = solve16(getA, scr, b, x, dd);
-    } else {
-      si = solve_small<NL>(getA, b, x, dd);
-    }
-    fin = fin && si.fin;
-    uint8_t flag = 0;
-    const bool ok = si.ok && fin;
-    if (!fin) flag |= 4;
-    if (!si.ok || si.pmin < g.pivot_min * si.pmax) flag |= 1;
-    const size_t ridx = ((size_t)cell * nds + jj) * g.n_sc + k;
-    flags_out[ridx] = flag;
-#pragma unroll
-    for (int l = 0; l < NL; ++l) {
-      if (l < nl) {
-        const LayerOut o = layer_stats(s2, dd[l]);
-        const size_t li = ridx * nl + l;
-        if (ok) {
-          if (x_hat) st(x_hat + li, x[l]);
-          if (sinr_out) sinr_out[li] = o.sinr;
-          if (llr_out) {
-            const float im = 1.f / o.mu;
-            store_llr_rt(g.qm, llr_out + li * g.qm, im * x[l], o.s2eff);
-          }
-        } else {
-          if (x_hat) st(x_hat + li, mk(0.f, 0.f));
-          if (sinr_out) sinr_out[li] = 0.f;
-          if (llr_out)
-            for (int q = 0; q < g.qm; ++q) llr_out[li * g.qm + q] = 0.f;
-        }
-      }
+      const float be = seg_beta(g, j, lo + kk, l & 1);
+      bout[kk * NL + l] = (1.f - be) * z0 + be * z1;
     }
   }
 }
+
+struct LocalScratch {
+  cf* base;
+  __device__ __forceinline__ void st(int e, cf v) const { base[e] = v; }
+  __device__ __forceinline__ cf ld(int e) const { return base[e]; }
+};
+
+template <int QM>
+__device__ __forceinline__ void store_llr(float* dst, cf xt, float s2eff) {
+  float l[QM];
+  qam_llr<QM>(xt, s2eff, l);
+#pragma unroll
+  for (int q = 0; q < QM; q += 2) *reinterpret_cast<float2*>(dst + q) = make_float2(l[q], l[q + 1]);
+}
+
+template <int NL, int QM>
+__global__ void __launch_bounds__(kSolveThreads)
+    re_solve_fp32_kernel(Geo g, int cell0, int n_cells_chunk, const float4* __restrict__ ygg,
+                         const cf* __restrict__ bvec, const float* __restrict__ sigma2,
+                         phy_c32* __restrict__ x_hat, float* __restrict__ sinr_out,
+                         float* __restrict__ llr_out, uint8_t* __restrict__ flags_out) {
+  constexpr int NTRI = NL * (NL + 1) / 2;
+  const int nl = g.n_layers, nds = g.n_dsym;
+  const size_t n_re = (size_t)n_cells_chunk * nds * g.n_sc;
+  const size_t re = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (re >= n_re) return;
+  const int k = (int)(re % g.n_sc);
+  const int jj = (int)((re / g.n_sc) % nds);
+  const int lc = (int)(re / ((size_t)g.n_sc * nds));
+  const int cell = cell0 + lc;
+  const int j = seg_of(g, k);
+  const float s2 = sigma2[cell];
+  const float be0 = seg_beta(g, j, k, 0), be1 = seg_beta(g, j, k, 1);
+  const float4* yp = ygg + (((size_t)lc * g.n_seg + j) * nds + jj) * NTRI * 2;
+  auto getA = [&](int l, int m) -> cf {
+    if (l >= nl || m >= nl) return (l == m) ? mk(1.f, 0.f) : mk(0.f, 0.f);
+    const float bl = (l & 1) ? be1 : be0, bm = (m & 1) ? be1 : be0;
+    const float wl0 = 1.f - bl, wm0 = 1.f - bm;
+    const int e = tri(l, m);
+    const float4 p = __ldg(yp + 2 * e), q = __ldg(yp + 2 * e + 1);
+    const float c00 = wl0 * wm0, c01 = wl0 * bm, c10 = bl * wm0, c11 = bl * bm;
+    cf a;
+    a.x = fmaf(c00, p.x, fmaf(c01, p.z, fmaf(c10, q.x, c11 * q.z)));
+    a.y = fmaf(c00, p.y, fmaf(c01, p.w, fmaf(c10, q.y, c11 * q.w)));
+    if (l == m) {
+      a.x += s2;
+      a.y = 0.f;
+    }
+    return a;
+  };
+  cf b[NL], x[NL];
+  float dd[NL];
+  bool fin = true;
+  const float4* bp = reinterpret_cast<const float4*>(bvec + re * NL);
+#pragma unroll
+  for (int l = 0; l < NL; l += 2) {
+    const float4 v = __ldg(bp + l / 2);
+    b[l] = mk(v.x, v.y);
+    b[l + 1] = mk(v.z, v.w);
+  }
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    if (l >= nl) b[l] = mk(0.f, 0.f);
+    fin = fin && finite_cf(b[l]);
+  }
+  SolveInfo si;
+  if constexpr (NL == 16) {
+    cf scratch[kScrSlots];
+    si = solve16(getA, LocalScratch{scratch}, b, x, dd);
+  } else {
+    si = solve_small<NL>(getA, b, x, dd);
+  }
+  fin = fin && si.fin;
+  const bool ok = si.ok && fin;
+  uint8_t flag = 0;
+  if (!fin) flag |= 4;
+  if (!si.ok || si.pmin < g.pivot_min * si.pmax) flag |= 1;
+  const size_t ridx = ((size_t)cell * nds + jj) * g.n_sc + k;
+  flags_out[ridx] = flag;
+  // rolled on purpose: one copy of the per-layer epilogue keeps the kernel's code small
+#pragma unroll 1
+  for (int l = 0; l < nl; ++l) {
+    const LayerOut o = layer_stats(s2, dd[l]);
+    const size_t li = ridx * nl + l;
+    if (ok) {
+      if (x_hat) st(x_hat + li, x[l]);
+      if (sinr_out) sinr_out[li] = o.sinr;
+      if (llr_out) store_llr<QM>(llr_out + li * QM, (1.f / o.mu) * x[l], o.s2eff);
+    } else {
+      if (x_hat) st(x_hat + li, mk(0.f, 0.f));
+      if (sinr_out) sinr_out[li] = 0.f;
+      if (llr_out)
+        for (int q = 0; q < QM; ++q) llr_out[li * QM + q] = 0.f;
+    }
+  }
+}
+
+struct Sizes {
+  int NL, ntri;
+  size_t ygg_per_cell, b_per_cell;
+  int chunk;  // cells per chunk
+};
+
+Sizes sizes(const Geo& g) {
+  Sizes s;
+  s.NL = nl_class(g.n_layers);
+  s.ntri = s.NL * (s.NL + 1) / 2;
+  s.ygg_per_cell = (size_t)g.n_seg * g.n_dsym * s.ntri * 32;
+  s.b_per_cell = (size_t)g.n_dsym * g.n_sc * s.NL * 8;
+  const size_t per = s.ygg_per_cell + s.b_per_cell;
+  s.chunk = (int)std::max<size_t>(1, kChunkBudget / per);
+  s.chunk = std::min(s.chunk, g.n_cells);
+  return s;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 template <int NL>
-cudaError_t launch_fused(const Geo& g, int wmax, const phy_c32* anchors, const phy_c32* Y,
-                         const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
-                         uint8_t* flags, cudaStream_t st) {
-  constexpr int NT = FusedTraits<NL>::NT;
-  const FusedLayout f = fused_layout(NL, NT, g.n_dmrs, g.n_rx, g.n_dsym, wmax);
-  const size_t bytes = (size_t)f.total * sizeof(cf);
-  static size_t configured = 0;  // largest dynamic smem opted into so far
-  if (bytes > configured) {
-    cudaError_t e = cudaFuncSetAttribute(detect_fp32_kernel<NL>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+cudaError_t run_chunks(const Geo& g, int wmax, const Sizes& s, const phy_c32* anchors,
+                       const phy_c32* Y, const float* sigma2, phy_c32* x_hat, float* sinr,
+                       float* llr, uint8_t* flags, void* scratch, cudaStream_t st) {
+  const PrepLayout f = prep_layout(NL, g.n_dmrs, g.n_rx, wmax);
+  const size_t smem = (size_t)f.total * sizeof(cf);
+  static size_t configured = 0;
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(seg_prep_fp32_kernel<NL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    configured = bytes;
+    configured = smem;
   }
-  dim3 grid(g.n_seg, g.n_cells);
-  detect_fp32_kernel<NL><<<grid, NT, bytes, st>>>(g, wmax, anchors, Y, sigma2, x_hat, sinr, llr,
-                                                   flags);
+  float4* ygg = reinterpret_cast<float4*>(scratch);
+  cf* bvec = reinterpret_cast<cf*>(static_cast<char*>(scratch) + align256(s.ygg_per_cell * s.chunk));
+  for (int c0 = 0; c0 < g.n_cells; c0 += s.chunk) {
+    const int nc = std::min(s.chunk, g.n_cells - c0);
+    dim3 grid(g.n_seg, nc);
+    seg_prep_fp32_kernel<NL><<<grid, kPrepThreads, smem, st>>>(g, wmax, c0, anchors, Y, ygg, bvec);
+    const size_t n_re = (size_t)nc * g.n_dsym * g.n_sc;
+    const unsigned blocks = (unsigned)((n_re + kSolveThreads - 1) / kSolveThreads);
+    switch (g.qm) {
+      case 2:
+        re_solve_fp32_kernel<NL, 2><<<blocks, kSolveThreads, 0, st>>>(g, c0, nc, ygg, bvec, sigma2,
+                                                                     x_hat, sinr, llr, flags);
+        break;
+      case 4:
+        re_solve_fp32_kernel<NL, 4><<<blocks, kSolveThreads, 0, st>>>(g, c0, nc, ygg, bvec, sigma2,
+                                                                     x_hat, sinr, llr, flags);
+        break;
+      case 6:
+        re_solve_fp32_kernel<NL, 6><<<blocks, kSolveThreads, 0, st>>>(g, c0, nc, ygg, bvec, sigma2,
+                                                                     x_hat, sinr, llr, flags);
+        break;
+      default:
+        re_solve_fp32_kernel<NL, 8><<<blocks, kSolveThreads, 0, st>>>(g, c0, nc, ygg, bvec, sigma2,
+                                                                     x_hat, sinr, llr, flags);
+        break;
+    }
+  }
   return cudaGetLastError();
 }
-
-int nl_class(int nl) { return nl <= 2 ? 2 : nl <= 4 ? 4 : nl <= 8 ? 8 : 16; }
 
 }  // namespace
 
@@ -316,22 +403,30 @@ int host_max_segment_width(const Geo& g) {
 }
 
 size_t fused_fp32_smem_bytes(const Geo& g) {
-  const int NL = nl_class(g.n_layers);
-  const int NT = NL == 16 ? FusedTraits<16>::NT : FusedTraits<8>::NT;
-  const FusedLayout f =
-      fused_layout(NL, NT, g.n_dmrs, g.n_rx, g.n_dsym, host_max_segment_width(g));
+  const PrepLayout f =
+      prep_layout(nl_class(g.n_layers), g.n_dmrs, g.n_rx, host_max_segment_width(g));
   return (size_t)f.total * sizeof(cf);
+}
+
+size_t detect_fp32_scratch_bytes(const Geo& g) {
+  const Sizes s = sizes(g);
+  return align256(s.ygg_per_cell * s.chunk) + align256(s.b_per_cell * s.chunk);
 }
 
 cudaError_t launch_detect_fp32(const Geo& g, const phy_c32* anchors, const phy_c32* Y,
                                const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
-                               uint8_t* flags, cudaStream_t st) {
+                               uint8_t* flags, void* scratch, cudaStream_t st) {
   const int wmax = host_max_segment_width(g);
-  switch (nl_class(g.n_layers)) {
-    case 2: return launch_fused<2>(g, wmax, anchors, Y, sigma2, x_hat, sinr, llr, flags, st);
-    case 4: return launch_fused<4>(g, wmax, anchors, Y, sigma2, x_hat, sinr, llr, flags, st);
-    case 8: return launch_fused<8>(g, wmax, anchors, Y, sigma2, x_hat, sinr, llr, flags, st);
-    default: return launch_fused<16>(g, wmax, anchors, Y, sigma2, x_hat, sinr, llr, flags, st);
+  const Sizes s = sizes(g);
+  switch (s.NL) {
+    case 2:
+      return run_chunks<2>(g, wmax, s, anchors, Y, sigma2, x_hat, sinr, llr, flags, scratch, st);
+    case 4:
+      return run_chunks<4>(g, wmax, s, anchors, Y, sigma2, x_hat, sinr, llr, flags, scratch, st);
+    case 8:
+      return run_chunks<8>(g, wmax, s, anchors, Y, sigma2, x_hat, sinr, llr, flags, scratch, st);
+    default:
+      return run_chunks<16>(g, wmax, s, anchors, Y, sigma2, x_hat, sinr, llr, flags, scratch, st);
   }
 }
 

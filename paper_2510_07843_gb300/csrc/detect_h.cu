@@ -11,8 +11,8 @@ namespace {
 
 struct LocalScratch {
   cf* base;
-  __device__ __forceinline__ void st(int i, int j, cf v) const { base[i * 8 + j] = v; }
-  __device__ __forceinline__ cf ld(int i, int j) const { return base[i * 8 + j]; }
+  __device__ __forceinline__ void st(int e, cf v) const { base[e] = v; }
+  __device__ __forceinline__ cf ld(int e) const { return base[e]; }
 };
 
 template <int NL>
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(128) detect_h_kernel(Geo g, const phy_c32* __r
   float dd[NL];
   SolveInfo si;
   if constexpr (NL == 16) {
-    cf scratch[64];
+    cf scratch[kScrSlots];
     si = solve16(getA, LocalScratch{scratch}, b, x, dd);
   } else {
     si = solve_small<NL>(getA, b, x, dd);

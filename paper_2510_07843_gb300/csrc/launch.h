@@ -9,15 +9,17 @@ namespace phy {
 
 // Widest frequency segment (subcarriers) for g, computed on the host.
 int host_max_segment_width(const Geo& g);
-// Dynamic shared memory of the fused FP32 kernel for g (bytes), 0 if unsupported.
+// Dynamic shared memory of the FP32 segment kernel for g (bytes).
 size_t fused_fp32_smem_bytes(const Geo& g);
+// Workspace bytes the FP32 detector needs for its per-chunk intermediates.
+size_t detect_fp32_scratch_bytes(const Geo& g);
 
 cudaError_t launch_chest(const Geo& g, const phy_c32* Y, const phy_c32* pilots, phy_c32* anchors,
                          cudaStream_t st);
 
 cudaError_t launch_detect_fp32(const Geo& g, const phy_c32* anchors, const phy_c32* Y,
                                const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
-                               uint8_t* flags, cudaStream_t st);
+                               uint8_t* flags, void* scratch, cudaStream_t st);
 
 cudaError_t launch_detect_h(const Geo& g, const phy_c32* H, const phy_c32* Y, const float* sigma2,
                             phy_c32* x_hat, float* sinr, uint8_t* flags, cudaStream_t st);

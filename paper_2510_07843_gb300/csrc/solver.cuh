@@ -143,44 +143,57 @@ __device__ __forceinline__ SolveInfo solve_small(GetA getA, const cf (&b)[N], cf
   return si;
 }
 
-// 9..16 layers: two 8x8 blocks; Scr provides ld(i, j) / st(i, j, v) for the 8x8 block L21.
+// 9..16 layers: two 8x8 blocks. Scr is a thread-private scratch of kScrSlots complex values
+// (ld(e) / st(e, v)) holding M, L21 and a few vectors. The large repeated pieces (the rows of
+// L21, the Schur update, the columns of the block-1 inverse diagonal) are runtime loops over
+// small unrolled bodies, which keeps the kernel's code small enough for the instruction cache,
+// and M leaves the registers once L21 is formed.
+constexpr int kScrL21 = 0, kScrM = 64, kScrV = 100, kScrD = 108, kScrSlots = 116;
+
 template <class GetA, class Scr>
 __device__ __forceinline__ SolveInfo solve16(GetA getA, Scr scr, const cf (&b)[16], cf (&x)[16],
                                              float (&d)[16]) {
   constexpr int B = 8;
   SolveInfo si{true, true, 3.0e38f, 0.f};
-  // ---- block 1: L11, z1 = L11^-1 b1, M = L11^-1
-  cf m[B * (B + 1) / 2];
+  cf z1[B];
+  {
+    // ---- block 1: L11, z1 = L11^-1 b1, M = L11^-1
+    cf m[B * (B + 1) / 2];
 #pragma unroll
-  for (int i = 0; i < B; ++i)
+    for (int i = 0; i < B; ++i)
 #pragma unroll
-    for (int j = 0; j <= i; ++j) m[tri(i, j)] = getA(i, j);
-  float r1[B];
-  si.ok = chol_packed<B>(m, r1, si.pmin, si.pmax, si.fin);
-  cf b1[B], z1[B];
+      for (int j = 0; j <= i; ++j) m[tri(i, j)] = getA(i, j);
+    float r1[B];
+    si.ok = chol_packed<B>(m, r1, si.pmin, si.pmax, si.fin);
+    cf b1[B];
 #pragma unroll
-  for (int i = 0; i < B; ++i) b1[i] = b[i];
-  fwd_packed<B>(m, r1, b1, z1);
-  inv_packed<B>(m, r1);
-  // M as a full lower triangle accessor: (i, j) with j <= i
-  auto M = [&](int i, int j) -> cf { return (i == j) ? mk(r1[i], 0.f) : m[tri(i, j)]; };
-  // ---- L21 = A21 M^H row by row; v = b2 - L21 z1
-  cf v[B];
+    for (int i = 0; i < B; ++i) b1[i] = b[i];
+    fwd_packed<B>(m, r1, b1, z1);
+    inv_packed<B>(m, r1);
+    auto M = [&](int i, int j) -> cf { return (i == j) ? mk(r1[i], 0.f) : m[tri(i, j)]; };
 #pragma unroll
-  for (int i = 0; i < B; ++i) {
-    cf row[B];
+    for (int i = 0; i < B; ++i) {
 #pragma unroll
-    for (int k = 0; k < B; ++k) row[k] = getA(B + i, k);
-    cf acc = b[B + i];
-#pragma unroll
-    for (int j = 0; j < B; ++j) {
-      cf l = mk(0.f, 0.f);
-#pragma unroll
-      for (int k = 0; k <= j; ++k) l = cfma_cj(M(j, k), row[k], l);  // row[k] conj(M[j][k])
-      scr.st(i, j, l);
-      acc = cfms(l, z1[j], acc);
+      for (int j = 0; j <= i; ++j) scr.st(kScrM + tri(i, j), M(i, j));
+      scr.st(kScrV + i, b[B + i]);
     }
-    v[i] = acc;
+    // ---- L21 = A21 M^H row by row; v = b2 - L21 z1
+#pragma unroll 1
+    for (int i = 0; i < B; ++i) {
+      cf row[B];
+#pragma unroll
+      for (int k = 0; k < B; ++k) row[k] = getA(B + i, k);
+      cf acc = scr.ld(kScrV + i);
+#pragma unroll
+      for (int j = 0; j < B; ++j) {
+        cf l = mk(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k <= j; ++k) l = cfma_cj(M(j, k), row[k], l);  // row[k] conj(M[j][k])
+        scr.st(kScrL21 + i * B + j, l);
+        acc = cfms(l, z1[j], acc);
+      }
+      scr.st(kScrV + i, acc);
+    }
   }
   // ---- S = A22 - L21 L21^H
   cf s[B * (B + 1) / 2];
@@ -188,11 +201,11 @@ __device__ __forceinline__ SolveInfo solve16(GetA getA, Scr scr, const cf (&b)[1
   for (int i = 0; i < B; ++i)
 #pragma unroll
     for (int j = 0; j <= i; ++j) s[tri(i, j)] = getA(B + i, B + j);
-#pragma unroll
+#pragma unroll 1
   for (int c = 0; c < B; ++c) {
     cf col[B];
 #pragma unroll
-    for (int i = 0; i < B; ++i) col[i] = scr.ld(i, c);
+    for (int i = 0; i < B; ++i) col[i] = scr.ld(kScrL21 + i * B + c);
 #pragma unroll
     for (int i = 0; i < B; ++i)
 #pragma unroll
@@ -200,7 +213,9 @@ __device__ __forceinline__ SolveInfo solve16(GetA getA, Scr scr, const cf (&b)[1
   }
   float r2[B];
   si.ok = chol_packed<B>(s, r2, si.pmin, si.pmax, si.fin) && si.ok;
-  cf z2[B], x2[B];
+  cf v[B], z2[B], x2[B];
+#pragma unroll
+  for (int i = 0; i < B; ++i) v[i] = scr.ld(kScrV + i);
   fwd_packed<B>(s, r2, v, z2);
   bwd_packed<B>(s, r2, z2, x2);
   inv_packed<B>(s, r2);
@@ -214,7 +229,7 @@ __device__ __forceinline__ SolveInfo solve16(GetA getA, Scr scr, const cf (&b)[1
 #pragma unroll
     for (int j = 0; j < B; ++j) {
       // u_j -= conj(L21_ij) x2_i
-      const cf l = scr.ld(i, j);
+      const cf l = scr.ld(kScrL21 + i * B + j);
       u[j].x = fmaf(-l.x, x2[i].x, u[j].x);
       u[j].x = fmaf(-l.y, x2[i].y, u[j].x);
       u[j].y = fmaf(-l.x, x2[i].y, u[j].y);
@@ -225,7 +240,7 @@ __device__ __forceinline__ SolveInfo solve16(GetA getA, Scr scr, const cf (&b)[1
   for (int i = 0; i < B; ++i) {
     cf acc = mk(0.f, 0.f);
 #pragma unroll
-    for (int k = i; k < B; ++k) acc = cfma_cj(M(k, i), u[k], acc);
+    for (int k = i; k < B; ++k) acc = cfma_cj(scr.ld(kScrM + tri(k, i)), u[k], acc);
     x[i] = acc;
     x[B + i] = x2[i];
   }
@@ -237,30 +252,30 @@ __device__ __forceinline__ SolveInfo solve16(GetA getA, Scr scr, const cf (&b)[1
     for (int i = c; i < B; ++i) s2 += cabs2(Nn(i, c));
     d[B + c] = s2;
   }
-#pragma unroll
+#pragma unroll 1
   for (int c = 0; c < B; ++c) {
     float s1 = 0.f;
+    cf w[B];  // w = L21 M[:, c]
 #pragma unroll
-    for (int i = c; i < B; ++i) s1 += cabs2(M(i, c));
-    // w = L21 M[:, c]
-    cf w[B];
+    for (int i = 0; i < B; ++i) w[i] = mk(0.f, 0.f);
+#pragma unroll 1
+    for (int mm = c; mm < B; ++mm) {
+      const cf mc = scr.ld(kScrM + tri(mm, c));
+      s1 += cabs2(mc);
 #pragma unroll
-    for (int i = 0; i < B; ++i) {
-      cf acc = mk(0.f, 0.f);
-#pragma unroll
-      for (int mm = c; mm < B; ++mm) acc = cfma(scr.ld(i, mm), M(mm, c), acc);
-      w[i] = acc;
+      for (int i = 0; i < B; ++i) w[i] = cfma(scr.ld(kScrL21 + i * B + mm), mc, w[i]);
     }
-    // p = N w, add |p|^2
 #pragma unroll
-    for (int i = 0; i < B; ++i) {
+    for (int i = 0; i < B; ++i) {  // p = N w, add |p|^2
       cf acc = mk(0.f, 0.f);
 #pragma unroll
       for (int k = 0; k <= i; ++k) acc = cfma(Nn(i, k), w[k], acc);
       s1 += cabs2(acc);
     }
-    d[c] = s1;
+    scr.st(kScrD + c, mk(s1, 0.f));
   }
+#pragma unroll
+  for (int c = 0; c < B; ++c) d[c] = scr.ld(kScrD + c).x;
   return si;
 }
 

@@ -38,7 +38,7 @@ _SIGS = {
     "phy_workspace_size": (ctypes.c_size_t, [_P]),
     "phy_chest": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "phy_mmse_detect": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
-    "phy_detect_anchors": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "phy_detect_anchors": (ctypes.c_int, [_P] * 9 + [ctypes.c_size_t, _P]),
     "phy_llr_demap": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "phy_slot_run": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "phy_slot_run_host": (ctypes.c_int, [_P] * 14 + [ctypes.c_size_t, _P]),
@@ -46,7 +46,7 @@ _SIGS = {
 }
 
 # Bytes of the fixed scratch array behind phy_slot_run_noalloc (PHY_NOALLOC_SCRATCH_BYTES).
-NOALLOC_SCRATCH_BYTES = 32 << 20
+NOALLOC_SCRATCH_BYTES = 64 << 20
 
 _lib = None
 
@@ -145,12 +145,14 @@ def mmse_detect(cfg: SlotConfig, H, Y, sigma2, x_hat, sinr, flags, stream=None):
                                   _ptr(sinr), _ptr(flags), _stream(stream)))
 
 
-def detect_anchors(cfg: SlotConfig, anchors, Y, sigma2, x_hat, sinr, llr, flags, stream=None):
+def detect_anchors(cfg: SlotConfig, anchors, Y, sigma2, x_hat, sinr, llr, flags, workspace,
+                   stream=None):
     c = cfg.c()
+    ws_bytes = workspace.numel() * workspace.element_size()
     _check("phy_detect_anchors",
            load().phy_detect_anchors(ctypes.byref(c), _ptr(anchors), _ptr(Y), _ptr(sigma2),
                                      _ptr(x_hat), _ptr(sinr), _ptr(llr), _ptr(flags),
-                                     _stream(stream)))
+                                     _ptr(workspace), ws_bytes, _stream(stream)))
 
 
 def llr_demap(cfg: SlotConfig, x_hat, sinr, llr, stream=None):
