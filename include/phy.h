@@ -13,7 +13,7 @@
  * Conventions for every entry point:
  *  - All array arguments are DEVICE pointers owned by the caller, except where a name ends in
  *    _host. The library never allocates device memory; scratch space is a caller-provided
- *    workspace of phy_workspace_size() bytes (256-byte aligned).
+ *    workspace of phy_workspace_size() bytes (256-byte aligned). Y must be 16-byte aligned.
  *  - Work is enqueued on `stream` (a cudaStream_t passed as void*, NULL = legacy default stream)
  *    and the call returns without synchronising. Results are valid once the stream reaches
  *    the point after the call.
@@ -88,7 +88,7 @@ typedef struct {
   int32_t qm;             /* bits per QAM symbol: 2, 4, 6 or 8 */
   int32_t n_dmrs;         /* DMRS symbols, 1 or 2 */
   int32_t dmrs_sym[2];    /* their indices, increasing */
-  int32_t occ_len;        /* Walsh cover length L (power of two) or 0 for automatic */
+  int32_t occ_len;        /* Walsh cover length L (power of two, <= 16) or 0 for automatic */
   int32_t precision;      /* phy_precision */
   float pivot_ratio_min;  /* flag bit 0 threshold on min L_kk^2 / max L_kk^2, e.g. 1e-6 */
   int32_t fp64_refactor;  /* 1: re-compute flagged REs in FP64 (sets flag bit 1) */

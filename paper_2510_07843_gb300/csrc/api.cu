@@ -38,7 +38,7 @@ phy_status make_geo(const phy_slot_cfg* c, Geo* g) {
   if (!(c->pivot_ratio_min >= 0.f) || c->pivot_ratio_min > 1.f) return PHY_ERR_INVALID_ARG;
   const int need = auto_occ(c->n_layers);
   const int L = c->occ_len == 0 ? need : c->occ_len;
-  if (!pow2(L) || L < need || L > 64) return PHY_ERR_INVALID_ARG;
+  if (!pow2(L) || L < need || L > 16) return PHY_ERR_INVALID_ARG;
   const int n_sc = 12 * c->n_prb;
   const int n_comb = n_sc / 2;
   if (n_comb < L) return PHY_ERR_INVALID_ARG;
@@ -128,7 +128,7 @@ phy_status phy_chest(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32* p
   Geo g;
   phy_status s = make_geo(cfg, &g);
   if (s != PHY_OK) return s;
-  if (!Y || !pilots || !anchors) return PHY_ERR_INVALID_ARG;
+  if (!Y || !pilots || !anchors || ((uintptr_t)Y % 16)) return PHY_ERR_INVALID_ARG;
   return cuda_status(phy::launch_chest(g, Y, pilots, anchors, (cudaStream_t)stream));
 }
 
@@ -175,7 +175,8 @@ phy_status phy_slot_run(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32
   Geo g;
   phy_status s = make_geo(cfg, &g);
   if (s != PHY_OK) return s;
-  if (!Y || !pilots || !sigma2 || !flags || !workspace) return PHY_ERR_INVALID_ARG;
+  if (!Y || !pilots || !sigma2 || !flags || !workspace || ((uintptr_t)Y % 16))
+    return PHY_ERR_INVALID_ARG;
   if (((uintptr_t)workspace) % kAlign) return PHY_ERR_INVALID_ARG;
   if (workspace_bytes < phy_workspace_size(cfg)) return PHY_ERR_NO_MEMORY;
   s = check_precision(cfg, g);

@@ -1,43 +1,78 @@
 // DMRS least-squares channel estimation (the channel-estimation block named in Sec. III-B).
 //
-// One CTA per (LS group, DMRS symbol, cell); one thread per receive antenna. Each thread reads
-// the 2L subcarriers of its group on its antenna row of Y (one contiguous 16L-byte run) and, for
-// every layer, despreads the pilots of that layer's comb:
-//   anchor[cell][d][g][l][r] = (1/L) sum_{i<L} Y[cell][t_d][r][k_i] conj(P[cell][d][l][k_i]),
-//   k_i = 2 (s_g + i) + (l % 2).
-// Writes are coalesced over r. The pilots of a group are shared by all antennas (L1 broadcast).
+// anchor[cell][d][g][l][r] = (1/L) sum_{i<L} Y[cell][t_d][r][k_i] conj(P[cell][d][l][k_i]),
+// k_i = 2 (s_g + i) + (l % 2).
+//
+// One CTA per (group, DMRS symbol, cell), one thread per receive antenna. The group's 2L
+// subcarriers are one contiguous 16L-byte run of each antenna row of Y: each thread loads its
+// run once with 16-byte loads into registers; the pilots of the group (all layers) are staged in
+// shared memory once per CTA and read as broadcasts. Writes are coalesced over r.
 #include "launch.h"
 
 namespace phy {
 
-__global__ void __launch_bounds__(64) chest_ls_kernel(Geo g, const phy_c32* __restrict__ Y,
-                                                      const phy_c32* __restrict__ P,
-                                                      phy_c32* __restrict__ anchors) {
+namespace {
+
+constexpr int kChestThreads = 64;
+
+template <int L>
+__global__ void __launch_bounds__(kChestThreads)
+    chest_ls_kernel(Geo g, const phy_c32* __restrict__ Y, const phy_c32* __restrict__ P,
+                    phy_c32* __restrict__ anchors) {
+  __shared__ cf pil[kMaxLayers][2 * L];
   const int grp = blockIdx.x, d = blockIdx.y, cell = blockIdx.z;
   const int r = threadIdx.x;
-  if (r >= g.n_rx) return;
   const int t = (d == 0) ? g.dmrs0 : g.dmrs1;
   const int s = group_start(g, grp);
-  const phy_c32* yrow = Y + ((size_t)(cell * g.n_sym + t) * g.n_rx + r) * g.n_sc;
-  const phy_c32* prow = P + (size_t)(cell * g.n_dmrs + d) * g.n_layers * g.n_sc;
-  phy_c32* out = anchors + (((size_t)(cell * g.n_dmrs + d) * g.G + grp) * g.n_layers) * g.n_rx;
-  const float inv_l = 1.f / (float)g.L;
-  for (int l = 0; l < g.n_layers; ++l) {
+  const int k0 = 2 * s;  // first subcarrier of the group's run
+  const int nl = g.n_layers;
+  const phy_c32* prow = P + (size_t)(cell * g.n_dmrs + d) * nl * g.n_sc + k0;
+  for (int e = threadIdx.x; e < nl * 2 * L; e += blockDim.x) {
+    const int l = e / (2 * L), i = e % (2 * L);
+    pil[l][i] = ld(prow + (size_t)l * g.n_sc + i);
+  }
+  __syncthreads();
+  if (r >= g.n_rx) return;
+  const phy_c32* yrow = Y + ((size_t)(cell * g.n_sym + t) * g.n_rx + r) * g.n_sc + k0;
+  cf y[2 * L];
+  if constexpr (L >= 2) {
+    // k0 is even, so the run starts on a 16-byte boundary
+    const float4* y4 = reinterpret_cast<const float4*>(yrow);
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+      const float4 v = __ldg(y4 + i);
+      y[2 * i] = mk(v.x, v.y);
+      y[2 * i + 1] = mk(v.z, v.w);
+    }
+  } else {
+    y[0] = ld(yrow);
+    y[1] = ld(yrow + 1);
+  }
+  phy_c32* out = anchors + (((size_t)(cell * g.n_dmrs + d) * g.G + grp) * nl) * g.n_rx;
+  const float inv_l = 1.f / (float)L;
+  for (int l = 0; l < nl; ++l) {
     const int c = l & 1;
     cf acc = mk(0.f, 0.f);
-    for (int i = 0; i < g.L; ++i) {
-      const int k = 2 * (s + i) + c;
-      acc = cfma_cj(ld(prow + (size_t)l * g.n_sc + k), ld(yrow + k), acc);  // y conj(p)
-    }
+#pragma unroll
+    for (int i = 0; i < L; ++i) acc = cfma_cj(pil[l][2 * i + c], y[2 * i + c], acc);  // y conj(p)
     st(out + (size_t)l * g.n_rx + r, inv_l * acc);
   }
 }
 
+}  // namespace
+
 cudaError_t launch_chest(const Geo& g, const phy_c32* Y, const phy_c32* pilots, phy_c32* anchors,
                          cudaStream_t st) {
   dim3 grid(g.G, g.n_dmrs, g.n_cells);
-  int threads = g.n_rx <= 32 ? 32 : 64;
-  chest_ls_kernel<<<grid, threads, 0, st>>>(g, Y, pilots, anchors);
+  const int threads = g.n_rx <= 32 ? 32 : 64;
+  switch (g.L) {
+    case 1: chest_ls_kernel<1><<<grid, threads, 0, st>>>(g, Y, pilots, anchors); break;
+    case 2: chest_ls_kernel<2><<<grid, threads, 0, st>>>(g, Y, pilots, anchors); break;
+    case 4: chest_ls_kernel<4><<<grid, threads, 0, st>>>(g, Y, pilots, anchors); break;
+    case 8: chest_ls_kernel<8><<<grid, threads, 0, st>>>(g, Y, pilots, anchors); break;
+    case 16: chest_ls_kernel<16><<<grid, threads, 0, st>>>(g, Y, pilots, anchors); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

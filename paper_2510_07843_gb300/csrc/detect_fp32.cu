@@ -228,11 +228,16 @@ __global__ void __launch_bounds__(kPrepThreads)
   }
 }
 
-struct LocalScratch {
-  cf* base;
-  __device__ __forceinline__ void st(int e, cf v) const { base[e] = v; }
-  __device__ __forceinline__ cf ld(int e) const { return base[e]; }
+// Thread-private scratch in shared memory, interleaved by thread (conflict-free).
+struct SmemScratch {
+  cf* base;  // this thread's slot 0
+  __device__ __forceinline__ void st(int e, cf v) const { base[e * kSolveThreads] = v; }
+  __device__ __forceinline__ cf ld(int e) const { return base[e * kSolveThreads]; }
 };
+
+constexpr size_t solve_smem_bytes(int NL) {
+  return NL == 16 ? (size_t)kScrSlots * kSolveThreads * sizeof(cf) : 0;
+}
 
 template <int QM>
 __device__ __forceinline__ void store_llr(float* dst, cf xt, float s2eff) {
@@ -294,8 +299,8 @@ __global__ void __launch_bounds__(kSolveThreads)
   }
   SolveInfo si;
   if constexpr (NL == 16) {
-    cf scratch[kScrSlots];
-    si = solve16(getA, LocalScratch{scratch}, b, x, dd);
+    extern __shared__ __align__(16) unsigned char solve_smem[];
+    si = solve16(getA, SmemScratch{reinterpret_cast<cf*>(solve_smem) + threadIdx.x}, b, x, dd);
   } else {
     si = solve_small<NL>(getA, b, x, dd);
   }
@@ -344,6 +349,23 @@ Sizes sizes(const Geo& g) {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+template <int NL, int QM>
+cudaError_t launch_solve(unsigned blocks, const Geo& g, int c0, int nc, const float4* ygg,
+                         const cf* bvec, const float* sigma2, phy_c32* x_hat, float* sinr,
+                         float* llr, uint8_t* flags, cudaStream_t st) {
+  constexpr size_t smem = solve_smem_bytes(NL);
+  static bool configured = false;
+  if (smem > 48 * 1024 && !configured) {
+    cudaError_t e = cudaFuncSetAttribute(re_solve_fp32_kernel<NL, QM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  re_solve_fp32_kernel<NL, QM><<<blocks, kSolveThreads, smem, st>>>(g, c0, nc, ygg, bvec, sigma2,
+                                                                   x_hat, sinr, llr, flags);
+  return cudaGetLastError();
+}
+
 template <int NL>
 cudaError_t run_chunks(const Geo& g, int wmax, const Sizes& s, const phy_c32* anchors,
                        const phy_c32* Y, const float* sigma2, phy_c32* x_hat, float* sinr,
@@ -365,24 +387,14 @@ cudaError_t run_chunks(const Geo& g, int wmax, const Sizes& s, const phy_c32* an
     seg_prep_fp32_kernel<NL><<<grid, kPrepThreads, smem, st>>>(g, wmax, c0, anchors, Y, ygg, bvec);
     const size_t n_re = (size_t)nc * g.n_dsym * g.n_sc;
     const unsigned blocks = (unsigned)((n_re + kSolveThreads - 1) / kSolveThreads);
+    cudaError_t e;
     switch (g.qm) {
-      case 2:
-        re_solve_fp32_kernel<NL, 2><<<blocks, kSolveThreads, 0, st>>>(g, c0, nc, ygg, bvec, sigma2,
-                                                                     x_hat, sinr, llr, flags);
-        break;
-      case 4:
-        re_solve_fp32_kernel<NL, 4><<<blocks, kSolveThreads, 0, st>>>(g, c0, nc, ygg, bvec, sigma2,
-                                                                     x_hat, sinr, llr, flags);
-        break;
-      case 6:
-        re_solve_fp32_kernel<NL, 6><<<blocks, kSolveThreads, 0, st>>>(g, c0, nc, ygg, bvec, sigma2,
-                                                                     x_hat, sinr, llr, flags);
-        break;
-      default:
-        re_solve_fp32_kernel<NL, 8><<<blocks, kSolveThreads, 0, st>>>(g, c0, nc, ygg, bvec, sigma2,
-                                                                     x_hat, sinr, llr, flags);
-        break;
+      case 2: e = launch_solve<NL, 2>(blocks, g, c0, nc, ygg, bvec, sigma2, x_hat, sinr, llr, flags, st); break;
+      case 4: e = launch_solve<NL, 4>(blocks, g, c0, nc, ygg, bvec, sigma2, x_hat, sinr, llr, flags, st); break;
+      case 6: e = launch_solve<NL, 6>(blocks, g, c0, nc, ygg, bvec, sigma2, x_hat, sinr, llr, flags, st); break;
+      default: e = launch_solve<NL, 8>(blocks, g, c0, nc, ygg, bvec, sigma2, x_hat, sinr, llr, flags, st); break;
     }
+    if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }

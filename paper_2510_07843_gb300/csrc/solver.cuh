@@ -12,8 +12,7 @@
 //   L11 = chol(A11), M = L11^-1, L21 = A21 M^H, S = A22 - L21 L21^H, L22 = chol(S), N = L22^-1,
 //   L^-1 = [M 0; -N L21 M  N],
 // so z = L^-1 b = [M b1; N (b2 - L21 z1)], x = L^-H z = [M^H (z1 - L21^H x2); N^H z2], and the
-// column norms of L^-1 give d. M, S/N and the vectors stay in registers; L21 goes to a
-// thread-private scratch (shared memory in the fused kernel).
+// column norms of L^-1 give d: block 2 from N, block 1 from M and N T with T = L21 M.
 #pragma once
 
 #include "common.cuh"
@@ -24,7 +23,7 @@ __device__ __forceinline__ constexpr int tri(int i, int j) { return i * (i + 1) 
 
 // Cholesky in place on a packed lower triangle (left-looking). rinv[j] = 1 / L_jj; the diagonal
 // entries of `a` are left holding the pivots L_jj^2. Returns false on a non-positive or
-// non-finite pivot.
+// non-finite pivot; fin turns false on a non-finite one.
 template <int N>
 __device__ __forceinline__ bool chol_packed(cf (&a)[N * (N + 1) / 2], float (&rinv)[N],
                                             float& pmin, float& pmax, bool& fin) {
@@ -85,10 +84,9 @@ __device__ __forceinline__ void bwd_packed(const cf (&a)[N * (N + 1) / 2], const
   }
 }
 
-// Overwrite the strictly-lower part of the factor with that of L^-1 and return its diagonal in
-// rinv (unchanged: (L^-1)_jj = 1/L_jj). Columns left to right, rows top to bottom: entry (i, c)
-// of the inverse needs row i of L at columns >= c (still intact) and rows < i of the inverse's
-// column c (already written).
+// Overwrite the strictly-lower part of the factor with that of L^-1; its diagonal is rinv.
+// Columns left to right, rows top to bottom: entry (i, c) of the inverse needs row i of L at
+// columns >= c (still intact) and rows < i of the inverse's column c (already written).
 template <int N>
 __device__ __forceinline__ void inv_packed(cf (&a)[N * (N + 1) / 2], const float (&rinv)[N]) {
 #pragma unroll
@@ -144,56 +142,50 @@ __device__ __forceinline__ SolveInfo solve_small(GetA getA, const cf (&b)[N], cf
 }
 
 // 9..16 layers: two 8x8 blocks. Scr is a thread-private scratch of kScrSlots complex values
-// (ld(e) / st(e, v)) holding M, L21 and a few vectors. The large repeated pieces (the rows of
-// L21, the Schur update, the columns of the block-1 inverse diagonal) are runtime loops over
-// small unrolled bodies, which keeps the kernel's code small enough for the instruction cache,
-// and M leaves the registers once L21 is formed.
-constexpr int kScrL21 = 0, kScrM = 64, kScrV = 100, kScrD = 108, kScrSlots = 116;
+// (ld(e) / st(e, v)) holding L21 (later overwritten by T = L21 M) and two 8-vectors. M and the
+// Schur factor stay in registers. The large repeated pieces (rows of L21 and T, the Schur
+// update, the columns of N T) are runtime loops over small unrolled bodies: the kernel's code
+// then fits the instruction cache, which the fully unrolled form did not.
+constexpr int kScrL21 = 0, kScrV = 64, kScrD = 72, kScrSlots = 80;
 
 template <class GetA, class Scr>
 __device__ __forceinline__ SolveInfo solve16(GetA getA, Scr scr, const cf (&b)[16], cf (&x)[16],
                                              float (&d)[16]) {
   constexpr int B = 8;
   SolveInfo si{true, true, 3.0e38f, 0.f};
-  cf z1[B];
-  {
-    // ---- block 1: L11, z1 = L11^-1 b1, M = L11^-1
-    cf m[B * (B + 1) / 2];
+  // ---- block 1: L11, z1 = L11^-1 b1, M = L11^-1
+  cf m[B * (B + 1) / 2];
 #pragma unroll
-    for (int i = 0; i < B; ++i)
+  for (int i = 0; i < B; ++i)
 #pragma unroll
-      for (int j = 0; j <= i; ++j) m[tri(i, j)] = getA(i, j);
-    float r1[B];
-    si.ok = chol_packed<B>(m, r1, si.pmin, si.pmax, si.fin);
-    cf b1[B];
+    for (int j = 0; j <= i; ++j) m[tri(i, j)] = getA(i, j);
+  float r1[B];
+  si.ok = chol_packed<B>(m, r1, si.pmin, si.pmax, si.fin);
+  cf b1[B], z1[B];
 #pragma unroll
-    for (int i = 0; i < B; ++i) b1[i] = b[i];
-    fwd_packed<B>(m, r1, b1, z1);
-    inv_packed<B>(m, r1);
-    auto M = [&](int i, int j) -> cf { return (i == j) ? mk(r1[i], 0.f) : m[tri(i, j)]; };
-#pragma unroll
-    for (int i = 0; i < B; ++i) {
-#pragma unroll
-      for (int j = 0; j <= i; ++j) scr.st(kScrM + tri(i, j), M(i, j));
-      scr.st(kScrV + i, b[B + i]);
-    }
-    // ---- L21 = A21 M^H row by row; v = b2 - L21 z1
+  for (int i = 0; i < B; ++i) {
+    b1[i] = b[i];
+    scr.st(kScrV + i, b[B + i]);
+  }
+  fwd_packed<B>(m, r1, b1, z1);
+  inv_packed<B>(m, r1);
+  auto M = [&](int i, int j) -> cf { return (i == j) ? mk(r1[i], 0.f) : m[tri(i, j)]; };
+  // ---- L21 = A21 M^H row by row; v = b2 - L21 z1
 #pragma unroll 1
-    for (int i = 0; i < B; ++i) {
-      cf row[B];
+  for (int i = 0; i < B; ++i) {
+    cf row[B];
 #pragma unroll
-      for (int k = 0; k < B; ++k) row[k] = getA(B + i, k);
-      cf acc = scr.ld(kScrV + i);
+    for (int k = 0; k < B; ++k) row[k] = getA(B + i, k);
+    cf acc = scr.ld(kScrV + i);
 #pragma unroll
-      for (int j = 0; j < B; ++j) {
-        cf l = mk(0.f, 0.f);
+    for (int j = 0; j < B; ++j) {
+      cf l = mk(0.f, 0.f);
 #pragma unroll
-        for (int k = 0; k <= j; ++k) l = cfma_cj(M(j, k), row[k], l);  // row[k] conj(M[j][k])
-        scr.st(kScrL21 + i * B + j, l);
-        acc = cfms(l, z1[j], acc);
-      }
-      scr.st(kScrV + i, acc);
+      for (int k = 0; k <= j; ++k) l = cfma_cj(M(j, k), row[k], l);  // row[k] conj(M[j][k])
+      scr.st(kScrL21 + i * B + j, l);
+      acc = cfms(l, z1[j], acc);
     }
+    scr.st(kScrV + i, acc);
   }
   // ---- S = A22 - L21 L21^H
   cf s[B * (B + 1) / 2];
@@ -240,42 +232,52 @@ __device__ __forceinline__ SolveInfo solve16(GetA getA, Scr scr, const cf (&b)[1
   for (int i = 0; i < B; ++i) {
     cf acc = mk(0.f, 0.f);
 #pragma unroll
-    for (int k = i; k < B; ++k) acc = cfma_cj(scr.ld(kScrM + tri(k, i)), u[k], acc);
+    for (int k = i; k < B; ++k) acc = cfma_cj(M(k, i), u[k], acc);
     x[i] = acc;
     x[B + i] = x2[i];
   }
-  // ---- diagonal of A^-1: block 2 from N, block 1 from M and N L21 M
+  // ---- diagonal of A^-1. Block 2: column norms of N. Block 1: column norms of M plus those
+  // of N T, T = L21 M (row i of T from row i of L21, written over it).
 #pragma unroll
   for (int c = 0; c < B; ++c) {
-    float s2 = 0.f;
+    float s2 = 0.f, s1 = r1[c] * r1[c];
 #pragma unroll
     for (int i = c; i < B; ++i) s2 += cabs2(Nn(i, c));
+#pragma unroll
+    for (int i = c + 1; i < B; ++i) s1 += cabs2(M(i, c));
     d[B + c] = s2;
+    d[c] = s1;
+  }
+#pragma unroll 1
+  for (int i = 0; i < B; ++i) {
+    cf row[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) row[k] = scr.ld(kScrL21 + i * B + k);
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+      cf acc = mk(0.f, 0.f);
+#pragma unroll
+      for (int k = c; k < B; ++k) acc = cfma(row[k], M(k, c), acc);
+      scr.st(kScrL21 + i * B + c, acc);
+    }
   }
 #pragma unroll 1
   for (int c = 0; c < B; ++c) {
-    float s1 = 0.f;
-    cf w[B];  // w = L21 M[:, c]
+    cf t[B];
 #pragma unroll
-    for (int i = 0; i < B; ++i) w[i] = mk(0.f, 0.f);
-#pragma unroll 1
-    for (int mm = c; mm < B; ++mm) {
-      const cf mc = scr.ld(kScrM + tri(mm, c));
-      s1 += cabs2(mc);
+    for (int i = 0; i < B; ++i) t[i] = scr.ld(kScrL21 + i * B + c);
+    float acc2 = 0.f;
 #pragma unroll
-      for (int i = 0; i < B; ++i) w[i] = cfma(scr.ld(kScrL21 + i * B + mm), mc, w[i]);
+    for (int i = 0; i < B; ++i) {  // (N t)_i
+      cf p = mk(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k <= i; ++k) p = cfma(Nn(i, k), t[k], p);
+      acc2 += cabs2(p);
     }
-#pragma unroll
-    for (int i = 0; i < B; ++i) {  // p = N w, add |p|^2
-      cf acc = mk(0.f, 0.f);
-#pragma unroll
-      for (int k = 0; k <= i; ++k) acc = cfma(Nn(i, k), w[k], acc);
-      s1 += cabs2(acc);
-    }
-    scr.st(kScrD + c, mk(s1, 0.f));
+    scr.st(kScrD + c, mk(acc2, 0.f));
   }
 #pragma unroll
-  for (int c = 0; c < B; ++c) d[c] = scr.ld(kScrD + c).x;
+  for (int c = 0; c < B; ++c) d[c] += scr.ld(kScrD + c).x;
   return si;
 }
 
