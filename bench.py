@@ -65,15 +65,28 @@ def algorithmic_bytes(spec: S.SlotSpec) -> dict:
                 step=y_data + y_dmrs + pilots + outs)
 
 
-def detect_flops(spec: S.SlotSpec) -> float:
+def detect_chunks(spec: S.SlotSpec) -> int:
+    """Chunks of cells the detection stage runs in (two kernel launches each): the library
+    sizes a chunk so its intermediates (Gram blocks and matched filter) stay within 32 MiB."""
+    nl = next(c for c in (2, 4, 8, 16) if spec.n_layers <= c)
+    n_comb = spec.n_sc // 2
+    n_seg = max(-(-n_comb // spec.occ) - 1, 1)
+    J = len(spec.data_sym)
+    per_cell = n_seg * J * nl * (nl + 1) // 2 * 32 + J * spec.n_sc * nl * 8
+    chunk = min(max(1, (32 << 20) // per_cell), spec.n_cells)
+    return -(-spec.n_cells // chunk)
+
+
+def detect_flops(spec: S.SlotSpec) -> dict:
     """Floating-point operations of the segment-factored LMMSE per launch (FMA = 2).
 
-    Counts what the method needs, not what the kernel issues: Hermitian halves only, no layer
-    padding. Per segment: corner cross-Gram X = C^H C (NX = 2 n_dmrs n_layers, Hermitian);
-    per segment and data symbol: the three time-folded blocks and H_g(t); per RE: two matched
-    filters against H_0(t), H_1(t), the frequency-weighted Gram, Cholesky (n^3/6 complex MACs),
-    forward and backward solves (n^2), the diagonal of the inverse (n^3/6 + n^2/2), SINR and the
-    max-log demapper (2^(qm/2) levels per axis).
+    Counts what the method needs, not what the kernels issue: Hermitian halves only, no layer
+    padding. 'products': per segment the corner cross-Gram X = C^H C (NX = 2 n_dmrs n_layers,
+    Hermitian) and per RE the matched filter (two n_rx x n_layers products against the
+    time-interpolated anchors); these run on the tensor cores in the TF32/FP16/BF16 variants.
+    'solve': per segment and data symbol the time folding of X, per RE the weighted Gram,
+    Cholesky (n^3/6 complex MACs), forward and backward solves (n^2), the inverse diagonal
+    (n^3/6 + n^2/2), SINR and the max-log demapper (H folds per axis).
     """
     nr, nl, qm = spec.n_rx, spec.n_layers, spec.qm
     nd = len(spec.dmrs_sym)
@@ -84,13 +97,14 @@ def detect_flops(spec: S.SlotSpec) -> float:
     J = len(spec.data_sym)
     cm = 8.0  # flops per complex multiply-add
     nx = 2 * nd * nl
-    per_seg = nx * (nx + 1) / 2 * nr * cm
-    per_seg_sym = (2 * nl * (nl + 1) / 2 + nl * nl) * (4 if nd == 2 else 1) * 4 + \
-        (2 * nl * nr * 6 if nd == 2 else 0)
-    per_re = (2 * nl * nr * cm + nl * 6 + nl * (nl + 1) / 2 * 4 * 6
+    n_re = n_data_res(spec)
+    products = spec.n_cells * n_seg * nx * (nx + 1) / 2 * nr * cm + n_re * 2 * nl * nr * cm
+    per_seg_sym = (2 * nl * (nl + 1) / 2 + nl * nl) * (4 if nd == 2 else 1) * 4
+    per_re = (nl * 6 + nl * (nl + 1) / 2 * 4 * 6
               + (nl ** 3 / 6) * cm + nl ** 2 * cm + (nl ** 3 / 6 + nl ** 2 / 2) * cm
-              + nl * 10 + nl * 2 * (2 ** (qm // 2)) * 3)
-    return spec.n_cells * (n_seg * per_seg + n_seg * J * per_seg_sym) + n_data_res(spec) * per_re
+              + nl * 10 + nl * 2 * (qm // 2) * 8)
+    solve = spec.n_cells * n_seg * J * per_seg_sym + n_re * per_re
+    return {"products": products, "solve": solve}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -211,7 +225,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="massive", choices=["massive", "carrier", "small"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "fp16", "bf16"])
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle timing")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -374,8 +388,11 @@ def run_ours(args, spec, rank, world, local):
                          f"numpy float64 single thread"}
 
     det_avg = statistics.mean(det_ms)
-    flops = detect_flops(spec)
-    sm_max = clk.get("sm_max_mhz") or SM_MAX_MHZ_NOMINAL
+    fl = detect_flops(spec)
+    on_tc = args.precision != "fp32"
+    # FP32-pipe work: everything in the FP32 variant, the solve only when the products run on
+    # the tensor cores
+    flops = fl["solve"] + (0.0 if on_tc else fl["products"])
     peak_tf = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
     achieved_tf = flops / (det_avg * 1e-3) / 1e12
     ab = algorithmic_bytes(spec)
@@ -396,20 +413,24 @@ def run_ours(args, spec, rank, world, local):
                        "p99": float(np.percentile(step_ms, 99)), "deadline_ms": 0.5,
                        "what": "one step (8-cell batch) on an idle GPU, CUDA events"},
         "stages_ms": {"chest": statistics.mean(chest_ms), "detect": det_avg},
-        "roofline": {"bound": "alu", "kernel": "detect_fp32_kernel<16>",
+        "roofline": {"bound": "alu",
+                     "kernel": "detection stage: segment kernel (" +
+                               ("tcgen05 " + args.precision if on_tc else "FP32") +
+                               ") + re_solve_fp32_kernel, per chunk of cells",
                      "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                      "frac": achieved_tf / peak_tf,
                      "peak_source": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
                                     f"x {SM_MAX_MHZ_NOMINAL:.0f} MHz",
                      "flops_per_launch": flops,
-                     "traffic": committed_traffic("detect_fp32_kernel", args.workload),
+                     "tensor_flops_per_launch": fl["products"] if on_tc else 0.0,
+                     "traffic": committed_traffic("detect_" + args.precision, args.workload),
                      "hbm_view": {"algorithmic_bytes": det_bytes,
                                   "achieved_gbs": det_bytes / (det_avg * 1e-3) / 1e9,
                                   "peak_gbs": hbm_peak,
                                   "frac": det_bytes / (det_avg * 1e-3) / 1e9 / hbm_peak}},
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": (1 + 2 * detect_chunks(spec)) * args.steps,
         "clocks": clk,
     }
     print(json.dumps(line))

@@ -58,6 +58,7 @@ phy_status make_geo(const phy_slot_cfg* c, Geo* g) {
   t.G = (n_comb + L - 1) / L;
   t.n_seg = t.G > 1 ? t.G - 1 : 1;
   t.pivot_min = c->pivot_ratio_min;
+  t.prec = c->precision;
   int nd = 0;
   for (int s = 0; s < c->n_sym; ++s) {
     bool is_dmrs = false;
@@ -86,7 +87,7 @@ size_t anchor_bytes(const Geo& g) {
 phy_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PHY_OK : PHY_ERR_CUDA; }
 
 phy_status check_precision(const phy_slot_cfg* cfg, const Geo& g) {
-  if (cfg->precision != PHY_PREC_FP32) return PHY_ERR_UNSUPPORTED;
+  (void)cfg;
   if (phy::fused_fp32_smem_bytes(g) > 227 * 1024) return PHY_ERR_UNSUPPORTED;
   return PHY_OK;
 }

@@ -22,6 +22,7 @@ struct Geo {
   int n_comb;   // n_sc / 2
   int n_dsym;   // data symbols
   int n_seg;    // frequency segments (anchor pairs), max(G - 1, 1)
+  int prec;     // phy_precision of the Gram and matched-filter products
   float pivot_min;
   int dsym[kMaxSym];    // data symbol index j -> OFDM symbol t
   float tw[kMaxSym];    // weight of the second DMRS estimate at data symbol j

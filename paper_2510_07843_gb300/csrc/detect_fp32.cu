@@ -18,8 +18,10 @@
 //    solves (solver.cuh), SINR, unbiasing, max-log LLRs, stores.
 // The two kernels run per chunk of cells so that the intermediates stay small (L2-sized).
 #include <algorithm>
+#include <cstdlib>
 
 #include "launch.h"
+#include "segment.cuh"
 #include "solver.cuh"
 
 namespace phy {
@@ -29,6 +31,16 @@ namespace {
 constexpr int kPrepThreads = 256;
 constexpr int kSolveThreads = 128;
 constexpr size_t kChunkBudget = 32ull << 20;  // bytes of intermediates per chunk of cells
+
+// Intermediates budget per chunk; the environment variable PHY_CHUNK_MB overrides it (tuning).
+size_t chunk_budget() {
+  static const size_t v = [] {
+    const char* e = std::getenv("PHY_CHUNK_MB");
+    const long mb = e ? std::atol(e) : 0;
+    return mb > 0 ? (size_t)mb << 20 : kChunkBudget;
+  }();
+  return v;
+}
 
 int nl_class(int nl) { return nl <= 2 ? 2 : nl <= 4 ? 4 : nl <= 8 ? 8 : 16; }
 
@@ -50,22 +62,6 @@ __host__ __device__ inline PrepLayout prep_layout(int NL, int n_dmrs, int n_rx, 
   f.off_Y = f.off_Hg + n_rx * f.hs;
   f.total = f.off_Y + 2 * n_rx * f.yw;
   return f;
-}
-
-// Row l (l >= m) of the packed lower triangle from its index.
-__device__ __forceinline__ void tri_decode(int e, int& l, int& m) {
-  int r = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
-  while (r * (r + 1) / 2 > e) --r;
-  while ((r + 1) * (r + 2) / 2 <= e) ++r;
-  l = r;
-  m = e - r * (r + 1) / 2;
-}
-
-__device__ __forceinline__ int seg_of(const Geo& g, int k) {
-  if (g.G == 1) return 0;
-  int j = (k - g.L) / (2 * g.L);
-  if (k < g.L) j = 0;
-  return j < g.n_seg - 1 ? j : g.n_seg - 1;
 }
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
@@ -165,31 +161,7 @@ __global__ void __launch_bounds__(kPrepThreads)
       const cf v = Xs[k * f.xs + i];
       return mk(v.x, -v.y);
     };
-    float4* out = ygg + (((size_t)lc * g.n_seg + j) * nds) * NTRI * 2;
-    for (int e = tid; e < nds * NTRI; e += NT) {
-      const int jj = e / NTRI, te = e % NTRI;
-      int l, m;
-      tri_decode(te, l, m);
-      cf y[4];
-#pragma unroll
-      for (int gg = 0; gg < 2; ++gg)
-#pragma unroll
-        for (int gp = 0; gp < 2; ++gp) {
-          cf v;
-          if (g.n_dmrs == 2) {
-            const float t1 = g.tw[jj], t0 = 1.f - t1;
-            v = (t0 * t0) * Xget(gg * NL + l, gp * NL + m) +
-                (t0 * t1) * Xget(gg * NL + l, (2 + gp) * NL + m) +
-                (t1 * t0) * Xget((2 + gg) * NL + l, gp * NL + m) +
-                (t1 * t1) * Xget((2 + gg) * NL + l, (2 + gp) * NL + m);
-          } else {
-            v = Xget(gg * NL + l, gp * NL + m);
-          }
-          y[gg * 2 + gp] = v;
-        }
-      out[(size_t)e * 2] = make_float4(y[0].x, y[0].y, y[1].x, y[1].y);
-      out[(size_t)e * 2 + 1] = make_float4(y[2].x, y[2].y, y[3].x, y[3].y);
-    }
+    form_gram_blocks<NL, NT>(g, Xget, ygg + (((size_t)lc * g.n_seg + j) * nds) * NTRI * 2, tid);
   }
   // ---- matched filter per data symbol
   for (int jj = 0; jj < nds; ++jj) {
@@ -342,7 +314,7 @@ Sizes sizes(const Geo& g) {
   s.ygg_per_cell = (size_t)g.n_seg * g.n_dsym * s.ntri * 32;
   s.b_per_cell = (size_t)g.n_dsym * g.n_sc * s.NL * 8;
   const size_t per = s.ygg_per_cell + s.b_per_cell;
-  s.chunk = (int)std::max<size_t>(1, kChunkBudget / per);
+  s.chunk = (int)std::max<size_t>(1, chunk_budget() / per);
   s.chunk = std::min(s.chunk, g.n_cells);
   return s;
 }
@@ -379,15 +351,23 @@ cudaError_t run_chunks(const Geo& g, int wmax, const Sizes& s, const phy_c32* an
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  float4* ygg = reinterpret_cast<float4*>(scratch);
-  cf* bvec = reinterpret_cast<cf*>(static_cast<char*>(scratch) + align256(s.ygg_per_cell * s.chunk));
+  char* base = static_cast<char*>(scratch);
+  unsigned* err = reinterpret_cast<unsigned*>(base);
+  float4* ygg = reinterpret_cast<float4*>(base + 256);
+  cf* bvec = reinterpret_cast<cf*>(base + 256 + align256(s.ygg_per_cell * s.chunk));
   for (int c0 = 0; c0 < g.n_cells; c0 += s.chunk) {
     const int nc = std::min(s.chunk, g.n_cells - c0);
-    dim3 grid(g.n_seg, nc);
-    seg_prep_fp32_kernel<NL><<<grid, kPrepThreads, smem, st>>>(g, wmax, c0, anchors, Y, ygg, bvec);
+    cudaError_t e;
+    if (g.prec == PHY_PREC_FP32) {
+      dim3 grid(g.n_seg, nc);
+      seg_prep_fp32_kernel<NL><<<grid, kPrepThreads, smem, st>>>(g, wmax, c0, anchors, Y, ygg,
+                                                                bvec);
+    } else {
+      e = launch_seg_prep_tc(g, NL, c0, nc, anchors, Y, ygg, bvec, err, st);
+      if (e != cudaSuccess) return e;
+    }
     const size_t n_re = (size_t)nc * g.n_dsym * g.n_sc;
     const unsigned blocks = (unsigned)((n_re + kSolveThreads - 1) / kSolveThreads);
-    cudaError_t e;
     switch (g.qm) {
       case 2: e = launch_solve<NL, 2>(blocks, g, c0, nc, ygg, bvec, sigma2, x_hat, sinr, llr, flags, st); break;
       case 4: e = launch_solve<NL, 4>(blocks, g, c0, nc, ygg, bvec, sigma2, x_hat, sinr, llr, flags, st); break;
@@ -422,7 +402,8 @@ size_t fused_fp32_smem_bytes(const Geo& g) {
 
 size_t detect_fp32_scratch_bytes(const Geo& g) {
   const Sizes s = sizes(g);
-  return align256(s.ygg_per_cell * s.chunk) + align256(s.b_per_cell * s.chunk);
+  // error counter of the tensor-core kernels, then the two intermediates
+  return 256 + align256(s.ygg_per_cell * s.chunk) + align256(s.b_per_cell * s.chunk);
 }
 
 cudaError_t launch_detect_fp32(const Geo& g, const phy_c32* anchors, const phy_c32* Y,

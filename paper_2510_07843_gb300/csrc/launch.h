@@ -21,6 +21,11 @@ cudaError_t launch_detect_fp32(const Geo& g, const phy_c32* anchors, const phy_c
                                const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
                                uint8_t* flags, void* scratch, cudaStream_t st);
 
+// Tensor-core segment kernel (same outputs as the FP32 one) for g.prec != PHY_PREC_FP32.
+cudaError_t launch_seg_prep_tc(const Geo& g, int NL, int c0, int nc, const phy_c32* anchors,
+                               const phy_c32* Y, float4* ygg, cf* bvec, unsigned* err,
+                               cudaStream_t st);
+
 cudaError_t launch_detect_h(const Geo& g, const phy_c32* H, const phy_c32* Y, const float* sigma2,
                             phy_c32* x_hat, float* sinr, uint8_t* flags, cudaStream_t st);
 

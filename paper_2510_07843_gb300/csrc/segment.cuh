@@ -1,0 +1,60 @@
+// Pieces shared by the FP32 and tensor-core segment kernels: index helpers and the folding of
+// the corner cross-Gram X into the per-symbol Gram blocks Y_gg'(t).
+#pragma once
+
+#include "common.cuh"
+
+namespace phy {
+
+// Row l and column m (l >= m) of packed lower-triangle index e.
+__device__ __forceinline__ void tri_decode(int e, int& l, int& m) {
+  int r = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+  while (r * (r + 1) / 2 > e) --r;
+  while ((r + 1) * (r + 2) / 2 <= e) ++r;
+  l = r;
+  m = e - r * (r + 1) / 2;
+}
+
+// Frequency segment holding subcarrier k (see segment_range).
+__device__ __forceinline__ int seg_of(const Geo& g, int k) {
+  if (g.G == 1) return 0;
+  int j = (k - g.L) / (2 * g.L);
+  if (k < g.L) j = 0;
+  return j < g.n_seg - 1 ? j : g.n_seg - 1;
+}
+
+// Y_gg'(t)[l][m] = sum_{d,d'} tau_d(t) tau_d'(t) X[(d,g) l][(d',g') m] for every data symbol and
+// every lower-triangle entry (l, m), written as 4-tuples (Y00, Y01, Y10, Y11) of complex values
+// (two float4 per entry) to out[jj][e]. Xget(i, k) returns X at corner-layer indices
+// i = (2 d + g) NL + l (corners ordered (d0,g0), (d0,g1), (d1,g0), (d1,g1)).
+template <int NL, int NT, class XGet>
+__device__ __forceinline__ void form_gram_blocks(const Geo& g, XGet Xget, float4* out, int tid) {
+  constexpr int NTRI = NL * (NL + 1) / 2;
+  const int nds = g.n_dsym;
+  for (int e = tid; e < nds * NTRI; e += NT) {
+    const int jj = e / NTRI, te = e % NTRI;
+    int l, m;
+    tri_decode(te, l, m);
+    cf y[4];
+#pragma unroll
+    for (int gg = 0; gg < 2; ++gg)
+#pragma unroll
+      for (int gp = 0; gp < 2; ++gp) {
+        cf v;
+        if (g.n_dmrs == 2) {
+          const float t1 = g.tw[jj], t0 = 1.f - t1;
+          v = (t0 * t0) * Xget(gg * NL + l, gp * NL + m) +
+              (t0 * t1) * Xget(gg * NL + l, (2 + gp) * NL + m) +
+              (t1 * t0) * Xget((2 + gg) * NL + l, gp * NL + m) +
+              (t1 * t1) * Xget((2 + gg) * NL + l, (2 + gp) * NL + m);
+        } else {
+          v = Xget(gg * NL + l, gp * NL + m);
+        }
+        y[gg * 2 + gp] = v;
+      }
+    out[(size_t)e * 2] = make_float4(y[0].x, y[0].y, y[1].x, y[1].y);
+    out[(size_t)e * 2 + 1] = make_float4(y[2].x, y[2].y, y[3].x, y[3].y);
+  }
+}
+
+}  // namespace phy

@@ -228,3 +228,48 @@ def test_errors_enqueue_nothing(dev):
         phy.slot_run(bad, buf.Y, buf.pilots, buf.sigma2, buf.x_hat, buf.sinr, buf.llr, buf.flags,
                      buf.workspace)
     assert e.value.code == 1
+
+
+TC_CASES = {
+    "massive_6prb_64x16_256qam_2cells": (S.spec_massive_mimo(n_cells=2, n_prb=6), 3000),
+    "carrier_25prb_16x4_64qam_jakes": (S.spec_carrier_273prb(n_prb=25), 2000),
+    "massive_one_dmrs_5prb_32x16": (S.spec_massive_mimo(n_cells=1, n_prb=5, n_rx=32,
+                                                        dmrs_sym=(2,)), 15),
+    "small_51prb_4x2_16qam": (S.spec_small_51prb(), 1001),
+}
+
+
+@pytest.mark.parametrize("prec", ["tf32", "fp16", "bf16"])
+@pytest.mark.parametrize("name", list(TC_CASES))
+def test_tensor_core_variants_vs_oracle(dev, name, prec):
+    """Gram and matched-filter products on tcgen05 with operands rounded to TF32/FP16/BF16."""
+    spec, seed = TC_CASES[name]
+    sl = S.make_slot(spec, seed, keep_h=False)
+    got = gpu_slot(spec, sl, dev, precision=prec)
+    ref = oracle_dense(spec, sl)
+    nl, qm = spec.n_layers, spec.qm
+    flat = lambda a, tail: a.reshape((-1,) + tail)
+    mask = (ref["flags"].reshape(-1) == 0) & (got["flags"].reshape(-1) == 0)
+    m = compare_res(f"{name}[{prec}]",
+                    dict(x_hat=flat(got["x_hat"], (nl,)), sinr=flat(got["sinr"], (nl,)),
+                         llr=flat(got["llr"], (nl, qm))),
+                    dict(x_hat=flat(ref["x_hat"], (nl,)), sinr=flat(ref["sinr"], (nl,)),
+                         llr=flat(ref["llr"], (nl, qm))),
+                    qm, flat(ref["s2eff"], (nl,)), flat(ref["x_t"], (nl,)), mask)
+    hard = (got["llr"] < 0).astype(np.uint8)
+    hard_ref = (ref["llr"] < 0).astype(np.uint8)
+    m["bit_disagree"] = float(np.mean(hard != hard_ref))
+    m["ber"] = float(np.mean(hard != sl.bits))
+    m["ber_ref"] = float(np.mean(hard_ref != sl.bits))
+    print(f"{name}[{prec}] bits:", m["bit_disagree"], m["ber"], m["ber_ref"])
+    # Operand rounding u = 2^-11 (TF32, FP16) or 2^-8 (BF16) per product; the Gram and matched
+    # filter carry a few u of relative error and the solve multiplies it by the conditioning.
+    # Bounds: x_hat 2u / 2.5u aggregate, SINR 6u / 5u, normalised LLR 40u / 25u, hard-bit
+    # disagreement with the oracle 1e-3 / 5e-3, uncoded BER within 2% of the oracle's.
+    lim = {"tf32": (1e-3, 3e-3, 2e-2, 1e-3), "fp16": (1e-3, 3e-3, 2e-2, 1e-3),
+           "bf16": (1e-2, 2e-2, 1e-1, 5e-3)}[prec]
+    assert m["x_rel"] <= lim[0], m
+    assert m["sinr_rel_max"] <= lim[1], m
+    assert m["llr_norm_max"] <= lim[2], m
+    assert m["bit_disagree"] <= lim[3], m
+    assert abs(m["ber"] - m["ber_ref"]) <= 0.02 * m["ber_ref"] + 2e-4, m
