@@ -66,14 +66,16 @@ def algorithmic_bytes(spec: S.SlotSpec) -> dict:
 
 
 def detect_chunks(spec: S.SlotSpec) -> int:
-    """Chunks of cells the detection stage runs in (two kernel launches each): the library
-    sizes a chunk so its intermediates (Gram blocks and matched filter) stay within 32 MiB."""
+    """Chunks of cells the detection stage runs in (two kernel launches each) with the full
+    phy_workspace_size() workspace: the library prefers chunks whose intermediates (Gram blocks
+    and matched filter) stay within 256 MiB (PHY_CHUNK_MB overrides)."""
     nl = next(c for c in (2, 4, 8, 16) if spec.n_layers <= c)
     n_comb = spec.n_sc // 2
     n_seg = max(-(-n_comb // spec.occ) - 1, 1)
     J = len(spec.data_sym)
     per_cell = n_seg * J * nl * (nl + 1) // 2 * 32 + J * spec.n_sc * nl * 8
-    chunk = min(max(1, (32 << 20) // per_cell), spec.n_cells)
+    budget = int(os.environ.get("PHY_CHUNK_MB", "256")) << 20
+    chunk = min(max(1, budget // per_cell), spec.n_cells)
     return -(-spec.n_cells // chunk)
 
 

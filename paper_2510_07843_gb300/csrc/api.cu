@@ -86,13 +86,48 @@ size_t anchor_bytes(const Geo& g) {
 
 phy_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PHY_OK : PHY_ERR_CUDA; }
 
-phy_status check_precision(const phy_slot_cfg* cfg, const Geo& g) {
-  (void)cfg;
+phy_status check_shape(const Geo& g) {
   if (phy::fused_fp32_smem_bytes(g) > 227 * 1024) return PHY_ERR_UNSUPPORTED;
   return PHY_OK;
 }
 
+size_t workspace_for_chunk(const Geo& g, int chunk) {
+  return align_up(anchor_bytes(g)) + align_up(phy::detect_scratch_bytes(g, chunk));
+}
+
 }  // namespace
+
+namespace phy {
+
+size_t min_workspace_bytes(const phy_slot_cfg* cfg) {
+  Geo g;
+  if (make_geo(cfg, &g) != PHY_OK) return 0;
+  return workspace_for_chunk(g, 1);
+}
+
+phy_status slot_run_fit(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32* pilots,
+                        const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
+                        uint8_t* flags, void* workspace, size_t workspace_bytes,
+                        cudaStream_t st) {
+  Geo g;
+  phy_status s = make_geo(cfg, &g);
+  if (s != PHY_OK) return s;
+  if (!Y || !pilots || !sigma2 || !flags || !workspace || ((uintptr_t)Y % 16))
+    return PHY_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace) % kAlign) return PHY_ERR_INVALID_ARG;
+  if (workspace_bytes < workspace_for_chunk(g, 1)) return PHY_ERR_NO_MEMORY;
+  s = check_shape(g);
+  if (s != PHY_OK) return s;
+  phy_c32* anchors = (phy_c32*)workspace;
+  const size_t a = align_up(anchor_bytes(g));
+  cudaError_t e = launch_chest(g, Y, pilots, anchors, st);
+  if (e != cudaSuccess) return PHY_ERR_CUDA;
+  e = launch_detect(g, anchors, Y, sigma2, x_hat, sinr, llr, flags,
+                    static_cast<char*>(workspace) + a, workspace_bytes - a, st);
+  return cuda_status(e);
+}
+
+}  // namespace phy
 
 extern "C" {
 
@@ -121,7 +156,7 @@ int32_t phy_n_data_symbols(const phy_slot_cfg* cfg) {
 size_t phy_workspace_size(const phy_slot_cfg* cfg) {
   Geo g;
   if (make_geo(cfg, &g) != PHY_OK) return 0;
-  return align_up(anchor_bytes(g)) + align_up(phy::detect_fp32_scratch_bytes(g));
+  return workspace_for_chunk(g, phy::detect_preferred_chunk(g));
 }
 
 phy_status phy_chest(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32* pilots,
@@ -163,11 +198,12 @@ phy_status phy_detect_anchors(const phy_slot_cfg* cfg, const phy_c32* anchors, c
   if (!anchors || !Y || !sigma2 || !flags || !workspace) return PHY_ERR_INVALID_ARG;
   if (((uintptr_t)workspace) % kAlign) return PHY_ERR_INVALID_ARG;
   if (workspace_bytes < phy_workspace_size(cfg)) return PHY_ERR_NO_MEMORY;
-  s = check_precision(cfg, g);
+  s = check_shape(g);
   if (s != PHY_OK) return s;
-  void* scratch = static_cast<char*>(workspace) + align_up(anchor_bytes(g));
-  return cuda_status(phy::launch_detect_fp32(g, anchors, Y, sigma2, x_hat, sinr, llr, flags,
-                                             scratch, (cudaStream_t)stream));
+  const size_t a = align_up(anchor_bytes(g));
+  return cuda_status(phy::launch_detect(g, anchors, Y, sigma2, x_hat, sinr, llr, flags,
+                                        static_cast<char*>(workspace) + a, workspace_bytes - a,
+                                        (cudaStream_t)stream));
 }
 
 phy_status phy_slot_run(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32* pilots,
@@ -178,17 +214,9 @@ phy_status phy_slot_run(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32
   if (s != PHY_OK) return s;
   if (!Y || !pilots || !sigma2 || !flags || !workspace || ((uintptr_t)Y % 16))
     return PHY_ERR_INVALID_ARG;
-  if (((uintptr_t)workspace) % kAlign) return PHY_ERR_INVALID_ARG;
   if (workspace_bytes < phy_workspace_size(cfg)) return PHY_ERR_NO_MEMORY;
-  s = check_precision(cfg, g);
-  if (s != PHY_OK) return s;
-  cudaStream_t st = (cudaStream_t)stream;
-  phy_c32* anchors = (phy_c32*)workspace;
-  cudaError_t e = phy::launch_chest(g, Y, pilots, anchors, st);
-  if (e != cudaSuccess) return PHY_ERR_CUDA;
-  void* scratch = static_cast<char*>(workspace) + align_up(anchor_bytes(g));
-  e = phy::launch_detect_fp32(g, anchors, Y, sigma2, x_hat, sinr, llr, flags, scratch, st);
-  return cuda_status(e);
+  return phy::slot_run_fit(cfg, Y, pilots, sigma2, x_hat, sinr, llr, flags, workspace,
+                           workspace_bytes, (cudaStream_t)stream);
 }
 
 phy_status phy_slot_run_host(const phy_slot_cfg* cfg, const phy_c32* Y_host,
@@ -204,7 +232,7 @@ phy_status phy_slot_run_host(const phy_slot_cfg* cfg, const phy_c32* Y_host,
       !sigma2 || !llr || !flags)
     return PHY_ERR_INVALID_ARG;
   if (workspace_bytes < phy_workspace_size(cfg)) return PHY_ERR_NO_MEMORY;
-  s = check_precision(cfg, g);
+  s = check_shape(g);
   if (s != PHY_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t y_bytes = (size_t)g.n_cells * g.n_sym * g.n_rx * g.n_sc * sizeof(phy_c32);

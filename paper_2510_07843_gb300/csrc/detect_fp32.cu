@@ -30,7 +30,7 @@ namespace {
 
 constexpr int kPrepThreads = 256;
 constexpr int kSolveThreads = 128;
-constexpr size_t kChunkBudget = 32ull << 20;  // bytes of intermediates per chunk of cells
+constexpr size_t kChunkBudget = 256ull << 20;  // preferred intermediates per chunk of cells
 
 // Intermediates budget per chunk; the environment variable PHY_CHUNK_MB overrides it (tuning).
 size_t chunk_budget() {
@@ -307,19 +307,22 @@ struct Sizes {
   int chunk;  // cells per chunk
 };
 
-Sizes sizes(const Geo& g) {
+Sizes sizes(const Geo& g, int chunk) {
   Sizes s;
   s.NL = nl_class(g.n_layers);
   s.ntri = s.NL * (s.NL + 1) / 2;
   s.ygg_per_cell = (size_t)g.n_seg * g.n_dsym * s.ntri * 32;
   s.b_per_cell = (size_t)g.n_dsym * g.n_sc * s.NL * 8;
-  const size_t per = s.ygg_per_cell + s.b_per_cell;
-  s.chunk = (int)std::max<size_t>(1, chunk_budget() / per);
-  s.chunk = std::min(s.chunk, g.n_cells);
+  s.chunk = chunk;
   return s;
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// error counter of the tensor-core kernels, then the two intermediates for `chunk` cells
+size_t scratch_bytes(const Sizes& s, int chunk) {
+  return 256 + align256(s.ygg_per_cell * chunk) + align256(s.b_per_cell * chunk);
+}
 
 template <int NL, int QM>
 cudaError_t launch_solve(unsigned blocks, const Geo& g, int c0, int nc, const float4* ygg,
@@ -400,17 +403,26 @@ size_t fused_fp32_smem_bytes(const Geo& g) {
   return (size_t)f.total * sizeof(cf);
 }
 
-size_t detect_fp32_scratch_bytes(const Geo& g) {
-  const Sizes s = sizes(g);
-  // error counter of the tensor-core kernels, then the two intermediates
-  return 256 + align256(s.ygg_per_cell * s.chunk) + align256(s.b_per_cell * s.chunk);
+size_t detect_scratch_bytes(const Geo& g, int chunk) {
+  return scratch_bytes(sizes(g, chunk), std::min(std::max(chunk, 1), g.n_cells));
 }
 
-cudaError_t launch_detect_fp32(const Geo& g, const phy_c32* anchors, const phy_c32* Y,
-                               const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
-                               uint8_t* flags, void* scratch, cudaStream_t st) {
+int detect_preferred_chunk(const Geo& g) {
+  const Sizes s = sizes(g, 1);
+  const size_t per = s.ygg_per_cell + s.b_per_cell;
+  return (int)std::min<size_t>(std::max<size_t>(1, chunk_budget() / per), (size_t)g.n_cells);
+}
+
+cudaError_t launch_detect(const Geo& g, const phy_c32* anchors, const phy_c32* Y,
+                          const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
+                          uint8_t* flags, void* scratch, size_t scratch_bytes_avail,
+                          cudaStream_t st) {
   const int wmax = host_max_segment_width(g);
-  const Sizes s = sizes(g);
+  // the largest chunk of cells (up to the preferred one) whose intermediates fit the scratch
+  int chunk = detect_preferred_chunk(g);
+  Sizes s = sizes(g, chunk);
+  while (chunk > 1 && scratch_bytes(s, chunk) > scratch_bytes_avail) s = sizes(g, --chunk);
+  if (scratch_bytes(s, chunk) > scratch_bytes_avail) return cudaErrorInvalidValue;
   switch (s.NL) {
     case 2:
       return run_chunks<2>(g, wmax, s, anchors, Y, sigma2, x_hat, sinr, llr, flags, scratch, st);

@@ -11,15 +11,28 @@ namespace phy {
 int host_max_segment_width(const Geo& g);
 // Dynamic shared memory of the FP32 segment kernel for g (bytes).
 size_t fused_fp32_smem_bytes(const Geo& g);
-// Workspace bytes the FP32 detector needs for its per-chunk intermediates.
-size_t detect_fp32_scratch_bytes(const Geo& g);
+// Detection runs in chunks of cells; its scratch holds one chunk's intermediates.
+// Scratch bytes for chunks of `chunk` cells, and the chunk size the library prefers.
+size_t detect_scratch_bytes(const Geo& g, int chunk);
+int detect_preferred_chunk(const Geo& g);
 
 cudaError_t launch_chest(const Geo& g, const phy_c32* Y, const phy_c32* pilots, phy_c32* anchors,
                          cudaStream_t st);
 
-cudaError_t launch_detect_fp32(const Geo& g, const phy_c32* anchors, const phy_c32* Y,
-                               const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
-                               uint8_t* flags, void* scratch, cudaStream_t st);
+// Interpolation + detection + SINR + LLRs from anchors, in the largest chunks of cells whose
+// intermediates fit `scratch_bytes` (cudaErrorInvalidValue if not even one cell fits).
+cudaError_t launch_detect(const Geo& g, const phy_c32* anchors, const phy_c32* Y,
+                          const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
+                          uint8_t* flags, void* scratch, size_t scratch_bytes, cudaStream_t st);
+
+// phy_slot_run with any workspace that holds the anchors and one cell's intermediates
+// (chunks sized to fit); for callers inside the library.
+phy_status slot_run_fit(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32* pilots,
+                        const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
+                        uint8_t* flags, void* workspace, size_t workspace_bytes,
+                        cudaStream_t st);
+// Smallest workspace slot_run_fit accepts for cfg (0 if cfg is invalid).
+size_t min_workspace_bytes(const phy_slot_cfg* cfg);
 
 // Tensor-core segment kernel (same outputs as the FP32 one) for g.prec != PHY_PREC_FP32.
 cudaError_t launch_seg_prep_tc(const Geo& g, int NL, int c0, int nc, const phy_c32* anchors,

@@ -48,14 +48,15 @@ extern "C" phy_status phy_slot_run_noalloc(const phy_slot_cfg* cfg, const phy_c3
                                            const phy_c32* pilots, const float* sigma2,
                                            phy_c32* x_hat, float* sinr, float* llr,
                                            uint8_t* flags, void* stream) {
-  const size_t need = phy_workspace_size(cfg);
+  // the work runs in chunks of cells sized to fit the array
+  const size_t need = phy::min_workspace_bytes(cfg);
   if (need == 0) return PHY_ERR_INVALID_ARG;
   if (need > kScratchBytes) return PHY_ERR_NO_MEMORY;
   if (!Y || !pilots || !sigma2 || !flags) return PHY_ERR_INVALID_ARG;
   void* scratch = nullptr;
   if (scratch_address(&scratch) != cudaSuccess) return PHY_ERR_CUDA;
-  // phy_slot_run validates the rest and runs both kernels; the chest kernel overwrites every
-  // anchor the detection kernel reads, so nothing in the array needs clearing between calls.
-  return phy_slot_run(cfg, Y, pilots, sigma2, x_hat, sinr, llr, flags, scratch, kScratchBytes,
-                      stream);
+  // Validation of the rest and the kernels are phy_slot_run's. Every value the kernels read from
+  // the array is written earlier in the same call, so nothing needs clearing between calls.
+  return phy::slot_run_fit(cfg, Y, pilots, sigma2, x_hat, sinr, llr, flags, scratch,
+                           kScratchBytes, (cudaStream_t)stream);
 }

@@ -31,8 +31,6 @@ def test_noalloc_rejects_configs_beyond_the_fixed_scratch():
     fake = ctypes.c_void_p(256)  # never dereferenced
     rc = lib.phy_slot_run_noalloc(ctypes.byref(c), fake, fake, fake, fake, fake, fake, fake, None)
     assert rc == 3  # PHY_ERR_NO_MEMORY
-    fits = phy.SlotConfig(n_cells=8, n_prb=273, n_rx=64, n_layers=16, qm=8, dmrs_sym=(2, 11))
-    assert phy.workspace_size(fits) <= phy.NOALLOC_SCRATCH_BYTES
 
 
 @pytest.mark.gpu
@@ -44,9 +42,10 @@ def test_noalloc_matches_slot_run_two_calls_in_a_row():
     build.build()
     phy.load()
     dev = torch.device("cuda:0")
-    # two different slots back to back: the second call must not see the first call's scratch
-    for seed in (61, 62):
-        spec, sl = _slot(seed)
+    # two different slots back to back: the second call must not see the first call's scratch;
+    # the second is the full 8-cell 273-PRB 64x16 batch, which runs in chunks of cells
+    for seed, n_cells, n_prb in ((61, 2, 8), (62, 8, 273)):
+        spec, sl = _slot(seed, n_cells, n_prb)
         cfg = phy.SlotConfig.from_spec(spec)
         Y = torch.from_numpy(sl.Y).to(dev)
         P = torch.from_numpy(sl.pilots).to(dev)
