@@ -23,6 +23,7 @@
 #include "launch.h"
 #include "segment.cuh"
 #include "solver.cuh"
+#include "tc.cuh"
 
 namespace phy {
 
@@ -207,9 +208,7 @@ struct SmemScratch {
   __device__ __forceinline__ cf ld(int e) const { return base[e * kSolveThreads]; }
 };
 
-constexpr size_t solve_smem_bytes(int NL) {
-  return NL == 16 ? (size_t)kScrSlots * kSolveThreads * sizeof(cf) : 0;
-}
+
 
 template <int QM>
 __device__ __forceinline__ void store_llr(float* dst, cf xt, float s2eff) {
@@ -219,31 +218,84 @@ __device__ __forceinline__ void store_llr(float* dst, cf xt, float s2eff) {
   for (int q = 0; q < QM; q += 2) *reinterpret_cast<float2*>(dst + q) = make_float2(l[q], l[q + 1]);
 }
 
+// Gram-block bytes of one (segment, data symbol): NTRI 4-tuples of complex values.
+constexpr uint32_t gram_block_bytes(int NL) { return (uint32_t)(NL * (NL + 1) / 2) * 32u; }
+
+constexpr size_t solve_scratch_bytes(int NL) {
+  return NL == 16 ? (size_t)kScrSlots * kSolveThreads * sizeof(cf) : 0;
+}
+
+// Shared memory of the solve kernel: scratch, the Gram blocks of up to max_segs segments, barrier.
+size_t solve_smem_bytes(int NL, int max_segs) {
+  return solve_scratch_bytes(NL) + (size_t)max_segs * gram_block_bytes(NL) + 16;
+}
+
+// One CTA per (128 subcarriers, data symbol, cell), one thread per RE. Thread 0 brings the
+// Gram-block 4-tuples of the segments the CTA spans into shared memory with bulk copies
+// (TMA engine, completion counted on an mbarrier); meanwhile every thread loads its matched
+// filter. A barrier timeout marks the CTA's REs with flag bit 3.
 template <int NL, int QM>
 __global__ void __launch_bounds__(kSolveThreads)
-    re_solve_fp32_kernel(Geo g, int cell0, int n_cells_chunk, const float4* __restrict__ ygg,
+    re_solve_fp32_kernel(Geo g, int cell0, int max_segs, const float4* __restrict__ ygg,
                          const cf* __restrict__ bvec, const float* __restrict__ sigma2,
                          phy_c32* __restrict__ x_hat, float* __restrict__ sinr_out,
                          float* __restrict__ llr_out, uint8_t* __restrict__ flags_out) {
   constexpr int NTRI = NL * (NL + 1) / 2;
+  constexpr uint32_t kBlk = gram_block_bytes(NL);
+  extern __shared__ __align__(128) unsigned char solve_smem[];
+  float4* ys = reinterpret_cast<float4*>(solve_smem + solve_scratch_bytes(NL));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(solve_smem + solve_scratch_bytes(NL) +
+                                              (size_t)max_segs * kBlk);
   const int nl = g.n_layers, nds = g.n_dsym;
-  const size_t n_re = (size_t)n_cells_chunk * nds * g.n_sc;
-  const size_t re = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (re >= n_re) return;
-  const int k = (int)(re % g.n_sc);
-  const int jj = (int)((re / g.n_sc) % nds);
-  const int lc = (int)(re / ((size_t)g.n_sc * nds));
-  const int cell = cell0 + lc;
+  const int jj = blockIdx.y, lc = blockIdx.z, cell = cell0 + lc;
+  const int k0 = blockIdx.x * kSolveThreads;
+  const int k = k0 + threadIdx.x;
+  const bool live = k < g.n_sc;
+  const int s0 = seg_of(g, k0), s1 = seg_of(g, min(k0 + kSolveThreads, g.n_sc) - 1);
+  const int nseg = s1 - s0 + 1;  // <= max_segs (host-computed bound)
+  if (threadIdx.x == 0) {
+    tc::mbar_init(bar, 1);
+    tc::mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tc::mbar_arrive_expect_tx(bar, (uint32_t)nseg * kBlk);
+    for (int s = 0; s < nseg; ++s)
+      tc::bulk_g2s(ys + (size_t)s * NTRI * 2,
+                   ygg + (((size_t)lc * g.n_seg + s0 + s) * nds + jj) * NTRI * 2, kBlk, bar);
+  }
+  const size_t re = ((size_t)lc * nds + jj) * g.n_sc + (live ? k : k0);
+  cf b[NL], x[NL];
+  float dd[NL];
+  bool fin = true;
+  if (live) {
+    const float4* bp = reinterpret_cast<const float4*>(bvec + re * NL);
+#pragma unroll
+    for (int l = 0; l < NL; l += 2) {
+      const float4 v = __ldg(bp + l / 2);
+      b[l] = mk(v.x, v.y);
+      b[l + 1] = mk(v.z, v.w);
+    }
+  }
+  constexpr uint32_t kWait = 1u << 22;
+  bool arrived = tc::mbar_wait(bar, 0, kWait);
+  if (!arrived) arrived = tc::mbar_wait(bar, 0, kWait);  // let copies in flight land
+  if (!live) return;
+  const size_t ridx = ((size_t)cell * nds + jj) * g.n_sc + k;
+  if (!arrived) {
+    flags_out[ridx] = 8;
+    return;
+  }
   const int j = seg_of(g, k);
   const float s2 = sigma2[cell];
   const float be0 = seg_beta(g, j, k, 0), be1 = seg_beta(g, j, k, 1);
-  const float4* yp = ygg + (((size_t)lc * g.n_seg + j) * nds + jj) * NTRI * 2;
+  const float4* yp = ys + (size_t)(j - s0) * NTRI * 2;
   auto getA = [&](int l, int m) -> cf {
     if (l >= nl || m >= nl) return (l == m) ? mk(1.f, 0.f) : mk(0.f, 0.f);
     const float bl = (l & 1) ? be1 : be0, bm = (m & 1) ? be1 : be0;
     const float wl0 = 1.f - bl, wm0 = 1.f - bm;
     const int e = tri(l, m);
-    const float4 p = __ldg(yp + 2 * e), q = __ldg(yp + 2 * e + 1);
+    const float4 p = yp[2 * e], q = yp[2 * e + 1];
     const float c00 = wl0 * wm0, c01 = wl0 * bm, c10 = bl * wm0, c11 = bl * bm;
     cf a;
     a.x = fmaf(c00, p.x, fmaf(c01, p.z, fmaf(c10, q.x, c11 * q.z)));
@@ -254,16 +306,6 @@ __global__ void __launch_bounds__(kSolveThreads)
     }
     return a;
   };
-  cf b[NL], x[NL];
-  float dd[NL];
-  bool fin = true;
-  const float4* bp = reinterpret_cast<const float4*>(bvec + re * NL);
-#pragma unroll
-  for (int l = 0; l < NL; l += 2) {
-    const float4 v = __ldg(bp + l / 2);
-    b[l] = mk(v.x, v.y);
-    b[l + 1] = mk(v.z, v.w);
-  }
 #pragma unroll
   for (int l = 0; l < NL; ++l) {
     if (l >= nl) b[l] = mk(0.f, 0.f);
@@ -281,7 +323,6 @@ __global__ void __launch_bounds__(kSolveThreads)
   uint8_t flag = 0;
   if (!fin) flag |= 4;
   if (!si.ok || si.pmin < g.pivot_min * si.pmax) flag |= 1;
-  const size_t ridx = ((size_t)cell * nds + jj) * g.n_sc + k;
   flags_out[ridx] = flag;
   // rolled on purpose: one copy of the per-layer epilogue keeps the kernel's code small
 #pragma unroll 1
@@ -319,25 +360,40 @@ Sizes sizes(const Geo& g, int chunk) {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// Most frequency segments any block of kSolveThreads consecutive subcarriers touches.
+int max_segments_per_block(const Geo& g) {
+  if (g.G == 1) return 1;
+  auto seg = [&](int k) {
+    int j = (k - g.L) / (2 * g.L);
+    if (k < g.L) j = 0;
+    return std::min(j, g.n_seg - 1);
+  };
+  int best = 1;
+  for (int k0 = 0; k0 < g.n_sc; k0 += kSolveThreads)
+    best = std::max(best, seg(std::min(k0 + kSolveThreads, g.n_sc) - 1) - seg(k0) + 1);
+  return best;
+}
+
 // error counter of the tensor-core kernels, then the two intermediates for `chunk` cells
 size_t scratch_bytes(const Sizes& s, int chunk) {
   return 256 + align256(s.ygg_per_cell * chunk) + align256(s.b_per_cell * chunk);
 }
 
 template <int NL, int QM>
-cudaError_t launch_solve(unsigned blocks, const Geo& g, int c0, int nc, const float4* ygg,
+cudaError_t launch_solve(const Geo& g, int c0, int nc, int max_segs, const float4* ygg,
                          const cf* bvec, const float* sigma2, phy_c32* x_hat, float* sinr,
                          float* llr, uint8_t* flags, cudaStream_t st) {
-  constexpr size_t smem = solve_smem_bytes(NL);
-  static bool configured = false;
-  if (smem > 48 * 1024 && !configured) {
+  const size_t smem = solve_smem_bytes(NL, max_segs);
+  static size_t configured = 0;
+  if (smem > 48 * 1024 && smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(re_solve_fp32_kernel<NL, QM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    configured = true;
+    configured = smem;
   }
-  re_solve_fp32_kernel<NL, QM><<<blocks, kSolveThreads, smem, st>>>(g, c0, nc, ygg, bvec, sigma2,
-                                                                   x_hat, sinr, llr, flags);
+  dim3 grid((g.n_sc + kSolveThreads - 1) / kSolveThreads, g.n_dsym, nc);
+  re_solve_fp32_kernel<NL, QM><<<grid, kSolveThreads, smem, st>>>(g, c0, max_segs, ygg, bvec,
+                                                                  sigma2, x_hat, sinr, llr, flags);
   return cudaGetLastError();
 }
 
@@ -369,13 +425,12 @@ cudaError_t run_chunks(const Geo& g, int wmax, const Sizes& s, const phy_c32* an
       e = launch_seg_prep_tc(g, NL, c0, nc, anchors, Y, ygg, bvec, err, st);
       if (e != cudaSuccess) return e;
     }
-    const size_t n_re = (size_t)nc * g.n_dsym * g.n_sc;
-    const unsigned blocks = (unsigned)((n_re + kSolveThreads - 1) / kSolveThreads);
+    const int ms = max_segments_per_block(g);
     switch (g.qm) {
-      case 2: e = launch_solve<NL, 2>(blocks, g, c0, nc, ygg, bvec, sigma2, x_hat, sinr, llr, flags, st); break;
-      case 4: e = launch_solve<NL, 4>(blocks, g, c0, nc, ygg, bvec, sigma2, x_hat, sinr, llr, flags, st); break;
-      case 6: e = launch_solve<NL, 6>(blocks, g, c0, nc, ygg, bvec, sigma2, x_hat, sinr, llr, flags, st); break;
-      default: e = launch_solve<NL, 8>(blocks, g, c0, nc, ygg, bvec, sigma2, x_hat, sinr, llr, flags, st); break;
+      case 2: e = launch_solve<NL, 2>(g, c0, nc, ms, ygg, bvec, sigma2, x_hat, sinr, llr, flags, st); break;
+      case 4: e = launch_solve<NL, 4>(g, c0, nc, ms, ygg, bvec, sigma2, x_hat, sinr, llr, flags, st); break;
+      case 6: e = launch_solve<NL, 6>(g, c0, nc, ms, ygg, bvec, sigma2, x_hat, sinr, llr, flags, st); break;
+      default: e = launch_solve<NL, 8>(g, c0, nc, ms, ygg, bvec, sigma2, x_hat, sinr, llr, flags, st); break;
     }
     if (e != cudaSuccess) return e;
   }

@@ -146,7 +146,7 @@ __device__ __forceinline__ SolveInfo solve_small(GetA getA, const cf (&b)[N], cf
 // Schur factor stay in registers. The large repeated pieces (rows of L21 and T, the Schur
 // update, the columns of N T) are runtime loops over small unrolled bodies: the kernel's code
 // then fits the instruction cache, which the fully unrolled form did not.
-constexpr int kScrL21 = 0, kScrV = 64, kScrD = 72, kScrSlots = 80;
+constexpr int kScrL21 = 0, kScrV = 64, kScrSlots = 72;
 
 template <class GetA, class Scr>
 __device__ __forceinline__ SolveInfo solve16(GetA getA, Scr scr, const cf (&b)[16], cf (&x)[16],
@@ -274,10 +274,10 @@ __device__ __forceinline__ SolveInfo solve16(GetA getA, Scr scr, const cf (&b)[1
       for (int k = 0; k <= i; ++k) p = cfma(Nn(i, k), t[k], p);
       acc2 += cabs2(p);
     }
-    scr.st(kScrD + c, mk(acc2, 0.f));
-  }
 #pragma unroll
-  for (int c = 0; c < B; ++c) d[c] += scr.ld(kScrD + c).x;
+    for (int cc = 0; cc < B; ++cc)  // d[c] += acc2 without indexing registers at run time
+      if (cc == c) d[cc] += acc2;
+  }
   return si;
 }
 
