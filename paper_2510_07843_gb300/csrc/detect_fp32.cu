@@ -389,6 +389,9 @@ cudaError_t launch_solve(const Geo& g, int c0, int nc, int max_segs, const float
     cudaError_t e = cudaFuncSetAttribute(re_solve_fp32_kernel<NL, QM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(re_solve_fp32_kernel<NL, QM>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
     configured = smem;
   }
   dim3 grid((g.n_sc + kSolveThreads - 1) / kSolveThreads, g.n_dsym, nc);
@@ -407,6 +410,9 @@ cudaError_t run_chunks(const Geo& g, int wmax, const Sizes& s, const phy_c32* an
   if (smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(seg_prep_fp32_kernel<NL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(seg_prep_fp32_kernel<NL>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     configured = smem;
   }

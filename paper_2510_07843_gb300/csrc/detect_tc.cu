@@ -16,6 +16,10 @@
 // mbarrier are set up once per CTA. Thread 0 issues the MMAs; every wait is bounded (a timeout
 // bumps an error counter, waits once more and still frees the tensor memory). Operand staging
 // keeps 16 global loads in flight per thread, one RE row per thread so a warp's loads coalesce.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+
 #include "launch.h"
 #include "segment.cuh"
 #include "tc.cuh"
@@ -264,17 +268,27 @@ cudaError_t launch_one(const Geo& g, int c0, int nc, const phy_c32* anchors, con
     cudaError_t e = cudaFuncSetAttribute(seg_prep_tc_kernel<NL, NC, FMT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // all of the unified L1/shared storage as shared memory, so that several CTAs fit
+    e = cudaFuncSetAttribute(seg_prep_tc_kernel<NL, NC, FMT>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev)) !=
         cudaSuccess)
       return e;
-    int b = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, seg_prep_tc_kernel<NL, NC, FMT>,
-                                                           kTcThreads, smem)) != cudaSuccess)
+    // The occupancy query answers 1 for kernels that allocate tensor memory, although several
+    // such CTAs do share an SM; size the persistent grid from shared and tensor memory instead
+    // (CTAs beyond what fits would only wait for a slot).
+    int smem_sm = 0;
+    if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) !=
+        cudaSuccess)
       return e;
-    // tensor memory: 512 columns per SM
+    const int b = smem_sm / (int)(smem + 1024);
     blocks_per_sm = std::max(1, std::min(b, (int)(512 / kTmemCols)));
+    if (std::getenv("PHY_DEBUG"))
+      std::fprintf(stderr, "seg_prep_tc<%d,%d,%u>: smem %zu, occupancy %d, SMs %d, blocks/SM %d\n",
+                   NL, NC, FMT, smem, b, g_num_sms, blocks_per_sm);
   }
   const int n_work = g.n_seg * nc;
   const int grid = std::min(n_work, blocks_per_sm * g_num_sms);
