@@ -48,6 +48,33 @@ def workload(name: str) -> S.SlotSpec:
     raise SystemExit(f"unknown workload {name}")
 
 
+def rank_seed(rank: int) -> int:
+    """Each rank draws its own cells (weak scaling: every rank owns a full batch)."""
+    return 3000 + 1000 * rank
+
+
+def max_over_ranks(ms: float, device=None) -> float:
+    """The slowest rank's time (the job's time); identity without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: int, steps: int, ms: float) -> float:
+    """Units processed by all ranks per second of the slowest rank's time."""
+    return world * units_per_rank * steps / (ms / 1e3)
+
+
+def anchor_bytes(spec: S.SlotSpec) -> int:
+    n_comb = spec.n_sc // 2
+    G = -(-n_comb // spec.occ)
+    return spec.n_cells * len(spec.dmrs_sym) * G * spec.n_layers * spec.n_rx * 8
+
+
 def n_data_res(spec: S.SlotSpec) -> int:
     return spec.n_cells * spec.n_sc * len(spec.data_sym)
 
@@ -130,7 +157,7 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
                 stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -227,6 +254,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="massive", choices=["massive", "carrier", "small"])
+    ap.add_argument("--cells", type=int, default=0,
+                    help="override the workload's cells per GPU (smaller cases for profiling)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "fp16", "bf16"])
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle timing")
     ap.add_argument("--no-e2e", action="store_true")
@@ -237,6 +266,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     spec = workload(args.workload)
+    if args.cells > 0:
+        spec = dataclasses.replace(spec, n_cells=args.cells)
     if args.impl == "reference":
         return run_reference(args, spec, rank, world)
     return run_ours(args, spec, rank, world, local)
@@ -294,7 +325,7 @@ def run_ours(args, spec, rank, world, local):
     build.build()
     phy.load()
     cfg = phy.SlotConfig.from_spec(spec, precision=args.precision)
-    slot = S.make_slot(spec, 3000 + 1000 * rank, keep_h=False)
+    slot = S.make_slot(spec, rank_seed(rank), keep_h=False)
     buf = phy.SlotBuffers(cfg, device=dev)
     buf.Y.copy_(torch.from_numpy(slot.Y))
     buf.pilots.copy_(torch.from_numpy(slot.pilots))
@@ -302,44 +333,55 @@ def run_ours(args, spec, rank, world, local):
     st = torch.cuda.Stream(device=dev)
     n_re = n_data_res(spec)
 
-    def step(e_mid=None):
-        phy.chest(cfg, buf.Y, buf.pilots, buf.anchors, stream=st)
-        if e_mid is not None:
-            e_mid.record(st)
-        phy.detect_anchors(cfg, buf.anchors, buf.Y, buf.sigma2, buf.x_hat, buf.sinr, buf.llr,
-                           buf.flags, buf.workspace, stream=st)
+    split = phy.stage_supported(cfg)
 
+    def step(e1=None, e2=None):
+        phy.chest(cfg, buf.Y, buf.pilots, buf.anchors, stream=st)
+        if e1 is not None:
+            e1.record(st)
+        args_ = (buf.anchors, buf.Y, buf.sigma2, buf.x_hat, buf.sinr, buf.llr, buf.flags,
+                 buf.workspace)
+        if split:  # the two detection kernels as separate calls, timed apart
+            phy.detect_stage(cfg, phy.STAGE_GRAM_MF, *args_, stream=st)
+            if e2 is not None:
+                e2.record(st)
+            phy.detect_stage(cfg, phy.STAGE_SOLVE, *args_, stream=st)
+        else:
+            if e2 is not None:
+                e2.record(st)
+            phy.detect_anchors(cfg, *args_, stream=st)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)  # let the sampler start before the GPU gets busy
     with torch.cuda.stream(st):
         for _ in range(max(args.warmup, 3)):
             step()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    clocks.start()
+    ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(4))
+          for _ in range(args.steps)]
     torch.cuda.synchronize()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(st)
     for i in range(args.steps):
         ev[i][0].record(st)
-        step(ev[i][1])
-        ev[i][2].record(st)
+        step(ev[i][1], ev[i][2])
+        ev[i][3].record(st)
     t_end.record(st)
     torch.cuda.synchronize()
     clk = clocks.stop()
     if world > 1:
         torch.distributed.barrier()
     total_ms = t_start.elapsed_time(t_end)
-    step_ms = [a.elapsed_time(c) for a, b, c in ev]
-    chest_ms = [a.elapsed_time(b) for a, b, c in ev]
-    det_ms = [b.elapsed_time(c) for a, b, c in ev]
-    t_max = torch.tensor([total_ms], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(t_max.item())
+    step_ms = [a.elapsed_time(d) for a, b, c, d in ev]
+    chest_ms = [a.elapsed_time(b) for a, b, c, d in ev]
+    gram_ms = [b.elapsed_time(c) for a, b, c, d in ev]
+    solve_ms = [c.elapsed_time(d) for a, b, c, d in ev]
+    det_ms = [b.elapsed_time(d) for a, b, c, d in ev]
+    total_ms = max_over_ranks(total_ms, dev)
 
     # e2e through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -366,12 +408,10 @@ def run_ours(args, spec, rank, world, local):
             e2e_step()
         b.record(st)
         torch.cuda.synchronize()
-        e_ms = torch.tensor([a.elapsed_time(b)], device=dev)
-        if world > 1:
-            torch.distributed.all_reduce(e_ms, op=torch.distributed.ReduceOp.MAX)
+        e_ms = max_over_ranks(a.elapsed_time(b), dev)
         h2d = Yh.numel() * 8 + Ph.numel() * 8 + sh.numel() * 4
         d2h = lh.numel() * 4 + fh.numel()
-        e2e = {"value": world * n_re * k2 / (float(e_ms.item()) / 1e3), "unit": "REs/s",
+        e2e = {"value": whole_job_rate(world, n_re, k2, e_ms), "unit": "REs/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "api": "phy_slot_run_host (pinned host buffers)"}
 
@@ -390,22 +430,47 @@ def run_ours(args, spec, rank, world, local):
                          f"numpy float64 single thread"}
 
     det_avg = statistics.mean(det_ms)
+    gram_avg, solve_avg = statistics.mean(gram_ms), statistics.mean(solve_ms)
     fl = detect_flops(spec)
     on_tc = args.precision != "fp32"
-    # FP32-pipe work: everything in the FP32 variant, the solve only when the products run on
-    # the tensor cores
-    flops = fl["solve"] + (0.0 if on_tc else fl["products"])
     peak_tf = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
-    achieved_tf = flops / (det_avg * 1e-3) / 1e12
+    peak_src = (f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
+                f"x {SM_MAX_MHZ_NOMINAL:.0f} MHz")
     ab = algorithmic_bytes(spec)
-    det_bytes = ab["y_data"] + ab["outputs"]
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    value = world * n_re * args.steps / (total_ms / 1e3)
+    # per-kernel rooflines. Solve: FP32 ALU work per RE. Gram/matched filter: its products on
+    # the FP32 pipe in the FP32 variant; with tensor cores it streams the grid (HBM bound).
+    solve_roof = {"bound": "alu", "kernel": f"re_solve_fp32_kernel<16,{spec.qm}>",
+                  "achieved": fl["solve"] / (solve_avg * 1e-3) / 1e12, "peak": peak_tf,
+                  "unit": "TFLOP/s", "peak_source": peak_src, "flops_per_launch": fl["solve"],
+                  "ms": solve_avg, "traffic": committed_traffic("re_solve", args.workload)}
+    gram_bytes = ab["y_data"] + anchor_bytes(spec)
+    if on_tc:
+        gram_roof = {"bound": "hbm", "kernel": f"seg_prep_tc_kernel ({args.precision})",
+                     "achieved": gram_bytes / (gram_avg * 1e-3) / 1e9, "peak": hbm_peak,
+                     "unit": "GB/s", "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                     "bytes_per_launch": gram_bytes,
+                     "tensor_flops_per_launch": fl["products"], "ms": gram_avg,
+                     "traffic": committed_traffic("seg_prep_tc", args.workload)}
+    else:
+        gram_roof = {"bound": "alu", "kernel": "seg_prep_fp32_kernel<16>",
+                     "achieved": fl["products"] / (gram_avg * 1e-3) / 1e12, "peak": peak_tf,
+                     "unit": "TFLOP/s", "peak_source": peak_src,
+                     "flops_per_launch": fl["products"], "ms": gram_avg,
+                     "traffic": committed_traffic("seg_prep_fp32", args.workload)}
+    for r in (solve_roof, gram_roof):
+        r["frac"] = r["achieved"] / r["peak"]
+    dominant = solve_roof if solve_avg >= gram_avg else gram_roof
+    roofline = {k: dominant[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+    roofline.update(kernel=dominant["kernel"], peak_source=dominant["peak_source"],
+                    per_kernel={"solve": solve_roof, "gram_mf": gram_roof},
+                    split_stages=bool(split))
+    value = whole_job_rate(world, n_re, args.steps, total_ms)
     line = {
         "metric": METRIC, "value": value, "unit": "REs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -414,22 +479,13 @@ def run_ours(args, spec, rank, world, local):
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99)), "deadline_ms": 0.5,
                        "what": "one step (8-cell batch) on an idle GPU, CUDA events"},
-        "stages_ms": {"chest": statistics.mean(chest_ms), "detect": det_avg},
-        "roofline": {"bound": "alu",
-                     "kernel": "detection stage: segment kernel (" +
-                               ("tcgen05 " + args.precision if on_tc else "FP32") +
-                               ") + re_solve_fp32_kernel, per chunk of cells",
-                     "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                     "frac": achieved_tf / peak_tf,
-                     "peak_source": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
-                                    f"x {SM_MAX_MHZ_NOMINAL:.0f} MHz",
-                     "flops_per_launch": flops,
-                     "tensor_flops_per_launch": fl["products"] if on_tc else 0.0,
-                     "traffic": committed_traffic("detect_" + args.precision, args.workload),
-                     "hbm_view": {"algorithmic_bytes": det_bytes,
-                                  "achieved_gbs": det_bytes / (det_avg * 1e-3) / 1e9,
-                                  "peak_gbs": hbm_peak,
-                                  "frac": det_bytes / (det_avg * 1e-3) / 1e9 / hbm_peak}},
+        "stages_ms": {"chest": statistics.mean(chest_ms), "gram_mf": gram_avg,
+                      "solve": solve_avg, "detect": det_avg},
+        "roofline": roofline,
+        "step_hbm": {"algorithmic_bytes": ab["step"],
+                     "achieved_gbs": ab["step"] / (total_ms / args.steps * 1e-3) / 1e9,
+                     "peak_gbs": hbm_peak,
+                     "frac": ab["step"] / (total_ms / args.steps * 1e-3) / 1e9 / hbm_peak},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": (1 + 2 * detect_chunks(spec)) * args.steps,

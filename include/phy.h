@@ -133,6 +133,26 @@ phy_status phy_detect_anchors(const phy_slot_cfg* cfg, const phy_c32* anchors, c
                               void* stream);
 
 /*
+ * The two stages of phy_detect_anchors, for callers that schedule or time them separately.
+ * PHY_STAGE_GRAM_MF (the covariance products of Fig. 2(b)): per frequency segment the
+ * time-folded Gram blocks of the interpolated channel and, per RE, the matched filter H^H y,
+ * written into the workspace. PHY_STAGE_SOLVE (the LMMSE block of Sec. IV): per RE the Gram
+ * matrix, Cholesky, solves, SINR and LLRs from those intermediates. The stages must run in that
+ * order on the same workspace with no other call in between; both need the whole batch to fit
+ * one chunk of the workspace (true when workspace_bytes >= phy_workspace_size(cfg) and
+ * phy_stage_supported(cfg) is 1).
+ */
+typedef enum { PHY_STAGE_GRAM_MF = 0, PHY_STAGE_SOLVE = 1 } phy_stage;
+
+/* 1 if phy_detect_stage() can run cfg's batch as one chunk with a phy_workspace_size() workspace. */
+int32_t phy_stage_supported(const phy_slot_cfg* cfg);
+
+phy_status phy_detect_stage(const phy_slot_cfg* cfg, int32_t stage, const phy_c32* anchors,
+                            const phy_c32* Y, const float* sigma2, phy_c32* x_hat, float* sinr,
+                            float* llr, uint8_t* flags, void* workspace, size_t workspace_bytes,
+                            void* stream);
+
+/*
  * Max-log LLR demapping of equalised symbols: from x_hat and SINR (as written by
  * phy_slot_run or phy_mmse_detect) computes llr[cell][dsym][sc][layer][qm].
  * REs whose SINR is not positive get zero LLRs.

@@ -123,7 +123,8 @@ phy_status slot_run_fit(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32
   cudaError_t e = launch_chest(g, Y, pilots, anchors, st);
   if (e != cudaSuccess) return PHY_ERR_CUDA;
   e = launch_detect(g, anchors, Y, sigma2, x_hat, sinr, llr, flags,
-                    static_cast<char*>(workspace) + a, workspace_bytes - a, st);
+                    static_cast<char*>(workspace) + a, workspace_bytes - a,
+                    kStageGramMf | kStageSolve, st);
   return cuda_status(e);
 }
 
@@ -192,18 +193,38 @@ phy_status phy_detect_anchors(const phy_slot_cfg* cfg, const phy_c32* anchors, c
                               const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
                               uint8_t* flags, void* workspace, size_t workspace_bytes,
                               void* stream) {
+  return phy_detect_stage(cfg, -1, anchors, Y, sigma2, x_hat, sinr, llr, flags, workspace,
+                          workspace_bytes, stream);
+}
+
+int32_t phy_stage_supported(const phy_slot_cfg* cfg) {
+  Geo g;
+  if (make_geo(cfg, &g) != PHY_OK) return 0;
+  return phy::detect_preferred_chunk(g) == g.n_cells ? 1 : 0;
+}
+
+phy_status phy_detect_stage(const phy_slot_cfg* cfg, int32_t stage, const phy_c32* anchors,
+                            const phy_c32* Y, const float* sigma2, phy_c32* x_hat, float* sinr,
+                            float* llr, uint8_t* flags, void* workspace, size_t workspace_bytes,
+                            void* stream) {
+  // stage -1 (internal): both stages, chunked as the workspace allows
   Geo g;
   phy_status s = make_geo(cfg, &g);
   if (s != PHY_OK) return s;
+  if (stage < -1 || stage > PHY_STAGE_SOLVE) return PHY_ERR_INVALID_ARG;
   if (!anchors || !Y || !sigma2 || !flags || !workspace) return PHY_ERR_INVALID_ARG;
   if (((uintptr_t)workspace) % kAlign) return PHY_ERR_INVALID_ARG;
   if (workspace_bytes < phy_workspace_size(cfg)) return PHY_ERR_NO_MEMORY;
+  if (stage >= 0 && !phy_stage_supported(cfg)) return PHY_ERR_UNSUPPORTED;
   s = check_shape(g);
   if (s != PHY_OK) return s;
+  const int stages = stage < 0 ? (phy::kStageGramMf | phy::kStageSolve)
+                               : (stage == PHY_STAGE_GRAM_MF ? phy::kStageGramMf
+                                                             : phy::kStageSolve);
   const size_t a = align_up(anchor_bytes(g));
   return cuda_status(phy::launch_detect(g, anchors, Y, sigma2, x_hat, sinr, llr, flags,
                                         static_cast<char*>(workspace) + a, workspace_bytes - a,
-                                        (cudaStream_t)stream));
+                                        stages, (cudaStream_t)stream));
 }
 
 phy_status phy_slot_run(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32* pilots,

@@ -403,7 +403,7 @@ cudaError_t launch_solve(const Geo& g, int c0, int nc, int max_segs, const float
 template <int NL>
 cudaError_t run_chunks(const Geo& g, int wmax, const Sizes& s, const phy_c32* anchors,
                        const phy_c32* Y, const float* sigma2, phy_c32* x_hat, float* sinr,
-                       float* llr, uint8_t* flags, void* scratch, cudaStream_t st) {
+                       float* llr, uint8_t* flags, void* scratch, int stages, cudaStream_t st) {
   const PrepLayout f = prep_layout(NL, g.n_dmrs, g.n_rx, wmax);
   const size_t smem = (size_t)f.total * sizeof(cf);
   static size_t configured = 0;
@@ -422,15 +422,16 @@ cudaError_t run_chunks(const Geo& g, int wmax, const Sizes& s, const phy_c32* an
   cf* bvec = reinterpret_cast<cf*>(base + 256 + align256(s.ygg_per_cell * s.chunk));
   for (int c0 = 0; c0 < g.n_cells; c0 += s.chunk) {
     const int nc = std::min(s.chunk, g.n_cells - c0);
-    cudaError_t e;
-    if (g.prec == PHY_PREC_FP32) {
+    cudaError_t e = cudaSuccess;
+    if ((stages & kStageGramMf) && g.prec == PHY_PREC_FP32) {
       dim3 grid(g.n_seg, nc);
       seg_prep_fp32_kernel<NL><<<grid, kPrepThreads, smem, st>>>(g, wmax, c0, anchors, Y, ygg,
                                                                 bvec);
-    } else {
+    } else if (stages & kStageGramMf) {
       e = launch_seg_prep_tc(g, NL, c0, nc, anchors, Y, ygg, bvec, err, st);
       if (e != cudaSuccess) return e;
     }
+    if (!(stages & kStageSolve)) continue;
     const int ms = max_segments_per_block(g);
     switch (g.qm) {
       case 2: e = launch_solve<NL, 2>(g, c0, nc, ms, ygg, bvec, sigma2, x_hat, sinr, llr, flags, st); break;
@@ -476,7 +477,7 @@ int detect_preferred_chunk(const Geo& g) {
 
 cudaError_t launch_detect(const Geo& g, const phy_c32* anchors, const phy_c32* Y,
                           const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
-                          uint8_t* flags, void* scratch, size_t scratch_bytes_avail,
+                          uint8_t* flags, void* scratch, size_t scratch_bytes_avail, int stages,
                           cudaStream_t st) {
   const int wmax = host_max_segment_width(g);
   // the largest chunk of cells (up to the preferred one) whose intermediates fit the scratch
@@ -484,15 +485,21 @@ cudaError_t launch_detect(const Geo& g, const phy_c32* anchors, const phy_c32* Y
   Sizes s = sizes(g, chunk);
   while (chunk > 1 && scratch_bytes(s, chunk) > scratch_bytes_avail) s = sizes(g, --chunk);
   if (scratch_bytes(s, chunk) > scratch_bytes_avail) return cudaErrorInvalidValue;
+  // a single stage is only meaningful when the whole batch is one chunk
+  if (stages != (kStageGramMf | kStageSolve) && chunk != g.n_cells) return cudaErrorInvalidValue;
   switch (s.NL) {
     case 2:
-      return run_chunks<2>(g, wmax, s, anchors, Y, sigma2, x_hat, sinr, llr, flags, scratch, st);
+      return run_chunks<2>(g, wmax, s, anchors, Y, sigma2, x_hat, sinr, llr, flags, scratch,
+                           stages, st);
     case 4:
-      return run_chunks<4>(g, wmax, s, anchors, Y, sigma2, x_hat, sinr, llr, flags, scratch, st);
+      return run_chunks<4>(g, wmax, s, anchors, Y, sigma2, x_hat, sinr, llr, flags, scratch,
+                           stages, st);
     case 8:
-      return run_chunks<8>(g, wmax, s, anchors, Y, sigma2, x_hat, sinr, llr, flags, scratch, st);
+      return run_chunks<8>(g, wmax, s, anchors, Y, sigma2, x_hat, sinr, llr, flags, scratch,
+                           stages, st);
     default:
-      return run_chunks<16>(g, wmax, s, anchors, Y, sigma2, x_hat, sinr, llr, flags, scratch, st);
+      return run_chunks<16>(g, wmax, s, anchors, Y, sigma2, x_hat, sinr, llr, flags, scratch,
+                            stages, st);
   }
 }
 

@@ -20,10 +20,14 @@ cudaError_t launch_chest(const Geo& g, const phy_c32* Y, const phy_c32* pilots, 
                          cudaStream_t st);
 
 // Interpolation + detection + SINR + LLRs from anchors, in the largest chunks of cells whose
-// intermediates fit `scratch_bytes` (cudaErrorInvalidValue if not even one cell fits).
+// intermediates fit `scratch_bytes` (cudaErrorInvalidValue if not even one cell fits). `stages`
+// selects the Gram/matched-filter kernel, the solve kernel or both; a single stage needs the
+// whole batch in one chunk.
+constexpr int kStageGramMf = 1, kStageSolve = 2;
 cudaError_t launch_detect(const Geo& g, const phy_c32* anchors, const phy_c32* Y,
                           const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
-                          uint8_t* flags, void* scratch, size_t scratch_bytes, cudaStream_t st);
+                          uint8_t* flags, void* scratch, size_t scratch_bytes, int stages,
+                          cudaStream_t st);
 
 // phy_slot_run with any workspace that holds the anchors and one cell's intermediates
 // (chunks sized to fit); for callers inside the library.

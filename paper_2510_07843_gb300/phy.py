@@ -43,7 +43,11 @@ _SIGS = {
     "phy_slot_run": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "phy_slot_run_host": (ctypes.c_int, [_P] * 14 + [ctypes.c_size_t, _P]),
     "phy_slot_run_noalloc": (ctypes.c_int, [_P] * 9),
+    "phy_stage_supported": (ctypes.c_int32, [_P]),
+    "phy_detect_stage": (ctypes.c_int, [_P, ctypes.c_int32] + [_P] * 8 + [ctypes.c_size_t, _P]),
 }
+
+STAGE_GRAM_MF, STAGE_SOLVE = 0, 1
 
 # Bytes of the fixed scratch array behind phy_slot_run_noalloc (PHY_NOALLOC_SCRATCH_BYTES).
 NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -153,6 +157,22 @@ def detect_anchors(cfg: SlotConfig, anchors, Y, sigma2, x_hat, sinr, llr, flags,
            load().phy_detect_anchors(ctypes.byref(c), _ptr(anchors), _ptr(Y), _ptr(sigma2),
                                      _ptr(x_hat), _ptr(sinr), _ptr(llr), _ptr(flags),
                                      _ptr(workspace), ws_bytes, _stream(stream)))
+
+
+def stage_supported(cfg: SlotConfig) -> bool:
+    c = cfg.c()
+    return bool(load().phy_stage_supported(ctypes.byref(c)))
+
+
+def detect_stage(cfg: SlotConfig, stage: int, anchors, Y, sigma2, x_hat, sinr, llr, flags,
+                 workspace, stream=None):
+    """One of the two detection stages (STAGE_GRAM_MF then STAGE_SOLVE) on a shared workspace."""
+    c = cfg.c()
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check("phy_detect_stage",
+           load().phy_detect_stage(ctypes.byref(c), stage, _ptr(anchors), _ptr(Y), _ptr(sigma2),
+                                   _ptr(x_hat), _ptr(sinr), _ptr(llr), _ptr(flags),
+                                   _ptr(workspace), ws_bytes, _stream(stream)))
 
 
 def llr_demap(cfg: SlotConfig, x_hat, sinr, llr, stream=None):
