@@ -59,6 +59,7 @@ phy_status make_geo(const phy_slot_cfg* c, Geo* g) {
   t.n_seg = t.G > 1 ? t.G - 1 : 1;
   t.pivot_min = c->pivot_ratio_min;
   t.prec = c->precision;
+  t.refactor = c->fp64_refactor ? 1 : 0;
   int nd = 0;
   for (int s = 0; s < c->n_sym; ++s) {
     bool is_dmrs = false;

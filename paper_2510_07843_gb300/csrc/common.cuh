@@ -23,6 +23,7 @@ struct Geo {
   int n_dsym;   // data symbols
   int n_seg;    // frequency segments (anchor pairs), max(G - 1, 1)
   int prec;     // phy_precision of the Gram and matched-filter products
+  int refactor; // 1: recompute flagged (ill-conditioned) REs in FP64
   float pivot_min;
   int dsym[kMaxSym];    // data symbol index j -> OFDM symbol t
   float tw[kMaxSym];    // weight of the second DMRS estimate at data symbol j

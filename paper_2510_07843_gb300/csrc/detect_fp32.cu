@@ -22,6 +22,7 @@
 
 #include "launch.h"
 #include "segment.cuh"
+#include "refactor64.cuh"
 #include "solver.cuh"
 #include "tc.cuh"
 
@@ -238,6 +239,7 @@ template <int NL, int QM>
 __global__ void __launch_bounds__(kSolveThreads)
     re_solve_fp32_kernel(Geo g, int cell0, int max_segs, const float4* __restrict__ ygg,
                          const cf* __restrict__ bvec, const float* __restrict__ sigma2,
+                         const phy_c32* __restrict__ anchors, const phy_c32* __restrict__ Y,
                          phy_c32* __restrict__ x_hat, float* __restrict__ sinr_out,
                          float* __restrict__ llr_out, uint8_t* __restrict__ flags_out) {
   constexpr int NTRI = NL * (NL + 1) / 2;
@@ -319,10 +321,25 @@ __global__ void __launch_bounds__(kSolveThreads)
     si = solve_small<NL>(getA, b, x, dd);
   }
   fin = fin && si.fin;
-  const bool ok = si.ok && fin;
+  bool ok = si.ok && fin;
   uint8_t flag = 0;
   if (!fin) flag |= 4;
   if (!si.ok || si.pmin < g.pivot_min * si.pmax) flag |= 1;
+  if (g.refactor && (flag & 1) && fin) {
+    Refactor64Out r64;
+    refactor_fp64(g, anchors, Y, cell, jj, k, j, s2, &r64);
+    if (r64.ok) {
+#pragma unroll
+      for (int l = 0; l < NL; ++l) {
+        if (l < nl) {
+          x[l] = r64.x[l];
+          dd[l] = r64.d[l];
+        }
+      }
+      ok = true;
+      flag |= 2;
+    }
+  }
   flags_out[ridx] = flag;
   // rolled on purpose: one copy of the per-layer epilogue keeps the kernel's code small
 #pragma unroll 1
@@ -381,8 +398,9 @@ size_t scratch_bytes(const Sizes& s, int chunk) {
 
 template <int NL, int QM>
 cudaError_t launch_solve(const Geo& g, int c0, int nc, int max_segs, const float4* ygg,
-                         const cf* bvec, const float* sigma2, phy_c32* x_hat, float* sinr,
-                         float* llr, uint8_t* flags, cudaStream_t st) {
+                         const cf* bvec, const float* sigma2, const phy_c32* anchors,
+                         const phy_c32* Y, phy_c32* x_hat, float* sinr, float* llr,
+                         uint8_t* flags, cudaStream_t st) {
   const size_t smem = solve_smem_bytes(NL, max_segs);
   static size_t configured = 0;
   if (smem > 48 * 1024 && smem > configured) {
@@ -395,8 +413,8 @@ cudaError_t launch_solve(const Geo& g, int c0, int nc, int max_segs, const float
     configured = smem;
   }
   dim3 grid((g.n_sc + kSolveThreads - 1) / kSolveThreads, g.n_dsym, nc);
-  re_solve_fp32_kernel<NL, QM><<<grid, kSolveThreads, smem, st>>>(g, c0, max_segs, ygg, bvec,
-                                                                  sigma2, x_hat, sinr, llr, flags);
+  re_solve_fp32_kernel<NL, QM><<<grid, kSolveThreads, smem, st>>>(
+      g, c0, max_segs, ygg, bvec, sigma2, anchors, Y, x_hat, sinr, llr, flags);
   return cudaGetLastError();
 }
 
@@ -434,10 +452,14 @@ cudaError_t run_chunks(const Geo& g, int wmax, const Sizes& s, const phy_c32* an
     if (!(stages & kStageSolve)) continue;
     const int ms = max_segments_per_block(g);
     switch (g.qm) {
-      case 2: e = launch_solve<NL, 2>(g, c0, nc, ms, ygg, bvec, sigma2, x_hat, sinr, llr, flags, st); break;
-      case 4: e = launch_solve<NL, 4>(g, c0, nc, ms, ygg, bvec, sigma2, x_hat, sinr, llr, flags, st); break;
-      case 6: e = launch_solve<NL, 6>(g, c0, nc, ms, ygg, bvec, sigma2, x_hat, sinr, llr, flags, st); break;
-      default: e = launch_solve<NL, 8>(g, c0, nc, ms, ygg, bvec, sigma2, x_hat, sinr, llr, flags, st); break;
+      case 2: e = launch_solve<NL, 2>(g, c0, nc, ms, ygg, bvec, sigma2, anchors, Y, x_hat, sinr, llr,
+                                           flags, st); break;
+      case 4: e = launch_solve<NL, 4>(g, c0, nc, ms, ygg, bvec, sigma2, anchors, Y, x_hat, sinr, llr,
+                                           flags, st); break;
+      case 6: e = launch_solve<NL, 6>(g, c0, nc, ms, ygg, bvec, sigma2, anchors, Y, x_hat, sinr, llr,
+                                           flags, st); break;
+      default: e = launch_solve<NL, 8>(g, c0, nc, ms, ygg, bvec, sigma2, anchors, Y, x_hat, sinr, llr,
+                                           flags, st); break;
     }
     if (e != cudaSuccess) return e;
   }

@@ -33,7 +33,8 @@ __device__ __forceinline__ bool chol_packed(cf (&a)[N * (N + 1) / 2], float (&ri
     float d = a[tri(j, j)].x;
 #pragma unroll
     for (int k = 0; k < j; ++k) d -= cabs2(a[tri(j, k)]);
-    fin = fin && isfinite(d);
+    // a non-finite pivot after an earlier failed one is a consequence, not bad input
+    if (ok) fin = fin && isfinite(d);
     ok = ok && (d > 0.f) && (d < 3.0e38f);
     pmin = fminf(pmin, d);
     pmax = fmaxf(pmax, d);

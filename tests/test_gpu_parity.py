@@ -273,3 +273,26 @@ def test_tensor_core_variants_vs_oracle(dev, name, prec):
     assert m["llr_norm_max"] <= lim[2], m
     assert m["bit_disagree"] <= lim[3], m
     assert abs(m["ber"] - m["ber_ref"]) <= 0.02 * m["ber_ref"] + 2e-4, m
+
+
+def test_fp64_refactor_of_ill_conditioned_res(dev):
+    """Nearly collinear layers: kappa(H) ~ 3e3, so kappa(A) ~ 1e7 trips the 1e-6 pivot-ratio flag.
+    FP32 loses ~kappa(A) u of accuracy; the FP64 recomputation from the (FP32) LS anchors keeps
+    ~kappa(H) u. Flag bit 0 marks the REs on both sides; bit 1 marks the FP64 recomputation."""
+    rng = np.random.default_rng(71)
+    nr, nl = 4, 4
+    h = (rng.standard_normal((nr, nl)) + 1j * rng.standard_normal((nr, nl))) / math.sqrt(2)
+    h[:, 1] = h[:, 0] + 3e-4 * (rng.standard_normal(nr) + 1j * rng.standard_normal(nr))
+    spec = S.SlotSpec(n_prb=4, n_rx=nr, n_layers=nl, qm=4, dmrs_sym=(2, 11), snr_db=120.0)
+    ch = np.broadcast_to(h, (1, 14, spec.n_sc, nr, nl))
+    sl = S.make_slot(spec, 72, noise=False, channel=ch)
+    ref = oracle_dense(spec, sl)
+    assert np.all(ref["flags"] & 1)
+    plain = gpu_slot(spec, sl, dev)
+    fixed = gpu_slot(spec, sl, dev, fp64_refactor=True)
+    assert np.all(plain["flags"] & 1) and not np.any(plain["flags"] & 2)
+    assert np.all((fixed["flags"] & 3) == 3)
+    e32 = rel_fro(plain["x_hat"], ref["x_hat"])
+    e64 = rel_fro(fixed["x_hat"], ref["x_hat"])
+    print("ill-conditioned x_hat rel err: fp32", e32, "fp64 refactor", e64)
+    assert e64 < 1e-2 and e64 < e32 / 10
