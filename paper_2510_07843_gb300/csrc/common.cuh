@@ -173,16 +173,17 @@ __device__ __forceinline__ void qam_llr(cf xt, float s2eff, float* llr) {
 
 // Per-layer SINR bookkeeping from d = (A^-1)_kk.
 struct LayerOut {
-  float sinr, mu, s2eff;
+  float sinr, inv_mu, s2eff;  // SINR, 1 / mu (unbiasing gain), effective noise e / mu
 };
 __device__ __forceinline__ LayerOut layer_stats(float sigma2, float dkk) {
   float e = sigma2 * dkk;
   e = fminf(fmaxf(e, 1e-30f), 1.f - 1e-7f);
   float mu = 1.f - e;
   LayerOut o;
-  o.mu = mu;
-  o.sinr = mu / e;
-  o.s2eff = e / mu;
+  // correctly rounded reciprocals, then products (one rounding more than a division)
+  o.inv_mu = __frcp_rn(mu);
+  o.sinr = mu * __frcp_rn(e);
+  o.s2eff = e * o.inv_mu;
   return o;
 }
 

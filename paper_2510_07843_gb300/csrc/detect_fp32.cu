@@ -292,13 +292,28 @@ __global__ void __launch_bounds__(kSolveThreads)
   const float s2 = sigma2[cell];
   const float be0 = seg_beta(g, j, k, 0), be1 = seg_beta(g, j, k, 1);
   const float4* yp = ys + (size_t)(j - s0) * NTRI * 2;
+  // weight products w_g(comb l) w_g'(comb m) for the four comb pairs (cl, cm), built once
+  float cw[2][2][4];
+#pragma unroll
+  for (int cl = 0; cl < 2; ++cl)
+#pragma unroll
+    for (int cm = 0; cm < 2; ++cm) {
+      const float bl = cl ? be1 : be0, bm = cm ? be1 : be0;
+      cw[cl][cm][0] = (1.f - bl) * (1.f - bm);
+      cw[cl][cm][1] = (1.f - bl) * bm;
+      cw[cl][cm][2] = bl * (1.f - bm);
+      cw[cl][cm][3] = bl * bm;
+    }
   auto getA = [&](int l, int m) -> cf {
     if (l >= nl || m >= nl) return (l == m) ? mk(1.f, 0.f) : mk(0.f, 0.f);
-    const float bl = (l & 1) ? be1 : be0, bm = (m & 1) ? be1 : be0;
-    const float wl0 = 1.f - bl, wm0 = 1.f - bm;
     const int e = tri(l, m);
     const float4 p = yp[2 * e], q = yp[2 * e + 1];
-    const float c00 = wl0 * wm0, c01 = wl0 * bm, c10 = bl * wm0, c11 = bl * bm;
+    // comb parities are compile-time except in the solver's rolled row loop (a select there)
+    const bool ol = l & 1, om = m & 1;
+    const float c00 = ol ? (om ? cw[1][1][0] : cw[1][0][0]) : (om ? cw[0][1][0] : cw[0][0][0]);
+    const float c01 = ol ? (om ? cw[1][1][1] : cw[1][0][1]) : (om ? cw[0][1][1] : cw[0][0][1]);
+    const float c10 = ol ? (om ? cw[1][1][2] : cw[1][0][2]) : (om ? cw[0][1][2] : cw[0][0][2]);
+    const float c11 = ol ? (om ? cw[1][1][3] : cw[1][0][3]) : (om ? cw[0][1][3] : cw[0][0][3]);
     cf a;
     a.x = fmaf(c00, p.x, fmaf(c01, p.z, fmaf(c10, q.x, c11 * q.z)));
     a.y = fmaf(c00, p.y, fmaf(c01, p.w, fmaf(c10, q.y, c11 * q.w)));
@@ -341,21 +356,37 @@ __global__ void __launch_bounds__(kSolveThreads)
     }
   }
   flags_out[ridx] = flag;
-  // rolled on purpose: one copy of the per-layer epilogue keeps the kernel's code small
-#pragma unroll 1
-  for (int l = 0; l < nl; ++l) {
-    const LayerOut o = layer_stats(s2, dd[l]);
+  auto epilogue = [&](int l, cf xl, float dl) {
+    const LayerOut o = layer_stats(s2, dl);
     const size_t li = ridx * nl + l;
     if (ok) {
-      if (x_hat) st(x_hat + li, x[l]);
+      if (x_hat) st(x_hat + li, xl);
       if (sinr_out) sinr_out[li] = o.sinr;
-      if (llr_out) store_llr<QM>(llr_out + li * QM, (1.f / o.mu) * x[l], o.s2eff);
+      if (llr_out) store_llr<QM>(llr_out + li * QM, o.inv_mu * xl, o.s2eff);
     } else {
       if (x_hat) st(x_hat + li, mk(0.f, 0.f));
       if (sinr_out) sinr_out[li] = 0.f;
       if (llr_out)
         for (int q = 0; q < QM; ++q) llr_out[li * QM + q] = 0.f;
     }
+  };
+  if constexpr (NL == 16) {
+    // Rolled on purpose: one copy of the per-layer epilogue keeps the kernel's code small. The
+    // loop index is dynamic, so x and d go through this thread's shared scratch (free after
+    // the solve) rather than a register array that would be demoted to local memory.
+    extern __shared__ __align__(16) unsigned char solve_smem[];
+    const SmemScratch sc{reinterpret_cast<cf*>(solve_smem) + threadIdx.x};
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      sc.st(l, x[l]);
+      sc.st(NL + l, mk(dd[l], 0.f));
+    }
+#pragma unroll 1
+    for (int l = 0; l < nl; ++l) epilogue(l, sc.ld(l), sc.ld(NL + l).x);
+  } else {
+#pragma unroll
+    for (int l = 0; l < NL; ++l)
+      if (l < nl) epilogue(l, x[l], dd[l]);
   }
 }
 
