@@ -13,7 +13,8 @@
  * Conventions for every entry point:
  *  - All array arguments are DEVICE pointers owned by the caller, except where a name ends in
  *    _host. The library never allocates device memory; scratch space is a caller-provided
- *    workspace of phy_workspace_size() bytes (256-byte aligned). Y must be 16-byte aligned.
+ *    workspace of phy_workspace_size() bytes (256-byte aligned). Y and caller-supplied anchors
+ *    must be 16-byte aligned.
  *  - Work is enqueued on `stream` (a cudaStream_t passed as void*, NULL = legacy default stream)
  *    and the call returns without synchronising. Results are valid once the stream reaches
  *    the point after the call.
@@ -74,7 +75,9 @@ typedef enum {
 
 typedef enum {
   PHY_PREC_FP32 = 0,    /* every product on FP32 CUDA cores */
-  PHY_PREC_TC_TF32 = 1, /* Gram and H^H y products on tcgen05 tensor cores, TF32 in, FP32 acc */
+  /* Gram and H^H y products on tcgen05 tensor cores, TF32 in, FP32 accumulation. The operands
+     are streamed by TMA tensor copies, which need an even n_rx (PHY_ERR_UNSUPPORTED otherwise). */
+  PHY_PREC_TC_TF32 = 1,
   PHY_PREC_TC_BF16 = 2, /* same with BF16 operands */
   PHY_PREC_TC_FP16 = 3  /* same with FP16 operands */
 } phy_precision;

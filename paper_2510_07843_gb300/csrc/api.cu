@@ -89,6 +89,7 @@ phy_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PHY_OK : PHY_E
 
 phy_status check_shape(const Geo& g) {
   if (phy::fused_fp32_smem_bytes(g) > 227 * 1024) return PHY_ERR_UNSUPPORTED;
+  if (g.prec != PHY_PREC_FP32 && !phy::seg_prep_tc_supported(g)) return PHY_ERR_UNSUPPORTED;
   return PHY_OK;
 }
 
@@ -214,7 +215,8 @@ phy_status phy_detect_stage(const phy_slot_cfg* cfg, int32_t stage, const phy_c3
   if (s != PHY_OK) return s;
   if (stage < -1 || stage > PHY_STAGE_SOLVE) return PHY_ERR_INVALID_ARG;
   if (!anchors || !Y || !sigma2 || !flags || !workspace) return PHY_ERR_INVALID_ARG;
-  if (((uintptr_t)workspace) % kAlign) return PHY_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace) % kAlign || ((uintptr_t)Y % 16) || ((uintptr_t)anchors % 16))
+    return PHY_ERR_INVALID_ARG;
   if (workspace_bytes < phy_workspace_size(cfg)) return PHY_ERR_NO_MEMORY;
   if (stage >= 0 && !phy_stage_supported(cfg)) return PHY_ERR_UNSUPPORTED;
   s = check_shape(g);

@@ -330,7 +330,6 @@ __global__ void __launch_bounds__(kSolveThreads)
   }
   SolveInfo si;
   if constexpr (NL == 16) {
-    extern __shared__ __align__(16) unsigned char solve_smem[];
     si = solve16(getA, SmemScratch{reinterpret_cast<cf*>(solve_smem) + threadIdx.x}, b, x, dd);
   } else {
     si = solve_small<NL>(getA, b, x, dd);
@@ -374,7 +373,6 @@ __global__ void __launch_bounds__(kSolveThreads)
     // Rolled on purpose: one copy of the per-layer epilogue keeps the kernel's code small. The
     // loop index is dynamic, so x and d go through this thread's shared scratch (free after
     // the solve) rather than a register array that would be demoted to local memory.
-    extern __shared__ __align__(16) unsigned char solve_smem[];
     const SmemScratch sc{reinterpret_cast<cf*>(solve_smem) + threadIdx.x};
 #pragma unroll
     for (int l = 0; l < NL; ++l) {

@@ -12,13 +12,26 @@
 // into the per-symbol Gram blocks (as the FP32 kernel does) and V into the matched filter
 // b = sum over corners of the interpolation weights times V, per RE, straight from TMEM.
 //
-// Persistent CTAs of 128 threads loop over (segment, cell) items; tensor memory and the
-// mbarrier are set up once per CTA. Thread 0 issues the MMAs; every wait is bounded (a timeout
-// bumps an error counter, waits once more and still frees the tensor memory). Operand staging
-// keeps 16 global loads in flight per thread, one RE row per thread so a warp's loads coalesce.
+// One persistent CTA per SM, warp-specialised:
+//  - a producer warp streams the received grid through a ring of shared-memory stages with TMA
+//    tensor copies (one box = 16 subcarriers x all antennas of one data symbol) and the anchors
+//    of the next segment's corners, running ahead of the consumers by up to the ring's depth;
+//  - eight converter warps turn anchors into the CC operand and boxes into the RE-tile operand
+//    (conversion to the MMA type and K-major core-matrix order); one of their threads issues
+//    the MMAs;
+//  - four drain warps fold X into the Gram blocks and the accumulators into the matched filter.
+// RE tiles are whole data symbols of the segment (floor(128 / W) of them), double-buffered in
+// shared and tensor memory, so that converting one tile overlaps the MMA of the previous one
+// and the drain of the one before. The groups hand over through mbarriers.
+// Every wait is bounded: on a timeout a group agrees (barrier with OR-reduction), bumps an
+// error counter and leaves; outstanding copies and MMAs are waited for before the CTA ends.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
+#include <mutex>
 
 #include "launch.h"
 #include "segment.cuh"
@@ -28,11 +41,21 @@ namespace phy {
 
 namespace {
 
-constexpr int kTcThreads = 128;
-constexpr int kRows = 128;  // UMMA M and rows of every operand tile
-constexpr int kK = 128;     // K elements per operand row: (re, im) x 64 antennas
-constexpr uint32_t kTmemCols = 128;
-constexpr uint32_t kWaitIters = 1u << 22;
+constexpr int kConvWarps = 8;   // converters: anchors -> CC, boxes -> RE tiles, MMA issue
+constexpr int kDrainWarps = 4;  // drain: X -> Gram blocks, accumulators -> matched filter
+constexpr int kConv = 32 * kConvWarps;
+constexpr int kProducerWarp = kConvWarps + kDrainWarps;
+constexpr int kTcThreads = 32 * (kProducerWarp + 1);
+constexpr int kRows = 128;                 // UMMA M and rows of every operand tile
+constexpr int kK = 128;                    // K elements per operand row: (re, im) x 64 antennas
+constexpr int kBoxSc = 16;                 // subcarriers per received-grid box
+constexpr uint32_t kStageBytes = kBoxSc * 8 * 64;  // one box with 64 antennas
+constexpr int kBoxItems = 16 * (kBoxSc / 2);       // converter work items per box
+constexpr int kBoxWarps = kBoxItems / 32;          // converter warps per box
+constexpr uint32_t kRingBytes = 48 * 1024;         // ring of boxes (FP16/BF16 tiles)
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kColX = 0, kColMf = 128;  // MF accumulator b at kColMf + 128 b
+constexpr uint32_t kWaitIters = 1u << 20;  // polls of up to ~1 us each
 
 template <uint32_t FMT>
 struct Layout {
@@ -46,6 +69,31 @@ struct Layout {
     const int bk = kel * kEs;
     return ((bk >> 4) * (kRows / 8) + (row >> 3)) * 128 + (row & 7) * 16 + (bk & 15);
   }
+  // RE-tile operand buffers and ring stages: TF32 tiles are twice as large, so that variant
+  // keeps one tile buffer and a shallower ring to stay inside 227 KB.
+  static constexpr int kYBufs = FMT == tc::kFmtTF32 ? 1 : 2;
+  static constexpr int kStages = (FMT == tc::kFmtTF32 ? 32 * 1024 : kRingBytes) / kStageBytes;
+};
+
+constexpr int nxp_of(int nx) { return nx <= 16 ? 16 : (nx + 15) / 16 * 16; }
+constexpr size_t up128(size_t v) { return (v + 127) & ~(size_t)127; }
+
+// Shared-memory map: CC tile | RE tiles | X (FP32) | anchor corners | ring | barriers.
+template <int NL, int NC, uint32_t FMT>
+struct Smem {
+  using Lay = Layout<FMT>;
+  static constexpr int NXP = nxp_of(NC * NL);
+  static constexpr size_t kCc = 0;
+  static constexpr size_t kYop = kCc + Lay::kTileBytes;
+  static constexpr size_t kXs = kYop + (size_t)Lay::kYBufs * Lay::kTileBytes;
+  static constexpr size_t kAnch = kXs + up128((size_t)NXP * (NXP + 2) * 8);
+  static constexpr size_t kCorner = up128((size_t)NL * 64 * 8);  // one corner's [l][r] block
+  static constexpr size_t kRing = kAnch + NC * kCorner;
+  static constexpr size_t kBars = kRing + (size_t)Lay::kStages * kStageBytes;
+  // full[S], empty[S], anchors full / empty, X done / drained, MF done[2] / drained[2]
+  static constexpr int kNumBars = 2 * Lay::kStages + 8;
+  static constexpr size_t kMisc = kBars + 8 * kNumBars;  // TMEM address, consumed counts
+  static constexpr size_t kTotal = kMisc + 16;
 };
 
 template <uint32_t FMT>
@@ -56,16 +104,21 @@ __device__ __forceinline__ void store_pair(unsigned char* p, float a, float b) {
     *reinterpret_cast<uint32_t*>(p) = tc::Elem<FMT>::pack(a, b);
 }
 
-constexpr int nxp_of(int nx) { return nx <= 16 ? 16 : (nx + 15) / 16 * 16; }
-
-// CC tile, then one region that holds X in FP32 and afterwards the RE tile, then the barrier.
-template <int NL, int NC, uint32_t FMT>
-constexpr size_t tc_smem_bytes() {
-  constexpr int NXP = nxp_of(NC * NL);
-  constexpr size_t xs_bytes = (size_t)NXP * (NXP + 2) * 8;
-  constexpr size_t r2 =
-      (size_t)Layout<FMT>::kTileBytes > xs_bytes ? Layout<FMT>::kTileBytes : xs_bytes;
-  return Layout<FMT>::kTileBytes + ((r2 + 15) & ~(size_t)15) + 16;
+// Four consecutive antennas (8 K elements) of one operand row: one 16-byte chunk in FP16/BF16,
+// two in TF32.
+template <uint32_t FMT>
+__device__ __forceinline__ void store_quad(unsigned char* tile, int row, int q, const cf (&v)[4]) {
+  using Lay = Layout<FMT>;
+  if constexpr (FMT == tc::kFmtTF32) {
+    const uint2 a = tc::Elem<FMT>::pack(v[0].x, v[0].y), b = tc::Elem<FMT>::pack(v[1].x, v[1].y);
+    const uint2 c = tc::Elem<FMT>::pack(v[2].x, v[2].y), d = tc::Elem<FMT>::pack(v[3].x, v[3].y);
+    *reinterpret_cast<uint4*>(tile + Lay::off(row, 8 * q)) = make_uint4(a.x, a.y, b.x, b.y);
+    *reinterpret_cast<uint4*>(tile + Lay::off(row, 8 * q + 4)) = make_uint4(c.x, c.y, d.x, d.y);
+  } else {
+    *reinterpret_cast<uint4*>(tile + Lay::off(row, 8 * q)) =
+        make_uint4(tc::Elem<FMT>::pack(v[0].x, v[0].y), tc::Elem<FMT>::pack(v[1].x, v[1].y),
+                   tc::Elem<FMT>::pack(v[2].x, v[2].y), tc::Elem<FMT>::pack(v[3].x, v[3].y));
+  }
 }
 
 // Issues one K-loop of MMAs (A and B tiles in the same layout) and commits to the barrier.
@@ -84,216 +137,420 @@ __device__ __forceinline__ void gemm_issue(uint32_t tmem, const unsigned char* a
   tc::mma_commit(bar);
 }
 
-// Makes staged shared memory visible to the tensor core and synchronises the CTA.
-__device__ __forceinline__ void publish_smem() {
-  tc::fence_proxy_async();
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
+// One (segment, cell) work item and its RE tiles: whole data symbols of the segment. Boxes
+// start at the even subcarrier lo2 <= lo (TMA needs 16-byte aligned inner coordinates).
+struct Item {
+  int j, lc, cell, lo, lo2, W, spt, ntile, nb;  // nb: boxes per symbol
+};
+__device__ __forceinline__ Item item_of(const Geo& g, int w, int cell0) {
+  Item it;
+  it.j = w % g.n_seg;
+  it.lc = w / g.n_seg;
+  it.cell = cell0 + it.lc;
+  int hi;
+  segment_range(g, it.j, it.lo, hi);
+  it.W = hi - it.lo;  // <= 64 (host-checked), so spt >= 2
+  it.spt = kRows / it.W;
+  it.ntile = (g.n_dsym + it.spt - 1) / it.spt;
+  it.lo2 = it.lo & ~1;
+  it.nb = (hi - it.lo2 + kBoxSc - 1) / kBoxSc;
+  return it;
+}
+__device__ __forceinline__ int tile_syms(const Geo& g, const Item& it, int t) {
+  return min(it.spt, g.n_dsym - t * it.spt);
 }
 
 template <int NL, int NC, uint32_t FMT>
-__global__ void __launch_bounds__(kTcThreads)
-    seg_prep_tc_kernel(Geo g, int cell0, int nc, const phy_c32* __restrict__ anchors,
-                       const phy_c32* __restrict__ Y, float4* __restrict__ ygg,
-                       cf* __restrict__ bvec, unsigned* __restrict__ err) {
+__global__ void __launch_bounds__(kTcThreads, 1)
+    seg_prep_tc_kernel(const __grid_constant__ CUtensorMap tmY,
+                       const __grid_constant__ CUtensorMap tmA, Geo g, int cell0, int nc,
+                       float4* __restrict__ ygg, cf* __restrict__ bvec,
+                       unsigned* __restrict__ err) {
   using Lay = Layout<FMT>;
+  using Sm = Smem<NL, NC, FMT>;
+  constexpr int S = Lay::kStages;
   constexpr int NX = NC * NL;
-  constexpr int NXP = nxp_of(NX);
+  constexpr int NXP = Sm::NXP;
   constexpr int xs = NXP + 2;
   constexpr int NTRI = NL * (NL + 1) / 2;
   static_assert(2 * NXP <= kRows, "corner-layer count too large for one tile");
+  static_assert(Sm::kTotal <= 227 * 1024, "shared memory map too large");
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* cc = smem;
-  unsigned char* r2 = smem + Lay::kTileBytes;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + tc_smem_bytes<NL, NC, FMT>() - 16);
-  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
-  cf* Xs = reinterpret_cast<cf*>(r2);
-  unsigned char* yt = r2;
+  unsigned char* cc = smem + Sm::kCc;
+  cf* Xs = reinterpret_cast<cf*>(smem + Sm::kXs);
+  unsigned char* anch = smem + Sm::kAnch;
+  unsigned char* ring = smem + Sm::kRing;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Sm::kBars);
+  uint64_t* empty = full + S;
+  uint64_t* a_full = empty + S;
+  uint64_t* a_empty = a_full + 1;
+  uint64_t* x_bar = a_full + 2;
+  uint64_t* x_free = a_full + 3;
+  uint64_t* mf_bar = a_full + 4;     // [2]
+  uint64_t* tmem_free = a_full + 6;  // [2]
+  uint32_t* misc = reinterpret_cast<uint32_t*>(smem + Sm::kMisc);  // TMEM address
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nr = g.n_rx, nl = g.n_layers, nds = g.n_dsym;
+  const int n_work = g.n_seg * nc;
+  const uint32_t y_box_bytes = (uint32_t)nr * kBoxSc * 8;
+  const uint32_t a_box_bytes = (uint32_t)nl * nr * 8;
 
   if (tid == 0) {
-    tc::mbar_init(bar, 1);
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(full + s, 1);
+      tc::mbar_init(empty + s, kBoxWarps);  // arrivals: the converter warps of a box
+    }
+    tc::mbar_init(a_full, 1);
+    tc::mbar_init(a_empty, kConvWarps);
+    tc::mbar_init(x_bar, 1);
+    tc::mbar_init(x_free, 4);  // arrivals: the four drain warps
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(mf_bar + b, 1);
+      tc::mbar_init(tmem_free + b, 4);
+    }
     tc::mbar_fence_init();
   }
-  if (warp == 0) tc::tmem_alloc(slot, kTmemCols);
+  if (warp == 0) tc::tmem_alloc(misc, kTmemCols);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  const uint32_t tmem = *slot;
-  const uint32_t tmem_warp = tmem + ((uint32_t)(32 * warp) << 16);
-  uint32_t phase = 0;
-  bool fail = false;
+  const uint32_t tmem = misc[0];
 
-  const int n_work = g.n_seg * nc;
-  for (int w = blockIdx.x; w < n_work && !fail; w += gridDim.x) {
-    const int j = w % g.n_seg, lc = w / g.n_seg, cell = cell0 + lc;
-    int lo, hi;
-    segment_range(g, j, lo, hi);
-    const int W = hi - lo, nre = W * nds;
-
-    // ---- CC = [C ; iC]
-    {
-      const int g1 = seg_g1(g, j);
-#pragma unroll 8
-      for (int it = 0; it < NXP * 64 / kTcThreads; ++it) {
-        const int e = tid + it * kTcThreads;
-        const int r = e & 63, c = e >> 6;
-        const int corner = c / NL, l = c % NL;
-        cf v = mk(0.f, 0.f);
-        if (c < NX && l < nl && r < nr) {
-          const int d = corner >> 1, grp = (corner & 1) ? g1 : j;
-          v = ld(anchors + ((((size_t)cell * g.n_dmrs + d) * g.G + grp) * nl + l) * nr + r);
+  if (warp == kProducerWarp) {
+    // ------------------------------------------------------------ producer
+    uint32_t nbox = 0, nitem = 0;  // boxes and anchor sets issued
+    if (lane == 0) {
+      bool ok = true;
+      for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
+        const Item it = item_of(g, w, cell0);
+        if (nitem > 0) ok = tc::mbar_wait_sleep(a_empty, (nitem - 1) & 1, kWaitIters);
+        if (!ok) break;
+        tc::mbar_arrive_expect_tx(a_full, NC * a_box_bytes);
+        const int g1 = seg_g1(g, it.j);
+        for (int corner = 0; corner < NC; ++corner) {
+          const int d = corner >> 1, grp = (corner & 1) ? g1 : it.j;
+          tc::tma_load_3d(anch + corner * Sm::kCorner, &tmA, 0, 0,
+                          (it.cell * g.n_dmrs + d) * g.G + grp, a_full);
         }
-        store_pair<FMT>(cc + Lay::off(c, 2 * r), v.x, v.y);
-        store_pair<FMT>(cc + Lay::off(NXP + c, 2 * r), -v.y, v.x);
-      }
-    }
-    publish_smem();
-
-    // ---- X = C^H C
-    if (tid == 0) gemm_issue<FMT>(tmem, cc, cc, tc::instr_desc(FMT, kRows, NXP), bar);
-    fail = !tc::mbar_wait(bar, phase, kWaitIters);
-    phase ^= 1;
-    fail = __syncthreads_or(fail);
-    if (fail) break;
-    tc::fence_after_sync();
-    {
-      const int row = 32 * warp + lane;
-#pragma unroll
-      for (int c0 = 0; c0 < NXP; c0 += 32) {
-        float v[32];
-        tc::tmem_ld32(tmem_warp + c0, v);
-        if (row < 2 * NXP) {
-          const int c = row % NXP, part = row / NXP;
-#pragma unroll
-          for (int q = 0; q < 32; ++q)
-            if (c0 + q < NXP) reinterpret_cast<float*>(Xs + c * xs + c0 + q)[part] = v[q];
-        }
-      }
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    auto Xget = [&](int i, int k) -> cf { return Xs[i * xs + k]; };
-    form_gram_blocks<NL, kTcThreads>(g, Xget,
-                                     ygg + (((size_t)lc * g.n_seg + j) * nds) * NTRI * 2, tid);
-    __syncthreads();  // Xs shares its space with the RE tiles below
-
-    // ---- matched filter, 128 REs per tile, one RE row per thread
-    const int ntile = (nre + kRows - 1) / kRows;
-    for (int t = 0; t < ntile; ++t) {
-      const int re = kRows * t + tid;
-      const bool valid = re < nre;
-      const int jj = valid ? re / W : 0, kk = valid ? re - jj * W : 0, k = lo + kk;
-      {
-        const phy_c32* yp = Y + ((size_t)cell * g.n_sym + g.dsym[jj]) * nr * g.n_sc + k;
-#pragma unroll 1
-        for (int r0 = 0; r0 < 64; r0 += 16) {
-          cf v[16];
-#pragma unroll
-          for (int q = 0; q < 16; ++q)
-            v[q] = (valid && r0 + q < nr) ? ld(yp + (size_t)(r0 + q) * g.n_sc) : mk(0.f, 0.f);
-#pragma unroll
-          for (int q = 0; q < 16; ++q) store_pair<FMT>(yt + Lay::off(tid, 2 * (r0 + q)), v[q].x, v[q].y);
-        }
-      }
-      publish_smem();
-      if (tid == 0) gemm_issue<FMT>(tmem, yt, cc, tc::instr_desc(FMT, kRows, 2 * NXP), bar);
-      fail = !tc::mbar_wait(bar, phase, kWaitIters);
-      phase ^= 1;
-      fail = __syncthreads_or(fail);
-      if (fail) break;
-      tc::fence_after_sync();
-      // this thread's TMEM lane is its RE row
-      const int jr = 32 * warp + lane;
-      const int re2 = kRows * t + jr;
-      const bool valid2 = re2 < nre;
-      const int jj2 = valid2 ? re2 / W : 0, kk2 = valid2 ? re2 - jj2 * W : 0, k2 = lo + kk2;
-      const float t1 = g.tw[jj2], t0 = 1.f - t1;
-      const float be0 = seg_beta(g, j, k2, 0), be1 = seg_beta(g, j, k2, 1);
-      float bre[NL], bim[NL];
-#pragma unroll
-      for (int l = 0; l < NL; ++l) bre[l] = bim[l] = 0.f;
-#pragma unroll
-      for (int part = 0; part < 2; ++part) {
-#pragma unroll
-        for (int c0 = 0; c0 < NXP; c0 += 32) {
-          float v[32];
-          tc::tmem_ld32(tmem_warp + part * NXP + c0, v);
-#pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            const int c = c0 + q;
-            if (c < NX) {
-              const int corner = c / NL, l = c % NL;
-              const float be = (l & 1) ? be1 : be0;
-              const float wt = ((corner >> 1) ? t1 : t0) * ((corner & 1) ? be : 1.f - be);
-              if (part == 0)
-                bre[l] = fmaf(wt, v[q], bre[l]);
-              else
-                bim[l] = fmaf(wt, v[q], bim[l]);
-            }
+        ++nitem;
+        for (int jj = 0; jj < nds && ok; ++jj) {
+          const int z = it.cell * g.n_sym + g.dsym[jj];
+          for (int b = 0; b < it.nb; ++b) {
+            const uint32_t s = nbox % S;
+            if (nbox >= (uint32_t)S) ok = tc::mbar_wait_sleep(empty + s, ((nbox / S) - 1) & 1, kWaitIters);
+            if (!ok) break;
+            tc::mbar_arrive_expect_tx(full + s, y_box_bytes);
+            tc::tma_load_3d(ring + s * kStageBytes, &tmY, 2 * (it.lo2 + kBoxSc * b), 0, z, full + s);
+            ++nbox;
           }
         }
       }
-      if (valid2) {
-        float4* bo =
-            reinterpret_cast<float4*>(bvec + ((size_t)(lc * nds + jj2) * g.n_sc + k2) * NL);
+    }
+    __syncwarp();
+    __syncthreads();
+    if (lane == 0) {
+      // Copies the workers did not wait for (only after a timeout) must land before the CTA
+      // ends. A stage's copies complete in order, so waiting for its latest one is enough.
+      for (uint32_t s = 0; s < (uint32_t)S && s < nbox; ++s) {
+        const uint32_t last = s + ((nbox - 1 - s) / S) * S;
+        tc::mbar_wait_sleep(full + s, (last / S) & 1, kWaitIters);
+      }
+      if (nitem > 0) tc::mbar_wait_sleep(a_full, (nitem - 1) & 1, kWaitIters);
+    }
+    return;
+  }
+
+  // -------------------------------------------------------------- workers
+  // Each group agrees on timeouts at its own named barrier (1: converters, 2: drain).
+  const int quarter = warp & 3, gtid = warp < kConvWarps ? tid : tid - kConv;
+  const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
+  bool fail = false;  // this thread saw a timeout
+  bool stop = false;  // a thread of its group did (agreed at a group barrier)
+
+  if (warp < kConvWarps) {
+    uint32_t nbox = 0, nitem = 0, ntile = 0;  // boxes, anchor sets and RE tiles consumed
+    uint32_t x_count = 0, mf_count[2] = {0, 0};  // MMA commits per barrier
+    for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
+      const Item it = item_of(g, w, cell0);
+      // every MMA of the previous item read CC; its last commit covers them all
+      if (ntile > 0) fail |= !tc::mbar_wait_sleep(mf_bar + ((ntile - 1) & 1), ((ntile - 1) >> 1) & 1,
+                                            kWaitIters);
+      fail |= !tc::mbar_wait_sleep(a_full, nitem & 1, kWaitIters);
+      ++nitem;
+      // ---- CC = [C ; iC] from the anchors of the segment's corners, four antennas per item
+#pragma unroll 2
+      for (int e = gtid; e < NXP * 16; e += kConv) {
+        const int rq = e & 15, c = e >> 4;
+        const int corner = c / NL, l = c % NL;
+        cf v[4];
+        const float2* src =
+            reinterpret_cast<const float2*>(anch + corner * Sm::kCorner) + l * nr + 4 * rq;
+        if (c < NX && l < nl && 4 * rq + 3 < nr) {
+          const float4 a = reinterpret_cast<const float4*>(src)[0];
+          const float4 b = reinterpret_cast<const float4*>(src)[1];
+          v[0] = mk(a.x, a.y);
+          v[1] = mk(a.z, a.w);
+          v[2] = mk(b.x, b.y);
+          v[3] = mk(b.z, b.w);
+        } else {
 #pragma unroll
-        for (int l = 0; l < NL; l += 2)
-          bo[l / 2] = make_float4(bre[l], bim[l], bre[l + 1], bim[l + 1]);
+          for (int u = 0; u < 4; ++u) {
+            v[u] = mk(0.f, 0.f);
+            if (c < NX && l < nl && 4 * rq + u < nr) v[u] = mk(src[u].x, src[u].y);
+          }
+        }
+        cf iv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) iv[u] = mk(-v[u].y, v[u].x);
+        store_quad<FMT>(cc, c, rq, v);
+        store_quad<FMT>(cc, NXP + c, rq, iv);
+      }
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(a_empty);
+      tc::fence_proxy_async();
+      stop = tc::bar_or<1, kConv>(fail);
+      if (stop) break;
+      // ---- X = C^H C, once the drain group has read the previous X
+      if (gtid == 0) {
+        if (nitem > 1) fail |= !tc::mbar_wait_sleep(x_free, (nitem - 2) & 1, kWaitIters);
+        tc::fence_after_sync();
+        gemm_issue<FMT>(tmem + kColX, cc, cc, tc::instr_desc(FMT, kRows, NXP), x_bar);
+      }
+      ++x_count;
+      for (int t = 0; t < it.ntile; ++t, ++ntile) {
+        const uint32_t buf = ntile & 1;
+        unsigned char* yop =
+            smem + Sm::kYop + (size_t)(Lay::kYBufs == 2 ? buf : 0) * Lay::kTileBytes;
+        // the tile buffer is free once the MMA that last read it (kYBufs tiles back) is done
+        constexpr uint32_t back = Lay::kYBufs;
+        if (ntile >= back)
+          fail |= !tc::mbar_wait_sleep(mf_bar + ((ntile - back) & 1), ((ntile - back) >> 1) & 1,
+                                 kWaitIters);
+        // ---- boxes of tile t -> RE-tile operand: kSlots boxes per round, each thread two
+        // subcarriers x four antennas of a box (four 16-byte loads, two chunk stores)
+        const int nbx = tile_syms(g, it, t) * it.nb;
+        const int slot = gtid / kBoxItems, item = gtid % kBoxItems;
+        const int qa = item / (kBoxSc / 2), pr = item % (kBoxSc / 2);  // antenna quad, pair
+        int js = slot / it.nb, bb = slot % it.nb;  // (symbol, box) of box index slot
+        // Box bx goes to slot bx % kSlots. A stage's consecutive boxes are kStages apart, so
+        // with kStages a multiple of kSlots one slot consumes a stage's boxes in order and never
+        // polls a stage for its next phase while the previous one is still pending (parity
+        // waits cannot tell those two apart).
+        constexpr int kSlots = kConv / kBoxItems;
+        static_assert(S % kSlots == 0, "ring depth must be a multiple of the box slots");
+        for (int bx = slot; bx < nbx; bx += kSlots) {
+          const uint32_t n = nbox + bx, s = n % S;
+          fail |= !tc::mbar_wait_sleep(full + s, (n / S) & 1, kWaitIters);
+          const float4* raw = reinterpret_cast<const float4*>(ring + s * kStageBytes);
+          cf v0[4], v1[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int r = 4 * qa + u;
+            const float4 f = r < nr ? raw[r * (kBoxSc / 2) + pr] : make_float4(0.f, 0.f, 0.f, 0.f);
+            v0[u] = mk(f.x, f.y);
+            v1[u] = mk(f.z, f.w);
+          }
+          const int kk = bb * kBoxSc + 2 * pr + it.lo2 - it.lo;
+          if (kk >= 0 && kk < it.W) store_quad<FMT>(yop, js * it.W + kk, qa, v0);
+          if (kk + 1 >= 0 && kk + 1 < it.W) store_quad<FMT>(yop, js * it.W + kk + 1, qa, v1);
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(empty + s);
+          bb += kSlots;
+          while (bb >= it.nb) {
+            bb -= it.nb;
+            ++js;
+          }
+        }
+        nbox += nbx;
+        tc::fence_proxy_async();
+        stop = tc::bar_or<1, kConv>(fail);
+        if (stop) break;
+        // ---- V = C^H y, once the drain group has emptied this accumulator buffer
+        if (gtid == 0) {
+          if (ntile >= 2)
+            fail |= !tc::mbar_wait_sleep(tmem_free + buf, ((ntile - 2) >> 1) & 1, kWaitIters);
+          tc::fence_after_sync();
+          gemm_issue<FMT>(tmem + kColMf + 128 * buf, yop, cc,
+                          tc::instr_desc(FMT, kRows, 2 * NXP), mf_bar + buf);
+        }
+        ++mf_count[buf];
+      }
+      if (stop) break;
+    }
+    if (gtid == 0) {
+      if (stop) atomicAdd(err, 1u);
+      // MMAs still running (only after a timeout) must finish before tensor memory is released
+      if (x_count) tc::mbar_wait_sleep(x_bar, (x_count - 1) & 1, kWaitIters);
+      for (int b = 0; b < 2; ++b)
+        if (mf_count[b]) tc::mbar_wait_sleep(mf_bar + b, (mf_count[b] - 1) & 1, kWaitIters);
+    }
+  } else {
+    uint32_t nitem = 0, ntile = 0;
+    for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
+      const Item it = item_of(g, w, cell0);
+      // ---- X -> shared memory (after every drain warp is done with the previous item's X)
+      fail |= !tc::mbar_wait_sleep(x_bar, nitem & 1, kWaitIters);
+      tc::fence_after_sync();
+      tc::bar_sync<2, 128>();
+      {
+        const int row = 32 * quarter + lane;
+#pragma unroll
+        for (int c0 = 0; c0 < NXP; c0 += 32) {
+          float v[32];
+          tc::tmem_ld32(tmem + lane_base + kColX + c0, v);
+          if (row < 2 * NXP) {
+            const int c = row % NXP, part = row / NXP;
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+              if (c0 + q < NXP) reinterpret_cast<float*>(Xs + c * xs + c0 + q)[part] = v[q];
+          }
+        }
       }
       tc::fence_before_sync();
-      __syncthreads();  // TMEM and the tile are free for the next round
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(x_free);
+      stop = tc::bar_or<2, 128>(fail);
+      if (stop) break;
+      // ---- per-symbol Gram blocks
+      auto Xget = [&](int i, int k) -> cf { return Xs[i * xs + k]; };
+      form_gram_blocks<NL, 128>(g, Xget,
+                                ygg + (((size_t)it.lc * g.n_seg + it.j) * nds) * NTRI * 2, gtid);
+      // ---- matched filter of each RE tile: this thread's TMEM lane is its RE row
+      for (int t = 0; t < it.ntile; ++t, ++ntile) {
+        const uint32_t buf = ntile & 1;
+        fail |= !tc::mbar_wait_sleep(mf_bar + buf, (ntile >> 1) & 1, kWaitIters);
+        tc::fence_after_sync();
+        const int row = 32 * quarter + lane;
+        const int nrow = tile_syms(g, it, t) * it.W;
+        const bool valid = row < nrow;
+        const int jj = t * it.spt + (valid ? row / it.W : 0);
+        const int k = it.lo + (valid ? row % it.W : 0);
+        const float t1 = g.tw[jj], t0 = 1.f - t1;
+        const float be0 = seg_beta(g, it.j, k, 0), be1 = seg_beta(g, it.j, k, 1);
+        // weight of corner (d, g) for a layer on comb p: tau_d (1 - beta_p or beta_p)
+        float wc[2][4];
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          const float be = p ? be1 : be0;
+          wc[p][0] = t0 * (1.f - be);
+          wc[p][1] = t0 * be;
+          wc[p][2] = t1 * (1.f - be);
+          wc[p][3] = t1 * be;
+        }
+        float bre[NL], bim[NL];
+#pragma unroll
+        for (int l = 0; l < NL; ++l) bre[l] = bim[l] = 0.f;
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+#pragma unroll
+          for (int c0 = 0; c0 < NXP; c0 += 32) {
+            float v[32];
+            tc::tmem_ld32(tmem + lane_base + kColMf + 128 * buf + part * NXP + c0, v);
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+              const int c = c0 + q;
+              if (c < NX) {
+                const int corner = c / NL, l = c % NL;
+                const float wt = wc[l & 1][corner];
+                if (part == 0)
+                  bre[l] = fmaf(wt, v[q], bre[l]);
+                else
+                  bim[l] = fmaf(wt, v[q], bim[l]);
+              }
+            }
+          }
+        }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(tmem_free + buf);
+        if (valid) {
+          float4* bo = reinterpret_cast<float4*>(bvec +
+                                                 ((size_t)(it.lc * nds + jj) * g.n_sc + k) * NL);
+#pragma unroll
+          for (int l = 0; l < NL; l += 2)
+            bo[l / 2] = make_float4(bre[l], bim[l], bre[l + 1], bim[l + 1]);
+        }
+      }
+      ++nitem;
+      stop = tc::bar_or<2, 128>(fail);
+      if (stop) break;
     }
-  }
-  if (fail) {
-    if (tid == 0) atomicAdd(err, 1u);
-    tc::mbar_wait(bar, phase ^ 1, kWaitIters);  // give in-flight MMAs a second chance to land
+    if (gtid == 0 && stop) atomicAdd(err, 1u);
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, kTmemCols);
+  }
 }
 
+// ---------------------------------------------------------------- host side
 int g_num_sms = 0;
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 3-D FP32 tensor map, dims and box innermost first, strides of dims 1 and 2 in bytes.
+bool make_map(CUtensorMap* m, const void* base, const cuuint64_t (&dim)[3],
+              const cuuint64_t (&stride)[2], const cuuint32_t (&box)[3]) {
+  auto fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dim, stride, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
 
 template <int NL, int NC, uint32_t FMT>
 cudaError_t launch_one(const Geo& g, int c0, int nc, const phy_c32* anchors, const phy_c32* Y,
                        float4* ygg, cf* bvec, unsigned* err, cudaStream_t st) {
-  constexpr size_t smem = tc_smem_bytes<NL, NC, FMT>();
-  static int blocks_per_sm = 0;
-  if (blocks_per_sm == 0) {
+  constexpr size_t smem = Smem<NL, NC, FMT>::kTotal;
+  static bool configured = false;
+  if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(seg_prep_tc_kernel<NL, NC, FMT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    // all of the unified L1/shared storage as shared memory, so that several CTAs fit
-    e = cudaFuncSetAttribute(seg_prep_tc_kernel<NL, NC, FMT>,
-                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev)) !=
         cudaSuccess)
       return e;
-    // The occupancy query answers 1 for kernels that allocate tensor memory, although several
-    // such CTAs do share an SM; size the persistent grid from shared and tensor memory instead
-    // (CTAs beyond what fits would only wait for a slot).
-    int smem_sm = 0;
-    if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) !=
-        cudaSuccess)
-      return e;
-    const int b = smem_sm / (int)(smem + 1024);
-    blocks_per_sm = std::max(1, std::min(b, (int)(512 / kTmemCols)));
     if (std::getenv("PHY_DEBUG"))
-      std::fprintf(stderr, "seg_prep_tc<%d,%d,%u>: smem %zu, occupancy %d, SMs %d, blocks/SM %d\n",
-                   NL, NC, FMT, smem, b, g_num_sms, blocks_per_sm);
+      std::fprintf(stderr, "seg_prep_tc<%d,%d,%u>: smem %zu, SMs %d\n", NL, NC, FMT, smem,
+                   g_num_sms);
+    configured = true;
   }
+  // Received grid: (2 n_sc floats, n_rx, n_cells n_sym), box = kBoxSc subcarriers x all antennas.
+  // Anchors: (2 n_rx floats, n_layers, n_cells n_dmrs G), box = one corner's [layer][antenna].
+  CUtensorMap tmY, tmA;
+  const cuuint64_t ydim[3] = {(cuuint64_t)2 * g.n_sc, (cuuint64_t)g.n_rx,
+                              (cuuint64_t)g.n_cells * g.n_sym};
+  const cuuint64_t ystr[2] = {(cuuint64_t)8 * g.n_sc, (cuuint64_t)8 * g.n_sc * g.n_rx};
+  const cuuint32_t ybox[3] = {2 * kBoxSc, (cuuint32_t)g.n_rx, 1};
+  const cuuint64_t adim[3] = {(cuuint64_t)2 * g.n_rx, (cuuint64_t)g.n_layers,
+                              (cuuint64_t)g.n_cells * g.n_dmrs * g.G};
+  const cuuint64_t astr[2] = {(cuuint64_t)8 * g.n_rx, (cuuint64_t)8 * g.n_rx * g.n_layers};
+  const cuuint32_t abox[3] = {(cuuint32_t)2 * g.n_rx, (cuuint32_t)g.n_layers, 1};
+  if (!make_map(&tmY, Y, ydim, ystr, ybox) || !make_map(&tmA, anchors, adim, astr, abox))
+    return cudaErrorInvalidValue;
   const int n_work = g.n_seg * nc;
-  const int grid = std::min(n_work, blocks_per_sm * g_num_sms);
-  seg_prep_tc_kernel<NL, NC, FMT><<<grid, kTcThreads, smem, st>>>(g, c0, nc, anchors, Y, ygg,
-                                                                 bvec, err);
+  const int grid = std::min(n_work, g_num_sms);
+  seg_prep_tc_kernel<NL, NC, FMT><<<grid, kTcThreads, smem, st>>>(tmY, tmA, g, c0, nc, ygg, bvec,
+                                                                  err);
   return cudaGetLastError();
 }
 
@@ -317,9 +574,18 @@ cudaError_t launch_fmt(const Geo& g, int NL, int c0, int nc, const phy_c32* anch
 
 }  // namespace
 
+bool seg_prep_tc_supported(const Geo& g) {
+  // tensor-map rules: 16-byte strides and inner box extents (even antenna count); tiles of
+  // whole data symbols (segments of at most 64 subcarriers, always the case for covers <= 16)
+  return g.n_rx % 2 == 0 && host_max_segment_width(g) <= 64;
+}
+
 cudaError_t launch_seg_prep_tc(const Geo& g, int NL, int c0, int nc, const phy_c32* anchors,
                                const phy_c32* Y, float4* ygg, cf* bvec, unsigned* err,
                                cudaStream_t st) {
+  if (!seg_prep_tc_supported(g) || (reinterpret_cast<uintptr_t>(anchors) % 16) ||
+      (reinterpret_cast<uintptr_t>(Y) % 16))
+    return cudaErrorInvalidValue;
   switch (g.prec) {
     case PHY_PREC_TC_TF32:
       return launch_fmt<tc::kFmtTF32>(g, NL, c0, nc, anchors, Y, ygg, bvec, err, st);

@@ -39,6 +39,8 @@ phy_status slot_run_fit(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32
 size_t min_workspace_bytes(const phy_slot_cfg* cfg);
 
 // Tensor-core segment kernel (same outputs as the FP32 one) for g.prec != PHY_PREC_FP32.
+// Needs an even antenna count and 16-byte aligned anchors and grid (TMA tensor maps).
+bool seg_prep_tc_supported(const Geo& g);
 cudaError_t launch_seg_prep_tc(const Geo& g, int NL, int c0, int nc, const phy_c32* anchors,
                                const phy_c32* Y, float4* ygg, cf* bvec, unsigned* err,
                                cudaStream_t st);

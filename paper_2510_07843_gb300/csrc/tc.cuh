@@ -38,6 +38,25 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
   return false;
 }
 
+// As mbar_wait, but each poll lets the thread sleep up to ~1 us in hardware (woken when the
+// phase completes), so that waiting warps do not take issue slots from working ones.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity,
+                                                uint32_t max_iter) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t it = 0; it < max_iter; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity), "n"(1000)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
 // Arrive on the barrier and announce tx_bytes of incoming bulk-copy data for this phase.
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t tx_bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
@@ -54,6 +73,44 @@ __device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gmem_src, u
           "r"(smem_u32(smem_dst)),
       "l"(gmem_src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
+}
+
+// Plain arrival (one of the barrier's expected count), release semantics for this CTA.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Tiled 3-D tensor copy (TMA engine) of one box at coordinates (x, y, z) of the tensor map into
+// shared memory (128-byte aligned); completion counted on the barrier's transaction count. The
+// innermost coordinate times the element size must be a multiple of 16 bytes; elements outside
+// the tensor read as zero.
+__device__ __forceinline__ void tma_load_3d(void* smem_dst, const void* tmap, int x, int y, int z,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_u32(smem_dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Named barrier `id` (1..15) over `n` threads (a multiple of 32), optionally with an
+// OR-reduction of a predicate so that every participant takes the same branch afterwards.
+template <int id, int n>
+__device__ __forceinline__ void bar_sync() {
+  asm volatile("bar.sync %0, %1;\n" ::"n"(id), "n"(n) : "memory");
+}
+template <int id, int n>
+__device__ __forceinline__ bool bar_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(id), "n"(n)
+      : "memory");
+  return r != 0;
 }
 
 // ---------------------------------------------------------------- TMEM allocation (one warp)
