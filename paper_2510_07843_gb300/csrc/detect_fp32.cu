@@ -226,15 +226,43 @@ constexpr size_t solve_scratch_bytes(int NL) {
   return NL == 16 ? (size_t)kScrSlots * kSolveThreads * sizeof(cf) : 0;
 }
 
-// Shared memory of the solve kernel: scratch, the Gram blocks of up to max_segs segments, barrier.
-size_t solve_smem_bytes(int NL, int max_segs) {
-  return solve_scratch_bytes(NL) + (size_t)max_segs * gram_block_bytes(NL) + 16;
+// 9..16 layers: after the solve, shared memory holds each thread's x (scratch slots 0..15) and d
+// (floats, [layer][thread]), then the CTA's LLRs [RE][layer][qm], SINRs [RE][layer] and
+// x_hat [RE][layer], each leaving as one block of coalesced stores.
+constexpr size_t kStageX = (size_t)16 * kSolveThreads * sizeof(cf);
+constexpr size_t kStageXd = kStageX + (size_t)16 * kSolveThreads * sizeof(float);
+constexpr size_t solve_stage_bytes(int QM) {
+  return kStageXd + (size_t)kSolveThreads * 16 * ((QM + 1) * sizeof(float) + sizeof(cf));
+}
+
+// Shared memory of the solve kernel: scratch and the Gram blocks of up to max_segs segments (for
+// 9..16 layers at least the output staging), then the mbarrier in the last 16 bytes, which the
+// staging never reaches.
+__host__ __device__ constexpr size_t solve_smem_bytes(int NL, int QM, int max_segs) {
+  const size_t main = solve_scratch_bytes(NL) + (size_t)max_segs * gram_block_bytes(NL);
+  const size_t stage = NL == 16 ? solve_stage_bytes(QM) : 0;
+  return (main > stage ? main : stage) + 16;
+}
+
+// Cooperative copy of n floats from shared memory to global memory (16-byte stores when dst is
+// 16-byte aligned; src is).
+__device__ __forceinline__ void copy_out(float* dst, const float* src, int n) {
+  int i0 = 0;
+  if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+    const int n4 = n >> 2;
+    for (int i = threadIdx.x; i < n4; i += kSolveThreads)
+      reinterpret_cast<float4*>(dst)[i] = reinterpret_cast<const float4*>(src)[i];
+    i0 = n4 << 2;
+  }
+  for (int i = i0 + threadIdx.x; i < n; i += kSolveThreads) dst[i] = src[i];
 }
 
 // One CTA per (128 subcarriers, data symbol, cell), one thread per RE. Thread 0 brings the
 // Gram-block 4-tuples of the segments the CTA spans into shared memory with bulk copies
 // (TMA engine, completion counted on an mbarrier); meanwhile every thread loads its matched
-// filter. A barrier timeout marks the CTA's REs with flag bit 3.
+// filter. A barrier timeout marks the CTA's REs with flag bit 3. With 9..16 layers the LLRs
+// and SINRs are staged in shared memory and leave as one contiguous block per CTA: per-thread
+// stores of whole records (512 B apart) would keep each warp waiting on the store path.
 template <int NL, int QM>
 __global__ void __launch_bounds__(kSolveThreads)
     re_solve_fp32_kernel(Geo g, int cell0, int max_segs, const float4* __restrict__ ygg,
@@ -246,8 +274,8 @@ __global__ void __launch_bounds__(kSolveThreads)
   constexpr uint32_t kBlk = gram_block_bytes(NL);
   extern __shared__ __align__(128) unsigned char solve_smem[];
   float4* ys = reinterpret_cast<float4*>(solve_smem + solve_scratch_bytes(NL));
-  uint64_t* bar = reinterpret_cast<uint64_t*>(solve_smem + solve_scratch_bytes(NL) +
-                                              (size_t)max_segs * kBlk);
+  uint64_t* bar =
+      reinterpret_cast<uint64_t*>(solve_smem + solve_smem_bytes(NL, QM, max_segs) - 16);
   const int nl = g.n_layers, nds = g.n_dsym;
   const int jj = blockIdx.y, lc = blockIdx.z, cell = cell0 + lc;
   const int k0 = blockIdx.x * kSolveThreads;
@@ -282,13 +310,14 @@ __global__ void __launch_bounds__(kSolveThreads)
   constexpr uint32_t kWait = 1u << 22;
   bool arrived = tc::mbar_wait(bar, 0, kWait);
   if (!arrived) arrived = tc::mbar_wait(bar, 0, kWait);  // let copies in flight land
-  if (!live) return;
-  const size_t ridx = ((size_t)cell * nds + jj) * g.n_sc + k;
+  arrived = __syncthreads_and(arrived);  // one decision for the CTA (it has barriers below)
+  const size_t ridx = ((size_t)cell * nds + jj) * g.n_sc + (live ? k : k0);
   if (!arrived) {
-    flags_out[ridx] = 8;
+    if (live) flags_out[ridx] = 8;
     return;
   }
-  const int j = seg_of(g, k);
+  if (NL != 16 && !live) return;
+  const int j = seg_of(g, live ? k : k0);
   const float s2 = sigma2[cell];
   const float be0 = seg_beta(g, j, k, 0), be1 = seg_beta(g, j, k, 1);
   const float4* yp = ys + (size_t)(j - s0) * NTRI * 2;
@@ -323,68 +352,108 @@ __global__ void __launch_bounds__(kSolveThreads)
     }
     return a;
   };
-#pragma unroll
-  for (int l = 0; l < NL; ++l) {
-    if (l >= nl) b[l] = mk(0.f, 0.f);
-    fin = fin && finite_cf(b[l]);
-  }
-  SolveInfo si;
-  if constexpr (NL == 16) {
-    si = solve16(getA, SmemScratch{reinterpret_cast<cf*>(solve_smem) + threadIdx.x}, b, x, dd);
-  } else {
-    si = solve_small<NL>(getA, b, x, dd);
-  }
-  fin = fin && si.fin;
-  bool ok = si.ok && fin;
-  uint8_t flag = 0;
-  if (!fin) flag |= 4;
-  if (!si.ok || si.pmin < g.pivot_min * si.pmax) flag |= 1;
-  if (g.refactor && (flag & 1) && fin) {
-    Refactor64Out r64;
-    refactor_fp64(g, anchors, Y, cell, jj, k, j, s2, &r64);
-    if (r64.ok) {
-#pragma unroll
-      for (int l = 0; l < NL; ++l) {
-        if (l < nl) {
-          x[l] = r64.x[l];
-          dd[l] = r64.d[l];
-        }
-      }
-      ok = true;
-      flag |= 2;
-    }
-  }
-  flags_out[ridx] = flag;
-  auto epilogue = [&](int l, cf xl, float dl) {
-    const LayerOut o = layer_stats(s2, dl);
-    const size_t li = ridx * nl + l;
-    if (ok) {
-      if (x_hat) st(x_hat + li, xl);
-      if (sinr_out) sinr_out[li] = o.sinr;
-      if (llr_out) store_llr<QM>(llr_out + li * QM, o.inv_mu * xl, o.s2eff);
-    } else {
-      if (x_hat) st(x_hat + li, mk(0.f, 0.f));
-      if (sinr_out) sinr_out[li] = 0.f;
-      if (llr_out)
-        for (int q = 0; q < QM; ++q) llr_out[li * QM + q] = 0.f;
-    }
-  };
-  if constexpr (NL == 16) {
-    // Rolled on purpose: one copy of the per-layer epilogue keeps the kernel's code small. The
-    // loop index is dynamic, so x and d go through this thread's shared scratch (free after
-    // the solve) rather than a register array that would be demoted to local memory.
-    const SmemScratch sc{reinterpret_cast<cf*>(solve_smem) + threadIdx.x};
+  bool ok = false;
+  if (live) {
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
-      sc.st(l, x[l]);
-      sc.st(NL + l, mk(dd[l], 0.f));
+      if (l >= nl) b[l] = mk(0.f, 0.f);
+      fin = fin && finite_cf(b[l]);
     }
-#pragma unroll 1
-    for (int l = 0; l < nl; ++l) epilogue(l, sc.ld(l), sc.ld(NL + l).x);
-  } else {
+    SolveInfo si;
+    if constexpr (NL == 16) {
+      si = solve16(getA, SmemScratch{reinterpret_cast<cf*>(solve_smem) + threadIdx.x}, b, x, dd);
+    } else {
+      si = solve_small<NL>(getA, b, x, dd);
+    }
+    fin = fin && si.fin;
+    ok = si.ok && fin;
+    uint8_t flag = 0;
+    if (!fin) flag |= 4;
+    if (!si.ok || si.pmin < g.pivot_min * si.pmax) flag |= 1;
+    if (g.refactor && (flag & 1) && fin) {
+      Refactor64Out r64;
+      refactor_fp64(g, anchors, Y, cell, jj, k, j, s2, &r64);
+      if (r64.ok) {
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+          if (l < nl) {
+            x[l] = r64.x[l];
+            dd[l] = r64.d[l];
+          }
+        }
+        ok = true;
+        flag |= 2;
+      }
+    }
+    flags_out[ridx] = flag;
+  }
+  if constexpr (NL == 16) {
+    // x and d to this thread's scratch slots; once every thread is past the solve, the rest
+    // of shared memory stages the outputs. The per-layer loop is rolled (one copy of the
+    // demapper keeps the code small), its index dynamic, so x and d are read back from shared
+    // memory rather than from a register array. Each thread starts at its own layer, which
+    // spreads the staging stores over the banks.
+    const SmemScratch sc{reinterpret_cast<cf*>(solve_smem) + threadIdx.x};
+    float* dsl = reinterpret_cast<float*>(solve_smem + kStageX) + threadIdx.x;
+    // x goes to this thread's own scratch slots at once; the d slots overlap other threads'
+    // scratch, so d waits until every thread is past the solve
 #pragma unroll
     for (int l = 0; l < NL; ++l)
-      if (l < nl) epilogue(l, x[l], dd[l]);
+      if (live) sc.st(l, x[l]);
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < NL; ++l)
+      if (live) dsl[l * kSolveThreads] = dd[l];
+    float* st_llr = reinterpret_cast<float*>(solve_smem + kStageXd);
+    float* st_sinr = st_llr + kSolveThreads * NL * QM;
+    cf* st_xh = reinterpret_cast<cf*>(st_sinr + kSolveThreads * NL);
+    const int r = threadIdx.x;
+    if (live) {
+      int l = r % nl;
+#pragma unroll 1
+      for (int i = 0; i < nl; ++i, l = (l + 1 == nl) ? 0 : l + 1) {
+        const cf xl = sc.ld(l);
+        const LayerOut o = layer_stats(s2, dsl[l * kSolveThreads]);
+        float v[QM];
+        if (ok) {
+          qam_llr<QM>(o.inv_mu * xl, o.s2eff, v);
+        } else {
+#pragma unroll
+          for (int q = 0; q < QM; ++q) v[q] = 0.f;
+        }
+        float2* d = reinterpret_cast<float2*>(st_llr + (r * nl + l) * QM);
+#pragma unroll
+        for (int q = 0; q < QM; q += 2) d[q / 2] = make_float2(v[q], v[q + 1]);
+        st_sinr[r * nl + l] = ok ? o.sinr : 0.f;
+        st_xh[r * nl + l] = ok ? xl : mk(0.f, 0.f);
+      }
+    }
+    __syncthreads();
+    // this CTA's live REs are consecutive, so their records form one block in each output
+    const int nlive = min(kSolveThreads, g.n_sc - k0);
+    const size_t r0 = ((size_t)cell * nds + jj) * g.n_sc + k0;
+    if (llr_out) copy_out(llr_out + r0 * nl * QM, st_llr, nlive * nl * QM);
+    if (sinr_out) copy_out(sinr_out + r0 * nl, st_sinr, nlive * nl);
+    if (x_hat)
+      copy_out(reinterpret_cast<float*>(x_hat + r0 * nl), reinterpret_cast<const float*>(st_xh),
+               2 * nlive * nl);
+  } else {
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      if (l >= nl) continue;
+      const LayerOut o = layer_stats(s2, dd[l]);
+      const size_t li = ridx * nl + l;
+      if (ok) {
+        if (x_hat) st(x_hat + li, x[l]);
+        if (sinr_out) sinr_out[li] = o.sinr;
+        if (llr_out) store_llr<QM>(llr_out + li * QM, o.inv_mu * x[l], o.s2eff);
+      } else {
+        if (x_hat) st(x_hat + li, mk(0.f, 0.f));
+        if (sinr_out) sinr_out[li] = 0.f;
+        if (llr_out)
+          for (int q = 0; q < QM; ++q) llr_out[li * QM + q] = 0.f;
+      }
+    }
   }
 }
 
@@ -430,7 +499,7 @@ cudaError_t launch_solve(const Geo& g, int c0, int nc, int max_segs, const float
                          const cf* bvec, const float* sigma2, const phy_c32* anchors,
                          const phy_c32* Y, phy_c32* x_hat, float* sinr, float* llr,
                          uint8_t* flags, cudaStream_t st) {
-  const size_t smem = solve_smem_bytes(NL, max_segs);
+  const size_t smem = solve_smem_bytes(NL, QM, max_segs);
   static size_t configured = 0;
   if (smem > 48 * 1024 && smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(re_solve_fp32_kernel<NL, QM>,
