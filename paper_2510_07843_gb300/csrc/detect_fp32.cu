@@ -46,23 +46,25 @@ size_t chunk_budget() {
 
 int nl_class(int nl) { return nl <= 2 ? 2 : nl <= 4 ? 4 : nl <= 8 ? 8 : 16; }
 
+// Shared memory of the FP32 segment kernel (cf units): the corner anchors C [rx][corner-layer],
+// two received-grid tiles [rx][subcarrier] (the data symbols of one round), and a region that
+// first holds X and then the next round's two tiles.
 struct PrepLayout {
-  int NC, NX, xs, hs, yw;
-  int off_C, off_X, off_Hg, off_Y, total;  // cf units
+  int NC, NX, xs, yw;
+  int off_C, off_Y, off_X, total;
 };
 
 __host__ __device__ inline PrepLayout prep_layout(int NL, int n_dmrs, int n_rx, int wmax) {
   PrepLayout f;
   f.NC = 2 * n_dmrs;
   f.NX = f.NC * NL;
-  f.xs = f.NX + 2;           // keeps 16-byte row alignment, spreads banks
-  f.hs = 2 * NL + 1;         // odd stride: conflict-free column reads
-  f.yw = wmax + 1;
+  f.xs = f.NX + 2;                     // keeps 16-byte row alignment, spreads banks
+  f.yw = ((wmax + 3) & ~3) + 2;        // room for whole 4-subcarrier quads, even (16-byte rows)
   f.off_C = 0;
-  f.off_X = f.off_C + n_rx * f.xs;
-  f.off_Hg = f.off_X + f.NX * f.xs;
-  f.off_Y = f.off_Hg + n_rx * f.hs;
-  f.total = f.off_Y + 2 * n_rx * f.yw;
+  f.off_Y = f.off_C + n_rx * f.xs;
+  f.off_X = f.off_Y + 2 * n_rx * f.yw;
+  const int xr = f.NX * f.xs, yr = 2 * n_rx * f.yw;
+  f.total = f.off_X + (xr > yr ? xr : yr);
   return f;
 }
 
@@ -70,12 +72,21 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
 }
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
+// One CTA per (segment, cell). X = C^H C from the corner anchors and the per-symbol Gram blocks,
+// then the matched filter b = sum_g w_g (tau_0 C_0g + tau_1 C_1g)^H y per RE, two data symbols
+// per round: 128 threads per symbol, each group of four lanes one 4-RE x (2 layers x 2 comb
+// groups) register tile with the antennas split four ways (a shuffle reduction at the end).
+// The received-grid tiles of the next round load (cp.async) while this round computes.
 template <int NL>
 __global__ void __launch_bounds__(kPrepThreads)
     seg_prep_fp32_kernel(Geo g, int wmax, int cell0, const phy_c32* __restrict__ anchors,
@@ -83,6 +94,8 @@ __global__ void __launch_bounds__(kPrepThreads)
                          cf* __restrict__ bvec) {
   constexpr int NT = kPrepThreads;
   constexpr int NTRI = NL * (NL + 1) / 2;
+  constexpr int LP = NL / 2;  // layer pairs
+  static_assert(NT == 256, "two symbols of 128 threads per round");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cf* sm = reinterpret_cast<cf*>(smem_raw);
   const int tid = threadIdx.x;
@@ -91,24 +104,39 @@ __global__ void __launch_bounds__(kPrepThreads)
   const PrepLayout f = prep_layout(NL, g.n_dmrs, nr, wmax);
   cf* Cs = sm + f.off_C;
   cf* Xs = sm + f.off_X;
-  cf* Hg = sm + f.off_Hg;
-  cf* Yt = sm + f.off_Y;
   int lo, hi;
   segment_range(g, j, lo, hi);
   const int W = hi - lo;
+  const int nrounds = (nds + 1) / 2;
 
-  auto load_tile = [&](int jj, int buf) {
-    const phy_c32* ysym = Y + ((size_t)cell * g.n_sym + g.dsym[jj]) * nr * g.n_sc + lo;
-    cf* dst = Yt + buf * nr * f.yw;
-    for (int e = tid; e < nr * W; e += NT) {
-      const int r = e / W, kk = e % W;
-      cp_async8(dst + r * f.yw + kk, ysym + (size_t)r * g.n_sc + kk);
+  // tiles of round n: buffers 0, 1 (even rounds) or 2, 3 (odd rounds, in the X region)
+  auto tile = [&](int buf) { return sm + (buf < 2 ? f.off_Y : f.off_X - 2 * nr * f.yw) +
+                                    buf * nr * f.yw; };
+  auto load_round = [&](int n) {
+    for (int s2 = 0; s2 < 2; ++s2) {
+      const int jj = 2 * n + s2;
+      if (jj >= nds) break;
+      const phy_c32* ysym = Y + ((size_t)cell * g.n_sym + g.dsym[jj]) * nr * g.n_sc + lo;
+      cf* dst = tile(2 * (n & 1) + s2);
+      if ((lo & 1) == 0) {  // subcarrier pairs (a trailing odd one pairs with padding)
+        const int wp = (W + 1) / 2;
+        for (int e = tid; e < nr * wp; e += NT) {
+          const int r = e / wp, kk = 2 * (e - r * wp);
+          if (kk + 1 < W)
+            cp_async16(dst + r * f.yw + kk, ysym + (size_t)r * g.n_sc + kk);
+          else
+            cp_async8(dst + r * f.yw + kk, ysym + (size_t)r * g.n_sc + kk);
+        }
+      } else {
+        for (int e = tid; e < nr * W; e += NT) {
+          const int r = e / W, kk = e % W;
+          cp_async8(dst + r * f.yw + kk, ysym + (size_t)r * g.n_sc + kk);
+        }
+      }
     }
     cp_async_commit();
   };
-  load_tile(0, 0);  // overlaps the Gram work below
-
-  // ---- corners
+  // ---- corners (asynchronous copies, transposed to [rx][corner-layer]), then round 0's tiles
   {
     const int total = f.NC * NL * nr;
     const int g1 = seg_g1(g, j);
@@ -119,12 +147,16 @@ __global__ void __launch_bounds__(kPrepThreads)
       const int corner = rest / NL;
       const int d = corner >> 1, gr = corner & 1;
       const int grp = gr ? g1 : j;
-      cf v = mk(0.f, 0.f);
+      cf* dst = Cs + r * f.xs + corner * NL + l;
       if (l < nl)
-        v = ld(anchors + ((((size_t)cell * g.n_dmrs + d) * g.G + grp) * nl + l) * nr + r);
-      Cs[r * f.xs + corner * NL + l] = v;
+        cp_async8(dst, anchors + ((((size_t)cell * g.n_dmrs + d) * g.G + grp) * nl + l) * nr + r);
+      else
+        *dst = mk(0.f, 0.f);
     }
+    cp_async_commit();
   }
+  load_round(0);  // overlaps the Gram work below
+  cp_async_wait<1>();  // the corners
   __syncthreads();
   // ---- X = C^H C, lower 4x4 tiles
   {
@@ -165,40 +197,89 @@ __global__ void __launch_bounds__(kPrepThreads)
     };
     form_gram_blocks<NL, NT>(g, Xget, ygg + (((size_t)lc * g.n_seg + j) * nds) * NTRI * 2, tid);
   }
-  // ---- matched filter per data symbol
-  for (int jj = 0; jj < nds; ++jj) {
-    const float t1 = g.tw[jj], t0 = 1.f - t1;
-    __syncthreads();  // Hg and the other tile buffer are free
-    if (jj + 1 < nds) load_tile(jj + 1, (jj + 1) & 1);
-    for (int e = tid; e < nr * 2 * NL; e += NT) {
-      const int col = e % (2 * NL);
-      const int r = e / (2 * NL);
-      const int gg = col / NL, l = col % NL;
-      cf v = Cs[r * f.xs + gg * NL + l];
-      if (g.n_dmrs == 2) v = t0 * v + t1 * Cs[r * f.xs + (2 + gg) * NL + l];
-      Hg[r * f.hs + col] = v;
-    }
-    if (jj + 1 < nds)
+  __syncthreads();  // the X region now takes the odd rounds' tiles
+  if (nrounds > 1) load_round(1);
+
+  // ---- matched filter, two data symbols per round
+  const int ks = tid & 3, slot = (tid & 127) >> 2, half = tid >> 7;
+  const int nitems = ((W + 3) / 4) * LP;
+  const int c1off = g.n_dmrs == 2 ? 2 * NL : 0;  // DMRS-1 corners (the DMRS-0 ones if single)
+  for (int n = 0; n < nrounds; ++n) {
+    if (n + 1 < nrounds)
       cp_async_wait<1>();
     else
       cp_async_wait<0>();
     __syncthreads();
-    const cf* yt = Yt + (jj & 1) * nr * f.yw;
-    cf* bout = bvec + ((size_t)(lc * nds + jj) * g.n_sc + lo) * NL;
-    for (int e = tid; e < W * NL; e += NT) {
-      const int l = e % NL, kk = e / NL;
-      cf z0 = mk(0.f, 0.f), z1 = mk(0.f, 0.f);
-      if (l < nl) {
+    const int jj = 2 * n + half;
+    if (jj < nds) {
+      const cf* yt = tile(2 * (n & 1) + half);
+      const float t1 = g.tw[jj];
+      cf* bout = bvec + ((size_t)(lc * nds + jj) * g.n_sc + lo) * NL;
+      for (int it = slot; it < nitems; it += 32) {
+        const int kq = it / LP, l0 = 2 * (it % LP), kk0 = 4 * kq;
+        cf acc[2][2][4];  // [comb group][layer][RE]
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[a][b][q] = mk(0.f, 0.f);
 #pragma unroll 4
-        for (int r = 0; r < nr; ++r) {
-          const cf y = yt[r * f.yw + kk];
-          z0 = cfma_cj(Hg[r * f.hs + l], y, z0);
-          z1 = cfma_cj(Hg[r * f.hs + NL + l], y, z1);
+        for (int r = ks; r < nr; r += 4) {
+          const float4* yr = reinterpret_cast<const float4*>(yt + r * f.yw + kk0);
+          const float4 y01 = yr[0], y23 = yr[1];
+          const cf y[4] = {mk(y01.x, y01.y), mk(y01.z, y01.w), mk(y23.x, y23.y), mk(y23.z, y23.w)};
+          const cf* cr = Cs + r * f.xs + l0;
+#pragma unroll
+          for (int gg = 0; gg < 2; ++gg) {
+            const float4 c0 = *reinterpret_cast<const float4*>(cr + gg * NL);
+            const float4 c1 = *reinterpret_cast<const float4*>(cr + c1off + gg * NL);
+            // interpolated channel of layers l0, l0 + 1 on comb group gg at this symbol
+            const cf h[2] = {mk(fmaf(t1, c1.x - c0.x, c0.x), fmaf(t1, c1.y - c0.y, c0.y)),
+                             mk(fmaf(t1, c1.z - c0.z, c0.z), fmaf(t1, c1.w - c0.w, c0.w))};
+#pragma unroll
+            for (int li = 0; li < 2; ++li)
+#pragma unroll
+              for (int q = 0; q < 4; ++q) acc[gg][li][q] = cfma_cj(h[li], y[q], acc[gg][li][q]);
+          }
+        }
+        // sum the four antenna subsets: the four lanes of this item (same trip count, so the
+        // mask names exactly the lanes that take part)
+        const unsigned quad = 0xFu << (tid & 28);
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+              for (int m = 1; m < 4; m <<= 1) {
+                acc[a][b][q].x += __shfl_xor_sync(quad, acc[a][b][q].x, m);
+                acc[a][b][q].y += __shfl_xor_sync(quad, acc[a][b][q].y, m);
+              }
+        // lane ks writes RE kk0 + ks: b = (1 - beta) V_g0 + beta V_g1 for layers l0, l0 + 1
+        const int kk = kk0 + ks;
+        if (kk < W) {
+          cf v[2];
+#pragma unroll
+          for (int li = 0; li < 2; ++li) {
+            const float be = seg_beta(g, j, lo + kk, (l0 + li) & 1);
+            cf z0 = acc[0][li][0], z1 = acc[1][li][0];
+#pragma unroll
+            for (int q = 1; q < 4; ++q)
+              if (ks == q) {
+                z0 = acc[0][li][q];
+                z1 = acc[1][li][q];
+              }
+            v[li] = (1.f - be) * z0 + be * z1;
+          }
+          *reinterpret_cast<float4*>(bout + (size_t)kk * NL + l0) =
+              make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
         }
       }
-      const float be = seg_beta(g, j, lo + kk, l & 1);
-      bout[kk * NL + l] = (1.f - be) * z0 + be * z1;
     }
+    __syncthreads();  // this round's tiles are free
+    if (n + 2 < nrounds) load_round(n + 2);
   }
 }
 
