@@ -48,9 +48,9 @@ int nl_class(int nl) { return nl <= 2 ? 2 : nl <= 4 ? 4 : nl <= 8 ? 8 : 16; }
 
 // Shared memory of the FP32 segment kernel (cf units): the corner anchors C [rx][corner-layer],
 // two received-grid tiles [rx][subcarrier] (the data symbols of one round), and a region that
-// first holds X and then the next round's two tiles.
+// first holds X and then the round's interpolated channels Hg [symbol][rx][comb group, layer].
 struct PrepLayout {
-  int NC, NX, xs, yw;
+  int NC, NX, xs, yw, hs;
   int off_C, off_Y, off_X, total;
 };
 
@@ -60,11 +60,12 @@ __host__ __device__ inline PrepLayout prep_layout(int NL, int n_dmrs, int n_rx, 
   f.NX = f.NC * NL;
   f.xs = f.NX + 2;                     // keeps 16-byte row alignment, spreads banks
   f.yw = ((wmax + 3) & ~3) + 2;        // room for whole 4-subcarrier quads, even (16-byte rows)
+  f.hs = 2 * NL + 2;
   f.off_C = 0;
   f.off_Y = f.off_C + n_rx * f.xs;
   f.off_X = f.off_Y + 2 * n_rx * f.yw;
-  const int xr = f.NX * f.xs, yr = 2 * n_rx * f.yw;
-  f.total = f.off_X + (xr > yr ? xr : yr);
+  const int xr = f.NX * f.xs, hr = 2 * n_rx * f.hs;
+  f.total = f.off_X + (xr > hr ? xr : hr);
   return f;
 }
 
@@ -109,27 +110,30 @@ __global__ void __launch_bounds__(kPrepThreads)
   const int W = hi - lo;
   const int nrounds = (nds + 1) / 2;
 
-  // tiles of round n: buffers 0, 1 (even rounds) or 2, 3 (odd rounds, in the X region)
-  auto tile = [&](int buf) { return sm + (buf < 2 ? f.off_Y : f.off_X - 2 * nr * f.yw) +
-                                    buf * nr * f.yw; };
+  // the two tiles of the current round
+  auto tile = [&](int buf) { return sm + f.off_Y + buf * nr * f.yw; };
   auto load_round = [&](int n) {
     for (int s2 = 0; s2 < 2; ++s2) {
       const int jj = 2 * n + s2;
       if (jj >= nds) break;
       const phy_c32* ysym = Y + ((size_t)cell * g.n_sym + g.dsym[jj]) * nr * g.n_sc + lo;
-      cf* dst = tile(2 * (n & 1) + s2);
+      cf* dst = tile(s2);
+      // row r, subcarrier pair p from the flat index without an integer division (exact:
+      // the flat index is below 2^12)
       if ((lo & 1) == 0) {  // subcarrier pairs (a trailing odd one pairs with padding)
         const int wp = (W + 1) / 2;
+        const float inv = 1.f / (float)wp;
         for (int e = tid; e < nr * wp; e += NT) {
-          const int r = e / wp, kk = 2 * (e - r * wp);
+          const int r = (int)(((float)e + 0.5f) * inv), kk = 2 * (e - r * wp);
           if (kk + 1 < W)
             cp_async16(dst + r * f.yw + kk, ysym + (size_t)r * g.n_sc + kk);
           else
             cp_async8(dst + r * f.yw + kk, ysym + (size_t)r * g.n_sc + kk);
         }
       } else {
+        const float inv = 1.f / (float)W;
         for (int e = tid; e < nr * W; e += NT) {
-          const int r = e / W, kk = e % W;
+          const int r = (int)(((float)e + 0.5f) * inv), kk = e - r * W;
           cp_async8(dst + r * f.yw + kk, ysym + (size_t)r * g.n_sc + kk);
         }
       }
@@ -138,20 +142,18 @@ __global__ void __launch_bounds__(kPrepThreads)
   };
   // ---- corners (asynchronous copies, transposed to [rx][corner-layer]), then round 0's tiles
   {
-    const int total = f.NC * NL * nr;
-    const int g1 = seg_g1(g, j);
-    for (int idx = tid; idx < total; idx += NT) {
-      const int r = idx % nr;
-      const int rest = idx / nr;
-      const int l = rest % NL;
-      const int corner = rest / NL;
-      const int d = corner >> 1, gr = corner & 1;
-      const int grp = gr ? g1 : j;
-      cf* dst = Cs + r * f.xs + corner * NL + l;
-      if (l < nl)
-        cp_async8(dst, anchors + ((((size_t)cell * g.n_dmrs + d) * g.G + grp) * nl + l) * nr + r);
-      else
-        *dst = mk(0.f, 0.f);
+    const int g1 = seg_g1(g, j), warp = tid >> 5, lane = tid & 31;
+    for (int cl = warp; cl < f.NC * NL; cl += NT / 32) {  // (corner, layer) per warp
+      const int corner = cl / NL, l = cl % NL;
+      const int d = corner >> 1, grp = (corner & 1) ? g1 : j;
+      const phy_c32* src = anchors + ((((size_t)cell * g.n_dmrs + d) * g.G + grp) * nl + l) * nr;
+      for (int r = lane; r < nr; r += 32) {
+        cf* dst = Cs + r * f.xs + cl;
+        if (l < nl)
+          cp_async8(dst, src + r);
+        else
+          *dst = mk(0.f, 0.f);
+      }
     }
     cp_async_commit();
   }
@@ -197,23 +199,31 @@ __global__ void __launch_bounds__(kPrepThreads)
     };
     form_gram_blocks<NL, NT>(g, Xget, ygg + (((size_t)lc * g.n_seg + j) * nds) * NTRI * 2, tid);
   }
-  __syncthreads();  // the X region now takes the odd rounds' tiles
-  if (nrounds > 1) load_round(1);
+  __syncthreads();  // the X region now takes the rounds' interpolated channels
+  cf* Hs = Xs;
 
   // ---- matched filter, two data symbols per round
   const int ks = tid & 3, slot = (tid & 127) >> 2, half = tid >> 7;
   const int nitems = ((W + 3) / 4) * LP;
   const int c1off = g.n_dmrs == 2 ? 2 * NL : 0;  // DMRS-1 corners (the DMRS-0 ones if single)
   for (int n = 0; n < nrounds; ++n) {
-    if (n + 1 < nrounds)
-      cp_async_wait<1>();
-    else
-      cp_async_wait<0>();
+    // Hg(t) = C_0g + t1(t) (C_1g - C_0g) for the round's two symbols, while its tiles land
+#pragma unroll
+    for (int s2 = 0; s2 < 2; ++s2) {
+      const float t1 = g.tw[min(2 * n + s2, nds - 1)];
+      for (int e = tid; e < nr * 2 * NL; e += NT) {
+        const int r = e / (2 * NL), col = e % (2 * NL);  // 2 NL is a power of two
+        const cf c0 = Cs[r * f.xs + col], c1 = Cs[r * f.xs + c1off + col];
+        Hs[(s2 * nr + r) * f.hs + col] =
+            mk(fmaf(t1, c1.x - c0.x, c0.x), fmaf(t1, c1.y - c0.y, c0.y));
+      }
+    }
+    cp_async_wait<0>();
     __syncthreads();
     const int jj = 2 * n + half;
     if (jj < nds) {
-      const cf* yt = tile(2 * (n & 1) + half);
-      const float t1 = g.tw[jj];
+      const cf* yt = tile(half);
+      const cf* hg = Hs + half * nr * f.hs;
       cf* bout = bvec + ((size_t)(lc * nds + jj) * g.n_sc + lo) * NL;
       for (int it = slot; it < nitems; it += 32) {
         const int kq = it / LP, l0 = 2 * (it % LP), kk0 = 4 * kq;
@@ -229,14 +239,12 @@ __global__ void __launch_bounds__(kPrepThreads)
           const float4* yr = reinterpret_cast<const float4*>(yt + r * f.yw + kk0);
           const float4 y01 = yr[0], y23 = yr[1];
           const cf y[4] = {mk(y01.x, y01.y), mk(y01.z, y01.w), mk(y23.x, y23.y), mk(y23.z, y23.w)};
-          const cf* cr = Cs + r * f.xs + l0;
+          const cf* hr = hg + r * f.hs + l0;
 #pragma unroll
           for (int gg = 0; gg < 2; ++gg) {
-            const float4 c0 = *reinterpret_cast<const float4*>(cr + gg * NL);
-            const float4 c1 = *reinterpret_cast<const float4*>(cr + c1off + gg * NL);
             // interpolated channel of layers l0, l0 + 1 on comb group gg at this symbol
-            const cf h[2] = {mk(fmaf(t1, c1.x - c0.x, c0.x), fmaf(t1, c1.y - c0.y, c0.y)),
-                             mk(fmaf(t1, c1.z - c0.z, c0.z), fmaf(t1, c1.w - c0.w, c0.w))};
+            const float4 hv = *reinterpret_cast<const float4*>(hr + gg * NL);
+            const cf h[2] = {mk(hv.x, hv.y), mk(hv.z, hv.w)};
 #pragma unroll
             for (int li = 0; li < 2; ++li)
 #pragma unroll
@@ -278,8 +286,8 @@ __global__ void __launch_bounds__(kPrepThreads)
         }
       }
     }
-    __syncthreads();  // this round's tiles are free
-    if (n + 2 < nrounds) load_round(n + 2);
+    __syncthreads();  // this round's tiles and channels are free
+    if (n + 1 < nrounds) load_round(n + 1);
   }
 }
 
