@@ -450,7 +450,29 @@ __global__ void __launch_bounds__(kSolveThreads)
     }
     SolveInfo si;
     if constexpr (NL == 16) {
-      si = solve16(getA, SmemScratch{reinterpret_cast<cf*>(solve_smem) + threadIdx.x}, b, x, dd);
+      // a runtime row of A: its entries (l, 0..7) are consecutive in the packed triangle, and
+      // the comb parity of l picks the weight products once for the row
+      auto rowA = [&](int l, cf (&row)[8]) {
+        const float4* e0 = yp + 2 * tri(l, 0);
+        const bool ol = l & 1, lv = l < nl;
+        float ce[4], co[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          ce[q] = ol ? cw[1][0][q] : cw[0][0][q];
+          co[q] = ol ? cw[1][1][q] : cw[0][1][q];
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float* c = (k & 1) ? co : ce;
+          const float4 p = e0[2 * k], q = e0[2 * k + 1];
+          cf a;
+          a.x = fmaf(c[0], p.x, fmaf(c[1], p.z, fmaf(c[2], q.x, c[3] * q.z)));
+          a.y = fmaf(c[0], p.y, fmaf(c[1], p.w, fmaf(c[2], q.y, c[3] * q.w)));
+          row[k] = (lv && k < nl) ? a : mk(0.f, 0.f);  // l >= 8 > k: never on the diagonal
+        }
+      };
+      si = solve16(getA, rowA, SmemScratch{reinterpret_cast<cf*>(solve_smem) + threadIdx.x}, b,
+                   x, dd);
     } else {
       si = solve_small<NL>(getA, b, x, dd);
     }

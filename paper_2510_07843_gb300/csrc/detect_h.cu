@@ -65,7 +65,15 @@ __global__ void __launch_bounds__(128) detect_h_kernel(Geo g, const phy_c32* __r
   SolveInfo si;
   if constexpr (NL == 16) {
     cf scratch[kScrSlots];
-    si = solve16(getA, LocalScratch{scratch}, b, x, dd);
+    // runtime row of the register-held matrix by predicated compile-time selects
+    auto rowA = [&](int l, cf (&row)[8]) {
+#pragma unroll
+      for (int li = 8; li < 16; ++li)
+        if (li == l)
+#pragma unroll
+          for (int k = 0; k < 8; ++k) row[k] = a[tri(li, k)];
+    };
+    si = solve16(getA, rowA, LocalScratch{scratch}, b, x, dd);
   } else {
     si = solve_small<NL>(getA, b, x, dd);
   }

@@ -149,9 +149,11 @@ __device__ __forceinline__ SolveInfo solve_small(GetA getA, const cf (&b)[N], cf
 // then fits the instruction cache, which the fully unrolled form did not.
 constexpr int kScrL21 = 0, kScrV = 64, kScrSlots = 72;
 
-template <class GetA, class Scr>
-__device__ __forceinline__ SolveInfo solve16(GetA getA, Scr scr, const cf (&b)[16], cf (&x)[16],
-                                             float (&d)[16]) {
+// rowA(l, row) fills row[k] = A(l, k), k = 0..7, for a row l >= 8 known only at run time (the
+// runtime-row form of getA, for the rolled L21 loop).
+template <class GetA, class RowA, class Scr>
+__device__ __forceinline__ SolveInfo solve16(GetA getA, RowA rowA, Scr scr, const cf (&b)[16],
+                                             cf (&x)[16], float (&d)[16]) {
   constexpr int B = 8;
   SolveInfo si{true, true, 3.0e38f, 0.f};
   // ---- block 1: L11, z1 = L11^-1 b1, M = L11^-1
@@ -175,18 +177,20 @@ __device__ __forceinline__ SolveInfo solve16(GetA getA, Scr scr, const cf (&b)[1
 #pragma unroll 1
   for (int i = 0; i < B; ++i) {
     cf row[B];
-#pragma unroll
-    for (int k = 0; k < B; ++k) row[k] = getA(B + i, k);
-    cf acc = scr.ld(kScrV + i);
+    rowA(B + i, row);
+    cf acc = scr.ld(kScrV + i), acc2 = mk(0.f, 0.f);
 #pragma unroll
     for (int j = 0; j < B; ++j) {
       cf l = mk(0.f, 0.f);
 #pragma unroll
       for (int k = 0; k <= j; ++k) l = cfma_cj(M(j, k), row[k], l);  // row[k] conj(M[j][k])
       scr.st(kScrL21 + i * B + j, l);
-      acc = cfms(l, z1[j], acc);
+      if (j & 1)
+        acc2 = cfms(l, z1[j], acc2);
+      else
+        acc = cfms(l, z1[j], acc);
     }
-    scr.st(kScrV + i, acc);
+    scr.st(kScrV + i, acc + acc2);
   }
   // ---- S = A22 - L21 L21^H
   cf s[B * (B + 1) / 2];
