@@ -213,6 +213,28 @@ phy_status phy_slot_run_noalloc(const phy_slot_cfg* cfg, const phy_c32* Y, const
                                 const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
                                 uint8_t* flags, void* stream);
 
+/*
+ * Tile autotuner for the detection chunk (no counterpart in the paper). Detection runs in chunks
+ * of cells: the Gram/matched-filter kernel writes one chunk's intermediates (about 16 MB per
+ * 273-PRB cell at 64x16) and the solve kernel reads them back, so the chunk size trades L2
+ * residency of those intermediates against launch count and tail effects. phy_autotune() runs
+ * phy_slot_run() on the caller's buffers for every chunk size that fits `workspace_bytes`
+ * (1, 2, 4, ... cells and the whole batch): one warm-up and three timed runs each (CUDA events
+ * on `stream`), and keeps the fastest in a process-wide table keyed by every field of cfg that
+ * shapes the work. Later phy_slot_run(), phy_detect_anchors() and phy_slot_run_host() calls
+ * with an equal cfg use that chunk (still shrunk to fit their workspace); phy_detect_stage()
+ * always runs the whole batch as one chunk.
+ *  - Synchronises `stream` (a tuning call, not for the hot path); same arguments and rules as
+ *    phy_slot_run(); afterwards the outputs hold a normal phy_slot_run() result.
+ *  - *chunk_out (may be NULL) receives the chosen cells per chunk.
+ * phy_autotune_clear() forgets every tuned configuration. Both are thread-safe.
+ */
+phy_status phy_autotune(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32* pilots,
+                        const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
+                        uint8_t* flags, void* workspace, size_t workspace_bytes, void* stream,
+                        int32_t* chunk_out);
+void phy_autotune_clear(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,6 +1,10 @@
 // C ABI of libphy.so: argument validation, slot geometry, workspace carving, stream enqueue.
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
 
 #include "../../include/phy.h"
 #include "launch.h"
@@ -97,9 +101,32 @@ size_t workspace_for_chunk(const Geo& g, int chunk) {
   return align_up(anchor_bytes(g)) + align_up(phy::detect_scratch_bytes(g, chunk));
 }
 
+// ---------------------------------------------------------------- autotuner table
+// Key: every Geo field that shapes the work (sizes, symbols, DMRS, cover, precision, refactor).
+struct TuneKey {
+  int v[12];
+  bool operator<(const TuneKey& o) const {
+    for (int i = 0; i < 12; ++i)
+      if (v[i] != o.v[i]) return v[i] < o.v[i];
+    return false;
+  }
+};
+TuneKey tune_key(const Geo& g) {
+  return TuneKey{{g.n_cells, g.n_sc, g.n_sym, g.n_rx, g.n_layers, g.qm, g.n_dmrs, g.dmrs0,
+                  g.dmrs1, g.L, g.prec, g.refactor}};
+}
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;
+
 }  // namespace
 
 namespace phy {
+
+int tuned_chunk(const Geo& g) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned.find(tune_key(g));
+  return it == g_tuned.end() ? 0 : it->second;
+}
 
 size_t min_workspace_bytes(const phy_slot_cfg* cfg) {
   Geo g;
@@ -275,6 +302,82 @@ phy_status phy_slot_run_host(const phy_slot_cfg* cfg, const phy_c32* Y_host,
       cudaMemcpyAsync(flags_host, flags, n_re, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return PHY_ERR_CUDA;
   return PHY_OK;
+}
+
+phy_status phy_autotune(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32* pilots,
+                        const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
+                        uint8_t* flags, void* workspace, size_t workspace_bytes, void* stream,
+                        int32_t* chunk_out) {
+  Geo g;
+  phy_status s = make_geo(cfg, &g);
+  if (s != PHY_OK) return s;
+  if (!Y || !pilots || !sigma2 || !flags || !workspace || ((uintptr_t)Y % 16))
+    return PHY_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace) % kAlign) return PHY_ERR_INVALID_ARG;
+  if (workspace_bytes < phy_workspace_size(cfg)) return PHY_ERR_NO_MEMORY;
+  s = check_shape(g);
+  if (s != PHY_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int> cand;
+  for (int c = 1; c < g.n_cells; c *= 2) cand.push_back(c);
+  cand.push_back(g.n_cells);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return PHY_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return PHY_ERR_CUDA;
+  }
+  const TuneKey key = tune_key(g);
+  int best = 0;
+  float best_ms = 0.f;
+  phy_status rs = PHY_OK;
+  for (int c : cand) {
+    if (workspace_for_chunk(g, c) > workspace_bytes) continue;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tuned[key] = c;
+    }
+    float t[3];
+    for (int rep = -1; rep < 3 && rs == PHY_OK; ++rep) {
+      if (rep >= 0 && cudaEventRecord(e0, st) != cudaSuccess) rs = PHY_ERR_CUDA;
+      if (rs == PHY_OK)
+        rs = phy::slot_run_fit(cfg, Y, pilots, sigma2, x_hat, sinr, llr, flags, workspace,
+                               workspace_bytes, st);
+      if (rep >= 0 && rs == PHY_OK) {
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t[rep], e0, e1) != cudaSuccess)
+          rs = PHY_ERR_CUDA;
+      }
+    }
+    if (rs != PHY_OK) break;
+    std::sort(t, t + 3);
+    if (best == 0 || t[1] < best_ms) {
+      best = c;
+      best_ms = t[1];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (rs == PHY_OK && best > 0)
+      g_tuned[key] = best;
+    else
+      g_tuned.erase(key);
+  }
+  if (rs != PHY_OK) return rs;
+  // leave the outputs as a plain call with the chosen chunk produces them
+  rs = phy::slot_run_fit(cfg, Y, pilots, sigma2, x_hat, sinr, llr, flags, workspace,
+                         workspace_bytes, st);
+  if (rs != PHY_OK) return rs;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return PHY_ERR_CUDA;
+  if (chunk_out) *chunk_out = best;
+  return PHY_OK;
+}
+
+void phy_autotune_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned.clear();
 }
 
 }  // extern "C"

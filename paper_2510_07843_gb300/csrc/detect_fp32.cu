@@ -711,8 +711,12 @@ cudaError_t launch_detect(const Geo& g, const phy_c32* anchors, const phy_c32* Y
                           uint8_t* flags, void* scratch, size_t scratch_bytes_avail, int stages,
                           cudaStream_t st) {
   const int wmax = host_max_segment_width(g);
-  // the largest chunk of cells (up to the preferred one) whose intermediates fit the scratch
-  int chunk = detect_preferred_chunk(g);
+  // the largest chunk of cells (up to the tuned or preferred one) whose intermediates fit the
+  // scratch; a single stage needs the whole batch in one chunk
+  const int tuned = tuned_chunk(g);
+  int chunk = stages != (kStageGramMf | kStageSolve) ? g.n_cells
+              : tuned > 0                            ? std::min(tuned, g.n_cells)
+                                                     : detect_preferred_chunk(g);
   Sizes s = sizes(g, chunk);
   while (chunk > 1 && scratch_bytes(s, chunk) > scratch_bytes_avail) s = sizes(g, --chunk);
   if (scratch_bytes(s, chunk) > scratch_bytes_avail) return cudaErrorInvalidValue;

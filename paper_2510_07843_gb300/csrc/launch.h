@@ -15,6 +15,8 @@ size_t fused_fp32_smem_bytes(const Geo& g);
 // Scratch bytes for chunks of `chunk` cells, and the chunk size the library prefers.
 size_t detect_scratch_bytes(const Geo& g, int chunk);
 int detect_preferred_chunk(const Geo& g);
+// Cells per chunk chosen by phy_autotune() for this geometry, or 0 if it was never tuned.
+int tuned_chunk(const Geo& g);
 
 cudaError_t launch_chest(const Geo& g, const phy_c32* Y, const phy_c32* pilots, phy_c32* anchors,
                          cudaStream_t st);

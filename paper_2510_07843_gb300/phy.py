@@ -45,6 +45,8 @@ _SIGS = {
     "phy_slot_run_noalloc": (ctypes.c_int, [_P] * 9),
     "phy_stage_supported": (ctypes.c_int32, [_P]),
     "phy_detect_stage": (ctypes.c_int, [_P, ctypes.c_int32] + [_P] * 8 + [ctypes.c_size_t, _P]),
+    "phy_autotune": (ctypes.c_int, [_P] * 9 + [ctypes.c_size_t, _P, _P]),
+    "phy_autotune_clear": (None, []),
 }
 
 STAGE_GRAM_MF, STAGE_SOLVE = 0, 1
@@ -189,6 +191,25 @@ def slot_run(cfg: SlotConfig, Y, pilots, sigma2, x_hat, sinr, llr, flags, worksp
            load().phy_slot_run(ctypes.byref(c), _ptr(Y), _ptr(pilots), _ptr(sigma2), _ptr(x_hat),
                                _ptr(sinr), _ptr(llr), _ptr(flags), _ptr(workspace), ws_bytes,
                                _stream(stream)))
+
+
+def autotune(cfg: SlotConfig, Y, pilots, sigma2, x_hat, sinr, llr, flags, workspace,
+             stream=None) -> int:
+    """phy_autotune: times phy_slot_run for each chunk size that fits the workspace and keeps the
+    fastest for cfg (process-wide); returns the chosen cells per chunk. Synchronises."""
+    c = cfg.c()
+    ws_bytes = workspace.numel() * workspace.element_size()
+    out = ctypes.c_int32(0)
+    _check("phy_autotune",
+           load().phy_autotune(ctypes.byref(c), _ptr(Y), _ptr(pilots), _ptr(sigma2), _ptr(x_hat),
+                               _ptr(sinr), _ptr(llr), _ptr(flags), _ptr(workspace), ws_bytes,
+                               _stream(stream), ctypes.byref(out)))
+    return int(out.value)
+
+
+def autotune_clear():
+    """phy_autotune_clear: forget every tuned configuration."""
+    load().phy_autotune_clear()
 
 
 def slot_run_noalloc(cfg: SlotConfig, Y, pilots, sigma2, x_hat, sinr, llr, flags, stream=None):

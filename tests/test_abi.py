@@ -76,3 +76,27 @@ def test_null_and_small_workspace_rejected(lib):
     assert rc == 3  # workspace too small
     assert lib.phy_chest(None, fake, fake, fake, None) == 1
     assert lib.phy_status_str(3) == b"workspace too small"
+
+
+def test_autotune_validates_before_any_cuda_call(lib):
+    bad = _cfg(qm=3).c()
+    fake = ctypes.c_void_p(256)  # never dereferenced: the call fails validation first
+    out = ctypes.c_int32(-7)
+    rc = lib.phy_autotune(ctypes.byref(bad), fake, fake, fake, None, None, None, fake, fake, 0,
+                          None, ctypes.byref(out))
+    assert rc == 1 and out.value == -7
+    c = _cfg().c()
+    rc = lib.phy_autotune(ctypes.byref(c), fake, fake, fake, None, None, None, fake, fake, 16,
+                          None, ctypes.byref(out))
+    assert rc == 3 and out.value == -7  # workspace too small, nothing tuned
+    lib.phy_autotune_clear()
+
+
+def test_tensor_core_precision_needs_even_antenna_count(lib):
+    c = _cfg(n_cells=1, n_prb=4, n_rx=5, n_layers=2, qm=4, precision="fp16").c()
+    assert lib.phy_workspace_size(ctypes.byref(c)) > 0  # a valid shape ...
+    ws = lib.phy_workspace_size(ctypes.byref(c))
+    fake = ctypes.c_void_p(256)
+    rc = lib.phy_slot_run(ctypes.byref(c), fake, fake, fake, None, None, None, fake, fake, ws,
+                          None)
+    assert rc == 2  # ... that the TMA-fed tensor-core kernel does not support
