@@ -259,6 +259,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "fp16", "bf16"])
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle timing")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop latency run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -311,6 +312,30 @@ def config_dict(spec, args, world):
             "n_layers": spec.n_layers, "qm": spec.qm, "snr_db": spec.snr_db,
             "precision": args.precision, "parallelism": f"replicas x{world} (cells per rank)",
             "l2": "working set per step larger than the 129 MB L2 (no flush needed)"}
+
+
+def serving_run(spec, precision, dev, buf, slots=100):
+    """Per-job latency in the serving loop: every 0.5 ms slot the batch's cells arrive as jobs
+    (one cell each, inputs resident on the device) and are served by captured receiver graphs."""
+    import dataclasses
+    from paper_2510_07843_gb300 import phy, serve
+    cfg1 = dataclasses.replace(phy.SlotConfig.from_spec(spec, precision=precision), n_cells=1)
+    s2 = buf.sigma2.cpu().tolist()
+    jobs = [serve.Job(cfg1, buf.Y[c:c + 1], buf.pilots[c:c + 1], s2[c],
+                      arrival=s * serve.DEADLINE_S, job_id=s * spec.n_cells + c,
+                      sigma2_dev=buf.sigma2[c:c + 1])
+            for s in range(slots) for c in range(spec.n_cells)]
+    srv = serve.SlotServer(device=dev, max_cells=spec.n_cells)
+    srv.prepare([cfg1])
+    srv.run(jobs[:spec.n_cells], realtime=False, keep=False)  # captures the in-place receiver
+    srv.service.clear()
+    srv.batches = 0
+    done = srv.run(jobs, realtime=True, keep=False)
+    out = serve.latency_summary(done, service=srv.service)
+    out.update(workload=f"{spec.n_cells} cells per {serve.DEADLINE_S * 1e3:g} ms slot, "
+                        "slot-synchronous arrivals, inputs resident (read in place)",
+               slots=slots, batches=srv.batches)
+    return out
 
 
 def run_ours(args, spec, rank, world, local):
@@ -420,6 +445,10 @@ def run_ours(args, spec, rank, world, local):
             torch.distributed.destroy_process_group()
         return 0
 
+    serving = None
+    if not args.no_serving:
+        serving = serving_run(spec, args.precision, dev, buf)
+
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         r = oracle_sample_rate(spec, S.make_slot(dataclasses.replace(spec, n_cells=1),
@@ -488,6 +517,7 @@ def run_ours(args, spec, rank, world, local):
                      "frac": ab["step"] / (total_ms / args.steps * 1e-3) / 1e9 / hbm_peak},
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "serving": serving,
         "gpu_launches": (1 + 2 * detect_chunks(spec)) * args.steps,
         "clocks": clk,
     }

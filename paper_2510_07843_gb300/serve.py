@@ -1,0 +1,265 @@
+"""Serving slot loop: continuous batching of uplink receiver jobs on one GPU.
+
+A job is one cell's slot (received grid, DMRS pilots, noise variance) with its receiver
+configuration (a SlotConfig with n_cells = 1). Cells are independent, so jobs with equal
+configurations batch by placing their cells side by side in one phy_slot_run call. The server
+keeps, per (configuration, batch size), persistent device buffers and a CUDA graph of the
+whole receiver captured on them; a batch copies its jobs' inputs into the buffers, replays the
+graph and copies each job's LLRs and flags out; when a batch's inputs already sit side by side
+in device memory (consecutive cells of one resident input), a receiver captured on those
+addresses reads them in place instead. Batch sizes are powers of two up to a limit
+that the configuration's device memory (buffers plus workspace) sets against a budget, so
+admission is by device memory. Latency is measured per job from its arrival to the host seeing
+its batch complete, against the slot deadline.
+
+Everything on the device runs in libphy.so; this module only schedules and marshals.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+from dataclasses import dataclass, field
+from typing import Callable, Dict, List, Optional, Sequence, Tuple
+
+from . import phy
+
+DEADLINE_S = 0.5e-3  # one 30 kHz slot
+
+
+def config_key(cfg: phy.SlotConfig) -> Tuple:
+    """Hashable identity of a per-cell configuration (n_cells excluded)."""
+    d = dataclasses.asdict(cfg)
+    d.pop("n_cells")
+    d["dmrs_sym"] = tuple(d["dmrs_sym"])
+    return tuple(sorted(d.items()))
+
+
+@dataclass
+class Job:
+    cfg: phy.SlotConfig        # per-cell configuration (n_cells is ignored)
+    Y: object                  # device tensor [1][sym][rx][sc] complex64
+    pilots: object             # device tensor [1][dmrs][layer][sc] complex64
+    sigma2: float
+    arrival: float = 0.0       # seconds on the server clock
+    job_id: int = 0
+    sigma2_dev: object = None  # optional device view [1] float32 of sigma2 (zero-copy batches)
+    llr: object = None         # filled: device tensor [1][dsym][sc][layer][qm]
+    flags: object = None       # filled: device tensor [1][dsym][sc]
+    done: float = field(default=float("nan"))
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+def batch_sizes(max_cells: int) -> List[int]:
+    """Powers of two up to max_cells (at least 1)."""
+    out, b = [], 1
+    while b <= max(1, max_cells):
+        out.append(b)
+        b *= 2
+    return out
+
+
+def pick_batch(n_waiting: int, max_cells: int) -> int:
+    """Largest power of two not above the waiting count and the admission limit."""
+    b = 1
+    while b * 2 <= min(n_waiting, max_cells):
+        b *= 2
+    return b
+
+
+def bytes_per_cell(cfg: phy.SlotConfig) -> int:
+    """Device bytes one cell of cfg takes in a batch: inputs, outputs and workspace share."""
+    one = dataclasses.replace(cfg, n_cells=1)
+    K, nds, nl = one.n_sc, one.n_dsym, one.n_layers
+    io = (one.n_sym * one.n_rx * K * 8 + len(one.dmrs_sym) * nl * K * 8 + 4
+          + nds * K * nl * (8 + 4 + 4 * one.qm) + nds * K
+          + len(one.dmrs_sym) * phy.n_groups(one) * nl * one.n_rx * 8)
+    return io + phy.workspace_size(one)
+
+
+def admission_limit(cfg: phy.SlotConfig, budget_bytes: int, max_cells: int) -> int:
+    """Cells of cfg one batch may hold under the device-memory budget (at least 1)."""
+    return max(1, min(max_cells, budget_bytes // max(1, bytes_per_cell(cfg))))
+
+
+def _follows(a, b) -> bool:
+    """b is the cell right after a in the same storage (both [1][...] views)."""
+    return (a.untyped_storage().data_ptr() == b.untyped_storage().data_ptr() and
+            b.data_ptr() == a.data_ptr() + a.numel() * a.element_size() and a.is_contiguous()
+            and b.is_contiguous())
+
+
+def _direct(jobs: Sequence[Job]) -> bool:
+    """All inputs of the batch are consecutive cells of their sources (and the source grid is
+    16-byte aligned), so the receiver can read them in place."""
+    if any(j.sigma2_dev is None for j in jobs) or jobs[0].Y.data_ptr() % 16:
+        return False
+    return all(_follows(a.Y, b.Y) and _follows(a.pilots, b.pilots) and
+               _follows(a.sigma2_dev, b.sigma2_dev) for a, b in zip(jobs, jobs[1:]))
+
+
+def _span(first, n: int):
+    """The n consecutive cells starting at view `first` as one [n][...] tensor."""
+    if n == 1:
+        return first
+    return first.as_strided((n,) + tuple(first.shape[1:]), first.stride())
+
+
+class _Graph:
+    """Persistent buffers and the captured receiver for one (configuration, batch size)."""
+
+    def __init__(self, cfg: phy.SlotConfig, n_cells: int, device, stream):
+        import torch
+        self.cfg = dataclasses.replace(cfg, n_cells=n_cells)
+        self.buf = phy.SlotBuffers(self.cfg, device=device)
+        self.buf.Y.zero_()
+        self.buf.pilots.zero_()
+        self.buf.sigma2.fill_(1.0)
+        self.stream = stream
+        args = (self.buf.Y, self.buf.pilots, self.buf.sigma2, self.buf.x_hat, self.buf.sinr,
+                self.buf.llr, self.buf.flags, self.buf.workspace)
+        with torch.cuda.stream(stream):
+            phy.slot_run(self.cfg, *args, stream=stream)  # configures kernels before capture
+        stream.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=stream):
+            phy.slot_run(self.cfg, *args, stream=stream)
+        self.direct = {}  # captured receivers reading resident inputs in place, by address
+
+    def run(self, jobs: Sequence[Job], keep: bool = True):
+        import torch
+        if _direct(jobs):  # inputs already side by side in device memory: read in place
+            b, n = self.buf, len(jobs)
+            key = (jobs[0].Y.data_ptr(), jobs[0].pilots.data_ptr(), jobs[0].sigma2_dev.data_ptr())
+            g = self.direct.get(key)
+            if g is None:  # one captured receiver per input location (a ring has few)
+                ins = (_span(jobs[0].Y, n), _span(jobs[0].pilots, n), _span(jobs[0].sigma2_dev, n))
+                outs = (b.x_hat, b.sinr, b.llr, b.flags, b.workspace)
+                if len(self.direct) >= 64:
+                    self.direct.clear()
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=self.stream):
+                    phy.slot_run(self.cfg, *ins, *outs, stream=self.stream)
+                self.direct[key] = g
+            with torch.cuda.stream(self.stream):
+                g.replay()
+                if keep:
+                    for i, j in enumerate(jobs):
+                        j.llr = b.llr[i:i + 1].clone()
+                        j.flags = b.flags[i:i + 1].clone()
+            self.stream.synchronize()
+            return
+        with torch.cuda.stream(self.stream):
+            # inputs into the batch buffers: one copy per run of jobs whose tensors are
+            # consecutive cells of one source (the common case of a cell-major input ring)
+            i = 0
+            while i < len(jobs):
+                e = i + 1
+                while (e < len(jobs) and _follows(jobs[e - 1].Y, jobs[e].Y) and
+                       _follows(jobs[e - 1].pilots, jobs[e].pilots)):
+                    e += 1
+                src_y = _span(jobs[i].Y, e - i)
+                src_p = _span(jobs[i].pilots, e - i)
+                self.buf.Y[i:e].copy_(src_y, non_blocking=True)
+                self.buf.pilots[i:e].copy_(src_p, non_blocking=True)
+                i = e
+            s2 = torch.tensor([float(j.sigma2) for j in jobs], dtype=torch.float32)
+            self.buf.sigma2[:len(jobs)].copy_(s2.pin_memory(), non_blocking=True)
+            self.graph.replay()
+            if keep:
+                for i, j in enumerate(jobs):
+                    j.llr = self.buf.llr[i:i + 1].clone()
+                    j.flags = self.buf.flags[i:i + 1].clone()
+        self.stream.synchronize()
+
+
+class SlotServer:
+    """Continuous batching over captured receiver graphs (see the module docstring)."""
+
+    def __init__(self, device="cuda", max_cells: int = 8, memory_budget: int = 2 << 30,
+                 clock: Callable[[], float] = time.perf_counter):
+        self.device = device
+        self.max_cells = max_cells
+        self.budget = memory_budget
+        self.clock = clock
+        self.stream = None  # created with the first graph
+        self.graphs: Dict[Tuple, _Graph] = {}
+        self.limits: Dict[Tuple, int] = {}
+        self.batches = 0
+        self.service: List[float] = []  # seconds per batch, launch to completion seen
+
+    def limit(self, cfg: phy.SlotConfig) -> int:
+        k = config_key(cfg)
+        if k not in self.limits:
+            self.limits[k] = admission_limit(cfg, self.budget, self.max_cells)
+        return self.limits[k]
+
+    def prepare(self, cfgs: Sequence[phy.SlotConfig]):
+        """Captures the graphs of every batch size each configuration may use (before timing)."""
+        for cfg in cfgs:
+            for b in batch_sizes(self.limit(cfg)):
+                self._graph(cfg, b)
+
+    def _graph(self, cfg: phy.SlotConfig, n: int) -> _Graph:
+        k = (config_key(cfg), n)
+        if k not in self.graphs:
+            import torch
+            if self.stream is None:
+                self.device = torch.device(self.device)
+                self.stream = torch.cuda.Stream(device=self.device)
+            self.graphs[k] = _Graph(cfg, n, self.device, self.stream)
+        return self.graphs[k]
+
+    def run(self, jobs: Sequence[Job], realtime: bool = True, keep: bool = True) -> List[Job]:
+        """Serves jobs in arrival order. With realtime, job.arrival is an offset in seconds from
+        the start of the call and jobs are not seen before they arrive; otherwise all are
+        waiting at once (done then counts from the start). Returns the jobs with done (and,
+        with keep, their own copies of llr and flags) filled, in completion order."""
+        pending = sorted(jobs, key=lambda j: j.arrival)
+        queues: Dict[Tuple, List[Job]] = {}
+        t0 = self.clock()
+        i = 0
+        finished: List[Job] = []
+        while i < len(pending) or any(queues.values()):
+            now = self.clock() - t0
+            while i < len(pending) and (not realtime or pending[i].arrival <= now):
+                queues.setdefault(config_key(pending[i].cfg), []).append(pending[i])
+                i += 1
+            ready = [(q[0].arrival, k) for k, q in queues.items() if q]
+            if not ready:  # idle until the next arrival
+                if realtime and i < len(pending):
+                    while self.clock() - t0 < pending[i].arrival:
+                        pass
+                continue
+            _, key = min(ready)  # the configuration whose oldest job has waited longest
+            q = queues[key]
+            cfg = q[0].cfg
+            b = pick_batch(len(q), self.limit(cfg))
+            batch, queues[key] = q[:b], q[b:]
+            ts = self.clock()
+            self._graph(cfg, b).run(batch, keep=keep)
+            self.batches += 1
+            t = self.clock() - t0
+            self.service.append(t + t0 - ts)
+            for j in batch:
+                j.done = t
+            finished.extend(batch)
+        return finished
+
+
+def latency_summary(jobs: Sequence[Job], deadline: float = DEADLINE_S,
+                    service: Optional[Sequence[float]] = None) -> dict:
+    """Per-job latency (arrival to completion seen by the host) percentiles against the
+    deadline; with `service`, also the per-batch service time (launch to completion)."""
+    import numpy as np
+    lat = np.array([j.latency for j in jobs]) * 1e3
+    out = {"jobs": len(jobs), "p50_ms": float(np.percentile(lat, 50)),
+           "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
+           "deadline_ms": deadline * 1e3, "missed": int((lat > deadline * 1e3).sum())}
+    if service:
+        sv = np.array(service) * 1e3
+        out.update(service_p50_ms=float(np.percentile(sv, 50)),
+                   service_p99_ms=float(np.percentile(sv, 99)))
+    return out

@@ -1,0 +1,135 @@
+"""Serving slot loop: host-side batching and admission (CPU), and on the GPU that every job's
+result in a mixed, batched stream equals its result alone."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_2510_07843_gb300 import phy, serve
+from paper_2510_07843_gb300 import synth as S
+
+SMALL = phy.SlotConfig(n_cells=1, n_prb=51, n_rx=4, n_layers=2, qm=4, dmrs_sym=(2,))
+CARRIER = phy.SlotConfig(n_cells=1, n_prb=25, n_rx=16, n_layers=4, qm=6, dmrs_sym=(2, 11))
+MASSIVE = phy.SlotConfig(n_cells=1, n_prb=273, n_rx=64, n_layers=16, qm=8, dmrs_sym=(2, 11))
+
+
+def test_batch_sizes_and_pick():
+    assert serve.batch_sizes(8) == [1, 2, 4, 8]
+    assert serve.batch_sizes(6) == [1, 2, 4]
+    assert serve.batch_sizes(0) == [1]
+    assert [serve.pick_batch(n, 8) for n in (1, 2, 3, 5, 8, 20)] == [1, 2, 2, 4, 8, 8]
+    assert serve.pick_batch(7, 3) == 2
+
+
+def test_config_key_ignores_cell_count():
+    a = dataclasses.replace(MASSIVE, n_cells=3)
+    assert serve.config_key(a) == serve.config_key(MASSIVE)
+    assert serve.config_key(SMALL) != serve.config_key(CARRIER)
+    assert serve.config_key(dataclasses.replace(MASSIVE, precision="fp16")) != \
+        serve.config_key(MASSIVE)
+
+
+def test_admission_by_device_memory():
+    phy.load()
+    per = serve.bytes_per_cell(MASSIVE)
+    assert per > serve.bytes_per_cell(CARRIER) > serve.bytes_per_cell(SMALL)
+    assert serve.admission_limit(MASSIVE, 3 * per + 1, 8) == 3
+    assert serve.admission_limit(MASSIVE, per // 2, 8) == 1  # one cell is always admitted
+    assert serve.admission_limit(SMALL, 1 << 40, 8) == 8
+
+
+class _FakeGraph:
+    def __init__(self, log, key, n):
+        self.log, self.key, self.n = log, key, n
+
+    def run(self, jobs, keep=True):
+        assert len(jobs) == self.n
+        self.log.append((self.key, [j.job_id for j in jobs]))
+
+
+def test_scheduling_oldest_first_powers_of_two(monkeypatch):
+    phy.load()
+    log = []
+    srv = serve.SlotServer(max_cells=4, memory_budget=1 << 40)
+    monkeypatch.setattr(srv, "_graph",
+                        lambda cfg, n: _FakeGraph(log, serve.config_key(cfg)[0], n))
+    jobs = ([serve.Job(SMALL, None, None, 1.0, arrival=0.5, job_id=i) for i in range(5)] +
+            [serve.Job(CARRIER, None, None, 1.0, arrival=0.0, job_id=10 + i) for i in range(3)])
+    jobs[5].arrival = -1.0  # the oldest job is a CARRIER one
+    done = srv.run(jobs, realtime=False)
+    assert sorted(j.job_id for j in done) == sorted(j.job_id for j in jobs)
+    # CARRIER first (oldest waiting job), as 2 + 1; SMALL as 4 + 1
+    assert [len(b) for _, b in log] == [2, 1, 4, 1]
+    assert log[0][1] == [10, 11] and log[1][1] == [12]
+    assert log[2][1] == [0, 1, 2, 3] and log[3][1] == [4]
+
+
+@pytest.mark.gpu
+def test_mixed_jobs_equal_alone():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_07843_gb300 import build
+    build.build()
+    phy.load()
+    dev = torch.device("cuda:0")
+    specs = {"small": (S.spec_small_51prb(), SMALL), "carrier": (S.spec_carrier_273prb(n_prb=25),
+                                                                 CARRIER)}
+    jobs, rng = [], np.random.default_rng(5)
+    for n in range(14):
+        name = "small" if rng.random() < 0.5 else "carrier"
+        spec, cfg = specs[name]
+        sl = S.make_slot(spec, 700 + n, keep_h=False)
+        jobs.append(serve.Job(cfg, torch.from_numpy(sl.Y).to(dev),
+                              torch.from_numpy(sl.pilots).to(dev), float(sl.sigma2[0]),
+                              arrival=0.0, job_id=n))
+    srv = serve.SlotServer(device=dev, max_cells=4)
+    srv.prepare([SMALL, CARRIER])
+    done = srv.run(jobs, realtime=False)
+    assert len(done) == len(jobs) and srv.batches < len(jobs)
+    for j in jobs:  # each job alone, plain call
+        cfg = dataclasses.replace(j.cfg, n_cells=1)
+        b = phy.SlotBuffers(cfg, device=dev)
+        b.Y.copy_(j.Y)
+        b.pilots.copy_(j.pilots)
+        b.sigma2.fill_(j.sigma2)
+        phy.slot_run(cfg, b.Y, b.pilots, b.sigma2, b.x_hat, b.sinr, b.llr, b.flags, b.workspace)
+        torch.cuda.synchronize()
+        assert torch.equal(b.llr, j.llr), j.job_id
+        assert torch.equal(b.flags, j.flags), j.job_id
+    summ = serve.latency_summary(done)
+    print("mixed batch latency:", summ)
+    assert summ["jobs"] == len(jobs)
+
+
+@pytest.mark.gpu
+def test_zero_copy_batches_equal_alone():
+    """Jobs that are consecutive cells of one resident input are read in place (no copies, no
+    graph); each result still equals the job run alone."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_07843_gb300 import build
+    build.build()
+    phy.load()
+    dev = torch.device("cuda:0")
+    spec = S.spec_carrier_273prb(n_prb=25, n_cells=4)
+    sl = S.make_slot(spec, 811, keep_h=False)
+    Y = torch.from_numpy(sl.Y).to(dev)
+    P = torch.from_numpy(sl.pilots).to(dev)
+    s2 = torch.from_numpy(sl.sigma2).to(dev)
+    jobs = [serve.Job(CARRIER, Y[c:c + 1], P[c:c + 1], float(sl.sigma2[c]), job_id=c,
+                      sigma2_dev=s2[c:c + 1]) for c in range(4)]
+    assert serve._direct(jobs)
+    srv = serve.SlotServer(device=dev, max_cells=4)
+    done = srv.run(jobs, realtime=False)
+    assert srv.batches == 1 and len(done) == 4
+    for j in jobs:
+        b = phy.SlotBuffers(CARRIER, device=dev)
+        b.Y.copy_(j.Y)
+        b.pilots.copy_(j.pilots)
+        b.sigma2.copy_(j.sigma2_dev)
+        phy.slot_run(CARRIER, b.Y, b.pilots, b.sigma2, b.x_hat, b.sinr, b.llr, b.flags,
+                     b.workspace)
+        torch.cuda.synchronize()
+        assert torch.equal(b.llr, j.llr) and torch.equal(b.flags, j.flags), j.job_id
