@@ -258,6 +258,7 @@ def main():
                     help="override the workload's cells per GPU (smaller cases for profiling)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "fp16", "bf16"])
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle timing")
+    ap.add_argument("--llr", default="f32", choices=["f32", "f16"], help="LLR output format")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop latency run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -310,16 +311,18 @@ def config_dict(spec, args, world):
                         f"{2 ** spec.qm}-QAM, DMRS {list(spec.dmrs_sym)}",
             "n_cells_per_gpu": spec.n_cells, "n_prb": spec.n_prb, "n_rx": spec.n_rx,
             "n_layers": spec.n_layers, "qm": spec.qm, "snr_db": spec.snr_db,
-            "precision": args.precision, "parallelism": f"replicas x{world} (cells per rank)",
+            "precision": args.precision, "llr_format": args.llr,
+            "parallelism": f"replicas x{world} (cells per rank)",
             "l2": "working set per step larger than the 129 MB L2 (no flush needed)"}
 
 
-def serving_run(spec, precision, dev, buf, slots=100):
+def serving_run(spec, precision, dev, buf, slots=100, llr="f32"):
     """Per-job latency in the serving loop: every 0.5 ms slot the batch's cells arrive as jobs
     (one cell each, inputs resident on the device) and are served by captured receiver graphs."""
     import dataclasses
     from paper_2510_07843_gb300 import phy, serve
-    cfg1 = dataclasses.replace(phy.SlotConfig.from_spec(spec, precision=precision), n_cells=1)
+    cfg1 = dataclasses.replace(phy.SlotConfig.from_spec(spec, precision=precision,
+                                                        llr_format=llr), n_cells=1)
     s2 = buf.sigma2.cpu().tolist()
     jobs = [serve.Job(cfg1, buf.Y[c:c + 1], buf.pilots[c:c + 1], s2[c],
                       arrival=s * serve.DEADLINE_S, job_id=s * spec.n_cells + c,
@@ -349,7 +352,7 @@ def run_ours(args, spec, rank, world, local):
     dev = torch.device("cuda", local)
     build.build()
     phy.load()
-    cfg = phy.SlotConfig.from_spec(spec, precision=args.precision)
+    cfg = phy.SlotConfig.from_spec(spec, precision=args.precision, llr_format=args.llr)
     slot = S.make_slot(spec, rank_seed(rank), keep_h=False)
     buf = phy.SlotBuffers(cfg, device=dev)
     buf.Y.copy_(torch.from_numpy(slot.Y))
@@ -414,7 +417,7 @@ def run_ours(args, spec, rank, world, local):
         Yh = torch.from_numpy(slot.Y).pin_memory()
         Ph = torch.from_numpy(slot.pilots).pin_memory()
         sh = torch.from_numpy(slot.sigma2).pin_memory()
-        lh = torch.empty(buf.llr.shape, dtype=torch.float32).pin_memory()
+        lh = torch.empty(buf.llr.shape, dtype=buf.llr.dtype).pin_memory()
         fh = torch.empty(buf.flags.shape, dtype=torch.uint8).pin_memory()
 
         def e2e_step():
@@ -435,7 +438,7 @@ def run_ours(args, spec, rank, world, local):
         torch.cuda.synchronize()
         e_ms = max_over_ranks(a.elapsed_time(b), dev)
         h2d = Yh.numel() * 8 + Ph.numel() * 8 + sh.numel() * 4
-        d2h = lh.numel() * 4 + fh.numel()
+        d2h = lh.numel() * lh.element_size() + fh.numel()
         e2e = {"value": whole_job_rate(world, n_re, k2, e_ms), "unit": "REs/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "api": "phy_slot_run_host (pinned host buffers)"}
@@ -447,7 +450,7 @@ def run_ours(args, spec, rank, world, local):
 
     serving = None
     if not args.no_serving:
-        serving = serving_run(spec, args.precision, dev, buf)
+        serving = serving_run(spec, args.precision, dev, buf, llr=args.llr)
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:

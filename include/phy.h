@@ -33,7 +33,8 @@
  *  H        [cell][dsym][sc][rx][layer]             full channel (phy_mmse_detect only)
  *  x_hat    [cell][dsym][sc][layer]                 biased LMMSE output W y
  *  sinr     [cell][dsym][sc][layer]      float      post-equalisation SINR
- *  llr      [cell][dsym][sc][layer][qm]  float      max-log LLRs, positive = bit 0
+ *  llr      [cell][dsym][sc][layer][qm]  float      max-log LLRs, positive = bit 0 (IEEE
+ *                                                   binary16 with cfg.llr_format = PHY_LLR_F16)
  *  flags    [cell][dsym][sc]             uint8      see above
  *  sigma2   [cell]                       float      noise variance per Rx per RE (known)
  * `dsym` counts data symbols only: the symbols 0..n_sym-1 that are not DMRS symbols, in order.
@@ -82,6 +83,11 @@ typedef enum {
   PHY_PREC_TC_FP16 = 3  /* same with FP16 operands */
 } phy_precision;
 
+/* Element type of the llr outputs. PHY_LLR_F16 halves the largest output: each LLR is the FP32
+   value rounded to nearest IEEE binary16, values beyond its range saturating to +-65504. The
+   buffer is passed through the same float* parameters (cast); it holds 2-byte elements. */
+typedef enum { PHY_LLR_F32 = 0, PHY_LLR_F16 = 1 } phy_llr_format;
+
 typedef struct {
   int32_t n_cells;        /* independent cells (slots) in one call, >= 1 */
   int32_t n_prb;          /* physical resource blocks; n_sc = 12 n_prb, 1..275 */
@@ -95,6 +101,7 @@ typedef struct {
   int32_t precision;      /* phy_precision */
   float pivot_ratio_min;  /* flag bit 0 threshold on min L_kk^2 / max L_kk^2, e.g. 1e-6 */
   int32_t fp64_refactor;  /* 1: re-compute flagged REs in FP64 (sets flag bit 1) */
+  int32_t llr_format;     /* phy_llr_format of the llr outputs */
 } phy_slot_cfg;
 
 /* Human-readable name of a status code (static string). */

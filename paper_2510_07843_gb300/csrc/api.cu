@@ -64,6 +64,8 @@ phy_status make_geo(const phy_slot_cfg* c, Geo* g) {
   t.pivot_min = c->pivot_ratio_min;
   t.prec = c->precision;
   t.refactor = c->fp64_refactor ? 1 : 0;
+  if (c->llr_format != PHY_LLR_F32 && c->llr_format != PHY_LLR_F16) return PHY_ERR_INVALID_ARG;
+  t.llr_f16 = c->llr_format == PHY_LLR_F16;
   int nd = 0;
   for (int s = 0; s < c->n_sym; ++s) {
     bool is_dmrs = false;
@@ -289,7 +291,7 @@ phy_status phy_slot_run_host(const phy_slot_cfg* cfg, const phy_c32* Y_host,
   const size_t y_bytes = (size_t)g.n_cells * g.n_sym * g.n_rx * g.n_sc * sizeof(phy_c32);
   const size_t p_bytes = (size_t)g.n_cells * g.n_dmrs * g.n_layers * g.n_sc * sizeof(phy_c32);
   const size_t n_re = (size_t)g.n_cells * g.n_dsym * g.n_sc;
-  const size_t l_bytes = n_re * g.n_layers * g.qm * sizeof(float);
+  const size_t l_bytes = n_re * g.n_layers * g.qm * (g.llr_f16 ? 2 : sizeof(float));
   if (cudaMemcpyAsync(Y, Y_host, y_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(pilots, pilots_host, p_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(sigma2, sigma2_host, g.n_cells * sizeof(float), cudaMemcpyHostToDevice,

@@ -2,6 +2,7 @@
 // interpolation weights and the max-log Gray QAM demapper.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -24,6 +25,7 @@ struct Geo {
   int n_seg;    // frequency segments (anchor pairs), max(G - 1, 1)
   int prec;     // phy_precision of the Gram and matched-filter products
   int refactor; // 1: recompute flagged (ill-conditioned) REs in FP64
+  int llr_f16;  // 1: LLR outputs as binary16
   float pivot_min;
   int dsym[kMaxSym];    // data symbol index j -> OFDM symbol t
   float tw[kMaxSym];    // weight of the second DMRS estimate at data symbol j
@@ -168,6 +170,19 @@ __device__ __forceinline__ void qam_llr(cf xt, float s2eff, float* llr) {
   for (int i = 0; i < H; ++i) {
     llr[2 * i] = li[i];
     llr[2 * i + 1] = lq[i];
+  }
+}
+
+// An LLR pair to the output at element index idx (even): FP32, or binary16 rounded to nearest
+// with saturation at +-65504 (the largest finite binary16) when f16.
+__device__ __forceinline__ void store_llr_pair(float* base, size_t idx, float a, float b,
+                                               bool f16) {
+  if (f16) {
+    const float m = 65504.f;
+    *reinterpret_cast<__half2*>(reinterpret_cast<__half*>(base) + idx) =
+        __floats2half2_rn(fminf(fmaxf(a, -m), m), fminf(fmaxf(b, -m), m));
+  } else {
+    *reinterpret_cast<float2*>(base + idx) = make_float2(a, b);
   }
 }
 

@@ -301,11 +301,11 @@ struct SmemScratch {
 
 
 template <int QM>
-__device__ __forceinline__ void store_llr(float* dst, cf xt, float s2eff) {
+__device__ __forceinline__ void store_llr(float* base, size_t idx, cf xt, float s2eff, bool f16) {
   float l[QM];
   qam_llr<QM>(xt, s2eff, l);
 #pragma unroll
-  for (int q = 0; q < QM; q += 2) *reinterpret_cast<float2*>(dst + q) = make_float2(l[q], l[q + 1]);
+  for (int q = 0; q < QM; q += 2) store_llr_pair(base, idx + q, l[q], l[q + 1], f16);
 }
 
 // Gram-block bytes of one (segment, data symbol): NTRI 4-tuples of complex values.
@@ -344,6 +344,28 @@ __device__ __forceinline__ void copy_out(float* dst, const float* src, int n) {
     i0 = n4 << 2;
   }
   for (int i = i0 + threadIdx.x; i < n; i += kSolveThreads) dst[i] = src[i];
+}
+
+// As copy_out, rounding to binary16 with saturation (n even; dst 8-byte aligned for the fast
+// path, which then writes four values per thread and step).
+__device__ __forceinline__ void copy_out_f16(__half* dst, const float* src, int n) {
+  int i0 = 0;
+  const float m = 65504.f;
+  if ((reinterpret_cast<uintptr_t>(dst) & 7) == 0) {
+    const int n4 = n >> 2;
+    for (int i = threadIdx.x; i < n4; i += kSolveThreads) {
+      const float4 v = reinterpret_cast<const float4*>(src)[i];
+      const __half2 a = __floats2half2_rn(fminf(fmaxf(v.x, -m), m), fminf(fmaxf(v.y, -m), m));
+      const __half2 b = __floats2half2_rn(fminf(fmaxf(v.z, -m), m), fminf(fmaxf(v.w, -m), m));
+      uint2 w;
+      w.x = *reinterpret_cast<const uint32_t*>(&a);
+      w.y = *reinterpret_cast<const uint32_t*>(&b);
+      reinterpret_cast<uint2*>(dst)[i] = w;
+    }
+    i0 = n4 << 2;
+  }
+  for (int i = i0 + threadIdx.x; i < n; i += kSolveThreads)
+    dst[i] = __float2half_rn(fminf(fmaxf(src[i], -m), m));
 }
 
 // One CTA per (128 subcarriers, data symbol, cell), one thread per RE. Thread 0 brings the
@@ -543,7 +565,12 @@ __global__ void __launch_bounds__(kSolveThreads)
     // this CTA's live REs are consecutive, so their records form one block in each output
     const int nlive = min(kSolveThreads, g.n_sc - k0);
     const size_t r0 = ((size_t)cell * nds + jj) * g.n_sc + k0;
-    if (llr_out) copy_out(llr_out + r0 * nl * QM, st_llr, nlive * nl * QM);
+    if (llr_out) {
+      if (g.llr_f16)
+        copy_out_f16(reinterpret_cast<__half*>(llr_out) + r0 * nl * QM, st_llr, nlive * nl * QM);
+      else
+        copy_out(llr_out + r0 * nl * QM, st_llr, nlive * nl * QM);
+    }
     if (sinr_out) copy_out(sinr_out + r0 * nl, st_sinr, nlive * nl);
     if (x_hat)
       copy_out(reinterpret_cast<float*>(x_hat + r0 * nl), reinterpret_cast<const float*>(st_xh),
@@ -557,12 +584,12 @@ __global__ void __launch_bounds__(kSolveThreads)
       if (ok) {
         if (x_hat) st(x_hat + li, x[l]);
         if (sinr_out) sinr_out[li] = o.sinr;
-        if (llr_out) store_llr<QM>(llr_out + li * QM, o.inv_mu * x[l], o.s2eff);
+        if (llr_out) store_llr<QM>(llr_out, li * QM, o.inv_mu * x[l], o.s2eff, g.llr_f16);
       } else {
         if (x_hat) st(x_hat + li, mk(0.f, 0.f));
         if (sinr_out) sinr_out[li] = 0.f;
         if (llr_out)
-          for (int q = 0; q < QM; ++q) llr_out[li * QM + q] = 0.f;
+          for (int q = 0; q < QM; q += 2) store_llr_pair(llr_out, li * QM + q, 0.f, 0.f, g.llr_f16);
       }
     }
   }

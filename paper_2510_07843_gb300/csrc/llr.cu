@@ -10,7 +10,7 @@ namespace {
 template <int QM>
 __global__ void __launch_bounds__(256) llr_kernel(size_t n, const phy_c32* __restrict__ x_hat,
                                                   const float* __restrict__ sinr,
-                                                  float* __restrict__ llr) {
+                                                  float* __restrict__ llr, bool f16) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const cf x = ld(x_hat + i);
@@ -25,8 +25,7 @@ __global__ void __launch_bounds__(256) llr_kernel(size_t n, const phy_c32* __res
     for (int q = 0; q < QM; ++q) out[q] = 0.f;
   }
 #pragma unroll
-  for (int q = 0; q < QM; q += 2)
-    *reinterpret_cast<float2*>(llr + i * QM + q) = make_float2(out[q], out[q + 1]);
+  for (int q = 0; q < QM; q += 2) store_llr_pair(llr, i * QM + q, out[q], out[q + 1], f16);
 }
 
 }  // namespace
@@ -37,10 +36,10 @@ cudaError_t launch_llr(const Geo& g, const phy_c32* x_hat, const float* sinr, fl
   const int threads = 256;
   const unsigned blocks = (unsigned)((n + threads - 1) / threads);
   switch (g.qm) {
-    case 2: llr_kernel<2><<<blocks, threads, 0, st>>>(n, x_hat, sinr, llr); break;
-    case 4: llr_kernel<4><<<blocks, threads, 0, st>>>(n, x_hat, sinr, llr); break;
-    case 6: llr_kernel<6><<<blocks, threads, 0, st>>>(n, x_hat, sinr, llr); break;
-    default: llr_kernel<8><<<blocks, threads, 0, st>>>(n, x_hat, sinr, llr); break;
+    case 2: llr_kernel<2><<<blocks, threads, 0, st>>>(n, x_hat, sinr, llr, g.llr_f16); break;
+    case 4: llr_kernel<4><<<blocks, threads, 0, st>>>(n, x_hat, sinr, llr, g.llr_f16); break;
+    case 6: llr_kernel<6><<<blocks, threads, 0, st>>>(n, x_hat, sinr, llr, g.llr_f16); break;
+    default: llr_kernel<8><<<blocks, threads, 0, st>>>(n, x_hat, sinr, llr, g.llr_f16); break;
   }
   return cudaGetLastError();
 }

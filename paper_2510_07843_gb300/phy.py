@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(PKG, "libphy.so")
 
 PHY_OK = 0
 PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "fp16": 3}
+LLR_FORMAT = {"f32": 0, "f16": 1}
 STATUS = {0: "PHY_OK", 1: "PHY_ERR_INVALID_ARG", 2: "PHY_ERR_UNSUPPORTED",
           3: "PHY_ERR_NO_MEMORY", 4: "PHY_ERR_CUDA", 5: "PHY_ERR_TIMEOUT"}
 
@@ -26,7 +27,8 @@ class CSlotCfg(ctypes.Structure):
                 ("n_layers", ctypes.c_int32), ("qm", ctypes.c_int32),
                 ("n_dmrs", ctypes.c_int32), ("dmrs_sym", ctypes.c_int32 * 2),
                 ("occ_len", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("pivot_ratio_min", ctypes.c_float), ("fp64_refactor", ctypes.c_int32)]
+                ("pivot_ratio_min", ctypes.c_float), ("fp64_refactor", ctypes.c_int32),
+                ("llr_format", ctypes.c_int32)]
 
 
 # Every entry point declared in include/phy.h, with its ctypes signature.
@@ -91,12 +93,14 @@ class SlotConfig:
     precision: str = "fp32"
     pivot_ratio_min: float = 1e-6
     fp64_refactor: bool = False
+    llr_format: str = "f32"  # "f16": LLRs as binary16 (saturating at +-65504)
 
     def c(self) -> CSlotCfg:
         ds = list(self.dmrs_sym) + [0] * (2 - len(self.dmrs_sym))
         return CSlotCfg(self.n_cells, self.n_prb, self.n_sym, self.n_rx, self.n_layers, self.qm,
                         len(self.dmrs_sym), (ctypes.c_int32 * 2)(*ds), self.occ_len,
-                        PREC[self.precision], self.pivot_ratio_min, int(self.fp64_refactor))
+                        PREC[self.precision], self.pivot_ratio_min, int(self.fp64_refactor),
+                        LLR_FORMAT.get(self.llr_format, -1))
 
     @property
     def n_sc(self) -> int:
@@ -246,7 +250,9 @@ class SlotBuffers:
             self.sigma2 = torch.empty((C,), dtype=f32, device=device)
         self.x_hat = torch.empty((C, nds, K, nl), dtype=c64, device=device)
         self.sinr = torch.empty((C, nds, K, nl), dtype=f32, device=device)
-        self.llr = torch.empty((C, nds, K, nl, cfg.qm), dtype=f32, device=device)
+        self.llr = torch.empty((C, nds, K, nl, cfg.qm),
+                               dtype=torch.float16 if cfg.llr_format == "f16" else f32,
+                               device=device)
         self.flags = torch.empty((C, nds, K), dtype=torch.uint8, device=device)
         self.anchors = torch.empty((C, len(cfg.dmrs_sym), n_groups(cfg), nl, cfg.n_rx),
                                    dtype=c64, device=device)

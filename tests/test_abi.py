@@ -55,7 +55,7 @@ def test_geometry_queries(lib):
     dict(n_layers=17), dict(n_layers=65, n_rx=64), dict(n_rx=65), dict(qm=3), dict(n_prb=0),
     dict(n_prb=276), dict(dmrs_sym=(11, 2)), dict(dmrs_sym=(2, 14)), dict(occ_len=3),
     dict(occ_len=4), dict(n_layers=16, n_prb=1), dict(n_cells=0), dict(n_layers=8, n_rx=4),
-    dict(precision="fp32", pivot_ratio_min=-1.0)])
+    dict(precision="fp32", pivot_ratio_min=-1.0), dict(llr_format="f8")])
 def test_invalid_configs_rejected(lib, bad):
     cfg = _cfg(**bad)
     c = cfg.c()

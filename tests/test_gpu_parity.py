@@ -296,3 +296,30 @@ def test_fp64_refactor_of_ill_conditioned_res(dev):
     e64 = rel_fro(fixed["x_hat"], ref["x_hat"])
     print("ill-conditioned x_hat rel err: fp32", e32, "fp64 refactor", e64)
     assert e64 < 1e-2 and e64 < e32 / 10
+
+
+def test_llr_binary16_output_is_the_rounded_fp32_output(dev):
+    """cfg.llr_format = f16: every LLR is the FP32 value rounded to nearest binary16, saturating
+    at +-65504; through the full receiver and through the stand-alone demapper."""
+    import torch
+    from paper_2510_07843_gb300 import phy
+    for spec, seed in ((S.spec_massive_mimo(n_cells=2, n_prb=6), 3200),
+                       (S.spec_small_51prb(), 1002)):
+        sl = S.make_slot(spec, seed, keep_h=False)
+        out = {}
+        for fmt in ("f32", "f16"):
+            cfg = phy.SlotConfig.from_spec(spec, llr_format=fmt)
+            b = phy.SlotBuffers(cfg, device=dev)
+            b.Y.copy_(torch.from_numpy(sl.Y))
+            b.pilots.copy_(torch.from_numpy(sl.pilots))
+            b.sigma2.copy_(torch.from_numpy(sl.sigma2))
+            phy.slot_run(cfg, b.Y, b.pilots, b.sigma2, b.x_hat, b.sinr, b.llr, b.flags,
+                         b.workspace)
+            demap = torch.empty_like(b.llr)
+            phy.llr_demap(cfg, b.x_hat, b.sinr, demap)
+            torch.cuda.synchronize()
+            out[fmt] = (b.llr, demap)
+        assert out["f16"][0].dtype == torch.float16
+        for k in range(2):
+            ref = out["f32"][k].clamp(-65504.0, 65504.0).half()
+            assert torch.equal(ref, out["f16"][k])
