@@ -259,6 +259,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "fp16", "bf16"])
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle timing")
     ap.add_argument("--llr", default="f32", choices=["f32", "f16"], help="LLR output format")
+    ap.add_argument("--streams", type=int, default=2,
+                    help="streams the timed steps alternate over (1: strictly serial)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop latency run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -312,6 +314,8 @@ def config_dict(spec, args, world):
             "n_cells_per_gpu": spec.n_cells, "n_prb": spec.n_prb, "n_rx": spec.n_rx,
             "n_layers": spec.n_layers, "qm": spec.qm, "snr_db": spec.snr_db,
             "precision": args.precision, "llr_format": args.llr,
+            "pipelining": (f"{args.streams} streams: consecutive steps overlap, own buffers"
+                           if args.streams > 1 else "serial"),
             "parallelism": f"replicas x{world} (cells per rank)",
             "l2": "working set per step larger than the 129 MB L2 (no flush needed)"}
 
@@ -400,10 +404,48 @@ def run_ours(args, spec, rank, world, local):
         ev[i][3].record(st)
     t_end.record(st)
     torch.cuda.synchronize()
-    clk = clocks.stop()
     if world > 1:
         torch.distributed.barrier()
     total_ms = t_start.elapsed_time(t_end)
+
+    # Pipelined pass: consecutive steps alternate over `streams` streams with their own buffers,
+    # so one step's kernels overlap the next one's (a continuous stream of slots). This is the
+    # throughput `value`; the serial pass above gives latency and the per-stage breakdown.
+    pipe_ms = None
+    if args.streams > 1:
+        sets = [(buf, st)]
+        for _ in range(args.streams - 1):
+            b2 = phy.SlotBuffers(cfg, device=dev)
+            b2.Y.copy_(buf.Y)
+            b2.pilots.copy_(buf.pilots)
+            b2.sigma2.copy_(buf.sigma2)
+            sets.append((b2, torch.cuda.Stream(device=dev)))
+
+        def pstep(i):
+            b, s_ = sets[i % len(sets)]
+            phy.slot_run(cfg, b.Y, b.pilots, b.sigma2, b.x_hat, b.sinr, b.llr, b.flags,
+                         b.workspace, stream=s_)
+
+        for i in range(max(args.warmup, 3) * len(sets)):
+            pstep(i)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(st)
+        for _, s_ in sets[1:]:
+            s_.wait_event(p0)
+        for i in range(args.steps):
+            pstep(i)
+        for _, s_ in sets[1:]:
+            st.wait_stream(s_)
+        p1.record(st)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        pipe_ms = max_over_ranks(p0.elapsed_time(p1), dev)
+    clk = clocks.stop()
     step_ms = [a.elapsed_time(d) for a, b, c, d in ev]
     chest_ms = [a.elapsed_time(b) for a, b, c, d in ev]
     gram_ms = [b.elapsed_time(c) for a, b, c, d in ev]
@@ -502,12 +544,14 @@ def run_ours(args, spec, rank, world, local):
     roofline.update(kernel=dominant["kernel"], peak_source=dominant["peak_source"],
                     per_kernel={"solve": solve_roof, "gram_mf": gram_roof},
                     split_stages=bool(split))
-    value = whole_job_rate(world, n_re, args.steps, total_ms)
+    timed_ms = pipe_ms if pipe_ms is not None else total_ms
+    value = whole_job_rate(world, n_re, args.steps, timed_ms)
     line = {
         "metric": METRIC, "value": value, "unit": "REs/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": timed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config_dict(spec, args, world),
+        "serial_ms_per_step": total_ms / args.steps,
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99)), "deadline_ms": 0.5,
                        "what": "one step (8-cell batch) on an idle GPU, CUDA events"},
