@@ -320,7 +320,7 @@ def config_dict(spec, args, world):
             "l2": "working set per step larger than the 129 MB L2 (no flush needed)"}
 
 
-def serving_run(spec, precision, dev, buf, slots=100, llr="f32"):
+def serving_run(spec, precision, dev, buf, slots=100, llr="f32", streams=2):
     """Per-job latency in the serving loop: every 0.5 ms slot the batch's cells arrive as jobs
     (one cell each, inputs resident on the device) and are served by captured receiver graphs."""
     import dataclasses
@@ -332,15 +332,17 @@ def serving_run(spec, precision, dev, buf, slots=100, llr="f32"):
                       arrival=s * serve.DEADLINE_S, job_id=s * spec.n_cells + c,
                       sigma2_dev=buf.sigma2[c:c + 1])
             for s in range(slots) for c in range(spec.n_cells)]
-    srv = serve.SlotServer(device=dev, max_cells=spec.n_cells)
+    srv = serve.SlotServer(device=dev, max_cells=spec.n_cells, streams=streams)
     srv.prepare([cfg1])
-    srv.run(jobs[:spec.n_cells], realtime=False, keep=False)  # captures the in-place receiver
+    # captures the in-place receiver on every lane
+    srv.run(jobs[:spec.n_cells * streams], realtime=False, keep=False)
     srv.service.clear()
     srv.batches = 0
     done = srv.run(jobs, realtime=True, keep=False)
     out = serve.latency_summary(done, service=srv.service)
     out.update(workload=f"{spec.n_cells} cells per {serve.DEADLINE_S * 1e3:g} ms slot, "
-                        "slot-synchronous arrivals, inputs resident (read in place)",
+                        "slot-synchronous arrivals, inputs resident (read in place), "
+                        f"{streams} batches in flight",
                slots=slots, batches=srv.batches)
     return out
 
@@ -492,7 +494,8 @@ def run_ours(args, spec, rank, world, local):
 
     serving = None
     if not args.no_serving:
-        serving = serving_run(spec, args.precision, dev, buf, llr=args.llr)
+        serving = serving_run(spec, args.precision, dev, buf, llr=args.llr,
+                              streams=args.streams)
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:

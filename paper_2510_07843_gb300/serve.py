@@ -128,7 +128,8 @@ class _Graph:
             phy.slot_run(self.cfg, *args, stream=stream)
         self.direct = {}  # captured receivers reading resident inputs in place, by address
 
-    def run(self, jobs: Sequence[Job], keep: bool = True):
+    def launch(self, jobs: Sequence[Job], keep: bool = True):
+        """Enqueues the batch on this graph's stream (no host synchronisation)."""
         import torch
         if _direct(jobs):  # inputs already side by side in device memory: read in place
             b, n = self.buf, len(jobs)
@@ -149,7 +150,6 @@ class _Graph:
                     for i, j in enumerate(jobs):
                         j.llr = b.llr[i:i + 1].clone()
                         j.flags = b.flags[i:i + 1].clone()
-            self.stream.synchronize()
             return
         with torch.cuda.stream(self.stream):
             # inputs into the batch buffers: one copy per run of jobs whose tensors are
@@ -172,23 +172,31 @@ class _Graph:
                 for i, j in enumerate(jobs):
                     j.llr = self.buf.llr[i:i + 1].clone()
                     j.flags = self.buf.flags[i:i + 1].clone()
-        self.stream.synchronize()
 
 
 class SlotServer:
     """Continuous batching over captured receiver graphs (see the module docstring)."""
 
     def __init__(self, device="cuda", max_cells: int = 8, memory_budget: int = 2 << 30,
-                 clock: Callable[[], float] = time.perf_counter):
+                 clock: Callable[[], float] = time.perf_counter, streams: int = 1):
         self.device = device
         self.max_cells = max_cells
         self.budget = memory_budget
         self.clock = clock
-        self.stream = None  # created with the first graph
+        self.lanes = max(1, streams)  # batches in flight at once, one stream each
+        self.streams = None  # created with the first graph
         self.graphs: Dict[Tuple, _Graph] = {}
         self.limits: Dict[Tuple, int] = {}
         self.batches = 0
-        self.service: List[float] = []  # seconds per batch, launch to completion seen
+        self.service: List[float] = []  # seconds per batch on the GPU (start to end event)
+
+    def _event(self):
+        import torch
+        return torch.cuda.Event(enable_timing=True)
+
+    def _sync(self):
+        import torch
+        torch.cuda.synchronize(self.device)
 
     def limit(self, cfg: phy.SlotConfig) -> int:
         k = config_key(cfg)
@@ -200,52 +208,83 @@ class SlotServer:
         """Captures the graphs of every batch size each configuration may use (before timing)."""
         for cfg in cfgs:
             for b in batch_sizes(self.limit(cfg)):
-                self._graph(cfg, b)
+                for lane in range(self.lanes):
+                    self._graph(cfg, b, lane)
 
-    def _graph(self, cfg: phy.SlotConfig, n: int) -> _Graph:
-        k = (config_key(cfg), n)
+    def _graph(self, cfg: phy.SlotConfig, n: int, lane: int = 0) -> _Graph:
+        k = (config_key(cfg), n, lane)
         if k not in self.graphs:
             import torch
-            if self.stream is None:
+            if self.streams is None:
                 self.device = torch.device(self.device)
-                self.stream = torch.cuda.Stream(device=self.device)
-            self.graphs[k] = _Graph(cfg, n, self.device, self.stream)
+                self.streams = [torch.cuda.Stream(device=self.device) for _ in range(self.lanes)]
+            self.graphs[k] = _Graph(cfg, n, self.device, self.streams[lane])
         return self.graphs[k]
 
     def run(self, jobs: Sequence[Job], realtime: bool = True, keep: bool = True) -> List[Job]:
         """Serves jobs in arrival order. With realtime, job.arrival is an offset in seconds from
         the start of the call and jobs are not seen before they arrive; otherwise all are
-        waiting at once (done then counts from the start). Returns the jobs with done (and,
-        with keep, their own copies of llr and flags) filled, in completion order."""
+        waiting at once (done then counts from the start). Up to `streams` batches are in
+        flight at once, each on its own stream with its own buffers; a batch's completion time
+        is its end event on the GPU clock, placed on the host clock by an event recorded at the
+        start. Returns the jobs with done (and, with keep, their own copies of llr and flags)
+        filled, in completion order."""
+        import collections
         pending = sorted(jobs, key=lambda j: j.arrival)
         queues: Dict[Tuple, List[Job]] = {}
-        t0 = self.clock()
-        i = 0
         finished: List[Job] = []
+        inflight = collections.deque()  # (lane, start event, end event, batch)
+        free = list(range(self.lanes))
+        if self.streams is None and pending:
+            self._graph(pending[0].cfg, 1)  # creates the streams
+        self._sync()
+        ref = self._event()
+        ref.record(self.streams[0])
+        t0 = self.clock()
+        ref.synchronize()
+
+        def retire(block: bool):
+            while inflight and (block or inflight[0][2].query()):
+                lane, e0, e1, batch = inflight.popleft()
+                e1.synchronize()
+                t = ref.elapsed_time(e1) * 1e-3
+                self.service.append(e0.elapsed_time(e1) * 1e-3)
+                for j in batch:
+                    j.done = t
+                finished.extend(batch)
+                free.append(lane)
+                block = False
+
+        i = 0
         while i < len(pending) or any(queues.values()):
             now = self.clock() - t0
             while i < len(pending) and (not realtime or pending[i].arrival <= now):
                 queues.setdefault(config_key(pending[i].cfg), []).append(pending[i])
                 i += 1
+            retire(False)
             ready = [(q[0].arrival, k) for k, q in queues.items() if q]
             if not ready:  # idle until the next arrival
                 if realtime and i < len(pending):
                     while self.clock() - t0 < pending[i].arrival:
-                        pass
+                        retire(False)
                 continue
+            if not free:  # every lane busy: wait for the oldest batch
+                retire(True)
             _, key = min(ready)  # the configuration whose oldest job has waited longest
             q = queues[key]
             cfg = q[0].cfg
             b = pick_batch(len(q), self.limit(cfg))
             batch, queues[key] = q[:b], q[b:]
-            ts = self.clock()
-            self._graph(cfg, b).run(batch, keep=keep)
+            lane = free.pop(0)
+            g = self._graph(cfg, b, lane)
+            e0, e1 = self._event(), self._event()
+            e0.record(g.stream)
+            g.launch(batch, keep=keep)
+            e1.record(g.stream)
+            inflight.append((lane, e0, e1, batch))
             self.batches += 1
-            t = self.clock() - t0
-            self.service.append(t + t0 - ts)
-            for j in batch:
-                j.done = t
-            finished.extend(batch)
+        while inflight:
+            retire(True)
         return finished
 
 

@@ -39,20 +39,39 @@ def test_admission_by_device_memory():
 
 
 class _FakeGraph:
+    stream = None
+
     def __init__(self, log, key, n):
         self.log, self.key, self.n = log, key, n
 
-    def run(self, jobs, keep=True):
+    def launch(self, jobs, keep=True):
         assert len(jobs) == self.n
         self.log.append((self.key, [j.job_id for j in jobs]))
+
+
+class _FakeEvent:
+    def record(self, stream):
+        pass
+
+    def query(self):
+        return True
+
+    def synchronize(self):
+        pass
+
+    def elapsed_time(self, other):
+        return 0.0
 
 
 def test_scheduling_oldest_first_powers_of_two(monkeypatch):
     phy.load()
     log = []
     srv = serve.SlotServer(max_cells=4, memory_budget=1 << 40)
+    srv.streams = [None]  # host-only: no CUDA streams, events or graphs
     monkeypatch.setattr(srv, "_graph",
-                        lambda cfg, n: _FakeGraph(log, serve.config_key(cfg)[0], n))
+                        lambda cfg, n, lane=0: _FakeGraph(log, serve.config_key(cfg)[0], n))
+    monkeypatch.setattr(srv, "_event", lambda: _FakeEvent())
+    monkeypatch.setattr(srv, "_sync", lambda: None)
     jobs = ([serve.Job(SMALL, None, None, 1.0, arrival=0.5, job_id=i) for i in range(5)] +
             [serve.Job(CARRIER, None, None, 1.0, arrival=0.0, job_id=10 + i) for i in range(3)])
     jobs[5].arrival = -1.0  # the oldest job is a CARRIER one
@@ -65,7 +84,8 @@ def test_scheduling_oldest_first_powers_of_two(monkeypatch):
 
 
 @pytest.mark.gpu
-def test_mixed_jobs_equal_alone():
+@pytest.mark.parametrize("streams", [1, 2])
+def test_mixed_jobs_equal_alone(streams):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -83,7 +103,7 @@ def test_mixed_jobs_equal_alone():
         jobs.append(serve.Job(cfg, torch.from_numpy(sl.Y).to(dev),
                               torch.from_numpy(sl.pilots).to(dev), float(sl.sigma2[0]),
                               arrival=0.0, job_id=n))
-    srv = serve.SlotServer(device=dev, max_cells=4)
+    srv = serve.SlotServer(device=dev, max_cells=4, streams=streams)
     srv.prepare([SMALL, CARRIER])
     done = srv.run(jobs, realtime=False)
     assert len(done) == len(jobs) and srv.batches < len(jobs)
