@@ -52,7 +52,7 @@ constexpr int kBoxSc = 16;                 // subcarriers per received-grid box
 constexpr uint32_t kStageBytes = kBoxSc * 8 * 64;  // one box with 64 antennas
 constexpr int kBoxItems = 16 * (kBoxSc / 2);       // converter work items per box
 constexpr int kBoxWarps = kBoxItems / 32;          // converter warps per box
-constexpr uint32_t kRingBytes = 48 * 1024;         // ring of boxes (FP16/BF16 tiles)
+constexpr uint32_t kRingBytes = 64 * 1024;         // ring of boxes (FP16/BF16 tiles)
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kColX = 0, kColMf = 128;  // MF accumulator b at kColMf + 128 b
 constexpr uint32_t kWaitIters = 1u << 20;  // polls of up to ~1 us each
@@ -72,7 +72,7 @@ struct Layout {
   // RE-tile operand buffers and ring stages: TF32 tiles are twice as large, so that variant
   // keeps one tile buffer and a shallower ring to stay inside 227 KB.
   static constexpr int kYBufs = FMT == tc::kFmtTF32 ? 1 : 2;
-  static constexpr int kStages = (FMT == tc::kFmtTF32 ? 32 * 1024 : kRingBytes) / kStageBytes;
+  static constexpr int kStages = (FMT == tc::kFmtTF32 ? 48 * 1024 : kRingBytes) / kStageBytes;
 };
 
 constexpr int nxp_of(int nx) { return nx <= 16 ? 16 : (nx + 15) / 16 * 16; }
@@ -86,7 +86,7 @@ struct Smem {
   static constexpr size_t kCc = 0;
   static constexpr size_t kYop = kCc + Lay::kTileBytes;
   static constexpr size_t kXs = kYop + (size_t)Lay::kYBufs * Lay::kTileBytes;
-  static constexpr size_t kAnch = kXs + up128((size_t)NXP * (NXP + 2) * 8);
+  static constexpr size_t kAnch = kXs + up128((size_t)NXP * (NXP + 1) / 2 * 8);  // X, lower
   static constexpr size_t kCorner = up128((size_t)NL * 64 * 8);  // one corner's [l][r] block
   static constexpr size_t kRing = kAnch + NC * kCorner;
   static constexpr size_t kBars = kRing + (size_t)Lay::kStages * kStageBytes;
@@ -171,7 +171,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   constexpr int S = Lay::kStages;
   constexpr int NX = NC * NL;
   constexpr int NXP = Sm::NXP;
-  constexpr int xs = NXP + 2;
   constexpr int NTRI = NL * (NL + 1) / 2;
   static_assert(2 * NXP <= kRows, "corner-layer count too large for one tile");
   static_assert(Sm::kTotal <= 227 * 1024, "shared memory map too large");
@@ -403,7 +402,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int c = row % NXP, part = row / NXP;
 #pragma unroll
             for (int q = 0; q < 32; ++q)
-              if (c0 + q < NXP) reinterpret_cast<float*>(Xs + c * xs + c0 + q)[part] = v[q];
+              if (c0 + q <= c)  // lower triangle, packed by rows
+                reinterpret_cast<float*>(Xs + c * (c + 1) / 2 + c0 + q)[part] = v[q];
           }
         }
       }
@@ -413,7 +413,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       stop = tc::bar_or<2, 128>(fail);
       if (stop) break;
       // ---- per-symbol Gram blocks
-      auto Xget = [&](int i, int k) -> cf { return Xs[i * xs + k]; };
+      auto Xget = [&](int i, int k) -> cf {  // X is Hermitian
+        if (i >= k) return Xs[i * (i + 1) / 2 + k];
+        const cf v = Xs[k * (k + 1) / 2 + i];
+        return mk(v.x, -v.y);
+      };
       form_gram_blocks<NL, 128>(g, Xget,
                                 ygg + (((size_t)it.lc * g.n_seg + it.j) * nds) * NTRI * 2, gtid);
       // ---- matched filter of each RE tile: this thread's TMEM lane is its RE row
