@@ -27,13 +27,10 @@ __global__ void __launch_bounds__(kChestThreads)
   const int k0 = 2 * s;  // first subcarrier of the group's run
   const int nl = g.n_layers;
   const phy_c32* prow = P + (size_t)(cell * g.n_dmrs + d) * nl * g.n_sc + k0;
-  for (int e = threadIdx.x; e < nl * 2 * L; e += blockDim.x) {
-    const int l = e / (2 * L), i = e % (2 * L);
-    pil[l][i] = ld(prow + (size_t)l * g.n_sc + i);
-  }
-  __syncthreads();
-  if (r >= g.n_rx) return;
-  const phy_c32* yrow = Y + ((size_t)(cell * g.n_sym + t) * g.n_rx + r) * g.n_sc + k0;
+  // this antenna's run of Y first, so that its loads are in flight with the pilots' ones
+  const bool live = r < g.n_rx;
+  const phy_c32* yrow =
+      Y + ((size_t)(cell * g.n_sym + t) * g.n_rx + (live ? r : 0)) * g.n_sc + k0;
   cf y[2 * L];
   if constexpr (L >= 2) {
     // k0 is even, so the run starts on a 16-byte boundary
@@ -48,6 +45,12 @@ __global__ void __launch_bounds__(kChestThreads)
     y[0] = ld(yrow);
     y[1] = ld(yrow + 1);
   }
+  for (int e = threadIdx.x; e < nl * 2 * L; e += blockDim.x) {
+    const int l = e / (2 * L), i = e % (2 * L);
+    pil[l][i] = ld(prow + (size_t)l * g.n_sc + i);
+  }
+  __syncthreads();
+  if (!live) return;
   phy_c32* out = anchors + (((size_t)(cell * g.n_dmrs + d) * g.G + grp) * nl) * g.n_rx;
   const float inv_l = 1.f / (float)L;
   for (int l = 0; l < nl; ++l) {

@@ -323,3 +323,35 @@ def test_llr_binary16_output_is_the_rounded_fp32_output(dev):
         for k in range(2):
             ref = out["f32"][k].clamp(-65504.0, 65504.0).half()
             assert torch.equal(ref, out["f16"][k])
+
+
+def test_slot_parity_full_size_sampled_tensor_core_fp16(dev):
+    """The FP16 tensor-core launch on the benchmark's full batch (8 cells x 273 PRB x 64 Rx x 16
+    layers), sampled REs against the oracle with the reduced-precision bounds of the small
+    tensor-core cases, and hard decisions nearly all equal to the oracle's."""
+    spec = S.spec_massive_mimo()
+    sl = S.make_slot(spec, 3001, keep_h=False)
+    got = gpu_slot(spec, sl, dev, precision="fp16")
+    rng = np.random.default_rng(1)
+    K, J = spec.n_sc, len(spec.data_sym)
+    res = {}
+    for c in range(spec.n_cells):
+        kk = np.concatenate([np.arange(0, 24), np.arange(K - 24, K), rng.integers(0, K, 48)])
+        res[c] = (rng.integers(0, J, kk.size), kk)
+    ref = O.run_slot(sl.Y, sl.pilots, sl.sigma2, spec.dmrs_sym, spec.n_layers, spec.qm, res=res)
+    gx, rx, gs, rs, gl, rl, gf, rf = [], [], [], [], [], [], [], []
+    for c, (jj, kk) in res.items():
+        gx.append(got["x_hat"][c, jj, kk]); rx.append(ref[f"x_hat_{c}"])
+        gs.append(got["sinr"][c, jj, kk]); rs.append(ref[f"sinr_{c}"])
+        gl.append(got["llr"][c, jj, kk]); rl.append(ref[f"llr_{c}"])
+        gf.append(got["flags"][c, jj, kk]); rf.append(ref[f"flags_{c}"])
+    gx, rx, gs, rs = map(np.concatenate, (gx, rx, gs, rs))
+    gl, rl, gf, rf = map(np.concatenate, (gl, rl, gf, rf))
+    mask = (gf == 0) & (rf == 0)
+    m = compare_res("full_size_sampled[fp16]", dict(x_hat=gx, sinr=gs, llr=gl),
+                    dict(x_hat=rx, sinr=rs, llr=rl), spec.qm, 1.0 / rs, rx / (rs / (1 + rs)),
+                    mask)
+    assert m["x_rel"] <= 1e-3, m
+    assert m["sinr_rel_max"] <= 3e-3, m
+    assert m["llr_norm_max"] <= 2e-2, m
+    assert np.mean((gl < 0) != (rl < 0)) <= 1e-3
