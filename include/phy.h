@@ -25,6 +25,9 @@
  *    (bit 0: ill-conditioned Gram matrix, Cholesky pivot ratio below cfg.pivot_ratio_min or a
  *    non-positive pivot; bit 1: RE re-computed in FP64; bit 2: non-finite input). An RE whose
  *    factorisation fails in FP32 and is not re-computed gets zero x_hat, SINR and LLRs.
+ *    Bit 3 (alone) marks an RE whose results were never written because a bounded device wait
+ *    in the detection kernels timed out (a stalled copy or tensor-core operation); its x_hat,
+ *    SINR and LLRs hold whatever the buffers held before.
  *
  * Layouts (complex values are interleaved float pairs, phy_c32):
  *  Y        [cell][sym][rx][sc]                     received grid, all n_sym symbols

@@ -371,7 +371,8 @@ __device__ __forceinline__ void copy_out_f16(__half* dst, const float* src, int 
 // One CTA per (128 subcarriers, data symbol, cell), one thread per RE. Thread 0 brings the
 // Gram-block 4-tuples of the segments the CTA spans into shared memory with bulk copies
 // (TMA engine, completion counted on an mbarrier); meanwhile every thread loads its matched
-// filter. A barrier timeout marks the CTA's REs with flag bit 3. With 9..16 layers the LLRs
+// filter. A barrier timeout, here or in the segment kernel before (its error word), marks the
+// CTA's REs with flag bit 3 and leaves their outputs unwritten. With 9..16 layers the LLRs
 // and SINRs are staged in shared memory and leave as one contiguous block per CTA: per-thread
 // stores of whole records (512 B apart) would keep each warp waiting on the store path.
 template <int NL, int QM>
@@ -380,7 +381,8 @@ __global__ void __launch_bounds__(kSolveThreads)
                          const cf* __restrict__ bvec, const float* __restrict__ sigma2,
                          const phy_c32* __restrict__ anchors, const phy_c32* __restrict__ Y,
                          phy_c32* __restrict__ x_hat, float* __restrict__ sinr_out,
-                         float* __restrict__ llr_out, uint8_t* __restrict__ flags_out) {
+                         float* __restrict__ llr_out, uint8_t* __restrict__ flags_out,
+                         const unsigned* __restrict__ prep_err) {
   constexpr int NTRI = NL * (NL + 1) / 2;
   constexpr uint32_t kBlk = gram_block_bytes(NL);
   extern __shared__ __align__(128) unsigned char solve_smem[];
@@ -421,7 +423,9 @@ __global__ void __launch_bounds__(kSolveThreads)
   constexpr uint32_t kWait = 1u << 22;
   bool arrived = tc::mbar_wait(bar, 0, kWait);
   if (!arrived) arrived = tc::mbar_wait(bar, 0, kWait);  // let copies in flight land
-  arrived = __syncthreads_and(arrived);  // one decision for the CTA (it has barriers below)
+  // one decision for the CTA (it has barriers below); a timed-out Gram/matched-filter kernel
+  // (its error word) voids every RE as a wait timeout here would
+  arrived = __syncthreads_and(arrived && (threadIdx.x != 0 || *prep_err == 0));
   const size_t ridx = ((size_t)cell * nds + jj) * g.n_sc + (live ? k : k0);
   if (!arrived) {
     if (live) flags_out[ridx] = 8;
@@ -636,7 +640,7 @@ template <int NL, int QM>
 cudaError_t launch_solve(const Geo& g, int c0, int nc, int max_segs, const float4* ygg,
                          const cf* bvec, const float* sigma2, const phy_c32* anchors,
                          const phy_c32* Y, phy_c32* x_hat, float* sinr, float* llr,
-                         uint8_t* flags, cudaStream_t st) {
+                         uint8_t* flags, const unsigned* err, cudaStream_t st) {
   const size_t smem = solve_smem_bytes(NL, QM, max_segs);
   static size_t configured = 0;
   if (smem > 48 * 1024 && smem > configured) {
@@ -650,7 +654,7 @@ cudaError_t launch_solve(const Geo& g, int c0, int nc, int max_segs, const float
   }
   dim3 grid((g.n_sc + kSolveThreads - 1) / kSolveThreads, g.n_dsym, nc);
   re_solve_fp32_kernel<NL, QM><<<grid, kSolveThreads, smem, st>>>(
-      g, c0, max_segs, ygg, bvec, sigma2, anchors, Y, x_hat, sinr, llr, flags);
+      g, c0, max_segs, ygg, bvec, sigma2, anchors, Y, x_hat, sinr, llr, flags, err);
   return cudaGetLastError();
 }
 
@@ -677,6 +681,10 @@ cudaError_t run_chunks(const Geo& g, int wmax, const Sizes& s, const phy_c32* an
   for (int c0 = 0; c0 < g.n_cells; c0 += s.chunk) {
     const int nc = std::min(s.chunk, g.n_cells - c0);
     cudaError_t e = cudaSuccess;
+    // the segment kernels' error word (bumped by a timed-out wait), read by the solve kernel
+    if ((stages & kStageGramMf) &&
+        (e = cudaMemsetAsync(err, 0, sizeof(unsigned), st)) != cudaSuccess)
+      return e;
     if ((stages & kStageGramMf) && g.prec == PHY_PREC_FP32) {
       dim3 grid(g.n_seg, nc);
       seg_prep_fp32_kernel<NL><<<grid, kPrepThreads, smem, st>>>(g, wmax, c0, anchors, Y, ygg,
@@ -689,13 +697,13 @@ cudaError_t run_chunks(const Geo& g, int wmax, const Sizes& s, const phy_c32* an
     const int ms = max_segments_per_block(g);
     switch (g.qm) {
       case 2: e = launch_solve<NL, 2>(g, c0, nc, ms, ygg, bvec, sigma2, anchors, Y, x_hat, sinr, llr,
-                                           flags, st); break;
+                                           flags, err, st); break;
       case 4: e = launch_solve<NL, 4>(g, c0, nc, ms, ygg, bvec, sigma2, anchors, Y, x_hat, sinr, llr,
-                                           flags, st); break;
+                                           flags, err, st); break;
       case 6: e = launch_solve<NL, 6>(g, c0, nc, ms, ygg, bvec, sigma2, anchors, Y, x_hat, sinr, llr,
-                                           flags, st); break;
+                                           flags, err, st); break;
       default: e = launch_solve<NL, 8>(g, c0, nc, ms, ygg, bvec, sigma2, anchors, Y, x_hat, sinr, llr,
-                                           flags, st); break;
+                                           flags, err, st); break;
     }
     if (e != cudaSuccess) return e;
   }
