@@ -355,3 +355,35 @@ def test_slot_parity_full_size_sampled_tensor_core_fp16(dev):
     assert m["sinr_rel_max"] <= 3e-3, m
     assert m["llr_norm_max"] <= 2e-2, m
     assert np.mean((gl < 0) != (rl < 0)) <= 1e-3
+
+
+def test_segment_kernel_timeout_voids_the_solve(dev):
+    """The solve reads the segment kernels' error word (bumped by a timed-out bounded wait): set
+    by hand between the two stages it makes every RE report flag bit 3 alone and nothing else;
+    cleared, the same solve is normal again. No wait is made to run out on the device."""
+    import torch
+    from paper_2510_07843_gb300 import phy
+    spec = S.spec_massive_mimo(n_cells=1, n_prb=6)
+    sl = S.make_slot(spec, 3300, keep_h=False)
+    cfg = phy.SlotConfig.from_spec(spec, precision="fp16")
+    if not phy.stage_supported(cfg):
+        pytest.skip("single-chunk stages not supported for this shape")
+    b = phy.SlotBuffers(cfg, device=dev)
+    b.Y.copy_(torch.from_numpy(sl.Y))
+    b.pilots.copy_(torch.from_numpy(sl.pilots))
+    b.sigma2.copy_(torch.from_numpy(sl.sigma2))
+    phy.chest(cfg, b.Y, b.pilots, b.anchors)
+    args = (b.anchors, b.Y, b.sigma2, b.x_hat, b.sinr, b.llr, b.flags, b.workspace)
+    phy.detect_stage(cfg, phy.STAGE_GRAM_MF, *args)
+    # the error word is the first word after the anchors' 256-byte-aligned region
+    a = (b.anchors.numel() * 8 + 255) // 256 * 256
+    word = b.workspace[a:a + 4].view(torch.int32)
+    word.fill_(1)
+    b.flags.fill_(0)
+    phy.detect_stage(cfg, phy.STAGE_SOLVE, *args)
+    torch.cuda.synchronize()
+    assert torch.all(b.flags == 8)
+    word.fill_(0)
+    phy.detect_stage(cfg, phy.STAGE_SOLVE, *args)
+    torch.cuda.synchronize()
+    assert not torch.any(b.flags & 8)
