@@ -25,13 +25,9 @@
 // and the drain of the one before. The groups hand over through mbarriers.
 // Every wait is bounded: on a timeout a group agrees (barrier with OR-reduction), bumps an
 // error counter and leaves; outstanding copies and MMAs are waited for before the CTA ends.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
-#include <mutex>
 
 #include "launch.h"
 #include "segment.cuh"
@@ -492,32 +488,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 // ---------------------------------------------------------------- host side
 int g_num_sms = 0;
-
-PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  });
-  return fn;
-}
-
-// 3-D FP32 tensor map, dims and box innermost first, strides of dims 1 and 2 in bytes.
-bool make_map(CUtensorMap* m, const void* base, const cuuint64_t (&dim)[3],
-              const cuuint64_t (&stride)[2], const cuuint32_t (&box)[3]) {
-  auto fn = encode_tiled();
-  if (!fn) return false;
-  const cuuint32_t es[3] = {1, 1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dim, stride, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
-         CUDA_SUCCESS;
-}
 
 template <int NL, int NC, uint32_t FMT>
 cudaError_t launch_one(const Geo& g, int c0, int nc, const phy_c32* anchors, const phy_c32* Y,

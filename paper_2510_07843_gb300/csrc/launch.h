@@ -1,6 +1,7 @@
 // Host-side launchers of the receiver kernels (internal to libphy.so).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -39,6 +40,11 @@ phy_status slot_run_fit(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32
                         cudaStream_t st);
 // Smallest workspace slot_run_fit accepts for cfg (0 if cfg is invalid).
 size_t min_workspace_bytes(const phy_slot_cfg* cfg);
+
+// 3-D FP32 tensor map (dims and box innermost first, strides of dims 1 and 2 in bytes), no
+// swizzle, zero fill outside the tensor; false if the driver refuses it.
+bool make_map(CUtensorMap* m, const void* base, const cuuint64_t (&dim)[3],
+              const cuuint64_t (&stride)[2], const cuuint32_t (&box)[3]);
 
 // Tensor-core segment kernel (same outputs as the FP32 one) for g.prec != PHY_PREC_FP32.
 // Needs an even antenna count and 16-byte aligned anchors and grid (TMA tensor maps).
