@@ -16,6 +16,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -195,12 +196,30 @@ class ClockSampler:
 # profiles: DRAM traffic of the dominant kernel from a committed ncu summary
 # ---------------------------------------------------------------------------------------------
 
-def kernel_source_hash() -> str:
-    h = hashlib.sha256()
+# translation unit that defines each profiled kernel
+KERNEL_SOURCE = {"seg_prep_tc": "detect_tc.cu", "re_solve": "detect_fp32.cu",
+                 "seg_prep_fp32": "detect_fp32.cu", "chest": "chest.cu"}
+
+
+def kernel_source_hash(kernel: str) -> str:
+    """Hash of the kernel's translation unit and every local header it includes (transitively).
+
+    Counters recorded for one hash stay valid while none of those files changes."""
     csrc = os.path.join(ROOT, "paper_2510_07843_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, fn), "rb").read())
+    seen, todo = [], [os.path.join(csrc, KERNEL_SOURCE[kernel])]
+    while todo:
+        path = os.path.normpath(todo.pop())
+        if path in seen:
+            continue
+        seen.append(path)
+        for line in open(path):
+            m = re.match(r'\s*#include\s+"([^"]+)"', line)
+            if m:
+                todo.append(os.path.join(os.path.dirname(path), m.group(1)))
+    h = hashlib.sha256()
+    for path in sorted(seen):
+        h.update(os.path.relpath(path, ROOT).encode())
+        h.update(open(path, "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -209,7 +228,7 @@ def committed_traffic(kernel: str, workload_name: str):
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    src = kernel_source_hash()
+    src = kernel_source_hash(kernel)
     for line in open(path):
         p = line.split()
         if len(p) >= 4 and not line.startswith("#") and p[0] == kernel and p[1] == workload_name \
