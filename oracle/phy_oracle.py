@@ -19,6 +19,10 @@ Steps and where they come from:
 * Demapping to soft bits (implied by the LDPC decoder that follows detection in Sec. IV; the paper
   gives no method): max-log LLRs over the NR Gray QAM constellation, by brute force over all points.
 * Ill-conditioning flag: Cholesky pivot ratio min L_kk^2 / max L_kk^2 below a threshold.
+* Noise-variance estimate (the paper treats the noise level as known; no method given): residuals
+  of the LS anchors against their prediction from neighbouring anchors in frequency or from the
+  other DMRS symbol, normalised by the exact noise gain of each residual (see the section at the
+  end of this file).
 
 Readings where the paper is silent (each also fixed in the C ABI):
   - Layer l uses comb c = l % 2 (k = 2m + c) and Walsh row o = l // 2; L is the smallest power of
@@ -361,3 +365,101 @@ def run_slot(Y: np.ndarray, pilots: np.ndarray, sigma2: np.ndarray, dmrs_sym: Se
         for key in parts:
             out[f"{key}_{c}"] = np.concatenate(parts[key], axis=0)[inv]
     return out
+
+
+
+
+# ----------------------------------------------------------------------------------------------
+# Noise-variance estimate from the DMRS (the paper takes the noise level as known)
+# ----------------------------------------------------------------------------------------------
+#
+# Reading (no method in the paper): a noise sample is the residual of an LS anchor against a
+# prediction of it from other anchors of the same layer, under the receiver's own channel model.
+#  * frequency: every interior anchor against the linear interpolation of its two neighbours,
+#      e = H_d,l(g) - a_g H_d,l(g-1) - b_g H_d,l(g+1),  g = 1 .. G-2, every DMRS symbol d,
+#      a_g = (p_g+1 - p_g) / (p_g+1 - p_g-1), b_g = (p_g - p_g-1) / (p_g+1 - p_g-1), p the anchor
+#      subcarriers;
+#  * time (two DMRS symbols): every anchor against the same anchor of the other symbol,
+#      e = H_0,l(g) - H_1,l(g).
+# Each residual is a fixed linear function of the DMRS REs, e = sum_k c_k Y(k), with
+# c_k = (1/L) conj(P(k)) times the signed weight of the group(s) holding k, so white noise of
+# variance s2 per RE leaves E|e|^2 = s2 gamma with gamma = sum_k |c_k|^2, and
+#   s2_hat = sum |e|^2 / (n_rx sum gamma)   (sums over d, l, g and, for |e|^2, the antennas r).
+# Without noise the frequency residual vanishes for a channel constant over the three groups (and,
+# with one layer per comb, for one linear in frequency), the time residual for a channel that does
+# not change between the DMRS symbols; any other channel variation only adds to E|e|^2. Each
+# estimate is therefore unbiased or too large, and the "min" mode takes the smaller of the two.
+# The frequency estimate needs three groups, the time one two DMRS symbols (NaN otherwise).
+
+NOISE_MODES = ("freq", "time", "min")
+
+
+def anchor_neighbour_weights(pos: np.ndarray, g: int) -> Tuple[float, float]:
+    """(a_g, b_g): weights of anchors g-1 and g+1 in the linear prediction of anchor g."""
+    span = pos[g + 1] - pos[g - 1]
+    return (pos[g + 1] - pos[g]) / span, (pos[g] - pos[g - 1]) / span
+
+
+def noise_residual_energy(anchors: np.ndarray, n_sc: int, L: int, mode: str) -> np.ndarray:
+    """sum |e|^2 per cell from anchors [cell][dmrs][group][layer][rx] ('freq' or 'time')."""
+    A = np.asarray(anchors, dtype=np.complex128)
+    n_cells, n_dmrs, G, _, _ = A.shape
+    out = np.zeros(n_cells)
+    if mode == "time":
+        if n_dmrs == 2:
+            out += np.sum(np.abs(A[:, 0] - A[:, 1]) ** 2, axis=(1, 2, 3))
+        return out
+    _, pos = ls_groups(n_sc, L)
+    for g in range(1, G - 1):
+        a, b = anchor_neighbour_weights(pos[0], g)  # the same on both combs
+        e = A[:, :, g] - a * A[:, :, g - 1] - b * A[:, :, g + 1]
+        out += np.sum(np.abs(e) ** 2, axis=(1, 2, 3))
+    return out
+
+
+def noise_gain(pilots: np.ndarray, n_layers: int, L: int, mode: str) -> np.ndarray:
+    """sum gamma per cell: for each residual the coefficient vector c over the DMRS REs of the
+    symbol(s) it uses, written out, and its squared norm."""
+    P = np.asarray(pilots, dtype=np.complex128)
+    n_cells, n_dmrs, _, n_sc = P.shape
+    s, pos = ls_groups(n_sc, L)
+    G = len(s)
+    out = np.zeros(n_cells)
+
+    def group_coef(cell, d, l, terms):
+        coef = np.zeros(n_sc, dtype=np.complex128)
+        for grp, w in terms:
+            ks = 2 * (s[grp] + np.arange(L)) + l % 2
+            coef[ks] += w * np.conj(P[cell, d, l, ks]) / L
+        return coef
+
+    for cell in range(n_cells):
+        for l in range(n_layers):
+            if mode == "time":
+                if n_dmrs < 2:
+                    continue
+                for g in range(G):
+                    c0 = group_coef(cell, 0, l, [(g, 1.0)])   # coefficients on symbol 0's REs
+                    c1 = group_coef(cell, 1, l, [(g, -1.0)])  # and on symbol 1's
+                    out[cell] += np.sum(np.abs(c0) ** 2) + np.sum(np.abs(c1) ** 2)
+                continue
+            for d in range(n_dmrs):
+                for g in range(1, G - 1):
+                    a, b = anchor_neighbour_weights(pos[l % 2], g)
+                    coef = group_coef(cell, d, l, [(g, 1.0), (g - 1, -a), (g + 1, -b)])
+                    out[cell] += np.sum(np.abs(coef) ** 2)
+    return out
+
+
+def noise_variance_dmrs(pilots: np.ndarray, anchors: np.ndarray, n_rx: int, n_layers: int,
+                        L: int, mode: str = "min") -> np.ndarray:
+    """s2_hat per cell from the LS anchors and the pilots; NaN where the mode has no residual."""
+    n_sc = np.asarray(pilots).shape[-1]
+    if mode == "min":
+        f = noise_variance_dmrs(pilots, anchors, n_rx, n_layers, L, "freq")
+        t = noise_variance_dmrs(pilots, anchors, n_rx, n_layers, L, "time")
+        return np.fmin(f, t)  # NaN only where both are
+    energy = noise_residual_energy(anchors, n_sc, L, mode)
+    gain = noise_gain(pilots, n_layers, L, mode)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return np.where(gain > 0.0, energy / (n_rx * gain), np.nan)

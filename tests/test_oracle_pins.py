@@ -396,3 +396,151 @@ def test_slot_sampled_matches_dense():
     samp = O.run_slot(sl.Y, sl.pilots, sl.sigma2, spec.dmrs_sym, 2, 4, res={0: (jj, kk)})
     np.testing.assert_allclose(samp["x_hat_0"], dense["x_hat"][0, jj, kk], rtol=1e-13)
     np.testing.assert_allclose(samp["llr_0"], dense["llr"][0, jj, kk], rtol=1e-12, atol=1e-12)
+
+
+# ------------------------------------------------------------------ noise-variance estimate
+
+def _golden_noise():
+    return {r[0]: float(r[1]) for r in golden_lines("noise_handworked.txt")}
+
+
+def test_noise_gain_handworked():
+    """Three PRB, cover 4, one comb-0 layer: the gains worked out by hand, overlap included."""
+    want = _golden_noise()
+    P = S.dmrs_pilots(np.random.default_rng(5), 36, 1, 2, 4)[None]  # complex128, |P| = 1
+    assert O.noise_gain(P[:, :1], 1, 4, "freq")[0] == pytest.approx(want["gain_freq"], rel=1e-14)
+    assert O.noise_gain(P, 1, 4, "time")[0] == pytest.approx(want["gain_time"], rel=1e-14)
+    # both DMRS symbols: the frequency residuals of each symbol
+    assert O.noise_gain(P, 1, 4, "freq")[0] == pytest.approx(2 * want["gain_freq"], rel=1e-14)
+
+
+def test_noise_residual_handworked_quadratic():
+    """Anchors p^2 at the anchor subcarriers: the frequency residuals of a quadratic, by hand."""
+    want = _golden_noise()
+    _, pos = O.ls_groups(36, 4)
+    for comb in range(2):
+        A = (pos[comb] ** 2).astype(np.complex128).reshape(1, 1, 5, 1, 1)
+        got = O.noise_residual_energy(A, 36, 4, "freq")[0]
+        assert got == pytest.approx(want["energy_quadratic"], rel=1e-14)
+
+
+@pytest.mark.parametrize("n_prb,nl,occ,nd", [(3, 1, 4, 2), (2, 4, 0, 2), (3, 8, 0, 1),
+                                             (4, 2, 1, 2), (5, 16, 0, 2), (3, 3, 8, 2)])
+def test_noise_gain_matches_probed_linear_map(n_prb, nl, occ, nd):
+    """The summed gain equals the residual energy of unit impulses sent through the LS estimator:
+    one 'antenna' per DMRS RE, carrying 1 on that RE and 0 elsewhere, so that the residual energy
+    summed over the antennas is sum over residuals of sum_k |c_k|^2."""
+    L = occ if occ else O.occ_length(nl)
+    if 6 * n_prb < L:
+        pytest.skip("cover longer than the comb")
+    dmrs = (2, 11)[:nd]
+    spec = S.SlotSpec(n_prb=n_prb, n_rx=1, n_layers=nl, qm=2, dmrs_sym=dmrs, occ_len=L)
+    sl = S.make_slot(spec, 17 + nl)
+    K = spec.n_sc
+    Yp = np.zeros((1, 14, nd * K, K), dtype=np.complex128)
+    for d, t in enumerate(dmrs):
+        Yp[0, t, d * K + np.arange(K), np.arange(K)] = 1.0
+    A = O.ls_anchors(Yp, sl.pilots, dmrs, nl, L)
+    for mode in ("freq", "time"):
+        probed = O.noise_residual_energy(A, K, L, mode)[0]
+        assert O.noise_gain(sl.pilots, nl, L, mode)[0] == pytest.approx(probed, rel=1e-12,
+                                                                        abs=1e-12)
+
+
+@pytest.mark.parametrize("n_prb,nl", [(3, 1), (5, 2), (4, 4), (7, 8), (6, 16)])
+def test_noise_residuals_vanish_without_noise(n_prb, nl):
+    """Noise-free channel constant over the band: both residuals are zero for any layer count
+    (Walsh orthogonality), ragged PRB counts included."""
+    rng = np.random.default_rng(100 + nl)
+    nr = 3
+    Hc = crandn(rng, nr, nl)
+    spec = S.SlotSpec(n_prb=n_prb, n_rx=nr, n_layers=nl, qm=2, dmrs_sym=(2, 11))
+    ch = np.broadcast_to(Hc, (1, 14, spec.n_sc, nr, nl))
+    sl = S.make_slot(spec, 1, noise=False, channel=ch)
+    A = O.ls_anchors(sl.Y, sl.pilots, spec.dmrs_sym, nl, spec.occ)
+    scale = np.sum(np.abs(A) ** 2)
+    for mode in ("freq", "time"):
+        assert O.noise_residual_energy(A, spec.n_sc, spec.occ, mode)[0] < 1e-12 * scale
+
+
+def test_noise_frequency_residual_vanishes_for_linear_channel_one_layer_per_comb():
+    """Two layers (one per comb), cover 4 forced, channel linear in k: every anchor is the channel
+    at its group's mean subcarrier, so linear prediction from the neighbours is exact."""
+    nr, nl, L = 2, 2, 4
+    spec = S.SlotSpec(n_prb=5, n_rx=nr, n_layers=nl, qm=2, dmrs_sym=(3,), occ_len=L)
+    rng = np.random.default_rng(9)
+    a, slope = crandn(rng, nr, nl), 0.02 * crandn(rng, nr, nl)
+    k = np.arange(spec.n_sc)
+    ch = a[None, None] + slope[None, None] * k[None, :, None, None]
+    ch = np.broadcast_to(ch, (14, spec.n_sc, nr, nl))[None]
+    sl = S.make_slot(spec, 2, noise=False, channel=ch)
+    A = O.ls_anchors(sl.Y, sl.pilots, spec.dmrs_sym, nl, L)
+    assert O.noise_residual_energy(A, spec.n_sc, L, "freq")[0] < 1e-11 * np.sum(np.abs(A) ** 2)
+
+
+def test_noise_time_residual_vanishes_for_static_channel():
+    """Noise-free frequency-selective channel that does not change in time: the time residual is
+    zero (the frequency one is not)."""
+    spec = S.spec_carrier_273prb(n_prb=20, doppler_hz=0.0)
+    sl = S.make_slot(spec, 3, noise=False)
+    A = O.ls_anchors(sl.Y, sl.pilots, spec.dmrs_sym, spec.n_layers, spec.occ)
+    scale = np.sum(np.abs(A) ** 2)
+    assert O.noise_residual_energy(A, spec.n_sc, spec.occ, "time")[0] < 1e-12 * scale
+    assert O.noise_residual_energy(A, spec.n_sc, spec.occ, "freq")[0] > 1e-6 * scale
+
+
+@pytest.mark.parametrize("nl", [1, 4, 16])
+@pytest.mark.parametrize("mode", ["freq", "time"])
+def test_noise_estimate_unbiased_on_flat_channel(nl, mode):
+    """Flat channel plus white noise: the mean estimate over independent slots is s2 within the
+    spread of the mean (the residual energy is a sum of many chi-square terms)."""
+    nr, snr = 8, 12.0
+    ests = []
+    for seed in range(8):
+        rng = np.random.default_rng(1000 * nl + seed)
+        spec = S.SlotSpec(n_prb=24, n_rx=nr, n_layers=nl, qm=2, dmrs_sym=(2, 11), snr_db=snr)
+        ch = np.broadcast_to(crandn(rng, nr, nl), (1, 14, spec.n_sc, nr, nl))
+        sl = S.make_slot(spec, 50 + seed, channel=ch)
+        A = O.ls_anchors(sl.Y, sl.pilots, spec.dmrs_sym, nl, spec.occ)
+        ests.append(O.noise_variance_dmrs(sl.pilots, A, nr, nl, spec.occ, mode)[0] / spec.sigma2)
+    ests = np.array(ests)
+    spread = ests.std(ddof=1) / math.sqrt(len(ests))
+    assert abs(ests.mean() - 1.0) < max(5.0 * spread, 0.01), (ests.mean(), spread)
+    assert spread < 0.05
+
+
+def test_noise_estimate_pure_noise():
+    """No signal at all: the estimate is the noise level (any pilots, any mode)."""
+    spec = S.SlotSpec(n_prb=40, n_rx=16, n_layers=4, qm=2, dmrs_sym=(2, 11), snr_db=0.0)
+    zero = np.zeros((1, 14, spec.n_sc, spec.n_rx, spec.n_layers))
+    sl = S.make_slot(spec, 77, channel=zero)
+    A = O.ls_anchors(sl.Y, sl.pilots, spec.dmrs_sym, spec.n_layers, spec.occ)
+    for mode in O.NOISE_MODES:
+        est = O.noise_variance_dmrs(sl.pilots, A, spec.n_rx, spec.n_layers, spec.occ, mode)[0]
+        assert est == pytest.approx(1.0, rel=0.05), mode
+
+
+def test_noise_estimate_modes_and_undefined_cases():
+    """'min' is the smaller estimate; time needs two DMRS symbols, frequency three groups."""
+    spec = S.spec_carrier_273prb(n_prb=30)
+    sl = S.make_slot(spec, 4)
+    A = O.ls_anchors(sl.Y, sl.pilots, spec.dmrs_sym, spec.n_layers, spec.occ)
+    est = {m: O.noise_variance_dmrs(sl.pilots, A, spec.n_rx, spec.n_layers, spec.occ, m)[0]
+           for m in O.NOISE_MODES}
+    assert est["min"] == min(est["freq"], est["time"])
+    one = O.noise_variance_dmrs(sl.pilots[:, :1], A[:, :1], spec.n_rx, spec.n_layers, spec.occ,
+                                "time")
+    assert np.isnan(one[0])
+    assert O.noise_variance_dmrs(sl.pilots[:, :1], A[:, :1], spec.n_rx, spec.n_layers, spec.occ,
+                                 "min")[0] == est_freq_one(sl, A, spec)
+    # 3 PRB with cover 16: two groups only, so no interior anchor
+    sp2 = S.SlotSpec(n_prb=3, n_rx=2, n_layers=2, qm=2, dmrs_sym=(2, 11), occ_len=16)
+    s2 = S.make_slot(sp2, 1)
+    A2 = O.ls_anchors(s2.Y, s2.pilots, sp2.dmrs_sym, 2, 16)
+    assert np.isnan(O.noise_variance_dmrs(s2.pilots, A2, 2, 2, 16, "freq")[0])
+    assert np.isfinite(O.noise_variance_dmrs(s2.pilots, A2, 2, 2, 16, "min")[0])
+
+
+def est_freq_one(sl, A, spec):
+    return O.noise_variance_dmrs(sl.pilots[:, :1], A[:, :1], spec.n_rx, spec.n_layers, spec.occ,
+                                 "freq")[0]
