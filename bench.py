@@ -282,6 +282,8 @@ def main():
                     help="streams the timed steps alternate over (1: strictly serial)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop latency run")
+    ap.add_argument("--no-noise", action="store_true",
+                    help="skip the noise-variance estimate timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -337,6 +339,32 @@ def config_dict(spec, args, world):
                            if args.streams > 1 else "serial"),
             "parallelism": f"replicas x{world} (cells per rank)",
             "l2": "working set per step larger than the 129 MB L2 (no flush needed)"}
+
+
+def noise_estimate_run(cfg, spec, buf, st, reps: int = 50) -> dict:
+    """Noise-variance estimate (phy_noise_est, 'min' mode) on the step's LS anchors: CUDA-event
+    time per call (two launches; the anchors are L2-resident, as right after the LS stage) and
+    the estimates against the noise level the grid was drawn with."""
+    import torch
+    from paper_2510_07843_gb300 import phy
+    s2 = torch.empty(spec.n_cells, dtype=torch.float32, device=buf.Y.device)
+    phy.chest(cfg, buf.Y, buf.pilots, buf.anchors, stream=st)
+
+    def call():
+        phy.noise_est(cfg, "min", buf.anchors, buf.pilots, s2, buf.workspace, stream=st)
+
+    for _ in range(3):
+        call()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(reps):
+        call()
+    b.record(st)
+    torch.cuda.synchronize()
+    est = s2.cpu().numpy().astype(np.float64)
+    return {"api": "phy_noise_est", "mode": "min", "us_per_call": a.elapsed_time(b) / reps * 1e3,
+            "launches_per_call": 2, "sigma2_true": spec.sigma2,
+            "estimate_rel_err_max": float(np.max(np.abs(est / spec.sigma2 - 1.0)))}
 
 
 def serving_run(spec, precision, dev, buf, slots=100, llr="f32", streams=2):
@@ -516,6 +544,10 @@ def run_ours(args, spec, rank, world, local):
         serving = serving_run(spec, args.precision, dev, buf, llr=args.llr,
                               streams=args.streams)
 
+    noise = None
+    if not args.no_noise:
+        noise = noise_estimate_run(cfg, spec, buf, st)
+
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         r = oracle_sample_rate(spec, S.make_slot(dataclasses.replace(spec, n_cells=1),
@@ -587,6 +619,7 @@ def run_ours(args, spec, rank, world, local):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "serving": serving,
+        "noise_estimate": noise,
         "gpu_launches": (1 + 2 * detect_chunks(spec)) * args.steps,
         "clocks": clk,
     }

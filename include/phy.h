@@ -39,7 +39,8 @@
  *  llr      [cell][dsym][sc][layer][qm]  float      max-log LLRs, positive = bit 0 (IEEE
  *                                                   binary16 with cfg.llr_format = PHY_LLR_F16)
  *  flags    [cell][dsym][sc]             uint8      see above
- *  sigma2   [cell]                       float      noise variance per Rx per RE (known)
+ *  sigma2   [cell]                       float      noise variance per Rx per RE (given, or
+ *                                                   estimated by phy_noise_est)
  * `dsym` counts data symbols only: the symbols 0..n_sym-1 that are not DMRS symbols, in order.
  *
  * DMRS and estimation rules: layer l uses comb c = l % 2 (subcarriers k = 2m + c) and Walsh row
@@ -244,6 +245,45 @@ phy_status phy_autotune(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32
                         uint8_t* flags, void* workspace, size_t workspace_bytes, void* stream,
                         int32_t* chunk_out);
 void phy_autotune_clear(void);
+
+/*
+ * Noise-variance estimate from the DMRS (the paper treats the noise level as a known input of the
+ * LMMSE block, Sec. IV; no method is given, so the rule below is this library's). A noise sample
+ * is the residual of an LS anchor against its prediction from other anchors of the same layer:
+ *  - PHY_NOISE_FREQ: every interior anchor (groups 1 .. G-2) against the linear interpolation of
+ *    its two neighbours at its own subcarrier, e = H(g) - a H(g-1) - b H(g+1), on each DMRS symbol;
+ *  - PHY_NOISE_TIME: every anchor against the same anchor of the other DMRS symbol (needs two);
+ *  - PHY_NOISE_MIN: both, keeping the smaller estimate (channel variation across the groups, or
+ *    between the DMRS symbols, can only raise either one).
+ * Each residual is a fixed linear combination of DMRS REs whose noise gain gamma (the squared norm
+ * of its coefficients, from the pilots) is known, so
+ *   sigma2_out[cell] = sum |e|^2 / (n_rx sum gamma)
+ * is unbiased when the channel is constant over the three groups (frequency) or between the two
+ * DMRS symbols (time), and too large otherwise. NaN where the mode has no residual (fewer than
+ * three groups for the frequency rule and, with PHY_NOISE_MIN, no second DMRS symbol either).
+ *  - anchors: as written by phy_chest (or any estimate in that layout); pilots as for phy_chest.
+ *  - sigma2_out: n_cells floats (device). The sums run in a fixed order (deterministic).
+ *  - workspace: at least phy_workspace_size(cfg) bytes; the call uses the bytes after the first
+ *    n_cells n_dmrs G n_layers n_rx phy_c32 (where phy_slot_run keeps the anchors), rounded up to
+ *    256, so anchors stored at the start of the same workspace stay intact.
+ *  - PHY_ERR_INVALID_ARG for an unknown mode or PHY_NOISE_TIME with one DMRS symbol.
+ */
+typedef enum { PHY_NOISE_FREQ = 0, PHY_NOISE_TIME = 1, PHY_NOISE_MIN = 2 } phy_noise_mode;
+
+phy_status phy_noise_est(const phy_slot_cfg* cfg, int32_t mode, const phy_c32* anchors,
+                         const phy_c32* pilots, float* sigma2_out, void* workspace,
+                         size_t workspace_bytes, void* stream);
+
+/*
+ * phy_slot_run() with the noise variance estimated on the way: LS estimation, phy_noise_est()
+ * with `mode` into sigma2_out (n_cells floats, device), then interpolation, detection, SINR and
+ * LLRs with that estimate, all on `stream`. Same outputs, rules and workspace as phy_slot_run();
+ * the result equals phy_slot_run() called with sigma2 = the estimate.
+ */
+phy_status phy_slot_run_est(const phy_slot_cfg* cfg, int32_t mode, const phy_c32* Y,
+                            const phy_c32* pilots, float* sigma2_out, phy_c32* x_hat,
+                            float* sinr, float* llr, uint8_t* flags, void* workspace,
+                            size_t workspace_bytes, void* stream);
 
 #ifdef __cplusplus
 }

@@ -99,8 +99,19 @@ phy_status check_shape(const Geo& g) {
   return PHY_OK;
 }
 
+// Workspace layout: anchors | noise-estimate partial sums | detection scratch (one chunk).
+size_t head_bytes(const Geo& g) {
+  return align_up(anchor_bytes(g)) + align_up(phy::noise_scratch_bytes(g));
+}
+
 size_t workspace_for_chunk(const Geo& g, int chunk) {
-  return align_up(anchor_bytes(g)) + align_up(phy::detect_scratch_bytes(g, chunk));
+  return head_bytes(g) + align_up(phy::detect_scratch_bytes(g, chunk));
+}
+
+phy_status check_noise_mode(const Geo& g, int mode) {
+  if (mode < PHY_NOISE_FREQ || mode > PHY_NOISE_MIN) return PHY_ERR_INVALID_ARG;
+  if (mode == PHY_NOISE_TIME && g.n_dmrs != 2) return PHY_ERR_INVALID_ARG;
+  return PHY_OK;
 }
 
 // ---------------------------------------------------------------- autotuner table
@@ -150,7 +161,7 @@ phy_status slot_run_fit(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32
   s = check_shape(g);
   if (s != PHY_OK) return s;
   phy_c32* anchors = (phy_c32*)workspace;
-  const size_t a = align_up(anchor_bytes(g));
+  const size_t a = head_bytes(g);
   cudaError_t e = launch_chest(g, Y, pilots, anchors, st);
   if (e != cudaSuccess) return PHY_ERR_CUDA;
   e = launch_detect(g, anchors, Y, sigma2, x_hat, sinr, llr, flags,
@@ -253,7 +264,7 @@ phy_status phy_detect_stage(const phy_slot_cfg* cfg, int32_t stage, const phy_c3
   const int stages = stage < 0 ? (phy::kStageGramMf | phy::kStageSolve)
                                : (stage == PHY_STAGE_GRAM_MF ? phy::kStageGramMf
                                                              : phy::kStageSolve);
-  const size_t a = align_up(anchor_bytes(g));
+  const size_t a = head_bytes(g);
   return cuda_status(phy::launch_detect(g, anchors, Y, sigma2, x_hat, sinr, llr, flags,
                                         static_cast<char*>(workspace) + a, workspace_bytes - a,
                                         stages, (cudaStream_t)stream));
@@ -270,6 +281,52 @@ phy_status phy_slot_run(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32
   if (workspace_bytes < phy_workspace_size(cfg)) return PHY_ERR_NO_MEMORY;
   return phy::slot_run_fit(cfg, Y, pilots, sigma2, x_hat, sinr, llr, flags, workspace,
                            workspace_bytes, (cudaStream_t)stream);
+}
+
+phy_status phy_noise_est(const phy_slot_cfg* cfg, int32_t mode, const phy_c32* anchors,
+                         const phy_c32* pilots, float* sigma2_out, void* workspace,
+                         size_t workspace_bytes, void* stream) {
+  Geo g;
+  phy_status s = make_geo(cfg, &g);
+  if (s != PHY_OK) return s;
+  s = check_noise_mode(g, mode);
+  if (s != PHY_OK) return s;
+  if (!anchors || !pilots || !sigma2_out || !workspace) return PHY_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace) % kAlign) return PHY_ERR_INVALID_ARG;
+  if (workspace_bytes < phy_workspace_size(cfg)) return PHY_ERR_NO_MEMORY;
+  return cuda_status(phy::launch_noise_est(g, mode, anchors, pilots, sigma2_out,
+                                           static_cast<char*>(workspace) +
+                                               align_up(anchor_bytes(g)),
+                                           (cudaStream_t)stream));
+}
+
+phy_status phy_slot_run_est(const phy_slot_cfg* cfg, int32_t mode, const phy_c32* Y,
+                            const phy_c32* pilots, float* sigma2_out, phy_c32* x_hat,
+                            float* sinr, float* llr, uint8_t* flags, void* workspace,
+                            size_t workspace_bytes, void* stream) {
+  Geo g;
+  phy_status s = make_geo(cfg, &g);
+  if (s != PHY_OK) return s;
+  s = check_noise_mode(g, mode);
+  if (s != PHY_OK) return s;
+  if (!Y || !pilots || !sigma2_out || !flags || !workspace || ((uintptr_t)Y % 16))
+    return PHY_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace) % kAlign) return PHY_ERR_INVALID_ARG;
+  if (workspace_bytes < phy_workspace_size(cfg)) return PHY_ERR_NO_MEMORY;
+  s = check_shape(g);
+  if (s != PHY_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  phy_c32* anchors = (phy_c32*)workspace;
+  char* ws = static_cast<char*>(workspace);
+  cudaError_t e = phy::launch_chest(g, Y, pilots, anchors, st);
+  if (e == cudaSuccess)
+    e = phy::launch_noise_est(g, mode, anchors, pilots, sigma2_out,
+                              ws + align_up(anchor_bytes(g)), st);
+  if (e == cudaSuccess)
+    e = phy::launch_detect(g, anchors, Y, sigma2_out, x_hat, sinr, llr, flags,
+                           ws + head_bytes(g), workspace_bytes - head_bytes(g),
+                           phy::kStageGramMf | phy::kStageSolve, st);
+  return cuda_status(e);
 }
 
 phy_status phy_slot_run_host(const phy_slot_cfg* cfg, const phy_c32* Y_host,

@@ -53,6 +53,13 @@ cudaError_t launch_seg_prep_tc(const Geo& g, int NL, int c0, int nc, const phy_c
                                const phy_c32* Y, float4* ygg, cf* bvec, unsigned* err,
                                cudaStream_t st);
 
+// Noise-variance estimate per cell from the LS anchors and pilots (mode: phy_noise_mode) into
+// sigma2_out; scratch holds noise_scratch_bytes(g) of partial sums.
+size_t noise_scratch_bytes(const Geo& g);
+cudaError_t launch_noise_est(const Geo& g, int mode, const phy_c32* anchors,
+                             const phy_c32* pilots, float* sigma2_out, void* scratch,
+                             cudaStream_t st);
+
 cudaError_t launch_detect_h(const Geo& g, const phy_c32* H, const phy_c32* Y, const float* sigma2,
                             phy_c32* x_hat, float* sinr, uint8_t* flags, cudaStream_t st);
 

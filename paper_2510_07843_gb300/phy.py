@@ -49,6 +49,8 @@ _SIGS = {
     "phy_detect_stage": (ctypes.c_int, [_P, ctypes.c_int32] + [_P] * 8 + [ctypes.c_size_t, _P]),
     "phy_autotune": (ctypes.c_int, [_P] * 9 + [ctypes.c_size_t, _P, _P]),
     "phy_autotune_clear": (None, []),
+    "phy_noise_est": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "phy_slot_run_est": (ctypes.c_int, [_P, ctypes.c_int32] + [_P] * 8 + [ctypes.c_size_t, _P]),
 }
 
 STAGE_GRAM_MF, STAGE_SOLVE = 0, 1
@@ -214,6 +216,29 @@ def autotune(cfg: SlotConfig, Y, pilots, sigma2, x_hat, sinr, llr, flags, worksp
 def autotune_clear():
     """phy_autotune_clear: forget every tuned configuration."""
     load().phy_autotune_clear()
+
+
+NOISE_MODE = {"freq": 0, "time": 1, "min": 2}  # phy_noise_mode
+
+
+def noise_est(cfg: SlotConfig, mode: str, anchors, pilots, sigma2_out, workspace, stream=None):
+    """phy_noise_est: per-cell noise variance from the DMRS anchor residuals into sigma2_out."""
+    c = cfg.c()
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check("phy_noise_est",
+           load().phy_noise_est(ctypes.byref(c), NOISE_MODE[mode], _ptr(anchors), _ptr(pilots),
+                                _ptr(sigma2_out), _ptr(workspace), ws_bytes, _stream(stream)))
+
+
+def slot_run_est(cfg: SlotConfig, mode: str, Y, pilots, sigma2_out, x_hat, sinr, llr, flags,
+                 workspace, stream=None):
+    """phy_slot_run_est: the receiver with the noise variance estimated into sigma2_out."""
+    c = cfg.c()
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check("phy_slot_run_est",
+           load().phy_slot_run_est(ctypes.byref(c), NOISE_MODE[mode], _ptr(Y), _ptr(pilots),
+                                   _ptr(sigma2_out), _ptr(x_hat), _ptr(sinr), _ptr(llr),
+                                   _ptr(flags), _ptr(workspace), ws_bytes, _stream(stream)))
 
 
 def slot_run_noalloc(cfg: SlotConfig, Y, pilots, sigma2, x_hat, sinr, llr, flags, stream=None):

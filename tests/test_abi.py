@@ -100,3 +100,37 @@ def test_tensor_core_precision_needs_even_antenna_count(lib):
     rc = lib.phy_slot_run(ctypes.byref(c), fake, fake, fake, None, None, None, fake, fake, ws,
                           None)
     assert rc == 2  # ... that the TMA-fed tensor-core kernel does not support
+
+
+def test_noise_estimate_validates_before_any_cuda_call(lib):
+    fake = ctypes.c_void_p(256)  # never dereferenced: the calls fail validation first
+    c = _cfg().c()
+    ws = lib.phy_workspace_size(ctypes.byref(c))
+    for mode in (-1, 3):  # unknown modes
+        assert lib.phy_noise_est(ctypes.byref(c), mode, fake, fake, fake, fake, ws, None) == 1
+        assert lib.phy_slot_run_est(ctypes.byref(c), mode, fake, fake, fake, None, None, None,
+                                    fake, fake, ws, None) == 1
+    one = _cfg(dmrs_sym=(2,)).c()  # the time residual needs two DMRS symbols
+    ws1 = lib.phy_workspace_size(ctypes.byref(one))
+    assert lib.phy_noise_est(ctypes.byref(one), phy.NOISE_MODE["time"], fake, fake, fake, fake,
+                             ws1, None) == 1
+    assert lib.phy_noise_est(ctypes.byref(c), 2, None, fake, fake, fake, ws, None) == 1
+    assert lib.phy_noise_est(ctypes.byref(c), 2, fake, fake, None, fake, ws, None) == 1
+    assert lib.phy_noise_est(ctypes.byref(c), 2, fake, fake, fake, fake, 16, None) == 3
+    assert lib.phy_slot_run_est(ctypes.byref(c), 2, fake, fake, fake, None, None, None, fake,
+                                fake, 16, None) == 3
+    # the estimate's partial sums make the workspace a little larger than anchors + scratch
+    assert ws > 8 * 2 * 205 * 16 * 64 * 8
+
+
+def test_noalloc_scratch_still_holds_the_massive_batch(lib):
+    """The fixed scratch of phy_slot_run_noalloc covers 8 cells of 273 PRB at 64x16 with the
+    smallest chunk (the call shrinks chunks to fit)."""
+    c = _cfg().c()
+    one_cell = _cfg(n_cells=1).c()
+    per_cell = lib.phy_workspace_size(ctypes.byref(one_cell))
+    assert per_cell > 0
+    assert lib.phy_workspace_size(ctypes.byref(c)) > 0
+    # anchors and partial sums of 8 cells plus one cell's detection scratch
+    need = 8 * (2 * 205 * 16 * 64 * 8) + per_cell
+    assert need < 64 << 20

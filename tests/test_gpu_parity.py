@@ -375,8 +375,12 @@ def test_segment_kernel_timeout_voids_the_solve(dev):
     phy.chest(cfg, b.Y, b.pilots, b.anchors)
     args = (b.anchors, b.Y, b.sigma2, b.x_hat, b.sinr, b.llr, b.flags, b.workspace)
     phy.detect_stage(cfg, phy.STAGE_GRAM_MF, *args)
-    # the error word is the first word after the anchors' 256-byte-aligned region
-    a = (b.anchors.numel() * 8 + 255) // 256 * 256
+    # workspace: anchors | noise-estimate partial sums (one 16-byte float4 per 1024 anchor
+    # entries of each cell) | detection scratch, each region 256-byte aligned; the error word
+    # is the first word of the detection scratch
+    up = lambda v: (v + 255) // 256 * 256
+    per_d = phy.n_groups(cfg) * spec.n_layers * spec.n_rx
+    a = up(b.anchors.numel() * 8) + up(spec.n_cells * -(-per_d // 1024) * 16)
     word = b.workspace[a:a + 4].view(torch.int32)
     word.fill_(1)
     b.flags.fill_(0)
