@@ -23,6 +23,9 @@ Steps and where they come from:
   of the LS anchors against their prediction from neighbouring anchors in frequency or from the
   other DMRS symbol, normalised by the exact noise gain of each residual (see the section at the
   end of this file).
+* Block-floating-point fronthaul decompression (the grid's arrival format in a split-7 software DU;
+  no format in the paper): bit unpacking of per-PRB blocks with a shared exponent, by Python
+  integers (see the last section).
 
 Readings where the paper is silent (each also fixed in the C ABI):
   - Layer l uses comb c = l % 2 (k = 2m + c) and Walsh row o = l // 2; L is the smallest power of
@@ -463,3 +466,42 @@ def noise_variance_dmrs(pilots: np.ndarray, anchors: np.ndarray, n_rx: int, n_la
     gain = noise_gain(pilots, n_layers, L, mode)
     with np.errstate(invalid="ignore", divide="ignore"):
         return np.where(gain > 0.0, energy / (n_rx * gain), np.nan)
+
+
+# ----------------------------------------------------------------------------------------------
+# Block-floating-point fronthaul decompression (the step before channel estimation in a split-7
+# fronthaul, which the paper's software-DU setting receives the grid over; no format is printed)
+# ----------------------------------------------------------------------------------------------
+#
+# Reading: the grid arrives per (cell, symbol, antenna, PRB) as one block of 1 + 3w bytes: a
+# parameter byte whose low four bits are the shared exponent e (high four bits ignored), then the
+# 24 mantissas of the PRB's 12 REs in the order I0, Q0, I1, Q1, ..., each a w-bit two's-complement
+# integer (1 <= w <= 16), packed most significant bit first across the bytes. The decompressed
+# value is mantissa * 2^e * scale.
+
+def bfp_block_bytes(iq_width: int) -> int:
+    return 1 + 3 * iq_width
+
+
+def bfp_decompress(Yc: np.ndarray, shape: Tuple[int, int, int, int], iq_width: int,
+                   scale: float) -> np.ndarray:
+    """Grid [cell][sym][rx][sc] (complex128) from the byte stream Yc of blocks [cell][sym][rx][prb]."""
+    n_cells, n_sym, n_rx, n_sc = shape
+    n_prb = n_sc // 12
+    w = iq_width
+    nb = bfp_block_bytes(w)
+    raw = np.asarray(Yc, dtype=np.uint8).reshape(n_cells, n_sym, n_rx, n_prb, nb)
+    out = np.zeros(shape, dtype=np.complex128)
+    for idx in np.ndindex(n_cells, n_sym, n_rx, n_prb):
+        blk = raw[idx]
+        e = int(blk[0]) & 0xF
+        bits = int.from_bytes(bytes(blk[1:]), "big")  # 24 w bits, first mantissa on top
+        vals = []
+        for i in range(24):
+            m = (bits >> (24 * w - (i + 1) * w)) & ((1 << w) - 1)
+            if m >= 1 << (w - 1):
+                m -= 1 << w
+            vals.append(m * (2.0 ** e) * scale)
+        c, t, r, p = idx
+        out[c, t, r, 12 * p:12 * p + 12] = np.array(vals[0::2]) + 1j * np.array(vals[1::2])
+    return out

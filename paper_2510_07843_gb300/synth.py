@@ -294,3 +294,38 @@ def make_slot(spec: SlotSpec, seed: int, keep_h: bool = True, noise: bool = True
             H_all.append(H)
     return Slot(spec=spec, Y=Y, pilots=P_all, sigma2=np.full(C, s2, dtype=np.float32),
                 bits=bits, x=X, H=H_all)
+
+
+# ----------------------------------------------------------------------------------------------
+# Fronthaul: block-floating-point compression at the radio unit (the sending side)
+# ----------------------------------------------------------------------------------------------
+
+def bfp_compress(Y: np.ndarray, iq_width: int, scale: float) -> np.ndarray:
+    """Byte stream of the grid Y [cell][sym][rx][sc] as blocks [cell][sym][rx][prb].
+
+    Each block: a parameter byte holding the exponent e (0..15) in its low four bits, then the 24
+    values I0, Q0, I1, Q1, ... of the PRB as w-bit two's-complement mantissas, most significant
+    bit first. The sender quantises round(Y / scale) to integers, takes the smallest e for which
+    every value of the block rounded to a multiple of 2^e fits w bits, and saturates what still
+    does not (e capped at 15).
+    """
+    w = int(iq_width)
+    if not 1 <= w <= 16:
+        raise ValueError("iq_width must be 1..16")
+    Y = np.asarray(Y)
+    n_cells, n_sym, n_rx, n_sc = Y.shape
+    v = np.empty(Y.shape + (2,), dtype=np.float64)
+    v[..., 0], v[..., 1] = Y.real, Y.imag
+    q = np.rint(v / np.float64(np.float32(scale))).reshape(-1, 24)  # [block][24]
+    lo, hi = -(1 << (w - 1)), (1 << (w - 1)) - 1
+    e = np.full(q.shape[0], 15, dtype=np.int64)
+    for cand in range(15, -1, -1):  # smallest exponent that fits
+        m = np.rint(q / (1 << cand))
+        fits = np.all((m >= lo) & (m <= hi), axis=1)
+        e = np.where(fits, cand, e)
+    m = np.clip(np.rint(q / (1 << e)[:, None]), lo, hi).astype(np.int64)
+    u = (m & ((1 << w) - 1)).astype(np.uint32)  # two's complement in w bits
+    bits = ((u[:, :, None] >> np.arange(w - 1, -1, -1, dtype=np.uint32)) & 1).astype(np.uint8)
+    payload = np.packbits(bits.reshape(q.shape[0], 24 * w), axis=1)  # 3w bytes per block
+    out = np.concatenate([e.astype(np.uint8)[:, None], payload], axis=1)
+    return out.reshape(-1)

@@ -544,3 +544,53 @@ def test_noise_estimate_modes_and_undefined_cases():
 def est_freq_one(sl, A, spec):
     return O.noise_variance_dmrs(sl.pilots[:, :1], A[:, :1], spec.n_rx, spec.n_layers, spec.occ,
                                  "freq")[0]
+
+
+# ------------------------------------------------------------------ BFP fronthaul decompression
+
+def test_bfp_handworked_blocks():
+    rows = list(golden_lines("bfp_handworked.txt"))
+    for blk, vals in zip(rows[0::2], rows[1::2]):
+        assert blk[0] == "block" and vals[0] == "re"
+        w, scale = int(blk[1]), float(blk[2])
+        raw = np.array([int(b, 16) for b in blk[3:]], dtype=np.uint8)
+        assert raw.size == O.bfp_block_bytes(w)
+        got = O.bfp_decompress(raw, (1, 1, 1, 12), w, scale)[0, 0, 0]
+        want = np.array([float(v) for v in vals[1:]])
+        np.testing.assert_array_equal(got.real, want[0::2])
+        np.testing.assert_array_equal(got.imag, want[1::2])
+
+
+@pytest.mark.parametrize("w,dtype", [(16, ">i2"), (8, "i1")])
+def test_bfp_byte_aligned_widths_are_plain_integers(w, dtype):
+    """At 8 and 16 bits the mantissas are whole (big-endian) integers: numpy reads them directly."""
+    rng = np.random.default_rng(w)
+    n = 50
+    raw = rng.integers(0, 256, size=(n, O.bfp_block_bytes(w)), dtype=np.uint8)
+    raw[:, 0] &= 0x3F  # some high-nibble junk stays in the parameter byte
+    got = O.bfp_decompress(raw.reshape(-1), (1, 1, 1, 12 * n), w, 0.25)[0, 0, 0]
+    for b in range(n):
+        m = np.frombuffer(raw[b, 1:].tobytes(), dtype=dtype).astype(np.float64)
+        v = m * 2.0 ** (raw[b, 0] & 0xF) * 0.25
+        np.testing.assert_array_equal(got[12 * b:12 * b + 12], v[0::2] + 1j * v[1::2])
+
+
+@pytest.mark.parametrize("w", list(range(1, 17)))
+def test_bfp_round_trip_within_the_quantisation_step(w):
+    """The sender's compressor (written independently, with numpy bit packing) and the oracle's
+    decompressor agree up to half a quantisation step 2^(e-1) scale per block (the mantissas are
+    rounded), or the saturation of the one-bit width."""
+    spec = S.SlotSpec(n_prb=3, n_rx=3, n_layers=2, qm=4, dmrs_sym=(2,), snr_db=15.0)
+    sl = S.make_slot(spec, 100 + w, keep_h=False)
+    scale = 2.0 ** -12
+    c = S.bfp_compress(sl.Y, w, scale)
+    nb = O.bfp_block_bytes(w)
+    assert c.size == sl.Y.size // 12 * nb
+    got = O.bfp_decompress(c, sl.Y.shape, w, scale)
+    e = (c.reshape(-1, nb)[:, 0] & 0xF).astype(np.float64)
+    step = (2.0 ** e * scale).reshape(sl.Y.shape[:-1] + (-1,)).repeat(12, axis=-1)
+    err = np.maximum(np.abs(got.real - sl.Y.real), np.abs(got.imag - sl.Y.imag))
+    if w > 1:
+        assert np.all(err <= 0.5 * step + 0.5 * scale + 1e-12)
+    else:  # one bit: -1 or 0 times the step
+        assert np.all(np.isin(np.round(got.real / step), [-1.0, 0.0]))
