@@ -284,6 +284,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop latency run")
     ap.add_argument("--no-noise", action="store_true",
                     help="skip the noise-variance estimate timing")
+    ap.add_argument("--no-bfp", action="store_true",
+                    help="skip the block-floating-point fronthaul timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -365,6 +367,41 @@ def noise_estimate_run(cfg, spec, buf, st, reps: int = 50) -> dict:
     return {"api": "phy_noise_est", "mode": "min", "us_per_call": a.elapsed_time(b) / reps * 1e3,
             "launches_per_call": 2, "sigma2_true": spec.sigma2,
             "estimate_rel_err_max": float(np.max(np.abs(est / spec.sigma2 - 1.0)))}
+
+
+def bfp_run(cfg, spec, slot, buf, st, hbm_peak: float, iq_width: int = 9, reps: int = 20) -> dict:
+    """Block-floating-point fronthaul input (9-bit mantissas) on the same batch: decompression of
+    the whole grid (stream read + grid written, inputs larger than L2) and the receiver fed from
+    the stream (phy_slot_run_bfp) next to the grid-fed one, CUDA events on the launch stream."""
+    import torch
+    from paper_2510_07843_gb300 import phy
+    scale = 2.0 ** -10
+    c = torch.from_numpy(S.bfp_compress(slot.Y, iq_width, scale)).to(buf.Y.device)
+    Yd = torch.empty_like(buf.Y)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(reps):
+            fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    dec_ms = timed(lambda: phy.bfp_decompress(cfg, c, iq_width, scale, Yd, stream=st))
+    bfp_ms = timed(lambda: phy.slot_run_bfp(cfg, c, iq_width, scale, Yd, buf.pilots, buf.sigma2,
+                                            buf.x_hat, buf.sinr, buf.llr, buf.flags,
+                                            buf.workspace, stream=st))
+    run_ms = timed(lambda: phy.slot_run(cfg, buf.Y, buf.pilots, buf.sigma2, buf.x_hat, buf.sinr,
+                                        buf.llr, buf.flags, buf.workspace, stream=st))
+    moved = c.numel() + Yd.numel() * 8
+    gbs = moved / (dec_ms * 1e-3) / 1e9
+    return {"iq_width": iq_width, "stream_mb": c.numel() / 1e6,
+            "decompress_us": dec_ms * 1e3, "decompress_gbs": gbs,
+            "decompress_hbm_frac": gbs / hbm_peak,
+            "slot_run_bfp_ms": bfp_ms, "slot_run_ms": run_ms}
 
 
 def serving_run(spec, precision, dev, buf, slots=100, llr="f32", streams=2):
@@ -571,6 +608,9 @@ def run_ours(args, spec, rank, world, local):
     except Exception:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    bfp = None
+    if not args.no_bfp:
+        bfp = bfp_run(cfg, spec, slot, buf, st, hbm_peak)
     # per-kernel rooflines. Solve: FP32 ALU work per RE. Gram/matched filter: its products on
     # the FP32 pipe in the FP32 variant; with tensor cores it streams the grid (HBM bound).
     solve_roof = {"bound": "alu", "kernel": f"re_solve_fp32_kernel<16,{spec.qm}>",
@@ -620,6 +660,7 @@ def run_ours(args, spec, rank, world, local):
         "e2e": e2e,
         "serving": serving,
         "noise_estimate": noise,
+        "bfp_fronthaul": bfp,
         "gpu_launches": (1 + 2 * detect_chunks(spec)) * args.steps,
         "clocks": clk,
     }

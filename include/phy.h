@@ -285,6 +285,41 @@ phy_status phy_slot_run_est(const phy_slot_cfg* cfg, int32_t mode, const phy_c32
                             float* sinr, float* llr, uint8_t* flags, void* workspace,
                             size_t workspace_bytes, void* stream);
 
+/*
+ * Block-floating-point (BFP) fronthaul input: the received grid as a split-7 fronthaul delivers it
+ * to a software DU (the setting of the paper, which prints no format; this is the library's
+ * reading of the usual shared-exponent block format). The stream Yc holds one block per (cell,
+ * symbol, antenna, PRB), in that order, of 1 + 3 iq_width bytes:
+ *  - a parameter byte whose low four bits are the exponent e (the high four bits are ignored);
+ *  - the PRB's 24 values I0 Q0 I1 Q1 ... I11 Q11, each an iq_width-bit two's-complement
+ *    mantissa m (1 <= iq_width <= 16), packed most significant bit first across the bytes.
+ * The decoded value is m 2^e scale, rounded once to FP32 (m 2^e is exact). Yc must be 4-byte
+ * aligned; scale finite and positive.
+ *
+ * phy_bfp_bytes: the stream's size in bytes for cfg (0 for an invalid cfg or width).
+ * phy_bfp_decompress: decodes the stream into the grid Y [cell][sym][rx][sc] (16-byte aligned).
+ *   With data_only != 0 the DMRS symbols' rows of Y are not written (phy_chest_bfp reads them
+ *   from the stream itself).
+ * phy_chest_bfp: phy_chest() reading the DMRS symbols straight from the stream; its anchors are
+ *   bitwise those of phy_chest() on the decoded grid.
+ * phy_slot_run_bfp: phy_slot_run() from the stream: decodes the data symbols into the caller's
+ *   grid buffer Y (device, n_cells n_sym n_rx n_sc phy_c32; its DMRS rows are left as they were),
+ *   estimates from the stream, and detects; outputs bitwise those of phy_slot_run() on the fully
+ *   decoded grid. Same workspace and rules as phy_slot_run().
+ */
+size_t phy_bfp_bytes(const phy_slot_cfg* cfg, int32_t iq_width);
+
+phy_status phy_bfp_decompress(const phy_slot_cfg* cfg, const uint8_t* Yc, int32_t iq_width,
+                              float scale, int32_t data_only, phy_c32* Y, void* stream);
+
+phy_status phy_chest_bfp(const phy_slot_cfg* cfg, const uint8_t* Yc, int32_t iq_width,
+                         float scale, const phy_c32* pilots, phy_c32* anchors, void* stream);
+
+phy_status phy_slot_run_bfp(const phy_slot_cfg* cfg, const uint8_t* Yc, int32_t iq_width,
+                            float scale, phy_c32* Y, const phy_c32* pilots, const float* sigma2,
+                            phy_c32* x_hat, float* sinr, float* llr, uint8_t* flags,
+                            void* workspace, size_t workspace_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

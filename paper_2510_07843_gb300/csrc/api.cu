@@ -329,6 +329,72 @@ phy_status phy_slot_run_est(const phy_slot_cfg* cfg, int32_t mode, const phy_c32
   return cuda_status(e);
 }
 
+size_t phy_bfp_bytes(const phy_slot_cfg* cfg, int32_t iq_width) {
+  Geo g;
+  if (make_geo(cfg, &g) != PHY_OK || iq_width < 1 || iq_width > 16) return 0;
+  return (size_t)g.n_cells * g.n_sym * g.n_rx * (g.n_sc / 12) * (size_t)(1 + 3 * iq_width);
+}
+
+namespace {
+phy_status check_bfp(int32_t iq_width, float scale, const uint8_t* Yc) {
+  if (iq_width < 1 || iq_width > 16) return PHY_ERR_INVALID_ARG;
+  if (!(scale > 0.f) || !(scale < 3.0e38f)) return PHY_ERR_INVALID_ARG;
+  if (!Yc || ((uintptr_t)Yc % 4)) return PHY_ERR_INVALID_ARG;
+  return PHY_OK;
+}
+}  // namespace
+
+phy_status phy_bfp_decompress(const phy_slot_cfg* cfg, const uint8_t* Yc, int32_t iq_width,
+                              float scale, int32_t data_only, phy_c32* Y, void* stream) {
+  Geo g;
+  phy_status s = make_geo(cfg, &g);
+  if (s != PHY_OK) return s;
+  s = check_bfp(iq_width, scale, Yc);
+  if (s != PHY_OK) return s;
+  if (!Y || ((uintptr_t)Y % 16)) return PHY_ERR_INVALID_ARG;
+  return cuda_status(phy::launch_bfp_decompress(g, Yc, iq_width, scale, data_only ? 1 : 0, Y,
+                                                (cudaStream_t)stream));
+}
+
+phy_status phy_chest_bfp(const phy_slot_cfg* cfg, const uint8_t* Yc, int32_t iq_width,
+                         float scale, const phy_c32* pilots, phy_c32* anchors, void* stream) {
+  Geo g;
+  phy_status s = make_geo(cfg, &g);
+  if (s != PHY_OK) return s;
+  s = check_bfp(iq_width, scale, Yc);
+  if (s != PHY_OK) return s;
+  if (!pilots || !anchors) return PHY_ERR_INVALID_ARG;
+  return cuda_status(phy::launch_chest_bfp(g, Yc, iq_width, scale, pilots, anchors,
+                                           (cudaStream_t)stream));
+}
+
+phy_status phy_slot_run_bfp(const phy_slot_cfg* cfg, const uint8_t* Yc, int32_t iq_width,
+                            float scale, phy_c32* Y, const phy_c32* pilots, const float* sigma2,
+                            phy_c32* x_hat, float* sinr, float* llr, uint8_t* flags,
+                            void* workspace, size_t workspace_bytes, void* stream) {
+  Geo g;
+  phy_status s = make_geo(cfg, &g);
+  if (s != PHY_OK) return s;
+  s = check_bfp(iq_width, scale, Yc);
+  if (s != PHY_OK) return s;
+  if (!Y || !pilots || !sigma2 || !flags || !workspace || ((uintptr_t)Y % 16))
+    return PHY_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace) % kAlign) return PHY_ERR_INVALID_ARG;
+  if (workspace_bytes < phy_workspace_size(cfg)) return PHY_ERR_NO_MEMORY;
+  s = check_shape(g);
+  if (s != PHY_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  phy_c32* anchors = (phy_c32*)workspace;
+  cudaError_t e = phy::launch_bfp_decompress(g, Yc, iq_width, scale, 1, Y, st);
+  if (e == cudaSuccess) e = phy::launch_chest_bfp(g, Yc, iq_width, scale, pilots, anchors, st);
+  if (e == cudaSuccess)
+    e = phy::launch_detect(g, anchors, Y, sigma2, x_hat, sinr, llr, flags,
+                           static_cast<char*>(workspace) + head_bytes(g),
+                           workspace_bytes - head_bytes(g), phy::kStageGramMf | phy::kStageSolve,
+                           st);
+  return cuda_status(e);
+}
+
 phy_status phy_slot_run_host(const phy_slot_cfg* cfg, const phy_c32* Y_host,
                              const phy_c32* pilots_host, const float* sigma2_host,
                              float* llr_host, uint8_t* flags_host, phy_c32* Y, phy_c32* pilots,

@@ -7,6 +7,11 @@
 // subcarriers are one contiguous 16L-byte run of each antenna row of Y: each thread loads its
 // run once with 16-byte loads into registers; the pilots of the group (all layers) are staged in
 // shared memory once per CTA and read as broadcasts. Writes are coalesced over r.
+//
+// The BFP variant reads the same runs straight from the compressed fronthaul stream (bfp.cuh)
+// instead of a decompressed grid, with the decompressor's arithmetic, so its anchors are bitwise
+// those of the plain kernel on the decompressed grid.
+#include "bfp.cuh"
 #include "launch.h"
 
 namespace phy {
@@ -15,10 +20,17 @@ namespace {
 
 constexpr int kChestThreads = 64;
 
-template <int L>
+// Compressed received grid: the stream, its mantissa width and scale.
+struct BfpGrid {
+  const uint8_t* yc;
+  int w;
+  float scale;
+};
+
+template <int L, bool BFP>
 __global__ void __launch_bounds__(kChestThreads)
-    chest_ls_kernel(Geo g, const phy_c32* __restrict__ Y, const phy_c32* __restrict__ P,
-                    phy_c32* __restrict__ anchors) {
+    chest_ls_kernel(Geo g, const phy_c32* __restrict__ Y, BfpGrid bfp,
+                    const phy_c32* __restrict__ P, phy_c32* __restrict__ anchors) {
   __shared__ cf pil[kMaxLayers][2 * L];
   const int grp = blockIdx.x, d = blockIdx.y, cell = blockIdx.z;
   const int r = threadIdx.x;
@@ -29,10 +41,14 @@ __global__ void __launch_bounds__(kChestThreads)
   const phy_c32* prow = P + (size_t)(cell * g.n_dmrs + d) * nl * g.n_sc + k0;
   // this antenna's run of Y first, so that its loads are in flight with the pilots' ones
   const bool live = r < g.n_rx;
-  const phy_c32* yrow =
-      Y + ((size_t)(cell * g.n_sym + t) * g.n_rx + (live ? r : 0)) * g.n_sc + k0;
   cf y[2 * L];
-  if constexpr (L >= 2) {
+  if constexpr (BFP) {
+#pragma unroll
+    for (int i = 0; i < 2 * L; ++i)
+      y[i] = bfp_load_re(g, bfp.yc, bfp.w, bfp.scale, cell, t, live ? r : 0, k0 + i);
+  } else if constexpr (L >= 2) {
+    const phy_c32* yrow =
+        Y + ((size_t)(cell * g.n_sym + t) * g.n_rx + (live ? r : 0)) * g.n_sc + k0;
     // k0 is even, so the run starts on a 16-byte boundary
     const float4* y4 = reinterpret_cast<const float4*>(yrow);
 #pragma unroll
@@ -42,6 +58,8 @@ __global__ void __launch_bounds__(kChestThreads)
       y[2 * i + 1] = mk(v.z, v.w);
     }
   } else {
+    const phy_c32* yrow =
+        Y + ((size_t)(cell * g.n_sym + t) * g.n_rx + (live ? r : 0)) * g.n_sc + k0;
     y[0] = ld(yrow);
     y[1] = ld(yrow + 1);
   }
@@ -57,26 +75,42 @@ __global__ void __launch_bounds__(kChestThreads)
     const int c = l & 1;
     cf acc = mk(0.f, 0.f);
 #pragma unroll
-    for (int i = 0; i < L; ++i) acc = cfma_cj(pil[l][2 * i + c], y[2 * i + c], acc);  // y conj(p)
+    for (int i = 0; i < L; ++i) {  // y conj(p); the select keeps y in registers
+      const cf yv = c ? y[2 * i + 1] : y[2 * i];
+      acc = cfma_cj(pil[l][2 * i + c], yv, acc);
+    }
     st(out + (size_t)l * g.n_rx + r, inv_l * acc);
   }
+}
+
+template <bool BFP>
+cudaError_t launch_chest_any(const Geo& g, const phy_c32* Y, BfpGrid bfp, const phy_c32* pilots,
+                             phy_c32* anchors, cudaStream_t st) {
+  dim3 grid(g.G, g.n_dmrs, g.n_cells);
+  const int threads = g.n_rx <= 32 ? 32 : 64;
+  switch (g.L) {
+    case 1: chest_ls_kernel<1, BFP><<<grid, threads, 0, st>>>(g, Y, bfp, pilots, anchors); break;
+    case 2: chest_ls_kernel<2, BFP><<<grid, threads, 0, st>>>(g, Y, bfp, pilots, anchors); break;
+    case 4: chest_ls_kernel<4, BFP><<<grid, threads, 0, st>>>(g, Y, bfp, pilots, anchors); break;
+    case 8: chest_ls_kernel<8, BFP><<<grid, threads, 0, st>>>(g, Y, bfp, pilots, anchors); break;
+    case 16:
+      chest_ls_kernel<16, BFP><<<grid, threads, 0, st>>>(g, Y, bfp, pilots, anchors);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_chest(const Geo& g, const phy_c32* Y, const phy_c32* pilots, phy_c32* anchors,
                          cudaStream_t st) {
-  dim3 grid(g.G, g.n_dmrs, g.n_cells);
-  const int threads = g.n_rx <= 32 ? 32 : 64;
-  switch (g.L) {
-    case 1: chest_ls_kernel<1><<<grid, threads, 0, st>>>(g, Y, pilots, anchors); break;
-    case 2: chest_ls_kernel<2><<<grid, threads, 0, st>>>(g, Y, pilots, anchors); break;
-    case 4: chest_ls_kernel<4><<<grid, threads, 0, st>>>(g, Y, pilots, anchors); break;
-    case 8: chest_ls_kernel<8><<<grid, threads, 0, st>>>(g, Y, pilots, anchors); break;
-    case 16: chest_ls_kernel<16><<<grid, threads, 0, st>>>(g, Y, pilots, anchors); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  return launch_chest_any<false>(g, Y, BfpGrid{nullptr, 0, 0.f}, pilots, anchors, st);
+}
+
+cudaError_t launch_chest_bfp(const Geo& g, const uint8_t* yc, int w, float scale,
+                             const phy_c32* pilots, phy_c32* anchors, cudaStream_t st) {
+  return launch_chest_any<true>(g, nullptr, BfpGrid{yc, w, scale}, pilots, anchors, st);
 }
 
 }  // namespace phy

@@ -60,6 +60,14 @@ cudaError_t launch_noise_est(const Geo& g, int mode, const phy_c32* anchors,
                              const phy_c32* pilots, float* sigma2_out, void* scratch,
                              cudaStream_t st);
 
+// Block-floating-point fronthaul stream (format in bfp.cuh): decompression into the grid Y
+// (data_only: the DMRS symbols' rows are left untouched), and LS estimation read straight from
+// the stream (anchors bitwise equal to launch_chest on the decompressed grid).
+cudaError_t launch_bfp_decompress(const Geo& g, const uint8_t* yc, int w, float scale,
+                                  int data_only, phy_c32* Y, cudaStream_t st);
+cudaError_t launch_chest_bfp(const Geo& g, const uint8_t* yc, int w, float scale,
+                             const phy_c32* pilots, phy_c32* anchors, cudaStream_t st);
+
 cudaError_t launch_detect_h(const Geo& g, const phy_c32* H, const phy_c32* Y, const float* sigma2,
                             phy_c32* x_hat, float* sinr, uint8_t* flags, cudaStream_t st);
 

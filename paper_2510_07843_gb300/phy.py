@@ -51,6 +51,12 @@ _SIGS = {
     "phy_autotune_clear": (None, []),
     "phy_noise_est": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "phy_slot_run_est": (ctypes.c_int, [_P, ctypes.c_int32] + [_P] * 8 + [ctypes.c_size_t, _P]),
+    "phy_bfp_bytes": (ctypes.c_size_t, [_P, ctypes.c_int32]),
+    "phy_bfp_decompress": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_float, ctypes.c_int32,
+                                          _P, _P]),
+    "phy_chest_bfp": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_float, _P, _P, _P]),
+    "phy_slot_run_bfp": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_float] + [_P] * 8
+                         + [ctypes.c_size_t, _P]),
 }
 
 STAGE_GRAM_MF, STAGE_SOLVE = 0, 1
@@ -238,6 +244,40 @@ def slot_run_est(cfg: SlotConfig, mode: str, Y, pilots, sigma2_out, x_hat, sinr,
     _check("phy_slot_run_est",
            load().phy_slot_run_est(ctypes.byref(c), NOISE_MODE[mode], _ptr(Y), _ptr(pilots),
                                    _ptr(sigma2_out), _ptr(x_hat), _ptr(sinr), _ptr(llr),
+                                   _ptr(flags), _ptr(workspace), ws_bytes, _stream(stream)))
+
+
+def bfp_bytes(cfg: SlotConfig, iq_width: int) -> int:
+    """phy_bfp_bytes: size of cfg's block-floating-point fronthaul stream."""
+    c = cfg.c()
+    return load().phy_bfp_bytes(ctypes.byref(c), iq_width)
+
+
+def bfp_decompress(cfg: SlotConfig, Yc, iq_width: int, scale: float, Y, data_only=False,
+                   stream=None):
+    """phy_bfp_decompress: the stream Yc (uint8 tensor) decoded into the grid Y."""
+    c = cfg.c()
+    _check("phy_bfp_decompress",
+           load().phy_bfp_decompress(ctypes.byref(c), _ptr(Yc), iq_width, scale,
+                                     1 if data_only else 0, _ptr(Y), _stream(stream)))
+
+
+def chest_bfp(cfg: SlotConfig, Yc, iq_width: int, scale: float, pilots, anchors, stream=None):
+    """phy_chest_bfp: LS anchors read straight from the compressed stream."""
+    c = cfg.c()
+    _check("phy_chest_bfp",
+           load().phy_chest_bfp(ctypes.byref(c), _ptr(Yc), iq_width, scale, _ptr(pilots),
+                                _ptr(anchors), _stream(stream)))
+
+
+def slot_run_bfp(cfg: SlotConfig, Yc, iq_width: int, scale: float, Y, pilots, sigma2, x_hat,
+                 sinr, llr, flags, workspace, stream=None):
+    """phy_slot_run_bfp: the receiver from the compressed stream (Y: grid buffer it decodes into)."""
+    c = cfg.c()
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check("phy_slot_run_bfp",
+           load().phy_slot_run_bfp(ctypes.byref(c), _ptr(Yc), iq_width, scale, _ptr(Y),
+                                   _ptr(pilots), _ptr(sigma2), _ptr(x_hat), _ptr(sinr), _ptr(llr),
                                    _ptr(flags), _ptr(workspace), ws_bytes, _stream(stream)))
 
 

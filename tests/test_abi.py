@@ -134,3 +134,25 @@ def test_noalloc_scratch_still_holds_the_massive_batch(lib):
     # anchors and partial sums of 8 cells plus one cell's detection scratch
     need = 8 * (2 * 205 * 16 * 64 * 8) + per_cell
     assert need < 64 << 20
+
+
+def test_bfp_entry_points_validate_before_any_cuda_call(lib):
+    fake = ctypes.c_void_p(256)  # never dereferenced: the calls fail validation first
+    c = _cfg().c()
+    assert lib.phy_bfp_bytes(ctypes.byref(c), 9) == 8 * 14 * 64 * 273 * 28
+    assert lib.phy_bfp_bytes(ctypes.byref(c), 16) == 8 * 14 * 64 * 273 * 49
+    assert lib.phy_bfp_bytes(ctypes.byref(c), 0) == 0
+    assert lib.phy_bfp_bytes(ctypes.byref(c), 17) == 0
+    for w, scale in ((0, 1.0), (17, 1.0), (9, 0.0), (9, -1.0), (9, float("nan")),
+                     (9, float("inf"))):
+        assert lib.phy_bfp_decompress(ctypes.byref(c), fake, w, scale, 0, fake, None) == 1
+        assert lib.phy_chest_bfp(ctypes.byref(c), fake, w, scale, fake, fake, None) == 1
+    odd = ctypes.c_void_p(257)  # the stream must be 4-byte aligned, the grid 16-byte aligned
+    assert lib.phy_bfp_decompress(ctypes.byref(c), odd, 9, 1.0, 0, fake, None) == 1
+    assert lib.phy_bfp_decompress(ctypes.byref(c), fake, 9, 1.0, 0, ctypes.c_void_p(264),
+                                  None) == 1
+    ws = lib.phy_workspace_size(ctypes.byref(c))
+    assert lib.phy_slot_run_bfp(ctypes.byref(c), fake, 9, 1.0, fake, fake, fake, None, None,
+                                None, fake, fake, 16, None) == 3
+    assert lib.phy_slot_run_bfp(ctypes.byref(c), fake, 9, 1.0, None, fake, fake, None, None,
+                                None, fake, fake, ws, None) == 1
