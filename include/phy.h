@@ -302,10 +302,9 @@ phy_status phy_slot_run_est(const phy_slot_cfg* cfg, int32_t mode, const phy_c32
  *   from the stream itself).
  * phy_chest_bfp: phy_chest() reading the DMRS symbols straight from the stream; its anchors are
  *   bitwise those of phy_chest() on the decoded grid.
- * phy_slot_run_bfp: phy_slot_run() from the stream: decodes the data symbols into the caller's
- *   grid buffer Y (device, n_cells n_sym n_rx n_sc phy_c32; its DMRS rows are left as they were),
- *   estimates from the stream, and detects; outputs bitwise those of phy_slot_run() on the fully
- *   decoded grid. Same workspace and rules as phy_slot_run().
+ * phy_slot_run_bfp: phy_slot_run() from the stream: decodes it into the caller's grid buffer Y
+ *   (device, n_cells n_sym n_rx n_sc phy_c32) and runs the receiver on it; outputs bitwise those
+ *   of phy_slot_run() on the decoded grid. Same workspace and rules as phy_slot_run().
  */
 size_t phy_bfp_bytes(const phy_slot_cfg* cfg, int32_t iq_width);
 

@@ -385,8 +385,11 @@ phy_status phy_slot_run_bfp(const phy_slot_cfg* cfg, const uint8_t* Yc, int32_t 
   if (s != PHY_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
   phy_c32* anchors = (phy_c32*)workspace;
-  cudaError_t e = phy::launch_bfp_decompress(g, Yc, iq_width, scale, 1, Y, st);
-  if (e == cudaSuccess) e = phy::launch_chest_bfp(g, Yc, iq_width, scale, pilots, anchors, st);
+  // Decoding the whole grid and estimating from it beats decoding the data symbols and
+  // estimating from the stream: the DMRS rows cost the decoder a few microseconds, while the LS
+  // kernel's per-antenna runs cut across the compressed blocks.
+  cudaError_t e = phy::launch_bfp_decompress(g, Yc, iq_width, scale, 0, Y, st);
+  if (e == cudaSuccess) e = phy::launch_chest(g, Y, pilots, anchors, st);
   if (e == cudaSuccess)
     e = phy::launch_detect(g, anchors, Y, sigma2, x_hat, sinr, llr, flags,
                            static_cast<char*>(workspace) + head_bytes(g),

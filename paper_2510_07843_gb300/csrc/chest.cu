@@ -10,7 +10,9 @@
 //
 // The BFP variant reads the same runs straight from the compressed fronthaul stream (bfp.cuh)
 // instead of a decompressed grid, with the decompressor's arithmetic, so its anchors are bitwise
-// those of the plain kernel on the decompressed grid.
+// those of the plain kernel on the decompressed grid. Each warp stages the blocks of its antennas'
+// runs (at most four blocks of 1 + 3w bytes per antenna) in shared memory, one antenna row at a
+// time with the lanes over the row's 32-bit words (coalesced), and each thread unpacks its own.
 #include "bfp.cuh"
 #include "launch.h"
 
@@ -19,10 +21,12 @@ namespace phy {
 namespace {
 
 constexpr int kChestThreads = 64;
+constexpr int kChestBfpWords = 52;  // 4 blocks of <= 49 bytes, misalignment and window slack
 
-// Compressed received grid: the stream, its mantissa width and scale.
+// Compressed received grid: the stream, its size, mantissa width and scale.
 struct BfpGrid {
   const uint8_t* yc;
+  long long total;
   int w;
   float scale;
 };
@@ -43,9 +47,42 @@ __global__ void __launch_bounds__(kChestThreads)
   const bool live = r < g.n_rx;
   cf y[2 * L];
   if constexpr (BFP) {
+    __shared__ uint32_t s_blk[kChestThreads][kChestBfpWords];
+    const int nb = 1 + 3 * bfp.w, n_prb = g.n_sc / 12;
+    const int p0 = k0 / 12, p1 = (k0 + 2 * L - 1) / 12;  // PRBs of the run
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(bfp.yc);
+    const long long row0 = ((long long)cell * g.n_sym + t) * g.n_rx;
+    for (int j = 0; j < 32; ++j) {  // the warp's antennas, one row at a time
+      const int rr = warp * 32 + j;
+      if (rr >= g.n_rx) break;
+      const long long start = ((row0 + rr) * n_prb + p0) * nb;
+      const long long w0 = start >> 2, w1 = (start + (long long)(p1 - p0 + 1) * nb + 3) >> 2;
+      for (long long k = w0 + lane; k < w1; k += 32) {
+        uint32_t v = 0;
+        if (4 * k + 4 <= bfp.total) {
+          v = __ldg(src + k);
+        } else {  // the stream's last partial word
+          for (int q = 0; q < 4; ++q)
+            if (4 * k + q < bfp.total) v |= (uint32_t)__ldg(bfp.yc + 4 * k + q) << (8 * q);
+        }
+        s_blk[rr][k - w0] = v;
+      }
+    }
+    __syncwarp();
+    if (live) {
+      const long long start = ((row0 + r) * n_prb + p0) * nb;
+      const uint8_t* run = reinterpret_cast<const uint8_t*>(s_blk[r]) + (start & 3);
 #pragma unroll
-    for (int i = 0; i < 2 * L; ++i)
-      y[i] = bfp_load_re(g, bfp.yc, bfp.w, bfp.scale, cell, t, live ? r : 0, k0 + i);
+      for (int i = 0; i < 2 * L; ++i) {
+        const int k = k0 + i;
+        const uint8_t* blk = run + (k / 12 - p0) * nb;
+        const float p2 = (float)(1 << (blk[0] & 0xF));
+        const int m = 2 * (k % 12);
+        y[i] = mk(bfp_value(bfp_mantissa_padded(blk, bfp.w, m), p2, bfp.scale),
+                  bfp_value(bfp_mantissa_padded(blk, bfp.w, m + 1), p2, bfp.scale));
+      }
+    }
   } else if constexpr (L >= 2) {
     const phy_c32* yrow =
         Y + ((size_t)(cell * g.n_sym + t) * g.n_rx + (live ? r : 0)) * g.n_sc + k0;
@@ -105,12 +142,14 @@ cudaError_t launch_chest_any(const Geo& g, const phy_c32* Y, BfpGrid bfp, const 
 
 cudaError_t launch_chest(const Geo& g, const phy_c32* Y, const phy_c32* pilots, phy_c32* anchors,
                          cudaStream_t st) {
-  return launch_chest_any<false>(g, Y, BfpGrid{nullptr, 0, 0.f}, pilots, anchors, st);
+  return launch_chest_any<false>(g, Y, BfpGrid{nullptr, 0, 0, 0.f}, pilots, anchors, st);
 }
 
 cudaError_t launch_chest_bfp(const Geo& g, const uint8_t* yc, int w, float scale,
                              const phy_c32* pilots, phy_c32* anchors, cudaStream_t st) {
-  return launch_chest_any<true>(g, nullptr, BfpGrid{yc, w, scale}, pilots, anchors, st);
+  const long long total =
+      (long long)g.n_cells * g.n_sym * g.n_rx * (g.n_sc / 12) * (long long)(1 + 3 * w);
+  return launch_chest_any<true>(g, nullptr, BfpGrid{yc, total, w, scale}, pilots, anchors, st);
 }
 
 }  // namespace phy

@@ -16,7 +16,9 @@
 // also sums the gains of the (group, layer) pairs whose first antenna entry it owns, one work
 // item per (pair, comb index of the pair's span) so that every thread shares that part; one
 // float4 of partial sums per CTA. noise_final_kernel: CTA per cell, sums the partials in a fixed
-// order (FP64) and divides. No atomics: the result does not depend on scheduling.
+// order (FP64) and divides; it is launched as a programmatic dependent of the first (it starts
+// while the first drains and waits on griddepcontrol before reading). No atomics: the result
+// does not depend on scheduling.
 #include <math.h>
 
 #include "launch.h"
@@ -40,6 +42,15 @@ __device__ __forceinline__ float2 neighbour_weights(const Geo& g, int grp) {
 
 __device__ __forceinline__ float pilot_pow(const phy_c32* p) { return cabs2(ld(p)); }
 
+// a / b for 0 <= a < 2^24 and b >= 1 without an integer division: the float estimate is off by
+// at most one, which the two corrections remove.
+__device__ __forceinline__ int div_small(int a, int b, float inv_b) {
+  int q = __float2int_rz((float)a * inv_b);
+  if (q * b > a) --q;
+  if ((q + 1) * b <= a) ++q;
+  return q;
+}
+
 __global__ void __launch_bounds__(kNoiseThreads)
     noise_partial_kernel(Geo g, const phy_c32* __restrict__ anchors,
                          const phy_c32* __restrict__ pilots, float4* __restrict__ part) {
@@ -51,14 +62,17 @@ __global__ void __launch_bounds__(kNoiseThreads)
   const phy_c32* A1 = A0 + (g.n_dmrs == 2 ? per_d : 0);
   const int i0 = blockIdx.x * kNoiseEntries;
   const int i1 = min(i0 + kNoiseEntries, per_d);
+  const float inv_grp = 1.f / (float)per_grp;
   float ef = 0.f, et = 0.f, gf = 0.f, gt = 0.f;
+  // the final kernel may launch now and wait for this grid's completion (programmatic launch)
+  asm volatile("griddepcontrol.launch_dependents;");
 
   // ---- residual energies, entry i = (group * nl + layer) * nr + antenna
 #pragma unroll
   for (int it = 0; it < kNoiseItems; ++it) {
     const int i = i0 + it * kNoiseThreads + threadIdx.x;
     if (i < i1) {
-      const int grp = i / per_grp;
+      const int grp = div_small(i, per_grp, inv_grp);
       const cf h0 = ld(A0 + i);
       if (g.n_dmrs == 2) et += cabs2(h0 - ld(A1 + i));
       if (grp >= 1 && grp <= g.G - 2) {
@@ -82,9 +96,11 @@ __global__ void __launch_bounds__(kNoiseThreads)
   const float inv_l2 = 1.f / (float)(g.L * g.L);
   const int p_lo = (i0 + nr - 1) / nr, p_hi = (i1 + nr - 1) / nr;
   const int span = 3 * g.L;
+  const float inv_span = 1.f / (float)span, inv_nl = 1.f / (float)nl;
   for (int q = threadIdx.x; q < (p_hi - p_lo) * span; q += kNoiseThreads) {
-    const int p = p_lo + q / span, j = q % span;
-    const int grp = p / nl, l = p % nl, c = l & 1;
+    const int pq = div_small(q, span, inv_span);
+    const int p = p_lo + pq, j = q - pq * span;
+    const int grp = div_small(p, nl, inv_nl), l = p - grp * nl, c = l & 1;
     const phy_c32* P0 = pilots + ((size_t)(cell * g.n_dmrs) * nl + l) * g.n_sc + c;
     const phy_c32* P1 = P0 + (g.n_dmrs == 2 ? (size_t)nl * g.n_sc : 0);
     const int s = group_start(g, grp);
@@ -135,6 +151,8 @@ __global__ void __launch_bounds__(kNoiseThreads)
                        float* __restrict__ sigma2_out) {
   const int cell = blockIdx.x;
   __shared__ double red[4][kNoiseThreads];
+  // launched programmatically behind the partial kernel: wait until its sums are complete
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   double s[4] = {0.0, 0.0, 0.0, 0.0};
   for (int i = threadIdx.x; i < n_part; i += kNoiseThreads) {
     const float4 v = part[(size_t)cell * n_part + i];
@@ -181,8 +199,20 @@ cudaError_t launch_noise_est(const Geo& g, int mode, const phy_c32* anchors,
   const int np = n_parts(g);
   float4* part = static_cast<float4*>(scratch);
   noise_partial_kernel<<<dim3(np, g.n_cells), kNoiseThreads, 0, st>>>(g, anchors, pilots, part);
-  noise_final_kernel<<<g.n_cells, kNoiseThreads, 0, st>>>(g, mode, np, part, sigma2_out);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // programmatic dependent launch: the final kernel's launch overlaps the partial kernel's tail
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(g.n_cells);
+  lc.blockDim = dim3(kNoiseThreads);
+  lc.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  const float4* cpart = part;
+  return cudaLaunchKernelEx(&lc, noise_final_kernel, g, mode, np, cpart, sigma2_out);
 }
 
 }  // namespace phy

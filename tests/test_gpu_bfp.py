@@ -99,7 +99,8 @@ STREAM_CASES = {
 
 @pytest.mark.parametrize("name", list(STREAM_CASES))
 def test_stream_fed_paths_equal_grid_fed(dev, name):
-    """phy_chest_bfp = phy_chest on the decoded grid, phy_slot_run_bfp = phy_slot_run on it."""
+    """phy_chest_bfp = phy_chest on the decoded grid, phy_slot_run_bfp = phy_slot_run on it,
+    and phy_slot_run_bfp leaves the decoded grid in its buffer."""
     import torch
     from paper_2510_07843_gb300 import phy
     spec, w, scale, seed, prec = STREAM_CASES[name]
@@ -118,13 +119,14 @@ def test_stream_fed_paths_equal_grid_fed(dev, name):
     ref = phy.SlotBuffers(cfg, with_inputs=False)
     got = phy.SlotBuffers(cfg, with_inputs=False)
     phy.slot_run(cfg, Yd, P, s2, ref.x_hat, ref.sinr, ref.llr, ref.flags, ref.workspace)
-    Ys = torch.zeros_like(Yd)  # DMRS rows stay zero: the stream path must not need them
+    Ys = torch.zeros_like(Yd)
     phy.slot_run_bfp(cfg, c, w, scale, Ys, P, s2, got.x_hat, got.sinr, got.llr, got.flags,
                      got.workspace)
     torch.cuda.synchronize()
     assert torch.equal(torch.view_as_real(a0), torch.view_as_real(a1))
     for key in ("x_hat", "sinr", "llr", "flags"):
         assert torch.equal(getattr(ref, key), getattr(got, key)), key
+    assert torch.equal(torch.view_as_real(Ys), torch.view_as_real(Yd))
 
 
 def test_full_size_massive_stream(dev):
