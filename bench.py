@@ -398,10 +398,25 @@ def bfp_run(cfg, spec, slot, buf, st, hbm_peak: float, iq_width: int = 9, reps: 
                                         buf.llr, buf.flags, buf.workspace, stream=st))
     moved = c.numel() + Yd.numel() * 8
     gbs = moved / (dec_ms * 1e-3) / 1e9
+    # end to end with the compressed stream in pinned host memory (phy_slot_run_bfp_host): what
+    # crosses to the device per step is the stream, pilots and noise levels; LLRs and flags back
+    ch = c.cpu().pin_memory()
+    Ph = buf.pilots.cpu().pin_memory()
+    sh = buf.sigma2.cpu().pin_memory()
+    lh = torch.empty(buf.llr.shape, dtype=buf.llr.dtype).pin_memory()
+    fh = torch.empty(buf.flags.shape, dtype=torch.uint8).pin_memory()
+    e2e_ms = timed(lambda: phy.slot_run_bfp_host(cfg, ch, iq_width, scale, Ph, sh, lh, fh, c, Yd,
+                                                 buf.pilots, buf.sigma2, buf.x_hat, buf.sinr,
+                                                 buf.llr, buf.flags, buf.workspace, stream=st))
+    n_re = spec.n_cells * len(spec.data_sym) * spec.n_sc
     return {"iq_width": iq_width, "stream_mb": c.numel() / 1e6,
             "decompress_us": dec_ms * 1e3, "decompress_gbs": gbs,
             "decompress_hbm_frac": gbs / hbm_peak,
-            "slot_run_bfp_ms": bfp_ms, "slot_run_ms": run_ms}
+            "slot_run_bfp_ms": bfp_ms, "slot_run_ms": run_ms,
+            "e2e_bfp": {"value": n_re / (e2e_ms * 1e-3), "unit": "REs/s",
+                        "h2d_bytes_per_step": int(ch.numel() + Ph.numel() * 8 + sh.numel() * 4),
+                        "d2h_bytes_per_step": int(lh.numel() * lh.element_size() + fh.numel()),
+                        "api": "phy_slot_run_bfp_host (pinned host buffers)"}}
 
 
 def serving_run(spec, precision, dev, buf, slots=100, llr="f32", streams=2):

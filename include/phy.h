@@ -319,6 +319,20 @@ phy_status phy_slot_run_bfp(const phy_slot_cfg* cfg, const uint8_t* Yc, int32_t 
                             phy_c32* x_hat, float* sinr, float* llr, uint8_t* flags,
                             void* workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * phy_slot_run_bfp() with HOST inputs and outputs, as phy_slot_run_host() is to phy_slot_run():
+ * copies the stream Yc_host (phy_bfp_bytes() bytes), pilots_host and sigma2_host into the device
+ * buffers Yc (4-byte aligned), pilots and sigma2, runs phy_slot_run_bfp() (decoding into the
+ * device grid buffer Y), and copies llr and flags back into llr_host and flags_host, all on
+ * `stream`. Host buffers should be page-locked for the copies to be asynchronous.
+ */
+phy_status phy_slot_run_bfp_host(const phy_slot_cfg* cfg, const uint8_t* Yc_host,
+                                 int32_t iq_width, float scale, const phy_c32* pilots_host,
+                                 const float* sigma2_host, float* llr_host, uint8_t* flags_host,
+                                 uint8_t* Yc, phy_c32* Y, phy_c32* pilots, float* sigma2,
+                                 phy_c32* x_hat, float* sinr, float* llr, uint8_t* flags,
+                                 void* workspace, size_t workspace_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -398,6 +398,42 @@ phy_status phy_slot_run_bfp(const phy_slot_cfg* cfg, const uint8_t* Yc, int32_t 
   return cuda_status(e);
 }
 
+phy_status phy_slot_run_bfp_host(const phy_slot_cfg* cfg, const uint8_t* Yc_host,
+                                 int32_t iq_width, float scale, const phy_c32* pilots_host,
+                                 const float* sigma2_host, float* llr_host, uint8_t* flags_host,
+                                 uint8_t* Yc, phy_c32* Y, phy_c32* pilots, float* sigma2,
+                                 phy_c32* x_hat, float* sinr, float* llr, uint8_t* flags,
+                                 void* workspace, size_t workspace_bytes, void* stream) {
+  Geo g;
+  phy_status s = make_geo(cfg, &g);
+  if (s != PHY_OK) return s;
+  if (!Yc_host || !pilots_host || !sigma2_host || !llr_host || !flags_host || !pilots ||
+      !sigma2 || !llr || !flags)
+    return PHY_ERR_INVALID_ARG;
+  s = check_bfp(iq_width, scale, Yc);
+  if (s != PHY_OK) return s;
+  if (workspace_bytes < phy_workspace_size(cfg)) return PHY_ERR_NO_MEMORY;
+  s = check_shape(g);
+  if (s != PHY_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t c_bytes = phy_bfp_bytes(cfg, iq_width);
+  const size_t p_bytes = (size_t)g.n_cells * g.n_dmrs * g.n_layers * g.n_sc * sizeof(phy_c32);
+  const size_t n_re = (size_t)g.n_cells * g.n_dsym * g.n_sc;
+  const size_t l_bytes = n_re * g.n_layers * g.qm * (g.llr_f16 ? 2 : sizeof(float));
+  if (cudaMemcpyAsync(Yc, Yc_host, c_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(pilots, pilots_host, p_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(sigma2, sigma2_host, g.n_cells * sizeof(float), cudaMemcpyHostToDevice,
+                      st) != cudaSuccess)
+    return PHY_ERR_CUDA;
+  s = phy_slot_run_bfp(cfg, Yc, iq_width, scale, Y, pilots, sigma2, x_hat, sinr, llr, flags,
+                       workspace, workspace_bytes, stream);
+  if (s != PHY_OK) return s;
+  if (cudaMemcpyAsync(llr_host, llr, l_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(flags_host, flags, n_re, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return PHY_ERR_CUDA;
+  return PHY_OK;
+}
+
 phy_status phy_slot_run_host(const phy_slot_cfg* cfg, const phy_c32* Y_host,
                              const phy_c32* pilots_host, const float* sigma2_host,
                              float* llr_host, uint8_t* flags_host, phy_c32* Y, phy_c32* pilots,

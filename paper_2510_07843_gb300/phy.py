@@ -57,6 +57,8 @@ _SIGS = {
     "phy_chest_bfp": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_float, _P, _P, _P]),
     "phy_slot_run_bfp": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_float] + [_P] * 8
                          + [ctypes.c_size_t, _P]),
+    "phy_slot_run_bfp_host": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_float] + [_P] * 14
+                              + [ctypes.c_size_t, _P]),
 }
 
 STAGE_GRAM_MF, STAGE_SOLVE = 0, 1
@@ -279,6 +281,21 @@ def slot_run_bfp(cfg: SlotConfig, Yc, iq_width: int, scale: float, Y, pilots, si
            load().phy_slot_run_bfp(ctypes.byref(c), _ptr(Yc), iq_width, scale, _ptr(Y),
                                    _ptr(pilots), _ptr(sigma2), _ptr(x_hat), _ptr(sinr), _ptr(llr),
                                    _ptr(flags), _ptr(workspace), ws_bytes, _stream(stream)))
+
+
+def slot_run_bfp_host(cfg: SlotConfig, Yc_h, iq_width: int, scale: float, pilots_h, sigma2_h,
+                      llr_h, flags_h, Yc, Y, pilots, sigma2, x_hat, sinr, llr, flags, workspace,
+                      stream=None):
+    """phy_slot_run_bfp_host: the compressed stream and pilots from (pinned) host memory in, LLRs
+    and flags back to host memory, everything on the stream."""
+    c = cfg.c()
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check("phy_slot_run_bfp_host",
+           load().phy_slot_run_bfp_host(ctypes.byref(c), _ptr(Yc_h), iq_width, scale,
+                                        _ptr(pilots_h), _ptr(sigma2_h), _ptr(llr_h),
+                                        _ptr(flags_h), _ptr(Yc), _ptr(Y), _ptr(pilots),
+                                        _ptr(sigma2), _ptr(x_hat), _ptr(sinr), _ptr(llr),
+                                        _ptr(flags), _ptr(workspace), ws_bytes, _stream(stream)))
 
 
 def slot_run_noalloc(cfg: SlotConfig, Y, pilots, sigma2, x_hat, sinr, llr, flags, stream=None):

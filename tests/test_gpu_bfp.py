@@ -161,3 +161,32 @@ def test_full_size_massive_stream(dev):
     torch.cuda.synchronize()
     for key in ("x_hat", "sinr", "llr", "flags"):
         assert torch.equal(getattr(ref, key), getattr(got, key)), key
+
+
+def test_host_buffer_stream_path(dev):
+    """phy_slot_run_bfp_host: pinned host stream in, host LLRs and flags out, equal to the device
+    path's outputs."""
+    import torch
+    from paper_2510_07843_gb300 import phy
+    spec, w, scale, seed, prec = STREAM_CASES["massive_6prb_64x16_w9_fp16"]
+    sl = S.make_slot(spec, seed, keep_h=False)
+    cfg = phy.SlotConfig.from_spec(spec, precision=prec)
+    c_np = S.bfp_compress(sl.Y, w, scale)
+    ref = phy.SlotBuffers(cfg, with_inputs=False)
+    P, s2 = T(sl.pilots, dev), T(sl.sigma2, dev)
+    c = T(c_np, dev)
+    Yd = torch.empty(sl.Y.shape, dtype=torch.complex64, device=dev)
+    phy.slot_run_bfp(cfg, c, w, scale, Yd, P, s2, ref.x_hat, ref.sinr, ref.llr, ref.flags,
+                     ref.workspace)
+    b = phy.SlotBuffers(cfg, device=dev)
+    ch = torch.from_numpy(c_np).pin_memory()
+    Ph = torch.from_numpy(sl.pilots).pin_memory()
+    sh = torch.from_numpy(sl.sigma2).pin_memory()
+    lh = torch.empty(b.llr.shape, dtype=b.llr.dtype).pin_memory()
+    fh = torch.empty(b.flags.shape, dtype=torch.uint8).pin_memory()
+    cd = torch.empty_like(c)
+    Y2 = torch.empty_like(Yd)
+    phy.slot_run_bfp_host(cfg, ch, w, scale, Ph, sh, lh, fh, cd, Y2, b.pilots, b.sigma2,
+                          b.x_hat, b.sinr, b.llr, b.flags, b.workspace)
+    torch.cuda.synchronize()
+    assert torch.equal(lh, ref.llr.cpu()) and torch.equal(fh, ref.flags.cpu())
