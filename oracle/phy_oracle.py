@@ -23,6 +23,9 @@ Steps and where they come from:
   of the LS anchors against their prediction from neighbouring anchors in frequency or from the
   other DMRS symbol, normalised by the exact noise gain of each residual (see the section at the
   end of this file).
+* Learned channel denoiser (no learned part in the paper): a residual 3x3 CNN on 12 x 14 tiles of
+  the interpolated LS estimate, its forward pass, loss, backward pass and Adam written out with
+  numpy (see the last section).
 * Block-floating-point fronthaul decompression (the grid's arrival format in a split-7 software DU;
   no format in the paper): bit unpacking of per-PRB blocks with a shared exponent, by Python
   integers (see the last section).
@@ -505,3 +508,111 @@ def bfp_decompress(Yc: np.ndarray, shape: Tuple[int, int, int, int], iq_width: i
         c, t, r, p = idx
         out[c, t, r, 12 * p:12 * p + 12] = np.array(vals[0::2]) + 1j * np.array(vals[1::2])
     return out
+
+
+# ----------------------------------------------------------------------------------------------
+# Learned channel denoiser (not in the paper, which has no learned part): a residual CNN on
+# 12-subcarrier x 14-symbol tiles of the interpolated LS estimate, one tile per (PRB, Rx, layer)
+# ----------------------------------------------------------------------------------------------
+#
+# Tiles are [2][14][12] (real, imaginary; symbol rows; subcarrier columns). Layers: 3x3
+# cross-correlations with zero padding, channels 2 -> 32 -> 32 -> 32 -> 2, ReLU after the first
+# three, and the input added to the output (the network predicts the correction). Parameters are
+# one flat vector in the order W1 [32][2][3][3], b1 [32], W2 [32][32][3][3], b2, W3, b3,
+# W4 [2][32][3][3], b4. Loss: the mean over tiles and tile positions of |out - H|^2 (real and
+# imaginary squared errors summed). Optimiser: Adam with bias correction.
+
+CNN_CHANNELS = (2, 32, 32, 32, 2)
+TILE_ROWS, TILE_COLS = 14, 12
+
+
+def cnn_param_shapes():
+    shapes = []
+    for cin, cout in zip(CNN_CHANNELS[:-1], CNN_CHANNELS[1:]):
+        shapes += [(cout, cin, 3, 3), (cout,)]
+    return shapes
+
+
+def cnn_unflatten(params: np.ndarray):
+    out, o = [], 0
+    for shp in cnn_param_shapes():
+        n = int(np.prod(shp))
+        out.append(np.asarray(params[o:o + n], dtype=np.float64).reshape(shp))
+        o += n
+    return out
+
+
+def conv3x3(a: np.ndarray, W: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """z[n][co][i][j] = b[co] + sum_{ci, di, dj} W[co][ci][di+1][dj+1] a[n][ci][i+di][j+dj]."""
+    n, cin, R, C = a.shape
+    ap = np.zeros((n, cin, R + 2, C + 2))
+    ap[:, :, 1:-1, 1:-1] = a
+    z = np.zeros((n, W.shape[0], R, C)) + b[None, :, None, None]
+    for di in range(3):
+        for dj in range(3):
+            z += np.einsum("oc,ncij->noij", W[:, :, di, dj], ap[:, :, di:di + R, dj:dj + C])
+    return z
+
+
+def cnn_forward(params: np.ndarray, x: np.ndarray):
+    """Output tiles and the post-ReLU activations [a0 = x, a1, a2, a3]."""
+    p = cnn_unflatten(params)
+    acts = [np.asarray(x, dtype=np.float64)]
+    a = acts[0]
+    for layer in range(4):
+        z = conv3x3(a, p[2 * layer], p[2 * layer + 1])
+        if layer < 3:
+            a = np.maximum(z, 0.0)
+            acts.append(a)
+        else:
+            return acts[0] + z, acts
+    raise AssertionError
+
+
+def cnn_loss(out: np.ndarray, label: np.ndarray) -> float:
+    n = out.shape[0]
+    return float(np.sum((out - label) ** 2) / (n * TILE_ROWS * TILE_COLS))
+
+
+def cnn_backward(params: np.ndarray, acts, out: np.ndarray, label: np.ndarray):
+    """(gradient of the loss w.r.t. the flat parameters, gradient w.r.t. the input tiles)."""
+    p = cnn_unflatten(params)
+    n = out.shape[0]
+    dz = 2.0 * (out - label) / (n * TILE_ROWS * TILE_COLS)  # d loss / d out = d loss / d z4
+    dx = dz.copy()  # through the residual connection
+    grads = [None] * 8
+    for layer in (3, 2, 1, 0):
+        a = acts[layer]
+        W = p[2 * layer]
+        _, cin, R, C = a.shape
+        ap = np.zeros((n, cin, R + 2, C + 2))
+        ap[:, :, 1:-1, 1:-1] = a
+        gW = np.zeros_like(W)
+        for di in range(3):
+            for dj in range(3):
+                gW[:, :, di, dj] = np.einsum("noij,ncij->oc", dz, ap[:, :, di:di + R, dj:dj + C])
+        grads[2 * layer] = gW
+        grads[2 * layer + 1] = dz.sum(axis=(0, 2, 3))
+        # d a[ci][i][j] = sum_{co, di, dj} W[co][ci][di][dj] dz[co][i-di+1][j-dj+1]
+        dzp = np.zeros((n, W.shape[0], R + 2, C + 2))
+        dzp[:, :, 1:-1, 1:-1] = dz
+        da = np.zeros_like(a)
+        for di in range(3):
+            for dj in range(3):
+                da += np.einsum("oc,noij->ncij", W[:, :, di, dj],
+                                dzp[:, :, 2 - di:2 - di + R, 2 - dj:2 - dj + C])
+        if layer > 0:
+            dz = da * (a > 0.0)  # through the ReLU that made a
+        else:
+            dx = dx + da
+    return np.concatenate([g.ravel() for g in grads]), dx
+
+
+def adam_step(params, grad, m, v, t: int, lr: float, b1: float = 0.9, b2: float = 0.999,
+              eps: float = 1e-8):
+    """One Adam update (step count t >= 1): returns new (params, m, v)."""
+    m = b1 * m + (1.0 - b1) * grad
+    v = b2 * v + (1.0 - b2) * grad * grad
+    mh = m / (1.0 - b1 ** t)
+    vh = v / (1.0 - b2 ** t)
+    return params - lr * mh / (np.sqrt(vh) + eps), m, v

@@ -594,3 +594,68 @@ def test_bfp_round_trip_within_the_quantisation_step(w):
         assert np.all(err <= 0.5 * step + 0.5 * scale + 1e-12)
     else:  # one bit: -1 or 0 times the step
         assert np.all(np.isin(np.round(got.real / step), [-1.0, 0.0]))
+
+
+# ------------------------------------------------------------------ CNN denoiser
+
+def test_conv3x3_matches_scipy_correlate():
+    """Each (out, in) channel pair is scipy's 2-D cross-correlation with zero fill."""
+    from scipy.signal import correlate2d
+    rng = np.random.default_rng(1)
+    a = rng.standard_normal((2, 3, 14, 12))
+    W = rng.standard_normal((4, 3, 3, 3))
+    b = rng.standard_normal(4)
+    z = O.conv3x3(a, W, b)
+    for n in range(2):
+        for co in range(4):
+            want = b[co] + sum(correlate2d(a[n, ci], W[co, ci], mode="same", boundary="fill")
+                               for ci in range(3))
+            np.testing.assert_allclose(z[n, co], want, rtol=1e-12, atol=1e-12)
+
+
+def test_cnn_is_the_identity_with_a_zero_last_layer():
+    rng = np.random.default_rng(2)
+    p = rng.standard_normal(19682) * 0.1
+    p[-(2 * 32 * 9 + 2):] = 0.0  # W4, b4
+    x = rng.standard_normal((3, 2, 14, 12))
+    out, _ = O.cnn_forward(p, x)
+    np.testing.assert_array_equal(out, x)
+
+
+def test_cnn_backward_matches_finite_differences():
+    """Central differences of the FP64 loss, on every parameter tensor and the input. The step
+    is small (1e-7) because the ReLUs put kinks within 1e-5 of many parameters; at 1e-7 the
+    differences match to 1e-5 (a wrong term or index errs by the size of the gradient)."""
+    rng = np.random.default_rng(3)
+    p = rng.standard_normal(19682) * 0.2
+    x = rng.standard_normal((2, 2, 14, 12))
+    lab = rng.standard_normal((2, 2, 14, 12))
+    out, acts = O.cnn_forward(p, x)
+    g, dx = O.cnn_backward(p, acts, out, lab)
+    h = 1e-7
+    offs = np.cumsum([0] + [int(np.prod(s)) for s in O.cnn_param_shapes()])
+    idx = []
+    for a, b in zip(offs[:-1], offs[1:]):  # a few entries of each tensor
+        idx += list(rng.choice(np.arange(a, b), size=min(6, b - a), replace=False))
+    for i in idx:
+        e = np.zeros_like(p)
+        e[i] = h
+        fd = (O.cnn_loss(O.cnn_forward(p + e, x)[0], lab)
+              - O.cnn_loss(O.cnn_forward(p - e, x)[0], lab)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-5 * max(abs(fd), 0.1), (i, fd, g[i])
+    for _ in range(8):
+        ii = tuple(rng.integers(0, s) for s in x.shape)
+        e = np.zeros_like(x)
+        e[ii] = h
+        fd = (O.cnn_loss(O.cnn_forward(p, x + e)[0], lab)
+              - O.cnn_loss(O.cnn_forward(p, x - e)[0], lab)) / (2 * h)
+        assert abs(fd - dx[ii]) <= 1e-5 * max(abs(fd), 0.1), (ii, fd, dx[ii])
+
+
+def test_adam_first_step_moves_by_the_learning_rate():
+    """After one step from zero moments the bias-corrected update is lr * g / (|g| + eps)."""
+    g = np.array([0.5, -2.0, 1e-3, 0.0])
+    p, m, v = O.adam_step(np.ones(4), g, np.zeros(4), np.zeros(4), 1, lr=0.01)
+    np.testing.assert_allclose(p, 1.0 - 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+    np.testing.assert_allclose(m, 0.1 * g)
+    np.testing.assert_allclose(v, 0.001 * g * g)
