@@ -286,6 +286,8 @@ def main():
                     help="skip the noise-variance estimate timing")
     ap.add_argument("--no-bfp", action="store_true",
                     help="skip the block-floating-point fronthaul timing")
+    ap.add_argument("--no-cnn", action="store_true",
+                    help="skip training and evaluating the learned channel denoiser")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -417,6 +419,54 @@ def bfp_run(cfg, spec, slot, buf, st, hbm_peak: float, iq_width: int = 9, reps: 
                         "h2d_bytes_per_step": int(ch.numel() + Ph.numel() * 8 + sh.numel() * 4),
                         "d2h_bytes_per_step": int(lh.numel() * lh.element_size() + fh.numel()),
                         "api": "phy_slot_run_bfp_host (pinned host buffers)"}}
+
+
+CNN_MACS_FWD = 168 * (32 * 18 + 2 * 32 * 288 + 2 * 288)  # per tile: the four 3x3 layers
+CNN_MACS_TRAIN = 2 * CNN_MACS_FWD + 168 * (2 * 288 + 2 * 32 * 288)  # + dW all, dX layers 2-4
+
+
+def cnn_run(dev, st, fp32_peak_tf: float) -> dict:
+    """The learned denoiser: trained on the GPU by the library's kernels on generated slots
+    (24 slots of 12 PRB, 32 Rx x 8 layers, 0-30 dB, 0-500 Hz Doppler; 8 epochs of Adam), then
+    evaluated on one 273-PRB 32 Rx x 8 layer 64-QAM slot at 5 dB and 300 Hz against LS +
+    interpolation (channel MSE, uncoded BER of LMMSE detection). Times by CUDA events."""
+    import torch
+    from paper_2510_07843_gb300 import denoise as D
+    from paper_2510_07843_gb300 import phy
+    x, y = D.training_set(n_slots=24, n_prb=12, seed=11, dev=dev)
+    tr = D.Trainer(D.init_params(0), batch=256, dev=dev, lr=2e-3)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for ep in range(8):
+        tr.epoch(x, y, seed=ep)
+    b.record(st)
+    torch.cuda.synchronize()
+    train_s = a.elapsed_time(b) * 1e-3
+    tiles = tr.step * tr.batch
+    ev = D.slot_tiles(D.train_spec(n_prb=273, snr_db=5.0, doppler_hz=300.0), 4000, dev)
+    res = D.evaluate(tr.p, ev, dev)
+    n_tiles = phy.cnn_n_tiles(ev.cfg)
+    H = torch.empty((1, len(ev.spec.data_sym), ev.spec.n_sc, 32, 8), dtype=torch.complex64,
+                    device=dev)
+    ws = torch.empty(phy.cnn_denoise_workspace_size(ev.cfg), dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        phy.cnn_denoise(ev.cfg, tr.p, ev.anchors, H, ws, stream=st)
+    a.record(st)
+    for _ in range(10):
+        phy.cnn_denoise(ev.cfg, tr.p, ev.anchors, H, ws, stream=st)
+    b.record(st)
+    torch.cuda.synchronize()
+    inf_s = a.elapsed_time(b) * 1e-3 / 10
+    train_tf = tiles * CNN_MACS_TRAIN * 2 / train_s / 1e12
+    inf_tf = n_tiles * CNN_MACS_FWD * 2 / inf_s / 1e12
+    return {"train": {"tiles": int(tiles), "steps": tr.step, "batch": tr.batch,
+                      "seconds": train_s, "tiles_per_s": tiles / train_s,
+                      "tflops": train_tf, "fp32_peak_frac": train_tf / fp32_peak_tf},
+            "denoise_slot": {"tiles": n_tiles, "ms": inf_s * 1e3, "tflops": inf_tf,
+                             "fp32_peak_frac": inf_tf / fp32_peak_tf,
+                             "what": "interpolation, tiles, 4 conv layers, untile (273 PRB, "
+                                     "32 Rx x 8 layers)"},
+            "eval": {"snr_db": 5.0, "doppler_hz": 300.0, **res}}
 
 
 def serving_run(spec, precision, dev, buf, slots=100, llr="f32", streams=2):
@@ -626,6 +676,9 @@ def run_ours(args, spec, rank, world, local):
     bfp = None
     if not args.no_bfp:
         bfp = bfp_run(cfg, spec, slot, buf, st, hbm_peak)
+    learned = None
+    if not args.no_cnn:
+        learned = cnn_run(dev, st, peak_tf)
     # per-kernel rooflines. Solve: FP32 ALU work per RE. Gram/matched filter: its products on
     # the FP32 pipe in the FP32 variant; with tensor cores it streams the grid (HBM bound).
     solve_roof = {"bound": "alu", "kernel": f"re_solve_fp32_kernel<16,{spec.qm}>",
@@ -676,6 +729,7 @@ def run_ours(args, spec, rank, world, local):
         "serving": serving,
         "noise_estimate": noise,
         "bfp_fronthaul": bfp,
+        "learned_denoiser": learned,
         "gpu_launches": (1 + 2 * detect_chunks(spec)) * args.steps,
         "clocks": clk,
     }

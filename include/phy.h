@@ -333,6 +333,53 @@ phy_status phy_slot_run_bfp_host(const phy_slot_cfg* cfg, const uint8_t* Yc_host
                                  phy_c32* x_hat, float* sinr, float* llr, uint8_t* flags,
                                  void* workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * Learned channel denoiser (the paper has no learned part; this is a refinement between channel
+ * estimation and detection). A residual CNN maps a 12-subcarrier x 14-symbol tile of the
+ * interpolated LS estimate of one (PRB, Rx antenna, layer) channel entry to a refined tile:
+ * 3x3 cross-correlations with zero padding, channels 2 -> 32 -> 32 -> 32 -> 2 (real, imaginary),
+ * ReLU after the first three, the input added to the output. Everything runs in FP32.
+ *  - Parameters: one flat float vector of phy_cnn_param_count() = 19682 values, in the order
+ *    W1 [32][2][3][3], b1 [32], W2 [32][32][3][3], b2 [32], W3 [32][32][3][3], b3 [32],
+ *    W4 [2][32][3][3], b4 [2].
+ *  - Tiles: float [n][2][14][12] (channel, symbol, subcarrier within the PRB).
+ *  - phy_cnn_forward: out = network(in) for n tiles; workspace of phy_cnn_workspace_size(n).
+ *  - phy_cnn_train_step: forward pass, loss = mean over tiles and positions of |out - label|^2
+ *    (written to *loss, device, if loss is not NULL), its gradient w.r.t. the parameters into
+ *    grad (phy_cnn_param_count() floats) and, if grad_in is not NULL, w.r.t. the input tiles;
+ *    then, if step >= 1, one Adam update of params (beta1 0.9, beta2 0.999, eps 1e-8, bias
+ *    correction for update number `step`) with moments adam_m, adam_v (zero before the first).
+ *    Gradients are summed in a fixed order: repeated calls give identical results.
+ *  - phy_cnn_n_tiles: tiles of a slot batch (n_cells n_prb n_rx n_layers; -1 unless n_sym == 14).
+ *  - phy_interp_channel: the interpolated LS channel at every symbol (DMRS symbols included),
+ *    H [cell][sym][sc][rx][layer], from anchors as written by phy_chest.
+ *  - phy_cnn_tiles: such an H (estimated or true) cut into tiles, tile index
+ *    ((cell n_prb + prb) n_rx + rx) n_layers + layer. phy_cnn_untile: the data symbols of tiles
+ *    back into H_data [cell][dsym][sc][rx][layer], the layout phy_mmse_detect() takes.
+ *  - phy_cnn_denoise: phy_interp_channel, phy_cnn_tiles, phy_cnn_forward and phy_cnn_untile in
+ *    one call, with a workspace of phy_cnn_denoise_workspace_size(cfg).
+ */
+int32_t phy_cnn_param_count(void);
+size_t phy_cnn_workspace_size(int32_t n_tiles);
+phy_status phy_cnn_forward(int32_t n_tiles, const float* params, const float* tiles_in,
+                           float* tiles_out, void* workspace, size_t workspace_bytes,
+                           void* stream);
+phy_status phy_cnn_train_step(int32_t n_tiles, float* params, float* adam_m, float* adam_v,
+                              int32_t step, float lr, const float* tiles_in,
+                              const float* tiles_label, float* grad, float* grad_in,
+                              float* loss, void* workspace, size_t workspace_bytes,
+                              void* stream);
+int32_t phy_cnn_n_tiles(const phy_slot_cfg* cfg);
+phy_status phy_interp_channel(const phy_slot_cfg* cfg, const phy_c32* anchors, phy_c32* H,
+                              void* stream);
+phy_status phy_cnn_tiles(const phy_slot_cfg* cfg, const phy_c32* H, float* tiles, void* stream);
+phy_status phy_cnn_untile(const phy_slot_cfg* cfg, const float* tiles, phy_c32* H_data,
+                          void* stream);
+size_t phy_cnn_denoise_workspace_size(const phy_slot_cfg* cfg);
+phy_status phy_cnn_denoise(const phy_slot_cfg* cfg, const float* params, const phy_c32* anchors,
+                           phy_c32* H_data, void* workspace, size_t workspace_bytes,
+                           void* stream);
+
 #ifdef __cplusplus
 }
 #endif

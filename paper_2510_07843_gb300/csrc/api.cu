@@ -434,6 +434,113 @@ phy_status phy_slot_run_bfp_host(const phy_slot_cfg* cfg, const uint8_t* Yc_host
   return PHY_OK;
 }
 
+// ---------------------------------------------------------------- learned channel denoiser
+int32_t phy_cnn_param_count(void) { return phy::cnn_param_count(); }
+
+size_t phy_cnn_workspace_size(int32_t n_tiles) {
+  if (n_tiles < 1) return 0;
+  return phy::cnn_scratch_floats(n_tiles) * sizeof(float);
+}
+
+phy_status phy_cnn_forward(int32_t n_tiles, const float* params, const float* tiles_in,
+                           float* tiles_out, void* workspace, size_t workspace_bytes,
+                           void* stream) {
+  if (n_tiles < 1 || !params || !tiles_in || !tiles_out || !workspace) return PHY_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace) % kAlign) return PHY_ERR_INVALID_ARG;
+  if (workspace_bytes < phy_cnn_workspace_size(n_tiles)) return PHY_ERR_NO_MEMORY;
+  return cuda_status(phy::cnn_forward(n_tiles, params, tiles_in, tiles_out, (float*)workspace,
+                                      (cudaStream_t)stream));
+}
+
+phy_status phy_cnn_train_step(int32_t n_tiles, float* params, float* adam_m, float* adam_v,
+                              int32_t step, float lr, const float* tiles_in,
+                              const float* tiles_label, float* grad, float* grad_in,
+                              float* loss, void* workspace, size_t workspace_bytes,
+                              void* stream) {
+  if (n_tiles < 1 || !params || !tiles_in || !tiles_label || !grad || !workspace)
+    return PHY_ERR_INVALID_ARG;
+  if (step > 0 && (!adam_m || !adam_v || !(lr >= 0.f))) return PHY_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace) % kAlign) return PHY_ERR_INVALID_ARG;
+  if (workspace_bytes < phy_cnn_workspace_size(n_tiles)) return PHY_ERR_NO_MEMORY;
+  return cuda_status(phy::cnn_train_step(n_tiles, params, adam_m, adam_v, step, lr, tiles_in,
+                                         tiles_label, grad, grad_in, loss, (float*)workspace,
+                                         (cudaStream_t)stream));
+}
+
+namespace {
+phy_status check_tiles(const phy_slot_cfg* cfg, Geo* g) {
+  phy_status s = make_geo(cfg, g);
+  if (s != PHY_OK) return s;
+  if (g->n_sym != 14) return PHY_ERR_UNSUPPORTED;  // tiles span the 14 symbols of a slot
+  return PHY_OK;
+}
+}  // namespace
+
+int32_t phy_cnn_n_tiles(const phy_slot_cfg* cfg) {
+  Geo g;
+  if (check_tiles(cfg, &g) != PHY_OK) return -1;
+  return g.n_cells * (g.n_sc / 12) * g.n_rx * g.n_layers;
+}
+
+phy_status phy_interp_channel(const phy_slot_cfg* cfg, const phy_c32* anchors, phy_c32* H,
+                              void* stream) {
+  Geo g;
+  phy_status s = make_geo(cfg, &g);
+  if (s != PHY_OK) return s;
+  if (!anchors || !H) return PHY_ERR_INVALID_ARG;
+  return cuda_status(phy::launch_interp_all(g, anchors, H, (cudaStream_t)stream));
+}
+
+phy_status phy_cnn_tiles(const phy_slot_cfg* cfg, const phy_c32* H, float* tiles, void* stream) {
+  Geo g;
+  phy_status s = check_tiles(cfg, &g);
+  if (s != PHY_OK) return s;
+  if (!H || !tiles) return PHY_ERR_INVALID_ARG;
+  return cuda_status(phy::launch_tiles_from_h(g, H, tiles, (cudaStream_t)stream));
+}
+
+phy_status phy_cnn_untile(const phy_slot_cfg* cfg, const float* tiles, phy_c32* H_data,
+                          void* stream) {
+  Geo g;
+  phy_status s = check_tiles(cfg, &g);
+  if (s != PHY_OK) return s;
+  if (!tiles || !H_data) return PHY_ERR_INVALID_ARG;
+  return cuda_status(phy::launch_tiles_to_h(g, tiles, H_data, (cudaStream_t)stream));
+}
+
+size_t phy_cnn_denoise_workspace_size(const phy_slot_cfg* cfg) {
+  Geo g;
+  if (check_tiles(cfg, &g) != PHY_OK) return 0;
+  const size_t n = (size_t)g.n_cells * (g.n_sc / 12) * g.n_rx * g.n_layers;
+  const size_t h = (size_t)g.n_cells * g.n_sym * g.n_sc * g.n_rx * g.n_layers * sizeof(phy_c32);
+  return align_up(h) + 2 * align_up(n * 2 * 168 * sizeof(float)) +
+         phy::cnn_scratch_floats((int)n) * sizeof(float);
+}
+
+phy_status phy_cnn_denoise(const phy_slot_cfg* cfg, const float* params, const phy_c32* anchors,
+                           phy_c32* H_data, void* workspace, size_t workspace_bytes,
+                           void* stream) {
+  Geo g;
+  phy_status s = check_tiles(cfg, &g);
+  if (s != PHY_OK) return s;
+  if (!params || !anchors || !H_data || !workspace) return PHY_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace) % kAlign) return PHY_ERR_INVALID_ARG;
+  if (workspace_bytes < phy_cnn_denoise_workspace_size(cfg)) return PHY_ERR_NO_MEMORY;
+  const int n = g.n_cells * (g.n_sc / 12) * g.n_rx * g.n_layers;
+  const size_t h = (size_t)g.n_cells * g.n_sym * g.n_sc * g.n_rx * g.n_layers * sizeof(phy_c32);
+  char* ws = static_cast<char*>(workspace);
+  phy_c32* H = (phy_c32*)ws;
+  float* t_in = (float*)(ws + align_up(h));
+  float* t_out = (float*)(ws + align_up(h) + align_up((size_t)n * 2 * 168 * sizeof(float)));
+  float* scratch = (float*)(ws + align_up(h) + 2 * align_up((size_t)n * 2 * 168 * sizeof(float)));
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = phy::launch_interp_all(g, anchors, H, st);
+  if (e == cudaSuccess) e = phy::launch_tiles_from_h(g, H, t_in, st);
+  if (e == cudaSuccess) e = phy::cnn_forward(n, params, t_in, t_out, scratch, st);
+  if (e == cudaSuccess) e = phy::launch_tiles_to_h(g, t_out, H_data, st);
+  return cuda_status(e);
+}
+
 phy_status phy_slot_run_host(const phy_slot_cfg* cfg, const phy_c32* Y_host,
                              const phy_c32* pilots_host, const float* sigma2_host,
                              float* llr_host, uint8_t* flags_host, phy_c32* Y, phy_c32* pilots,

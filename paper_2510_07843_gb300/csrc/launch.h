@@ -68,6 +68,20 @@ cudaError_t launch_bfp_decompress(const Geo& g, const uint8_t* yc, int w, float 
 cudaError_t launch_chest_bfp(const Geo& g, const uint8_t* yc, int w, float scale,
                              const phy_c32* pilots, phy_c32* anchors, cudaStream_t st);
 
+// Learned channel denoiser (cnn.cu): flat FP32 parameters, tiles [n][C][14][12].
+int cnn_param_count();
+size_t cnn_scratch_floats(int n_tiles);
+cudaError_t cnn_forward(int n, const float* params, const float* x, float* out, float* ws,
+                        cudaStream_t st);
+cudaError_t cnn_train_step(int n, float* params, float* m, float* v, int step, float lr,
+                           const float* x, const float* label, float* grad_out, float* dx_out,
+                           float* loss_out, float* ws, cudaStream_t st);
+// Interpolated channel at every symbol H[cell][t][k][r][l]; tiles per (cell, PRB, Rx, layer)
+// from such an H, and the data symbols of tiles back into Hd[cell][dsym][k][r][l].
+cudaError_t launch_interp_all(const Geo& g, const phy_c32* anchors, phy_c32* H, cudaStream_t st);
+cudaError_t launch_tiles_from_h(const Geo& g, const phy_c32* H, float* tiles, cudaStream_t st);
+cudaError_t launch_tiles_to_h(const Geo& g, const float* tiles, phy_c32* Hd, cudaStream_t st);
+
 cudaError_t launch_detect_h(const Geo& g, const phy_c32* H, const phy_c32* Y, const float* sigma2,
                             phy_c32* x_hat, float* sinr, uint8_t* flags, cudaStream_t st);
 

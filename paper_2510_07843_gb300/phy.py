@@ -57,8 +57,20 @@ _SIGS = {
     "phy_chest_bfp": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_float, _P, _P, _P]),
     "phy_slot_run_bfp": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_float] + [_P] * 8
                          + [ctypes.c_size_t, _P]),
-    "phy_slot_run_bfp_host": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_float] + [_P] * 14
+    "phy_slot_run_bfp_host": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_float] + [_P] * 13
                               + [ctypes.c_size_t, _P]),
+    "phy_cnn_param_count": (ctypes.c_int32, []),
+    "phy_cnn_workspace_size": (ctypes.c_size_t, [ctypes.c_int32]),
+    "phy_cnn_forward": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "phy_cnn_train_step": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, ctypes.c_int32,
+                                          ctypes.c_float, _P, _P, _P, _P, _P, _P,
+                                          ctypes.c_size_t, _P]),
+    "phy_cnn_n_tiles": (ctypes.c_int32, [_P]),
+    "phy_interp_channel": (ctypes.c_int, [_P, _P, _P, _P]),
+    "phy_cnn_tiles": (ctypes.c_int, [_P, _P, _P, _P]),
+    "phy_cnn_untile": (ctypes.c_int, [_P, _P, _P, _P]),
+    "phy_cnn_denoise_workspace_size": (ctypes.c_size_t, [_P]),
+    "phy_cnn_denoise": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
 }
 
 STAGE_GRAM_MF, STAGE_SOLVE = 0, 1
@@ -128,7 +140,11 @@ class SlotConfig:
 
 
 def _ptr(t) -> Optional[int]:
-    return None if t is None else t.data_ptr()
+    if t is None:
+        return None
+    if not t.is_contiguous():  # the library indexes dense row-major arrays
+        raise ValueError("libphy arguments must be contiguous tensors")
+    return t.data_ptr()
 
 
 def _stream(stream) -> Optional[int]:
@@ -296,6 +312,71 @@ def slot_run_bfp_host(cfg: SlotConfig, Yc_h, iq_width: int, scale: float, pilots
                                         _ptr(flags_h), _ptr(Yc), _ptr(Y), _ptr(pilots),
                                         _ptr(sigma2), _ptr(x_hat), _ptr(sinr), _ptr(llr),
                                         _ptr(flags), _ptr(workspace), ws_bytes, _stream(stream)))
+
+
+def cnn_param_count() -> int:
+    return load().phy_cnn_param_count()
+
+
+def cnn_workspace_size(n_tiles: int) -> int:
+    return load().phy_cnn_workspace_size(n_tiles)
+
+
+def cnn_forward(n_tiles: int, params, tiles_in, tiles_out, workspace, stream=None):
+    """phy_cnn_forward: the denoiser on n tiles [n][2][14][12]."""
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check("phy_cnn_forward",
+           load().phy_cnn_forward(n_tiles, _ptr(params), _ptr(tiles_in), _ptr(tiles_out),
+                                  _ptr(workspace), ws_bytes, _stream(stream)))
+
+
+def cnn_train_step(n_tiles: int, params, adam_m, adam_v, step: int, lr: float, tiles_in,
+                   tiles_label, grad, grad_in=None, loss=None, workspace=None, stream=None):
+    """phy_cnn_train_step: loss, gradients and (step >= 1) one Adam update, on the device."""
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check("phy_cnn_train_step",
+           load().phy_cnn_train_step(n_tiles, _ptr(params), _ptr(adam_m), _ptr(adam_v), step, lr,
+                                     _ptr(tiles_in), _ptr(tiles_label), _ptr(grad),
+                                     _ptr(grad_in), _ptr(loss), _ptr(workspace), ws_bytes,
+                                     _stream(stream)))
+
+
+def cnn_n_tiles(cfg: SlotConfig) -> int:
+    c = cfg.c()
+    return load().phy_cnn_n_tiles(ctypes.byref(c))
+
+
+def interp_channel(cfg: SlotConfig, anchors, H, stream=None):
+    """phy_interp_channel: interpolated LS channel at every symbol, [cell][sym][sc][rx][layer]."""
+    c = cfg.c()
+    _check("phy_interp_channel", load().phy_interp_channel(ctypes.byref(c), _ptr(anchors),
+                                                           _ptr(H), _stream(stream)))
+
+
+def cnn_tiles(cfg: SlotConfig, H, tiles, stream=None):
+    c = cfg.c()
+    _check("phy_cnn_tiles", load().phy_cnn_tiles(ctypes.byref(c), _ptr(H), _ptr(tiles),
+                                                 _stream(stream)))
+
+
+def cnn_untile(cfg: SlotConfig, tiles, H_data, stream=None):
+    c = cfg.c()
+    _check("phy_cnn_untile", load().phy_cnn_untile(ctypes.byref(c), _ptr(tiles), _ptr(H_data),
+                                                   _stream(stream)))
+
+
+def cnn_denoise_workspace_size(cfg: SlotConfig) -> int:
+    c = cfg.c()
+    return load().phy_cnn_denoise_workspace_size(ctypes.byref(c))
+
+
+def cnn_denoise(cfg: SlotConfig, params, anchors, H_data, workspace, stream=None):
+    """phy_cnn_denoise: refined channel at the data symbols, [cell][dsym][sc][rx][layer]."""
+    c = cfg.c()
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check("phy_cnn_denoise",
+           load().phy_cnn_denoise(ctypes.byref(c), _ptr(params), _ptr(anchors), _ptr(H_data),
+                                  _ptr(workspace), ws_bytes, _stream(stream)))
 
 
 def slot_run_noalloc(cfg: SlotConfig, Y, pilots, sigma2, x_hat, sinr, llr, flags, stream=None):

@@ -156,3 +156,24 @@ def test_bfp_entry_points_validate_before_any_cuda_call(lib):
                                 None, fake, fake, 16, None) == 3
     assert lib.phy_slot_run_bfp(ctypes.byref(c), fake, 9, 1.0, None, fake, fake, None, None,
                                 None, fake, fake, ws, None) == 1
+
+
+def test_cnn_entry_points_validate_before_any_cuda_call(lib):
+    fake = ctypes.c_void_p(256)  # never dereferenced: the calls fail validation first
+    assert lib.phy_cnn_param_count() == 19682
+    assert lib.phy_cnn_workspace_size(0) == 0
+    ws = lib.phy_cnn_workspace_size(64)
+    assert ws >= 64 * 7 * 32 * 168 * 4
+    assert lib.phy_cnn_forward(0, fake, fake, fake, fake, ws, None) == 1
+    assert lib.phy_cnn_forward(64, fake, fake, fake, fake, ws - 4, None) == 3
+    assert lib.phy_cnn_train_step(64, fake, None, None, 1, 1e-3, fake, fake, fake, None, None,
+                                  fake, ws, None) == 1  # an update needs the Adam moments
+    assert lib.phy_cnn_train_step(64, fake, fake, fake, 1, float("nan"), fake, fake, fake,
+                                  None, None, fake, ws, None) == 1
+    c = _cfg(n_cells=1, n_rx=32, n_layers=8, qm=6).c()
+    assert lib.phy_cnn_n_tiles(ctypes.byref(c)) == 273 * 32 * 8
+    assert lib.phy_cnn_denoise_workspace_size(ctypes.byref(c)) > 0
+    short = _cfg(n_cells=1, n_sym=12, n_rx=32, n_layers=8, qm=6).c()  # tiles need 14 symbols
+    assert lib.phy_cnn_n_tiles(ctypes.byref(short)) == -1
+    assert lib.phy_cnn_tiles(ctypes.byref(short), fake, fake, None) == 2
+    assert lib.phy_cnn_denoise(ctypes.byref(c), fake, fake, fake, fake, 16, None) == 3

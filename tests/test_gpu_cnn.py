@@ -1,0 +1,175 @@
+"""Learned channel denoiser: the CUDA forward, backward and Adam kernels against the FP64 oracle,
+and a trained network against the plain LS + interpolation estimate.
+
+Tolerances (FP32 kernels, FP64 oracle on the same FP32 inputs and parameters):
+  * forward output and activations: relative Frobenius error 1e-5 per batch (each output is a
+    sum of at most 288 products, three layers deep);
+  * parameter gradients: relative Frobenius error 1e-4 per tensor (sums over every position of
+    every tile in the batch, in a different order from the oracle's);
+  * Adam: 1e-6 relative on the updated parameters (elementwise, from the same gradient).
+"""
+import numpy as np
+import pytest
+
+from oracle import phy_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_07843_gb300 import build, phy
+    build.build()
+    phy.load()
+    return torch.device("cuda:0")
+
+
+def T(a, dev):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def random_net(seed, n):
+    rng = np.random.default_rng(seed)
+    p = (rng.standard_normal(19682) * 0.15).astype(np.float32)
+    x = rng.standard_normal((n, 2, 14, 12)).astype(np.float32)
+    y = rng.standard_normal((n, 2, 14, 12)).astype(np.float32)
+    return p, x, y
+
+
+@pytest.mark.parametrize("n", [1, 7, 300])
+def test_forward_matches_oracle(dev, n):
+    import torch
+    from paper_2510_07843_gb300 import phy
+    p, x, _ = random_net(n, n)
+    out = torch.empty((n, 2, 14, 12), dtype=torch.float32, device=dev)
+    ws = torch.empty(phy.cnn_workspace_size(n), dtype=torch.uint8, device=dev)
+    phy.cnn_forward(n, T(p, dev), T(x, dev), out, ws)
+    torch.cuda.synchronize()
+    want, acts = O.cnn_forward(p.astype(np.float64), x.astype(np.float64))
+    e = rel(out.cpu().numpy(), want)
+    print("forward rel", e)
+    assert e <= 1e-5
+    # the activations the backward pass reuses sit at the start of the workspace
+    a1 = ws[: n * 32 * 168 * 4].view(torch.float32).reshape(n, 32, 14, 12).cpu().numpy()
+    assert rel(a1, acts[1]) <= 1e-5
+
+
+@pytest.mark.parametrize("n", [5, 64])
+def test_gradients_match_oracle(dev, n):
+    import torch
+    from paper_2510_07843_gb300 import phy
+    p, x, y = random_net(100 + n, n)
+    g = torch.zeros(19682, dtype=torch.float32, device=dev)
+    gx = torch.zeros((n, 2, 14, 12), dtype=torch.float32, device=dev)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    ws = torch.empty(phy.cnn_workspace_size(n), dtype=torch.uint8, device=dev)
+    pd = T(p, dev)
+    phy.cnn_train_step(n, pd, None, None, 0, 0.0, T(x, dev), T(y, dev), g, gx, loss, ws)
+    torch.cuda.synchronize()
+    out, acts = O.cnn_forward(p.astype(np.float64), x.astype(np.float64))
+    want_g, want_gx = O.cnn_backward(p.astype(np.float64), acts, out, y.astype(np.float64))
+    assert float(loss.item()) == pytest.approx(O.cnn_loss(out, y), rel=1e-5)
+    gg = g.cpu().numpy()
+    offs = np.cumsum([0] + [int(np.prod(s)) for s in O.cnn_param_shapes()])
+    for a, b in zip(offs[:-1], offs[1:]):
+        e = rel(gg[a:b], want_g[a:b])
+        print("grad", a, b, e)
+        assert e <= 1e-4, (a, b, e)
+    assert rel(gx.cpu().numpy(), want_gx) <= 1e-4
+    assert torch.equal(pd, T(p, dev))  # step 0: no update
+
+
+def test_adam_update_and_repeatability(dev):
+    import torch
+    from paper_2510_07843_gb300 import phy
+    n = 32
+    p, x, y = random_net(7, n)
+    ws = torch.empty(phy.cnn_workspace_size(n), dtype=torch.uint8, device=dev)
+    runs = []
+    for _ in range(2):
+        pd = T(p, dev)
+        m = torch.zeros_like(pd)
+        v = torch.zeros_like(pd)
+        g = torch.zeros_like(pd)
+        for step in (1, 2, 3):
+            phy.cnn_train_step(n, pd, m, v, step, 1e-3, T(x, dev), T(y, dev), g, None, None, ws)
+        torch.cuda.synchronize()
+        runs.append((pd.clone(), m.clone(), v.clone(), g.clone()))
+    for a, b in zip(runs[0], runs[1]):
+        assert torch.equal(a, b)  # fixed-order sums: bitwise repeatable
+    # one more step checked against the oracle's Adam from the same gradient and moments
+    pd, m, v, _ = (t.clone() for t in runs[0])
+    p3, m3, v3 = (t.cpu().numpy().astype(np.float64) for t in (pd, m, v))
+    g = torch.zeros_like(pd)
+    phy.cnn_train_step(n, pd, m, v, 4, 1e-3, T(x, dev), T(y, dev), g, None, None, ws)
+    torch.cuda.synchronize()
+    want_p, want_m, want_v = O.adam_step(p3, g.cpu().numpy().astype(np.float64), m3, v3, 4,
+                                         lr=1e-3)
+    assert rel(pd.cpu().numpy(), want_p) <= 1e-6
+    assert rel(m.cpu().numpy(), want_m) <= 1e-6
+    assert rel(v.cpu().numpy(), want_v) <= 1e-6
+
+
+def test_interpolated_channel_and_tiles(dev):
+    """phy_interp_channel equals the oracle's interpolation at every symbol; tiles and untile are
+    exact index moves."""
+    import torch
+    from paper_2510_07843_gb300 import denoise as D
+    from paper_2510_07843_gb300 import phy
+    spec = D.train_spec(n_prb=5, snr_db=10.0, doppler_hz=200.0, n_rx=4, n_layers=3)
+    st = D.slot_tiles(spec, 5, dev)
+    torch.cuda.synchronize()
+    A = st.anchors.cpu().numpy().astype(np.complex128)
+    H = torch.empty((1, 14, spec.n_sc, spec.n_rx, spec.n_layers), dtype=torch.complex64,
+                    device=dev)
+    phy.interp_channel(st.cfg, st.anchors, H)
+    Hg = H.cpu().numpy()
+    k = np.arange(spec.n_sc)
+    for t in range(14):
+        want = O.interp_channel(A[0], spec.dmrs_sym, spec.n_sc, spec.occ, t, k)
+        assert rel(Hg[0, t], want) <= 1e-6, t
+    x = st.x.cpu().numpy()
+    # tile ((prb) n_rx + r) n_layers + l holds H[t][12 prb + kk][r][l]
+    for prb, r, l in ((0, 0, 0), (4, 3, 2), (2, 1, 1)):
+        tile = (prb * spec.n_rx + r) * spec.n_layers + l
+        blk = Hg[0, :, 12 * prb:12 * prb + 12, r, l]
+        assert np.array_equal(x[tile, 0], blk.real) and np.array_equal(x[tile, 1], blk.imag)
+    Hd = torch.empty((1, len(spec.data_sym), spec.n_sc, spec.n_rx, spec.n_layers),
+                     dtype=torch.complex64, device=dev)
+    phy.cnn_untile(st.cfg, st.x, Hd)
+    assert np.array_equal(Hd.cpu().numpy()[0], Hg[0, list(spec.data_sym)])
+
+
+def test_trained_denoiser_beats_ls_interpolation(dev):
+    """Trained on the GPU by the library's own kernels (16 generated slots of 12 PRB, 32 Rx x 8
+    layers, SNR 0-30 dB, Doppler 0-500 Hz; 8 epochs of Adam), the network lowers the channel MSE
+    of LS + interpolation on held-out slots at 0 and 5 dB and does not lose BER. An untrained
+    (identity) network reproduces LS + interpolation exactly. Measured when the bounds were set:
+    MSE 0.162 -> 0.134 at 0 dB and 0.074 -> 0.066 at 5 dB; BER 16.8% -> 15.6% and 9.45% ->
+    8.97%."""
+    import torch
+    from paper_2510_07843_gb300 import denoise as D
+    x, y = D.training_set(n_slots=16, n_prb=12, seed=11, dev=dev)
+    tr = D.Trainer(D.init_params(0), batch=256, dev=dev, lr=2e-3)
+    ident = tr.p.clone()
+    held = {snr: D.slot_tiles(D.train_spec(n_prb=24, snr_db=snr, doppler_hz=300.0), 999, dev)
+            for snr in (0.0, 5.0)}
+    r0 = D.evaluate(ident, held[0.0], dev)
+    assert r0["mse_cnn"] == r0["mse_ls"] and r0["ber_cnn"] == r0["ber_ls"]
+    for ep in range(8):
+        tr.epoch(x, y, seed=ep)
+    for snr, bound in ((0.0, 0.9), (5.0, 0.95)):
+        r = D.evaluate(tr.p, held[snr], dev)
+        print(snr, r)
+        assert r["mse_cnn"] < bound * r["mse_ls"]
+        assert r["ber_cnn"] <= r["ber_ls"]
