@@ -122,9 +122,12 @@ __global__ void __launch_bounds__(kCnnThreads)
     conv3x3_wgrad_kernel(int n, const float* __restrict__ a, const float* __restrict__ dz,
                          float* __restrict__ part) {
   constexpr int CP = CIN / 2, OP = COUT / 2;  // channel pairs
+  // channel stride of the staged activations padded by one word: the lanes of a warp read 16
+  // different channel pairs at once, which an unpadded stride (448 words) puts in one bank
+  constexpr int kCS = kPR * kPC + 1;
   extern __shared__ __align__(16) float cnn_smem[];
-  float* s_a = cnn_smem;                 // [CIN][kPR][kPC] zero-padded
-  float* s_d = s_a + CIN * kPR * kPC;    // [COUT][kTP]
+  float* s_a = cnn_smem;                 // [CIN][kCS] zero-padded
+  float* s_d = s_a + CIN * kCS;          // [COUT][kTP]
   const int op = threadIdx.x / CP, cp = threadIdx.x % CP;
   const bool active = threadIdx.x < CP * OP;
   float acc[2][2][9], bacc[2] = {0.f, 0.f};
@@ -134,12 +137,12 @@ __global__ void __launch_bounds__(kCnnThreads)
     for (int y = 0; y < 2; ++y)
 #pragma unroll
       for (int k = 0; k < 9; ++k) acc[x][y][k] = 0.f;
-  for (int e = threadIdx.x; e < CIN * kPR * kPC; e += kCnnThreads) s_a[e] = 0.f;
+  for (int e = threadIdx.x; e < CIN * kCS; e += kCnnThreads) s_a[e] = 0.f;
   for (int t = blockIdx.x; t < n; t += gridDim.x) {
     __syncthreads();
     for (int e = threadIdx.x; e < CIN * kTP; e += kCnnThreads) {
       const int ci = e / kTP, p = e % kTP;
-      s_a[(ci * kPR + p / kTC + 1) * kPC + p % kTC + 1] = __ldg(a + (size_t)t * CIN * kTP + e);
+      s_a[ci * kCS + (p / kTC + 1) * kPC + p % kTC + 1] = __ldg(a + (size_t)t * CIN * kTP + e);
     }
     for (int e = threadIdx.x; e < COUT * kTP; e += kCnnThreads)
       s_d[e] = __ldg(dz + (size_t)t * COUT * kTP + e);
@@ -162,7 +165,7 @@ __global__ void __launch_bounds__(kCnnThreads)
       for (int di = 0; di < 3; ++di) {
 #pragma unroll
         for (int y = 0; y < 2; ++y) {
-          const float* r = s_a + ((2 * cp + y) * kPR + row + di) * kPC;
+          const float* r = s_a + (2 * cp + y) * kCS + (row + di) * kPC;
           float v[kPC];
 #pragma unroll
           for (int j = 0; j < kPC; ++j) v[j] = r[j];
@@ -273,7 +276,7 @@ cudaError_t conv(int n, const float* in, const float* W, const float* b, const f
 template <int CIN, int COUT>
 cudaError_t wgrad(int n, const float* a, const float* dz, float* part, float* grad_w,
                   float* grad_b, cudaStream_t st) {
-  constexpr size_t smem = ((size_t)CIN * kPR * kPC + (size_t)COUT * kTP) * sizeof(float);
+  constexpr size_t smem = ((size_t)CIN * (kPR * kPC + 1) + (size_t)COUT * kTP) * sizeof(float);
   static bool set = false;
   if (!set) {
     cudaError_t e = cudaFuncSetAttribute(conv3x3_wgrad_kernel<CIN, COUT>,
@@ -281,7 +284,8 @@ cudaError_t wgrad(int n, const float* a, const float* dz, float* part, float* gr
     if (e != cudaSuccess) return e;
     set = true;
   }
-  const int grid = cnn_grid(n);
+  // at least four tiles per CTA: fewer partials to write and sum
+  const int grid = std::max(1, std::min(cnn_grid(n), n / 4));
   conv3x3_wgrad_kernel<CIN, COUT><<<grid, kCnnThreads, smem, st>>>(n, a, dz, part);
   constexpr int len = COUT * CIN * 9 + COUT;  // W then b, as in the flat parameter vector
   reduce_partials<<<(len + 255) / 256, 256, 0, st>>>(part, grid, len, grad_w);
