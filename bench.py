@@ -202,7 +202,9 @@ KERNEL_SOURCE = {"seg_prep_tc": "detect_tc.cu", "re_solve": "detect_fp32.cu",
 
 
 def kernel_source_hash(kernel: str) -> str:
-    """Hash of the kernel's translation unit and every local header it includes (transitively).
+    """Hash of the device code a kernel is built from: its translation unit and every local
+    .cuh header it includes, transitively (the .h headers on the way, the C ABI and the host
+    launchers' declarations, are followed but not hashed: they hold no device code).
 
     Counters recorded for one hash stay valid while none of those files changes."""
     csrc = os.path.join(ROOT, "paper_2510_07843_gb300", "csrc")
@@ -218,6 +220,8 @@ def kernel_source_hash(kernel: str) -> str:
                 todo.append(os.path.join(os.path.dirname(path), m.group(1)))
     h = hashlib.sha256()
     for path in sorted(seen):
+        if path.endswith(".h"):
+            continue
         h.update(os.path.relpath(path, ROOT).encode())
         h.update(open(path, "rb").read())
     return h.hexdigest()[:16]
@@ -288,6 +292,8 @@ def main():
                     help="skip the block-floating-point fronthaul timing")
     ap.add_argument("--no-cnn", action="store_true",
                     help="skip training and evaluating the learned channel denoiser")
+    ap.add_argument("--aux-probe", type=int, default=0, metavar="REPS",
+                    help="only time the auxiliary paths (noise estimate, BFP decoder, denoiser)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -299,7 +305,66 @@ def main():
         spec = dataclasses.replace(spec, n_cells=args.cells)
     if args.impl == "reference":
         return run_reference(args, spec, rank, world)
+    if args.aux_probe:
+        return aux_probe(spec, args.aux_probe)
     return run_ours(args, spec, rank, world, local)
+
+
+def aux_probe(spec, reps: int) -> int:
+    """Times the auxiliary paths alone (CUDA events, `reps` calls each after two warm-up calls):
+    the noise estimate and the 9-bit BFP decoder on `spec` (use --cells to size it), the
+    denoiser forward pass on 16,384 tiles and its training step on 1,024 tiles. Small enough to
+    run under ncu; prints one JSON line."""
+    import torch
+    from paper_2510_07843_gb300 import denoise as D
+    from paper_2510_07843_gb300 import phy
+    dev = torch.device("cuda:0")
+    st = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(reps):
+            fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps * 1e3
+
+    sl = S.make_slot(spec, 3000, keep_h=False)
+    cfg = phy.SlotConfig.from_spec(spec, precision="fp16")
+    b = phy.SlotBuffers(cfg, device=dev)
+    b.Y.copy_(torch.from_numpy(sl.Y))
+    b.pilots.copy_(torch.from_numpy(sl.pilots))
+    b.sigma2.copy_(torch.from_numpy(sl.sigma2))
+    phy.chest(cfg, b.Y, b.pilots, b.anchors)
+    s2 = torch.empty(spec.n_cells, device=dev)
+    out = {"noise_est_us": timed(lambda: phy.noise_est(cfg, "min", b.anchors, b.pilots, s2,
+                                                        b.workspace))}
+    c = torch.from_numpy(S.bfp_compress(sl.Y, 9, 2.0 ** -10)).to(dev)
+    Yd = torch.empty_like(b.Y)
+    out["bfp_decompress_us"] = timed(lambda: phy.bfp_decompress(cfg, c, 9, 2.0 ** -10, Yd))
+    rng = np.random.default_rng(0)
+    n = 16384
+    p = torch.from_numpy(D.init_params(0) + (0.01 * rng.standard_normal(19682)).astype(
+        np.float32)).to(dev)
+    x = torch.from_numpy(rng.standard_normal((n, 2, 14, 12)).astype(np.float32)).to(dev)
+    y = torch.empty_like(x)
+    ws = torch.empty(phy.cnn_workspace_size(n), dtype=torch.uint8, device=dev)
+    out["cnn_forward_us_16384_tiles"] = timed(lambda: phy.cnn_forward(n, p, x, y, ws))
+    nb = 1024
+    m, v, g = torch.zeros_like(p), torch.zeros_like(p), torch.zeros_like(p)
+    wsb = torch.empty(phy.cnn_workspace_size(nb), dtype=torch.uint8, device=dev)
+    step = [0]
+
+    def train():
+        step[0] += 1
+        phy.cnn_train_step(nb, p, m, v, step[0], 1e-4, x[:nb], y[:nb], g, None, None, wsb)
+
+    out["cnn_train_step_us_1024_tiles"] = timed(train)
+    print(json.dumps(out))
+    return 0
 
 
 def run_reference(args, spec, rank, world):
