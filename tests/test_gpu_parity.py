@@ -391,3 +391,42 @@ def test_segment_kernel_timeout_voids_the_solve(dev):
     phy.detect_stage(cfg, phy.STAGE_SOLVE, *args)
     torch.cuda.synchronize()
     assert not torch.any(b.flags & 8)
+
+
+def _ber(dev, spec, seed, precision):
+    import torch
+    from paper_2510_07843_gb300 import phy
+    sl = S.make_slot(spec, seed, keep_h=False)
+    cfg = phy.SlotConfig.from_spec(spec, precision=precision)
+    b = phy.SlotBuffers(cfg, with_inputs=False)
+    phy.slot_run(cfg, T(sl.Y, dev), T(sl.pilots, dev), T(sl.sigma2, dev), b.x_hat, b.sinr,
+                 b.llr, b.flags, b.workspace)
+    torch.cuda.synchronize()
+    hard = (b.llr.cpu().numpy() < 0).astype(np.uint8)
+    return float(np.mean(hard != sl.bits.reshape(hard.shape)))
+
+
+BER_CASES = {  # one 273-PRB 64 x 16 256-QAM cell; noise-limited enough for 0.1 dB to show
+    "flat_18dB": dict(n_taps=1, delay_spread_s=0.0, snr_db=18.0),
+    "6tap_100ns_20dB": dict(n_taps=6, delay_spread_s=100e-9, snr_db=20.0),
+}
+
+
+@pytest.mark.parametrize("name", list(BER_CASES))
+def test_reduced_precision_ber_within_a_tenth_of_a_db(dev, name):
+    """Uncoded BER of the tensor-core variants against plain FP32 on the same slot: FP16 products
+    may not need more than 0.1 dB extra SNR to match FP32, i.e. BER_fp16(s) <= BER_fp32(s - 0.1
+    dB); BF16 (8-bit mantissa) gets 0.5 dB. The slot redrawn at the lower SNR shares bits, channel
+    and noise samples (the noise scales with the SNR), so the comparison is deterministic. (On the
+    benchmark's 300 ns channel the BER sits on the LS estimation floor, about 24% at 22 dB, where
+    a tenth of a dB does not show.)"""
+    kw = BER_CASES[name]
+    snr = kw["snr_db"]
+    mk = lambda s: S.spec_massive_mimo(n_cells=1, **{**kw, "snr_db": s})
+    b32, b16, bb = (_ber(dev, mk(snr), 3100, p) for p in ("fp32", "fp16", "bf16"))
+    b32_01, b32_05 = (_ber(dev, mk(snr - d), 3100, "fp32") for d in (0.1, 0.5))
+    print(name, {"fp32": b32, "fp16": b16, "bf16": bb, "fp32_-0.1dB": b32_01,
+                 "fp32_-0.5dB": b32_05})
+    assert b32 < b32_01 < b32_05  # the SNR shift is resolvable on this slot
+    assert b16 <= b32_01
+    assert bb <= b32_05
