@@ -275,6 +275,23 @@ phy_status phy_noise_est(const phy_slot_cfg* cfg, int32_t mode, const phy_c32* a
                          size_t workspace_bytes, void* stream);
 
 /*
+ * Noise-variance state kept on the device across slots: phy_noise_track() estimates as
+ * phy_noise_est() and blends the estimate into sigma2_state[cell] (device, n_cells floats, kept
+ * by the caller from slot to slot): state = alpha estimate + (1 - alpha) state, 0 < alpha <= 1.
+ * A state that is not a positive finite number (e.g. zeroed before the first slot) takes the
+ * estimate as it is; an estimate that is not finite leaves a valid state unchanged.
+ * phy_slot_run_track() runs LS estimation, phy_noise_track() and detection with the updated state,
+ * all on `stream`, like phy_slot_run_est() with a smoothed noise level.
+ */
+phy_status phy_noise_track(const phy_slot_cfg* cfg, int32_t mode, float alpha,
+                           const phy_c32* anchors, const phy_c32* pilots, float* sigma2_state,
+                           void* workspace, size_t workspace_bytes, void* stream);
+phy_status phy_slot_run_track(const phy_slot_cfg* cfg, int32_t mode, float alpha,
+                              const phy_c32* Y, const phy_c32* pilots, float* sigma2_state,
+                              phy_c32* x_hat, float* sinr, float* llr, uint8_t* flags,
+                              void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * phy_slot_run() with the noise variance estimated on the way: LS estimation, phy_noise_est()
  * with `mode` into sigma2_out (n_cells floats, device), then interpolation, detection, SINR and
  * LLRs with that estimate, all on `stream`. Same outputs, rules and workspace as phy_slot_run();

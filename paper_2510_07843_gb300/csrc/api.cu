@@ -294,10 +294,58 @@ phy_status phy_noise_est(const phy_slot_cfg* cfg, int32_t mode, const phy_c32* a
   if (!anchors || !pilots || !sigma2_out || !workspace) return PHY_ERR_INVALID_ARG;
   if (((uintptr_t)workspace) % kAlign) return PHY_ERR_INVALID_ARG;
   if (workspace_bytes < phy_workspace_size(cfg)) return PHY_ERR_NO_MEMORY;
-  return cuda_status(phy::launch_noise_est(g, mode, anchors, pilots, sigma2_out,
+  return cuda_status(phy::launch_noise_est(g, mode, 1.f, anchors, pilots, sigma2_out,
                                            static_cast<char*>(workspace) +
                                                align_up(anchor_bytes(g)),
                                            (cudaStream_t)stream));
+}
+
+phy_status phy_noise_track(const phy_slot_cfg* cfg, int32_t mode, float alpha,
+                           const phy_c32* anchors, const phy_c32* pilots, float* sigma2_state,
+                           void* workspace, size_t workspace_bytes, void* stream) {
+  Geo g;
+  phy_status s = make_geo(cfg, &g);
+  if (s != PHY_OK) return s;
+  s = check_noise_mode(g, mode);
+  if (s != PHY_OK) return s;
+  if (!(alpha > 0.f && alpha <= 1.f)) return PHY_ERR_INVALID_ARG;
+  if (!anchors || !pilots || !sigma2_state || !workspace) return PHY_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace) % kAlign) return PHY_ERR_INVALID_ARG;
+  if (workspace_bytes < phy_workspace_size(cfg)) return PHY_ERR_NO_MEMORY;
+  return cuda_status(phy::launch_noise_est(g, mode, alpha, anchors, pilots, sigma2_state,
+                                           static_cast<char*>(workspace) +
+                                               align_up(anchor_bytes(g)),
+                                           (cudaStream_t)stream));
+}
+
+phy_status phy_slot_run_track(const phy_slot_cfg* cfg, int32_t mode, float alpha,
+                              const phy_c32* Y, const phy_c32* pilots, float* sigma2_state,
+                              phy_c32* x_hat, float* sinr, float* llr, uint8_t* flags,
+                              void* workspace, size_t workspace_bytes, void* stream) {
+  Geo g;
+  phy_status s = make_geo(cfg, &g);
+  if (s != PHY_OK) return s;
+  s = check_noise_mode(g, mode);
+  if (s != PHY_OK) return s;
+  if (!(alpha > 0.f && alpha <= 1.f)) return PHY_ERR_INVALID_ARG;
+  if (!Y || !pilots || !sigma2_state || !flags || !workspace || ((uintptr_t)Y % 16))
+    return PHY_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace) % kAlign) return PHY_ERR_INVALID_ARG;
+  if (workspace_bytes < phy_workspace_size(cfg)) return PHY_ERR_NO_MEMORY;
+  s = check_shape(g);
+  if (s != PHY_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  phy_c32* anchors = (phy_c32*)workspace;
+  char* ws = static_cast<char*>(workspace);
+  cudaError_t e = phy::launch_chest(g, Y, pilots, anchors, st);
+  if (e == cudaSuccess)
+    e = phy::launch_noise_est(g, mode, alpha, anchors, pilots, sigma2_state,
+                              ws + align_up(anchor_bytes(g)), st);
+  if (e == cudaSuccess)
+    e = phy::launch_detect(g, anchors, Y, sigma2_state, x_hat, sinr, llr, flags,
+                           ws + head_bytes(g), workspace_bytes - head_bytes(g),
+                           phy::kStageGramMf | phy::kStageSolve, st);
+  return cuda_status(e);
 }
 
 phy_status phy_slot_run_est(const phy_slot_cfg* cfg, int32_t mode, const phy_c32* Y,
@@ -320,7 +368,7 @@ phy_status phy_slot_run_est(const phy_slot_cfg* cfg, int32_t mode, const phy_c32
   char* ws = static_cast<char*>(workspace);
   cudaError_t e = phy::launch_chest(g, Y, pilots, anchors, st);
   if (e == cudaSuccess)
-    e = phy::launch_noise_est(g, mode, anchors, pilots, sigma2_out,
+    e = phy::launch_noise_est(g, mode, 1.f, anchors, pilots, sigma2_out,
                               ws + align_up(anchor_bytes(g)), st);
   if (e == cudaSuccess)
     e = phy::launch_detect(g, anchors, Y, sigma2_out, x_hat, sinr, llr, flags,

@@ -54,9 +54,10 @@ cudaError_t launch_seg_prep_tc(const Geo& g, int NL, int c0, int nc, const phy_c
                                cudaStream_t st);
 
 // Noise-variance estimate per cell from the LS anchors and pilots (mode: phy_noise_mode) into
-// sigma2_out; scratch holds noise_scratch_bytes(g) of partial sums.
+// sigma2_out (alpha = 1), or blended into it as a tracked state (alpha < 1); scratch holds
+// noise_scratch_bytes(g) of partial sums.
 size_t noise_scratch_bytes(const Geo& g);
-cudaError_t launch_noise_est(const Geo& g, int mode, const phy_c32* anchors,
+cudaError_t launch_noise_est(const Geo& g, int mode, float alpha, const phy_c32* anchors,
                              const phy_c32* pilots, float* sigma2_out, void* scratch,
                              cudaStream_t st);
 

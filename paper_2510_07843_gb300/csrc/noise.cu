@@ -16,7 +16,8 @@
 // also sums the gains of the (group, layer) pairs whose first antenna entry it owns, one work
 // item per (pair, comb index of the pair's span) so that every thread shares that part; one
 // float4 of partial sums per CTA. noise_final_kernel: CTA per cell, sums the partials in a fixed
-// order (FP64) and divides; it is launched as a programmatic dependent of the first (it starts
+// order (FP64) and divides (with alpha < 1 it blends the estimate into the cell's tracked value,
+// alpha est + (1 - alpha) prior); it is launched as a programmatic dependent of the first (it starts
 // while the first drains and waits on griddepcontrol before reading). No atomics: the result
 // does not depend on scheduling.
 #include <math.h>
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(kNoiseThreads)
 }
 
 __global__ void __launch_bounds__(kNoiseThreads)
-    noise_final_kernel(Geo g, int mode, int n_part, const float4* __restrict__ part,
+    noise_final_kernel(Geo g, int mode, float alpha, int n_part, const float4* __restrict__ part,
                        float* __restrict__ sigma2_out) {
   const int cell = blockIdx.x;
   __shared__ double red[4][kNoiseThreads];
@@ -178,6 +179,12 @@ __global__ void __launch_bounds__(kNoiseThreads)
     double r = f;
     if (mode == PHY_NOISE_TIME) r = t;
     if (mode == PHY_NOISE_MIN) r = fmin(f, t);  // NaN only if both are
+    if (alpha < 1.f) {  // tracking: blend into the cell's state, which a bad value leaves alone
+      const float prior = sigma2_out[cell];
+      const bool have = isfinite(prior) && prior > 0.f;
+      if (!isfinite(r)) r = have ? (double)prior : r;
+      else if (have) r = (double)alpha * r + (1.0 - (double)alpha) * (double)prior;
+    }
     sigma2_out[cell] = (float)r;
   }
 }
@@ -193,7 +200,7 @@ size_t noise_scratch_bytes(const Geo& g) {
   return (size_t)g.n_cells * n_parts(g) * sizeof(float4);
 }
 
-cudaError_t launch_noise_est(const Geo& g, int mode, const phy_c32* anchors,
+cudaError_t launch_noise_est(const Geo& g, int mode, float alpha, const phy_c32* anchors,
                              const phy_c32* pilots, float* sigma2_out, void* scratch,
                              cudaStream_t st) {
   const int np = n_parts(g);
@@ -212,7 +219,7 @@ cudaError_t launch_noise_est(const Geo& g, int mode, const phy_c32* anchors,
   lc.attrs = at;
   lc.numAttrs = 1;
   const float4* cpart = part;
-  return cudaLaunchKernelEx(&lc, noise_final_kernel, g, mode, np, cpart, sigma2_out);
+  return cudaLaunchKernelEx(&lc, noise_final_kernel, g, mode, alpha, np, cpart, sigma2_out);
 }
 
 }  // namespace phy

@@ -51,6 +51,10 @@ _SIGS = {
     "phy_autotune_clear": (None, []),
     "phy_noise_est": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "phy_slot_run_est": (ctypes.c_int, [_P, ctypes.c_int32] + [_P] * 8 + [ctypes.c_size_t, _P]),
+    "phy_noise_track": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_float, _P, _P, _P, _P,
+                                       ctypes.c_size_t, _P]),
+    "phy_slot_run_track": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_float] + [_P] * 8
+                           + [ctypes.c_size_t, _P]),
     "phy_bfp_bytes": (ctypes.c_size_t, [_P, ctypes.c_int32]),
     "phy_bfp_decompress": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_float, ctypes.c_int32,
                                           _P, _P]),
@@ -377,6 +381,29 @@ def cnn_denoise(cfg: SlotConfig, params, anchors, H_data, workspace, stream=None
     _check("phy_cnn_denoise",
            load().phy_cnn_denoise(ctypes.byref(c), _ptr(params), _ptr(anchors), _ptr(H_data),
                                   _ptr(workspace), ws_bytes, _stream(stream)))
+
+
+def noise_track(cfg: SlotConfig, mode: str, alpha: float, anchors, pilots, sigma2_state,
+                workspace, stream=None):
+    """phy_noise_track: blend this slot's noise estimate into the per-cell device state."""
+    c = cfg.c()
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check("phy_noise_track",
+           load().phy_noise_track(ctypes.byref(c), NOISE_MODE[mode], alpha, _ptr(anchors),
+                                  _ptr(pilots), _ptr(sigma2_state), _ptr(workspace), ws_bytes,
+                                  _stream(stream)))
+
+
+def slot_run_track(cfg: SlotConfig, mode: str, alpha: float, Y, pilots, sigma2_state, x_hat,
+                   sinr, llr, flags, workspace, stream=None):
+    """phy_slot_run_track: the receiver with the tracked noise state updated and used."""
+    c = cfg.c()
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check("phy_slot_run_track",
+           load().phy_slot_run_track(ctypes.byref(c), NOISE_MODE[mode], alpha, _ptr(Y),
+                                     _ptr(pilots), _ptr(sigma2_state), _ptr(x_hat), _ptr(sinr),
+                                     _ptr(llr), _ptr(flags), _ptr(workspace), ws_bytes,
+                                     _stream(stream)))
 
 
 def slot_run_noalloc(cfg: SlotConfig, Y, pilots, sigma2, x_hat, sinr, llr, flags, stream=None):

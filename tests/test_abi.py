@@ -177,3 +177,15 @@ def test_cnn_entry_points_validate_before_any_cuda_call(lib):
     assert lib.phy_cnn_n_tiles(ctypes.byref(short)) == -1
     assert lib.phy_cnn_tiles(ctypes.byref(short), fake, fake, None) == 2
     assert lib.phy_cnn_denoise(ctypes.byref(c), fake, fake, fake, fake, 16, None) == 3
+
+
+def test_noise_tracking_validates_alpha(lib):
+    fake = ctypes.c_void_p(256)
+    c = _cfg().c()
+    ws = lib.phy_workspace_size(ctypes.byref(c))
+    for alpha in (0.0, -0.5, 1.5, float("nan")):
+        assert lib.phy_noise_track(ctypes.byref(c), 2, alpha, fake, fake, fake, fake, ws,
+                                   None) == 1
+        assert lib.phy_slot_run_track(ctypes.byref(c), 2, alpha, fake, fake, fake, None, None,
+                                      None, fake, fake, ws, None) == 1
+    assert lib.phy_noise_track(ctypes.byref(c), 2, 0.5, fake, fake, fake, fake, 16, None) == 3

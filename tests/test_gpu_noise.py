@@ -131,3 +131,46 @@ def test_noise_estimate_full_size_massive(dev):
     assert np.all(np.abs(got["time"] / spec.sigma2 - 1.0) < 0.02), got["time"]
     _, again = gpu_estimates(spec, sl, dev, ("min",))
     assert np.array_equal(again["min"], got["min"])
+
+
+def test_noise_state_tracked_across_slots(dev):
+    """phy_noise_track keeps a per-cell noise level on the device from slot to slot: the first
+    slot takes its estimate, later ones blend alpha estimate + (1 - alpha) state, a NaN estimate
+    leaves the state alone; phy_slot_run_track detects with the updated state."""
+    import torch
+    from paper_2510_07843_gb300 import phy
+    spec, _ = CASES["carrier_25prb_16x4_jakes"]
+    alpha = 0.3
+    state = torch.zeros(1, dtype=torch.float32, device=dev)
+    prev = None
+    for k in range(4):
+        sl = S.make_slot(spec, 500 + k, keep_h=False)
+        cfg = phy.SlotConfig.from_spec(spec)
+        _, est = gpu_estimates(spec, sl, dev, ("min",))
+        e = float(est["min"][0])
+        Y, P = T(sl.Y, dev), T(sl.pilots, dev)
+        a = phy.SlotBuffers(cfg, with_inputs=False)
+        phy.slot_run_track(cfg, "min", alpha, Y, P, state, a.x_hat, a.sinr, a.llr, a.flags,
+                           a.workspace)
+        b = phy.SlotBuffers(cfg, with_inputs=False)
+        phy.slot_run(cfg, Y, P, state.clone(), b.x_hat, b.sinr, b.llr, b.flags, b.workspace)
+        torch.cuda.synchronize()
+        s_now = float(state.item())
+        want = e if prev is None else alpha * e + (1 - alpha) * prev
+        assert s_now == pytest.approx(want, rel=1e-6), (k, s_now, want)
+        for key in ("x_hat", "sinr", "llr", "flags"):
+            assert torch.equal(getattr(a, key), getattr(b, key)), key
+        prev = s_now
+    # an undefined estimate (two LS groups: no frequency residual) keeps the state
+    spec2, seed2 = CASES["cover_16_3prb_two_groups"]
+    sl2 = S.make_slot(spec2, seed2, keep_h=False)
+    cfg2 = phy.SlotConfig.from_spec(spec2)
+    G = phy.n_groups(cfg2)
+    anchors = torch.empty((1, 2, G, spec2.n_layers, spec2.n_rx), dtype=torch.complex64,
+                          device=dev)
+    phy.chest(cfg2, T(sl2.Y, dev), T(sl2.pilots, dev), anchors)
+    ws = torch.empty(phy.workspace_size(cfg2), dtype=torch.uint8, device=dev)
+    st2 = torch.full((1,), 0.5, dtype=torch.float32, device=dev)
+    phy.noise_track(cfg2, "freq", alpha, anchors, T(sl2.pilots, dev), st2, ws)
+    torch.cuda.synchronize()
+    assert float(st2.item()) == 0.5
