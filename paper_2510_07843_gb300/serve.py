@@ -43,6 +43,10 @@ class Job:
     arrival: float = 0.0       # seconds on the server clock
     job_id: int = 0
     sigma2_dev: object = None  # optional device view [1] float32 of sigma2 (zero-copy batches)
+    # > 0: estimate the noise level from the DMRS and track it in sigma2_dev, a per-cell device
+    # state kept across slots (state = alpha estimate + (1 - alpha) state); the batch must read
+    # resident inputs in place (consecutive cells, see _direct)
+    noise_alpha: float = 0.0
     llr: object = None         # filled: device tensor [1][dsym][sc][layer][qm]
     flags: object = None       # filled: device tensor [1][dsym][sc]
     done: float = field(default=float("nan"))
@@ -133,7 +137,9 @@ class _Graph:
         import torch
         if _direct(jobs):  # inputs already side by side in device memory: read in place
             b, n = self.buf, len(jobs)
-            key = (jobs[0].Y.data_ptr(), jobs[0].pilots.data_ptr(), jobs[0].sigma2_dev.data_ptr())
+            alpha = jobs[0].noise_alpha
+            key = (jobs[0].Y.data_ptr(), jobs[0].pilots.data_ptr(), jobs[0].sigma2_dev.data_ptr(),
+                   alpha)
             g = self.direct.get(key)
             if g is None:  # one captured receiver per input location (a ring has few)
                 ins = (_span(jobs[0].Y, n), _span(jobs[0].pilots, n), _span(jobs[0].sigma2_dev, n))
@@ -142,7 +148,11 @@ class _Graph:
                     self.direct.clear()
                 g = torch.cuda.CUDAGraph()
                 with torch.cuda.graph(g, stream=self.stream):
-                    phy.slot_run(self.cfg, *ins, *outs, stream=self.stream)
+                    if alpha > 0.0:  # the noise state is updated in place, then detected with
+                        phy.slot_run_track(self.cfg, "min", alpha, *ins, *outs,
+                                           stream=self.stream)
+                    else:
+                        phy.slot_run(self.cfg, *ins, *outs, stream=self.stream)
                 self.direct[key] = g
             with torch.cuda.stream(self.stream):
                 g.replay()
@@ -151,6 +161,8 @@ class _Graph:
                         j.llr = b.llr[i:i + 1].clone()
                         j.flags = b.flags[i:i + 1].clone()
             return
+        if any(j.noise_alpha > 0.0 for j in jobs):
+            raise ValueError("noise tracking needs the batch's inputs resident side by side")
         with torch.cuda.stream(self.stream):
             # inputs into the batch buffers: one copy per run of jobs whose tensors are
             # consecutive cells of one source (the common case of a cell-major input ring)
@@ -259,7 +271,8 @@ class SlotServer:
         while i < len(pending) or any(queues.values()):
             now = self.clock() - t0
             while i < len(pending) and (not realtime or pending[i].arrival <= now):
-                queues.setdefault(config_key(pending[i].cfg), []).append(pending[i])
+                queues.setdefault((config_key(pending[i].cfg), pending[i].noise_alpha),
+                                  []).append(pending[i])
                 i += 1
             retire(False)
             ready = [(q[0].arrival, k) for k, q in queues.items() if q]

@@ -153,3 +153,40 @@ def test_zero_copy_batches_equal_alone():
                      b.workspace)
         torch.cuda.synchronize()
         assert torch.equal(b.llr, j.llr) and torch.equal(b.flags, j.flags), j.job_id
+
+
+@pytest.mark.gpu
+def test_noise_state_tracked_through_the_server():
+    """Four cells of a resident input ring, served twice with noise tracking: each cell's noise
+    level lives in its device slot between the rounds, and the served results and states equal
+    the same cells run by phy_slot_run_track one at a time on a copy of the state."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_07843_gb300 import build
+    build.build()
+    phy.load()
+    dev = torch.device("cuda:0")
+    spec = S.spec_carrier_273prb(n_prb=25, n_cells=4)
+    Y = torch.empty((4, 14, spec.n_rx, spec.n_sc), dtype=torch.complex64, device=dev)
+    P = torch.empty((4, 2, spec.n_layers, spec.n_sc), dtype=torch.complex64, device=dev)
+    state = torch.zeros(4, dtype=torch.float32, device=dev)  # unset: the first round sets it
+    ref_state = state.clone()
+    srv = serve.SlotServer(device=dev, max_cells=4)
+    for rnd in range(2):
+        sl = S.make_slot(spec, 900 + rnd, keep_h=False)  # new slot data in the same ring
+        Y.copy_(torch.from_numpy(sl.Y))
+        P.copy_(torch.from_numpy(sl.pilots))
+        jobs = [serve.Job(CARRIER, Y[c:c + 1], P[c:c + 1], 0.0, job_id=c,
+                          sigma2_dev=state[c:c + 1], noise_alpha=0.25) for c in range(4)]
+        done = srv.run(jobs, realtime=False)
+        assert len(done) == 4
+        for j in jobs:
+            c = j.job_id
+            b = phy.SlotBuffers(CARRIER, device=dev)
+            phy.slot_run_track(CARRIER, "min", 0.25, j.Y, j.pilots, ref_state[c:c + 1], b.x_hat,
+                               b.sinr, b.llr, b.flags, b.workspace)
+            torch.cuda.synchronize()
+            assert torch.equal(b.llr, j.llr) and torch.equal(b.flags, j.flags), (rnd, c)
+        assert torch.equal(state, ref_state)
+        assert torch.all(state > 0)
