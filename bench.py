@@ -19,6 +19,7 @@ import os
 import re
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -146,15 +147,22 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, log_dir: str = ""):
         self.idx = gpu_index
         self.proc = None
         self.path = None
+        self.log_dir = log_dir  # keep the raw samples there; "" = a temporary file
 
     def start(self):
         try:
-            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+            if self.log_dir:
+                os.makedirs(self.log_dir, exist_ok=True)
+                self.path = os.path.join(self.log_dir, f"clocks_bench_{os.getpid()}.csv")
+                self.temp = False
+            else:
+                fd, self.path = tempfile.mkstemp(prefix="clocks_bench_", suffix=".csv")
+                os.close(fd)
+                self.temp = True
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
@@ -186,6 +194,8 @@ class ClockSampler:
             for n, v in zip(names, p[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
+        if self.temp:
+            os.remove(self.path)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
@@ -290,6 +300,8 @@ def main():
                     help="skip the noise-variance estimate timing")
     ap.add_argument("--no-bfp", action="store_true",
                     help="skip the block-floating-point fronthaul timing")
+    ap.add_argument("--clock-log", default="", metavar="DIR",
+                    help="keep the raw nvidia-smi clock samples of the timed region in DIR")
     ap.add_argument("--no-cnn", action="store_true",
                     help="skip training and evaluating the learned channel denoiser")
     ap.add_argument("--aux-probe", type=int, default=0, metavar="REPS",
@@ -599,7 +611,7 @@ def run_ours(args, spec, rank, world, local):
                 e2.record(st)
             phy.detect_anchors(cfg, *args_, stream=st)
 
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, args.clock_log)
     clocks.start()
     time.sleep(0.3)  # let the sampler start before the GPU gets busy
     with torch.cuda.stream(st):
