@@ -164,10 +164,7 @@ cudaError_t launch_bfp_decompress(const Geo& g, const uint8_t* yc, int w, float 
                                   int data_only, phy_c32* Y, cudaStream_t st) {
   const long long n_blocks = (long long)g.n_cells * g.n_sym * g.n_rx * (g.n_sc / 12);
   const long long total = n_blocks * (1 + 3 * w);
-  int dev = 0, sms = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return e;
+  const int sms = device_sm_count();
   switch (w) {  // the usual fronthaul widths get compile-time bit offsets
     case 8: return launch_w<8>(g, yc, n_blocks, total, w, scale, data_only, Y, sms, st);
     case 9: return launch_w<9>(g, yc, n_blocks, total, w, scale, data_only, Y, sms, st);

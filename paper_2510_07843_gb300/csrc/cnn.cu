@@ -245,23 +245,16 @@ __global__ void adam_kernel(int len, float* __restrict__ p, const float* __restr
 
 constexpr int kMaxCnnGrid = 512;  // persistent CTAs at most (bounds the gradient partials)
 constexpr size_t kPartFloats = (size_t)kMaxCnnGrid * (9216 + 32);
-int g_cnn_sms = 0;
-
 int cnn_grid(int n) {
-  if (g_cnn_sms == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess)
-      cudaDeviceGetAttribute(&g_cnn_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_cnn_sms <= 0) g_cnn_sms = 1;
-  }
-  return std::max(1, std::min(std::min(n, 3 * g_cnn_sms), kMaxCnnGrid));
+  return std::max(1, std::min(std::min(n, 3 * device_sm_count()), kMaxCnnGrid));
 }
 
 template <int CIN, int COUT, int MODE, bool BWD>
 cudaError_t conv(int n, const float* in, const float* W, const float* b, const float* aux,
                  float* out, cudaStream_t st) {
   constexpr size_t smem = conv_smem<CIN, COUT>();
-  static bool set = false;
+  static bool set_on[kMaxDevices] = {};
+  bool& set = set_on[current_device()];
   if (!set) {
     cudaError_t e = cudaFuncSetAttribute(conv3x3_kernel<CIN, COUT, MODE, BWD>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -277,7 +270,8 @@ template <int CIN, int COUT>
 cudaError_t wgrad(int n, const float* a, const float* dz, float* part, float* grad_w,
                   float* grad_b, cudaStream_t st) {
   constexpr size_t smem = ((size_t)CIN * (kPR * kPC + 1) + (size_t)COUT * kTP) * sizeof(float);
-  static bool set = false;
+  static bool set_on[kMaxDevices] = {};
+  bool& set = set_on[current_device()];
   if (!set) {
     cudaError_t e = cudaFuncSetAttribute(conv3x3_wgrad_kernel<CIN, COUT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

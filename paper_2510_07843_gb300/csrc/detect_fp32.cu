@@ -642,7 +642,8 @@ cudaError_t launch_solve(const Geo& g, int c0, int nc, int max_segs, const float
                          const phy_c32* Y, phy_c32* x_hat, float* sinr, float* llr,
                          uint8_t* flags, const unsigned* err, cudaStream_t st) {
   const size_t smem = solve_smem_bytes(NL, QM, max_segs);
-  static size_t configured = 0;
+  static size_t configured_on[kMaxDevices] = {};
+  size_t& configured = configured_on[current_device()];
   if (smem > 48 * 1024 && smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(re_solve_fp32_kernel<NL, QM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -664,7 +665,8 @@ cudaError_t run_chunks(const Geo& g, int wmax, const Sizes& s, const phy_c32* an
                        float* llr, uint8_t* flags, void* scratch, int stages, cudaStream_t st) {
   const PrepLayout f = prep_layout(NL, g.n_dmrs, g.n_rx, wmax);
   const size_t smem = (size_t)f.total * sizeof(cf);
-  static size_t configured = 0;
+  static size_t configured_on[kMaxDevices] = {};
+  size_t& configured = configured_on[current_device()];
   if (smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(seg_prep_fp32_kernel<NL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

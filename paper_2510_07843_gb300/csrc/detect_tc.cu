@@ -487,25 +487,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 // ---------------------------------------------------------------- host side
-int g_num_sms = 0;
-
 template <int NL, int NC, uint32_t FMT>
 cudaError_t launch_one(const Geo& g, int c0, int nc, const phy_c32* anchors, const phy_c32* Y,
                        float4* ygg, cf* bvec, unsigned* err, cudaStream_t st) {
   constexpr size_t smem = Smem<NL, NC, FMT>::kTotal;
-  static bool configured = false;
+  static bool configured_on[kMaxDevices] = {};
+  bool& configured = configured_on[current_device()];
+  const int num_sms = device_sm_count();
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(seg_prep_tc_kernel<NL, NC, FMT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int dev = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev)) !=
-        cudaSuccess)
-      return e;
     if (std::getenv("PHY_DEBUG"))
       std::fprintf(stderr, "seg_prep_tc<%d,%d,%u>: smem %zu, SMs %d\n", NL, NC, FMT, smem,
-                   g_num_sms);
+                   num_sms);
     configured = true;
   }
   // Received grid: (2 n_sc floats, n_rx, n_cells n_sym), box = kBoxSc subcarriers x all antennas.
@@ -522,7 +517,7 @@ cudaError_t launch_one(const Geo& g, int c0, int nc, const phy_c32* anchors, con
   if (!make_map(&tmY, Y, ydim, ystr, ybox) || !make_map(&tmA, anchors, adim, astr, abox))
     return cudaErrorInvalidValue;
   const int n_work = g.n_seg * nc;
-  const int grid = std::min(n_work, g_num_sms);
+  const int grid = std::min(n_work, num_sms);
   seg_prep_tc_kernel<NL, NC, FMT><<<grid, kTcThreads, smem, st>>>(tmY, tmA, g, c0, nc, ygg, bvec,
                                                                   err);
   return cudaGetLastError();

@@ -8,6 +8,26 @@
 
 namespace phy {
 
+// Kernel attributes (cudaFuncSetAttribute) and SM counts belong to a device: host-side caches of
+// them are kept per device, indexed by the current device (ids below kMaxDevices).
+constexpr int kMaxDevices = 64;
+inline int current_device() {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) d = 0;
+  return d;
+}
+inline int device_sm_count() {
+  static int sms[kMaxDevices] = {};
+  const int d = current_device();
+  if (sms[d] <= 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || v <= 0)
+      v = 1;
+    sms[d] = v;
+  }
+  return sms[d];
+}
+
 // Widest frequency segment (subcarriers) for g, computed on the host.
 int host_max_segment_width(const Geo& g);
 // Dynamic shared memory of the FP32 segment kernel for g (bytes).
