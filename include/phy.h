@@ -158,7 +158,8 @@ phy_status phy_detect_anchors(const phy_slot_cfg* cfg, const phy_c32* anchors, c
  */
 typedef enum { PHY_STAGE_GRAM_MF = 0, PHY_STAGE_SOLVE = 1 } phy_stage;
 
-/* 1 if phy_detect_stage() can run cfg's batch as one chunk with a phy_workspace_size() workspace. */
+/* 1 if phy_detect_stage() can run cfg's batch as one chunk with a phy_workspace_size()
+   workspace. */
 int32_t phy_stage_supported(const phy_slot_cfg* cfg);
 
 phy_status phy_detect_stage(const phy_slot_cfg* cfg, int32_t stage, const phy_c32* anchors,

@@ -488,7 +488,8 @@ def bfp_block_bytes(iq_width: int) -> int:
 
 def bfp_decompress(Yc: np.ndarray, shape: Tuple[int, int, int, int], iq_width: int,
                    scale: float) -> np.ndarray:
-    """Grid [cell][sym][rx][sc] (complex128) from the byte stream Yc of blocks [cell][sym][rx][prb]."""
+    """Grid [cell][sym][rx][sc] (complex128) from the byte stream Yc of blocks
+    [cell][sym][rx][prb]."""
     n_cells, n_sym, n_rx, n_sc = shape
     n_prb = n_sc // 12
     w = iq_width

@@ -309,7 +309,8 @@ __global__ void interp_all_kernel(Geo g, const phy_c32* __restrict__ anchors,
     cf h = mk(0.f, 0.f);
     for (int d = 0; d < g.n_dmrs; ++d) {
       const phy_c32* A = anchors + ((size_t)(cell * g.n_dmrs + d) * g.G) * nl * nr;
-      const cf h0 = ld(A + ((size_t)j * nl + l) * nr + r), h1 = ld(A + ((size_t)j1 * nl + l) * nr + r);
+      const cf h0 = ld(A + ((size_t)j * nl + l) * nr + r);
+      const cf h1 = ld(A + ((size_t)j1 * nl + l) * nr + r);
       const cf hf = (1.f - b) * h0 + b * h1;
       h = h + (d == 0 ? (g.n_dmrs == 2 ? 1.f - a : 1.f) : a) * hf;
     }

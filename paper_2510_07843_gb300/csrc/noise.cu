@@ -17,9 +17,9 @@
 // item per (pair, comb index of the pair's span) so that every thread shares that part; one
 // float4 of partial sums per CTA. noise_final_kernel: CTA per cell, sums the partials in a fixed
 // order (FP64) and divides (with alpha < 1 it blends the estimate into the cell's tracked value,
-// alpha est + (1 - alpha) prior); it is launched as a programmatic dependent of the first (it starts
-// while the first drains and waits on griddepcontrol before reading). No atomics: the result
-// does not depend on scheduling.
+// alpha est + (1 - alpha) prior); it is launched as a programmatic dependent of the first (it
+// starts while the first drains and waits on griddepcontrol before reading). No atomics: the
+// result does not depend on scheduling.
 #include <math.h>
 
 #include "launch.h"

@@ -90,7 +90,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     if _lib is not None:
         return _lib
     if not os.path.exists(path):
-        raise RuntimeError(f"libphy.so not built at {path}; run paper_2510_07843_gb300.build.build()")
+        raise RuntimeError(f"libphy.so not built at {path}; "
+                           "run paper_2510_07843_gb300.build.build()")
     lib = ctypes.CDLL(path)
     for name, (res, args) in _SIGS.items():
         fn = getattr(lib, name)
@@ -294,7 +295,8 @@ def chest_bfp(cfg: SlotConfig, Yc, iq_width: int, scale: float, pilots, anchors,
 
 def slot_run_bfp(cfg: SlotConfig, Yc, iq_width: int, scale: float, Y, pilots, sigma2, x_hat,
                  sinr, llr, flags, workspace, stream=None):
-    """phy_slot_run_bfp: the receiver from the compressed stream (Y: grid buffer it decodes into)."""
+    """phy_slot_run_bfp: the receiver from the compressed stream (Y: the grid buffer it decodes
+    into)."""
     c = cfg.c()
     ws_bytes = workspace.numel() * workspace.element_size()
     _check("phy_slot_run_bfp",

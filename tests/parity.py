@@ -47,7 +47,8 @@ def compare_res(tag, gpu, ref, qm, s2eff_ref, x_t_ref, mask=None):
     m = {}
     m["x_rel"] = rel_fro(xg[mask], xr[mask])
     m["x_rel_re_p999"] = float(np.quantile(
-        np.linalg.norm(xg[mask] - xr[mask], axis=-1) / np.maximum(np.linalg.norm(xr[mask], axis=-1), 1e-30),
+        np.linalg.norm(xg[mask] - xr[mask], axis=-1)
+        / np.maximum(np.linalg.norm(xr[mask], axis=-1), 1e-30),
         0.999)) if mask.any() else 0.0
     sg, sr = gpu["sinr"][mask], ref["sinr"][mask]
     m["sinr_rel_max"] = float(np.max(np.abs(sg - sr) / sr)) if mask.any() else 0.0

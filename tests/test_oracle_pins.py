@@ -169,7 +169,8 @@ def test_pivot_ratio_closed_forms():
 
 
 def test_ml_bruteforce_vs_mmse_2x2_qpsk():
-    """Exact ML over 16 hypotheses: never more bit errors than MMSE on average, agrees at high SNR."""
+    """Exact ML over 16 hypotheses: never more bit errors than MMSE on average, agrees at high
+    SNR."""
     rng = np.random.default_rng(6)
     nb = 4000
     for snr_db, agree_min in ((5.0, 0.5), (25.0, 0.98)):
