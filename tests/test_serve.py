@@ -190,3 +190,23 @@ def test_noise_state_tracked_through_the_server():
             assert torch.equal(b.llr, j.llr) and torch.equal(b.flags, j.flags), (rnd, c)
         assert torch.equal(state, ref_state)
         assert torch.all(state > 0)
+
+
+def test_noise_tracking_jobs_batch_apart(monkeypatch):
+    """Jobs that track their noise level and jobs with a given one never share a batch (the
+    captured receivers differ), even with the same configuration."""
+    phy.load()
+    log = []
+    srv = serve.SlotServer(max_cells=4, memory_budget=1 << 40)
+    srv.streams = [None]
+    monkeypatch.setattr(srv, "_graph",
+                        lambda cfg, n, lane=0: _FakeGraph(log, serve.config_key(cfg)[0], n))
+    monkeypatch.setattr(srv, "_event", lambda: _FakeEvent())
+    monkeypatch.setattr(srv, "_sync", lambda: None)
+    jobs = [serve.Job(SMALL, None, None, 1.0, arrival=0.1 * i, job_id=i,
+                      noise_alpha=0.25 if i % 2 else 0.0) for i in range(6)]
+    done = srv.run(jobs, realtime=False)
+    assert sorted(j.job_id for j in done) == list(range(6))
+    for _, ids in log:
+        assert len({ids_i % 2 for ids_i in ids}) == 1, ids
+    assert sorted(len(b) for _, b in log) == [1, 1, 2, 2]
