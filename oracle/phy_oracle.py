@@ -555,13 +555,23 @@ def conv3x3(a: np.ndarray, W: np.ndarray, b: np.ndarray) -> np.ndarray:
     return z
 
 
-def cnn_forward(params: np.ndarray, x: np.ndarray):
-    """Output tiles and the post-ReLU activations [a0 = x, a1, a2, a3]."""
+def round_bf16(a: np.ndarray) -> np.ndarray:
+    """a rounded to FP32, then to bfloat16 (8-bit significand) to nearest, ties to even."""
+    bits = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    bits = (bits + 0x7FFF + ((bits >> 16) & 1)) >> 16 << 16
+    return bits.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def cnn_forward(params: np.ndarray, x: np.ndarray, operands: str = "fp32"):
+    """Output tiles and the post-ReLU activations [a0 = x, a1, a2, a3]. With operands="bf16" the
+    weights and every convolution's input are rounded to bfloat16 before the products (the
+    tensor-core form; biases, sums and the residual stay exact)."""
     p = cnn_unflatten(params)
     acts = [np.asarray(x, dtype=np.float64)]
     a = acts[0]
+    rnd = round_bf16 if operands == "bf16" else (lambda v: v)
     for layer in range(4):
-        z = conv3x3(a, p[2 * layer], p[2 * layer + 1])
+        z = conv3x3(rnd(a), rnd(p[2 * layer]), p[2 * layer + 1])
         if layer < 3:
             a = np.maximum(z, 0.0)
             acts.append(a)

@@ -660,3 +660,27 @@ def test_adam_first_step_moves_by_the_learning_rate():
     np.testing.assert_allclose(p, 1.0 - 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
     np.testing.assert_allclose(m, 0.1 * g)
     np.testing.assert_allclose(v, 0.001 * g * g)
+
+
+def test_bf16_rounding_matches_torch():
+    """The oracle's bfloat16 rounding equals torch's float -> bfloat16 conversion (to nearest,
+    ties to even), including exact ties and values that carry into the exponent."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    v = np.concatenate([rng.standard_normal(4000) * 10.0 ** rng.integers(-6, 6, 4000),
+                        np.array([1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -(1.0 + 2.0 ** -8),
+                                  2.0 - 2.0 ** -9, 0.0, -0.0, 65504.0])]).astype(np.float32)
+    want = torch.from_numpy(v).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+    np.testing.assert_array_equal(O.round_bf16(v), want)
+
+
+def test_cnn_bf16_operands_stay_within_the_rounding_bound():
+    """Rounding weights and activations to bfloat16 (relative step 2^-8) moves the output of the
+    residual network by far less than the rounding of its largest terms would allow."""
+    rng = np.random.default_rng(6)
+    p = rng.standard_normal(19682) * 0.1
+    x = rng.standard_normal((4, 2, 14, 12))
+    out32, _ = O.cnn_forward(p, x)
+    out16, _ = O.cnn_forward(p, x, operands="bf16")
+    err = np.linalg.norm(out16 - out32) / np.linalg.norm(out32 - x)
+    assert 1e-4 < err < 3e-2, err  # rounding visible, and of the size 2^-8 predicts
