@@ -137,6 +137,32 @@ def test_slot_parity_full_size_sampled(dev):
     assert_parity(m)
 
 
+@pytest.mark.parametrize("n_sym,dmrs", [(14, (2, 11)), (12, (1, 9))])
+def test_slot_parity_maximum_carrier_sampled(dev, n_sym, dmrs):
+    """The largest grid the ABI takes: 275 PRB (3300 subcarriers, the last LS group overlapping),
+    64 Rx x 16 layers, 256-QAM, one cell; also with a 12-symbol slot. Sampled REs including both
+    band edges against the oracle."""
+    spec = S.spec_massive_mimo(n_cells=1, n_prb=275, n_sym=n_sym, dmrs_sym=dmrs)
+    sl = S.make_slot(spec, 3300 + n_sym, keep_h=False)
+    got = gpu_slot(spec, sl, dev)
+    rng = np.random.default_rng(1)
+    K, J = spec.n_sc, len(spec.data_sym)
+    kk = np.concatenate([np.arange(0, 24), np.arange(K - 40, K), rng.integers(0, K, 60)])
+    jj = rng.integers(0, J, kk.size)
+    ref = O.run_slot(sl.Y, sl.pilots, sl.sigma2, spec.dmrs_sym, spec.n_layers, spec.qm,
+                     res={0: (jj, kk)})
+    assert rel_fro(got["anchors"], ref["anchors"]) < 2e-7
+    rs = ref["sinr_0"]
+    gf, rf = got["flags"][0, jj, kk], ref["flags_0"]
+    mask = (gf == 0) & (rf == 0)
+    gpu = dict(x_hat=got["x_hat"][0, jj, kk], sinr=got["sinr"][0, jj, kk],
+               llr=got["llr"][0, jj, kk])
+    want = dict(x_hat=ref["x_hat_0"], sinr=rs, llr=ref["llr_0"])
+    m = compare_res("max_carrier", gpu, want, spec.qm, 1.0 / rs,
+                    ref["x_hat_0"] / (rs / (1 + rs)), mask)
+    assert_parity(m)
+
+
 def test_mmse_detect_genie_and_zero_forcing(dev):
     import torch
     from paper_2510_07843_gb300 import phy
