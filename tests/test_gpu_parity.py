@@ -77,6 +77,8 @@ CASES = {
     "one_prb_4x2": (S.SlotSpec(n_prb=1, n_rx=4, n_layers=2, qm=4, dmrs_sym=(2,)), 16),
     "forced_cover_4_single_layer": (S.SlotSpec(n_prb=4, n_rx=4, n_layers=1, qm=4,
                                                dmrs_sym=(2, 11), occ_len=4), 17),
+    "minimal_slot_1prb_1x1_two_symbols": (S.SlotSpec(n_prb=1, n_rx=1, n_layers=1, qm=2,
+                                                     dmrs_sym=(0,), n_sym=2, snr_db=15.0), 21),
 }
 
 
