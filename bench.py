@@ -1,10 +1,14 @@
 #!/usr/bin/env python3
 """Throughput of the uplink receiver hot path on GB300: MMSE-detected REs/s.
 
-One step = one pass of the whole path over one batch: DMRS LS estimation (phy_chest) then the
-fused interpolation + LMMSE + SINR + LLR kernel (phy_detect_anchors) for 8 cells x 273 PRB x
-14 symbols, 64 Rx x 16 layers, 256-QAM (the massive-MIMO workload). Inputs are seeded synthetic
-slots resident in HBM. Prints one JSON line (rank 0).
+One step = one pass of the whole path over one batch: DMRS LS estimation (phy_chest), then
+interpolation, Gram and matched-filter products (tensor cores in the headline form), Cholesky,
+solves, SINR and max-log LLRs for 8 cells x 273 PRB x 14 symbols, 64 Rx x 16 layers, 256-QAM,
+Kronecker rho = 0.7 (the massive-MIMO workload). The headline runs that workload as it is
+specified: FP16 tensor-core products with FP32 accumulation, FP32 Cholesky/solve/LLR, FP64
+re-computation of ill-conditioned REs. Plain FP32 and BF16 products are timed beside it on the same
+inputs (`variants`, `vs_plain_fp32`). Inputs are seeded synthetic slots resident in HBM. Prints
+one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -35,9 +39,6 @@ sys.path.insert(0, ROOT)
 from paper_2510_07843_gb300 import synth as S  # noqa: E402
 
 METRIC = "MMSE-detected REs/s (64Rx×16L, 273 PRB) & p99 slot latency vs plain FP32"
-N_SM = 152
-FP32_LANES_PER_SM = 128
-SM_MAX_MHZ_NOMINAL = 2070.0
 
 
 def workload(name: str) -> S.SlotSpec:
@@ -255,27 +256,134 @@ def committed_traffic(kernel: str, workload_name: str):
 # oracle baseline
 # ---------------------------------------------------------------------------------------------
 
+ORACLE_CHUNK = 256  # subcarriers of one data symbol per oracle detection call
+
+
+def oracle_chunk_res(spec: S.SlotSpec, anchors, slot, chunk: int) -> int:
+    """Detect one chunk (data symbol chunk % J, subcarriers 256 (chunk // J) ...) of cell 0."""
+    from oracle import phy_oracle as O
+    data = spec.data_sym
+    j = chunk % len(data)
+    k0 = (chunk // len(data)) * ORACLE_CHUNK % spec.n_sc
+    ks = np.arange(k0, min(k0 + ORACLE_CHUNK, spec.n_sc))
+    O.detect_res(anchors[0], slot.Y[0], spec.dmrs_sym, spec.n_layers, spec.occ, spec.qm,
+                 float(slot.sigma2[0]), data[j], ks)
+    return int(ks.size)
+
+
 def oracle_sample_rate(spec: S.SlotSpec, slot, budget_s: float) -> dict:
-    """Time the FP64 oracle on a bounded sample of the workload: LS estimation of cell 0, then
-    detection of whole data symbols of cell 0, 256 subcarriers at a time, until budget_s."""
+    """Time the FP64 oracle on one core on a bounded sample of the workload: LS estimation of
+    cell 0, then detection of whole data symbols of cell 0, 256 subcarriers at a time, until
+    budget_s."""
     from oracle import phy_oracle as O
     t0 = time.perf_counter()
     anchors = O.ls_anchors(slot.Y[:1], slot.pilots[:1], spec.dmrs_sym, spec.n_layers, spec.occ)
-    n = 0
-    chunks = 0
-    data = spec.data_sym
+    n = chunks = 0
     while True:
-        j = chunks % len(data)
-        k0 = (chunks // len(data)) * 256 % spec.n_sc
-        ks = np.arange(k0, min(k0 + 256, spec.n_sc))
-        O.detect_res(anchors[0], slot.Y[0], spec.dmrs_sym, spec.n_layers, spec.occ, spec.qm,
-                     float(slot.sigma2[0]), data[j], ks)
-        n += ks.size
+        n += oracle_chunk_res(spec, anchors, slot, chunks)
         chunks += 1
         if time.perf_counter() - t0 >= budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "res": n, "seconds": dt}
+    return {"value": n / dt, "res": n, "seconds": dt, "cores": 1}
+
+
+_ORACLE_WORKER = {}
+
+
+def _oracle_worker_init(spec: S.SlotSpec, seed: int):
+    """Pool worker set-up (untimed): its own copy of cell 0 and its LS anchors."""
+    from oracle import phy_oracle as O
+    sl = S.make_slot(dataclasses.replace(spec, n_cells=1), seed, keep_h=False)
+    _ORACLE_WORKER.update(spec=spec, slot=sl, anchors=O.ls_anchors(
+        sl.Y[:1], sl.pilots[:1], spec.dmrs_sym, spec.n_layers, spec.occ))
+
+
+def _oracle_worker_run(arg) -> int:
+    """Detect chunks first, first + stride, ... until the wall-clock deadline; REs detected."""
+    first, stride, deadline = arg
+    w = _ORACLE_WORKER
+    n, c = 0, first
+    while time.time() < deadline:
+        n += oracle_chunk_res(w["spec"], w["anchors"], w["slot"], c)
+        c += stride
+    return n
+
+
+class OraclePool:
+    """The oracle on every core this process may use (os.sched_getaffinity): one spawned worker
+    process per core, each detecting its own share of cell 0's chunks. Spawned (not forked), so
+    it is safe next to a CUDA context."""
+
+    def __init__(self, spec: S.SlotSpec, seed: int):
+        import multiprocessing as mp
+        self.cores = len(os.sched_getaffinity(0))
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_worker_init,
+                                                 initargs=(spec, seed))
+        # every worker set up before the first timing
+        self.pool.map(_oracle_worker_run, [(0, 1, 0.0)] * self.cores, chunksize=1)
+
+    def rate(self, budget_s: float) -> dict:
+        t0 = time.time()
+        deadline = t0 + budget_s
+        ns = self.pool.map(_oracle_worker_run,
+                           [(w, self.cores, deadline) for w in range(self.cores)], chunksize=1)
+        dt = time.time() - t0
+        return {"value": sum(ns) / dt, "res": int(sum(ns)), "seconds": dt, "cores": self.cores}
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline(spec: S.SlotSpec, budget_s: float) -> dict:
+    """The oracle as it stands on the host cores: one core (LS of cell 0 included) and every
+    allowed core (workers set up outside the timing), each for about budget_s / 2."""
+    half = max(budget_s / 2.0, 1.0)
+    one = oracle_sample_rate(spec, S.make_slot(dataclasses.replace(spec, n_cells=1), 3000,
+                                               keep_h=False), half)
+    pool = OraclePool(spec, 3000)
+    try:
+        allc = pool.rate(half)
+    finally:
+        pool.close()
+    return {"value": allc["value"], "unit": "REs/s", "cores": allc["cores"], "kind": "oracle",
+            "sample": f"cell 0 of the workload, whole data symbols {ORACLE_CHUNK} subcarriers at "
+                      f"a time, numpy float64: {allc['res']} REs in {allc['seconds']:.1f} s on "
+                      f"{allc['cores']} worker processes (one per allowed core, LS done per "
+                      f"worker before the timing); single core {one['value']:.0f} REs/s "
+                      f"({one['res']} REs in {one['seconds']:.1f} s, LS included)",
+            "single_core": {"value": one["value"], "cores": 1, "res": one["res"],
+                            "seconds": one["seconds"]},
+            "all_cores": {"value": allc["value"], "cores": allc["cores"], "res": allc["res"],
+                          "seconds": allc["seconds"]}}
+
+
+# ---------------------------------------------------------------------------------------------
+# measured arithmetic peaks
+# ---------------------------------------------------------------------------------------------
+
+def measured_fma_peaks(dev, st) -> dict:
+    """FMA throughput of this GPU, measured in-process by the library's probe kernel (8 CTAs of
+    256 threads per SM, eight independent chains per thread), CUDA events, best of 5 launches
+    after 2 warm-up launches: FP32 (fma.rn.f32), FP32 pairs (fma.rn.f32x2) and FP64."""
+    import torch
+    from paper_2510_07843_gb300 import phy
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.empty(512, dtype=torch.float64, device=dev)
+    out = {"sm_count": sms, "how": "phy_fma_probe, 8 x 256-thread CTAs per SM, best of 5"}
+    for kind, iters in (("fp32", 4096), ("fp32x2", 2048), ("fp64", 64)):
+        best = 0.0
+        for rep in range(7):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            fl = phy.fma_probe(kind, 8 * sms, iters, sink, stream=st)
+            b.record(st)
+            torch.cuda.synchronize()
+            if rep >= 2:
+                best = max(best, fl / (a.elapsed_time(b) * 1e-3) / 1e12)
+        out[f"{kind}_tflops"] = best
+    return out
 
 
 # ---------------------------------------------------------------------------------------------
@@ -289,7 +397,13 @@ def main():
     ap.add_argument("--workload", default="massive", choices=["massive", "carrier", "small"])
     ap.add_argument("--cells", type=int, default=0,
                     help="override the workload's cells per GPU (smaller cases for profiling)")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "fp16", "bf16"])
+    ap.add_argument("--precision", default="fp16", choices=["fp32", "tf32", "fp16", "bf16"],
+                    help="products of the headline step (the massive configuration specifies "
+                         "FP16/BF16 tensor-core products with an FP32 solve)")
+    ap.add_argument("--variants", default="fp32,bf16",
+                    help="other precisions timed on the same workload ('' for none)")
+    ap.add_argument("--no-refactor", action="store_true",
+                    help="headline without the FP64 re-computation of flagged REs")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle timing")
     ap.add_argument("--llr", default="f32", choices=["f32", "f16"], help="LLR output format")
     ap.add_argument("--streams", type=int, default=2,
@@ -380,28 +494,34 @@ def aux_probe(spec, reps: int) -> int:
 
 
 def run_reference(args, spec, rank, world):
-    """The oracle (the FP64 CPU definition of the method) timed on this host's cores."""
+    """The oracle (the FP64 CPU definition of the method) timed on this host's cores: one spawned
+    worker per allowed core, each step a bounded sample of the workload."""
     if rank != 0:
         return 0
-    slot = S.make_slot(dataclasses.replace(spec, n_cells=1), 3000, keep_h=False)
     per_step = max(args.cpu_budget / max(args.steps + args.warmup, 1), 0.5)
-    for _ in range(args.warmup):
-        oracle_sample_rate(spec, slot, per_step)
-    vals, secs = [], 0.0
-    for _ in range(args.steps):
-        r = oracle_sample_rate(spec, slot, per_step)
-        vals.append(r["value"])
-        secs += r["seconds"]
+    pool = OraclePool(spec, 3000)
+    try:
+        for _ in range(args.warmup):
+            pool.rate(per_step)
+        vals, secs, res = [], 0.0, 0
+        for _ in range(args.steps):
+            r = pool.rate(per_step)
+            vals.append(r["value"])
+            secs += r["seconds"]
+            res += r["res"]
+    finally:
+        pool.close()
     value = statistics.median(vals)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "REs/s", "n_gpus": 0,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config_dict(spec, args, world),
-        "cpu_baseline": {"value": value, "unit": "REs/s", "cores": 1, "kind": "oracle",
-                         "sample": f"cell 0 of the workload: LS on the whole cell, then whole "
-                                   f"data symbols 256 subcarriers at a time, {per_step:.1f} s "
-                                   f"per step"},
+        "cpu_baseline": {"value": value, "unit": "REs/s", "cores": pool.cores, "kind": "oracle",
+                         "sample": f"cell 0 of the workload, whole data symbols {ORACLE_CHUNK} "
+                                   f"subcarriers at a time, {per_step:.1f} s per step on "
+                                   f"{pool.cores} worker processes (one per allowed core); "
+                                   f"{res} REs over the timed steps"},
         "e2e": {"value": value, "unit": "REs/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -415,7 +535,11 @@ def config_dict(spec, args, world):
                         f"{2 ** spec.qm}-QAM, DMRS {list(spec.dmrs_sym)}",
             "n_cells_per_gpu": spec.n_cells, "n_prb": spec.n_prb, "n_rx": spec.n_rx,
             "n_layers": spec.n_layers, "qm": spec.qm, "snr_db": spec.snr_db,
-            "precision": args.precision, "llr_format": args.llr,
+            "precision": f"{args.precision} products on tensor cores, FP32 accumulation, "
+                         f"FP32 Cholesky/solve/LLR"
+                         + ("" if args.no_refactor else ", FP64 re-computation of flagged REs")
+            if args.precision != "fp32" else "fp32 throughout",
+            "llr_format": args.llr,
             "pipelining": (f"{args.streams} streams: consecutive steps overlap, own buffers"
                            if args.streams > 1 else "serial"),
             "parallelism": f"replicas x{world} (cells per rank)",
@@ -573,34 +697,34 @@ def serving_run(spec, precision, dev, buf, slots=100, llr="f32", streams=2):
     return out
 
 
-def run_ours(args, spec, rank, world, local):
-    import torch
-    from paper_2510_07843_gb300 import build, phy
+def time_variant(spec, precision, refactor, llr, args, slot, dev, world, fl_peak_tf,
+                 hbm_peak, first_buf=None):
+    """One precision of the receiver on the workload, inputs resident in HBM.
 
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    build.build()
-    phy.load()
-    cfg = phy.SlotConfig.from_spec(spec, precision=args.precision, llr_format=args.llr)
-    slot = S.make_slot(spec, rank_seed(rank), keep_h=False)
-    buf = phy.SlotBuffers(cfg, device=dev)
-    buf.Y.copy_(torch.from_numpy(slot.Y))
-    buf.pilots.copy_(torch.from_numpy(slot.pilots))
-    buf.sigma2.copy_(torch.from_numpy(slot.sigma2))
+    Serial pass: every step's stages bracketed by CUDA events on the launch stream (per-stage
+    times, step latency p50/p99, per-kernel rooflines). Pipelined pass (the throughput): the
+    steps alternate over `args.streams` streams with their own buffers, so one step's solve
+    overlaps the next step's estimation and Gram kernels, as a continuous stream of slots runs.
+    Returns the variant's record and its buffers."""
+    import torch
+    from paper_2510_07843_gb300 import phy
+    cfg = phy.SlotConfig.from_spec(spec, precision=precision, llr_format=llr,
+                                   fp64_refactor=refactor)
+    buf = first_buf if first_buf is not None else phy.SlotBuffers(cfg, device=dev)
+    if first_buf is None:
+        buf.Y.copy_(torch.from_numpy(slot.Y))
+        buf.pilots.copy_(torch.from_numpy(slot.pilots))
+        buf.sigma2.copy_(torch.from_numpy(slot.sigma2))
     st = torch.cuda.Stream(device=dev)
     n_re = n_data_res(spec)
-
     split = phy.stage_supported(cfg)
+    args_ = (buf.anchors, buf.Y, buf.sigma2, buf.x_hat, buf.sinr, buf.llr, buf.flags,
+             buf.workspace)
 
     def step(e1=None, e2=None):
         phy.chest(cfg, buf.Y, buf.pilots, buf.anchors, stream=st)
         if e1 is not None:
             e1.record(st)
-        args_ = (buf.anchors, buf.Y, buf.sigma2, buf.x_hat, buf.sinr, buf.llr, buf.flags,
-                 buf.workspace)
         if split:  # the two detection kernels as separate calls, timed apart
             phy.detect_stage(cfg, phy.STAGE_GRAM_MF, *args_, stream=st)
             if e2 is not None:
@@ -611,37 +735,35 @@ def run_ours(args, spec, rank, world, local):
                 e2.record(st)
             phy.detect_anchors(cfg, *args_, stream=st)
 
-    clocks = ClockSampler(local, args.clock_log)
-    clocks.start()
-    time.sleep(0.3)  # let the sampler start before the GPU gets busy
-    with torch.cuda.stream(st):
-        for _ in range(max(args.warmup, 3)):
-            step()
+    for _ in range(max(args.warmup, 3)):
+        step()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(4))
           for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(st)
+    t0.record(st)
     for i in range(args.steps):
         ev[i][0].record(st)
         step(ev[i][1], ev[i][2])
         ev[i][3].record(st)
-    t_end.record(st)
+    t1.record(st)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    total_ms = t_start.elapsed_time(t_end)
+    serial_ms = max_over_ranks(t0.elapsed_time(t1), dev)
+    fl = buf.flags.cpu().numpy()
+    flag_stats = {"flagged_frac": float(np.mean((fl & 1) != 0)),
+                  "fp64_refactored": int(np.count_nonzero(fl & 2)),
+                  "fp64_refactored_frac": float(np.mean((fl & 2) != 0)),
+                  "nonfinite": int(np.count_nonzero(fl & 4)),
+                  "timed_out": int(np.count_nonzero(fl & 8))}
 
-    # Pipelined pass: consecutive steps alternate over `streams` streams with their own buffers,
-    # so one step's kernels overlap the next one's (a continuous stream of slots). This is the
-    # throughput `value`; the serial pass above gives latency and the per-stage breakdown.
     pipe_ms = None
+    sets = [(buf, st)]
     if args.streams > 1:
-        sets = [(buf, st)]
         for _ in range(args.streams - 1):
             b2 = phy.SlotBuffers(cfg, device=dev)
             b2.Y.copy_(buf.Y)
@@ -673,13 +795,91 @@ def run_ours(args, spec, rank, world, local):
         if world > 1:
             torch.distributed.barrier()
         pipe_ms = max_over_ranks(p0.elapsed_time(p1), dev)
-    clk = clocks.stop()
     step_ms = [a.elapsed_time(d) for a, b, c, d in ev]
-    chest_ms = [a.elapsed_time(b) for a, b, c, d in ev]
-    gram_ms = [b.elapsed_time(c) for a, b, c, d in ev]
-    solve_ms = [c.elapsed_time(d) for a, b, c, d in ev]
-    det_ms = [b.elapsed_time(d) for a, b, c, d in ev]
-    total_ms = max_over_ranks(total_ms, dev)
+    chest_ms = statistics.mean(a.elapsed_time(b) for a, b, c, d in ev)
+    gram_ms = statistics.mean(b.elapsed_time(c) for a, b, c, d in ev)
+    solve_ms = statistics.mean(c.elapsed_time(d) for a, b, c, d in ev)
+    det_ms = statistics.mean(b.elapsed_time(d) for a, b, c, d in ev)
+
+    flops = detect_flops(spec)
+    ab = algorithmic_bytes(spec)
+    on_tc = precision != "fp32"
+    peak_src = "measured in this run: phy_fma_probe FP32 (fma.rn.f32 / f32x2, the larger)"
+    solve_roof = {"bound": "alu", "kernel": f"re_solve_fp32_kernel<16,{spec.qm}>",
+                  "achieved": flops["solve"] / (solve_ms * 1e-3) / 1e12, "peak": fl_peak_tf,
+                  "unit": "TFLOP/s", "peak_source": peak_src, "flops_per_launch": flops["solve"],
+                  "ms": solve_ms, "traffic": committed_traffic("re_solve", args.workload)}
+    gram_bytes = ab["y_data"] + anchor_bytes(spec)
+    if on_tc:
+        gram_roof = {"bound": "hbm", "kernel": f"seg_prep_tc_kernel ({precision})",
+                     "achieved": gram_bytes / (gram_ms * 1e-3) / 1e9, "peak": hbm_peak,
+                     "unit": "GB/s", "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                     "bytes_per_launch": gram_bytes,
+                     "tensor_flops_per_launch": flops["products"], "ms": gram_ms,
+                     "traffic": committed_traffic("seg_prep_tc", args.workload)}
+    else:
+        gram_roof = {"bound": "alu", "kernel": "seg_prep_fp32_kernel<16>",
+                     "achieved": flops["products"] / (gram_ms * 1e-3) / 1e12, "peak": fl_peak_tf,
+                     "unit": "TFLOP/s", "peak_source": peak_src,
+                     "flops_per_launch": flops["products"], "ms": gram_ms,
+                     "traffic": committed_traffic("seg_prep_fp32", args.workload)}
+    for r in (solve_roof, gram_roof):
+        r["frac"] = r["achieved"] / r["peak"]
+    dominant = solve_roof if solve_ms >= gram_ms else gram_roof
+    timed_ms = pipe_ms if pipe_ms is not None else serial_ms
+    rec = {"precision": precision, "fp64_refactor": bool(refactor),
+           "value": whole_job_rate(world, n_re, args.steps, timed_ms), "unit": "REs/s",
+           "ms_per_step": timed_ms / args.steps,
+           "serial_ms_per_step": serial_ms / args.steps,
+           "serial_value": whole_job_rate(world, n_re, args.steps, serial_ms),
+           "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                          "p99": float(np.percentile(step_ms, 99)), "deadline_ms": 0.5,
+                          "what": "one step (whole batch) on an idle GPU, CUDA events"},
+           "stages_ms": {"chest": chest_ms, "gram_mf": gram_ms, "solve": solve_ms,
+                         "detect": det_ms},
+           "dominant": dominant, "per_kernel": {"solve": solve_roof, "gram_mf": gram_roof},
+           "split_stages": bool(split), "flags": flag_stats,
+           "gpu_launches": (1 + 2 * detect_chunks(spec)) * args.steps}
+    return rec, cfg, buf, st
+
+
+def run_ours(args, spec, rank, world, local):
+    import torch
+    from paper_2510_07843_gb300 import build, phy
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    phy.load()
+    slot = S.make_slot(spec, rank_seed(rank), keep_h=False)
+    n_re = n_data_res(spec)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    probe_st = torch.cuda.Stream(device=dev)
+
+    clocks = ClockSampler(local, args.clock_log)
+    clocks.start()
+    time.sleep(0.3)  # let the sampler start before the GPU gets busy
+    fma = measured_fma_peaks(dev, probe_st)
+    fl_peak = max(fma["fp32_tflops"], fma["fp32x2_tflops"])
+    refactor = not args.no_refactor and args.precision != "fp32"
+    head, cfg, buf, st = time_variant(spec, args.precision, refactor, args.llr, args, slot, dev,
+                                      world, fl_peak, hbm_peak)
+    variants = {}
+    for v in [x for x in args.variants.split(",") if x and x != args.precision]:
+        rec, _, vbuf, _ = time_variant(spec, v, False, args.llr, args, slot, dev, world, fl_peak,
+                                       hbm_peak)
+        variants[v] = rec
+        del vbuf
+    torch.cuda.synchronize()
+    clk = clocks.stop()
 
     # e2e through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -727,87 +927,57 @@ def run_ours(args, spec, rank, world, local):
     if not args.no_noise:
         noise = noise_estimate_run(cfg, spec, buf, st)
 
-    cpu = None
-    if not args.no_cpu_baseline and world == 1:
-        r = oracle_sample_rate(spec, S.make_slot(dataclasses.replace(spec, n_cells=1),
-                                                 3000, keep_h=False), args.cpu_budget)
-        cpu = {"value": r["value"], "unit": "REs/s", "cores": 1, "kind": "oracle",
-               "sample": f"cell 0 of the workload: LS on the whole cell, then {r['res']} data "
-                         f"REs (whole symbols, 256 subcarriers at a time) in {r['seconds']:.1f} s, "
-                         f"numpy float64 single thread"}
-
-    det_avg = statistics.mean(det_ms)
-    gram_avg, solve_avg = statistics.mean(gram_ms), statistics.mean(solve_ms)
-    fl = detect_flops(spec)
-    on_tc = args.precision != "fp32"
-    peak_tf = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
-    peak_src = (f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
-                f"x {SM_MAX_MHZ_NOMINAL:.0f} MHz")
-    ab = algorithmic_bytes(spec)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
     bfp = None
     if not args.no_bfp:
         bfp = bfp_run(cfg, spec, slot, buf, st, hbm_peak)
     learned = None
     if not args.no_cnn:
-        learned = cnn_run(dev, st, peak_tf)
-    # per-kernel rooflines. Solve: FP32 ALU work per RE. Gram/matched filter: its products on
-    # the FP32 pipe in the FP32 variant; with tensor cores it streams the grid (HBM bound).
-    solve_roof = {"bound": "alu", "kernel": f"re_solve_fp32_kernel<16,{spec.qm}>",
-                  "achieved": fl["solve"] / (solve_avg * 1e-3) / 1e12, "peak": peak_tf,
-                  "unit": "TFLOP/s", "peak_source": peak_src, "flops_per_launch": fl["solve"],
-                  "ms": solve_avg, "traffic": committed_traffic("re_solve", args.workload)}
-    gram_bytes = ab["y_data"] + anchor_bytes(spec)
-    if on_tc:
-        gram_roof = {"bound": "hbm", "kernel": f"seg_prep_tc_kernel ({args.precision})",
-                     "achieved": gram_bytes / (gram_avg * 1e-3) / 1e9, "peak": hbm_peak,
-                     "unit": "GB/s", "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
-                     "bytes_per_launch": gram_bytes,
-                     "tensor_flops_per_launch": fl["products"], "ms": gram_avg,
-                     "traffic": committed_traffic("seg_prep_tc", args.workload)}
-    else:
-        gram_roof = {"bound": "alu", "kernel": "seg_prep_fp32_kernel<16>",
-                     "achieved": fl["products"] / (gram_avg * 1e-3) / 1e12, "peak": peak_tf,
-                     "unit": "TFLOP/s", "peak_source": peak_src,
-                     "flops_per_launch": fl["products"], "ms": gram_avg,
-                     "traffic": committed_traffic("seg_prep_fp32", args.workload)}
-    for r in (solve_roof, gram_roof):
-        r["frac"] = r["achieved"] / r["peak"]
-    dominant = solve_roof if solve_avg >= gram_avg else gram_roof
+        learned = cnn_run(dev, st, fl_peak)
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(spec, args.cpu_budget)
+
+    dominant = head["dominant"]
     roofline = {k: dominant[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
     roofline.update(kernel=dominant["kernel"], peak_source=dominant["peak_source"],
-                    per_kernel={"solve": solve_roof, "gram_mf": gram_roof},
-                    split_stages=bool(split))
-    timed_ms = pipe_ms if pipe_ms is not None else total_ms
-    value = whole_job_rate(world, n_re, args.steps, timed_ms)
+                    per_kernel=head["per_kernel"], split_stages=head["split_stages"],
+                    measured_peaks={"fma": fma, "hbm_gbs": hbm_peak})
+    ab = algorithmic_bytes(spec)
+    plain = variants.get("fp32")
+    vs_plain = None
+    if plain is not None:
+        vs_plain = {"value_ratio": head["value"] / plain["value"],
+                    "serial_ratio": head["serial_value"] / plain["serial_value"],
+                    "p99_ms": {args.precision: head["latency_ms"]["p99"],
+                               "fp32": plain["latency_ms"]["p99"]},
+                    "what": "headline form over plain FP32 on the same workload and buffers"}
+    strip = lambda r: {k: v for k, v in r.items() if k not in ("dominant",)}
     line = {
-        "metric": METRIC, "value": value, "unit": "REs/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": timed_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config_dict(spec, args, world),
-        "serial_ms_per_step": total_ms / args.steps,
-        "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
-                       "p99": float(np.percentile(step_ms, 99)), "deadline_ms": 0.5,
-                       "what": "one step (8-cell batch) on an idle GPU, CUDA events"},
-        "stages_ms": {"chest": statistics.mean(chest_ms), "gram_mf": gram_avg,
-                      "solve": solve_avg, "detect": det_avg},
+        "metric": METRIC, "value": head["value"], "unit": "REs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": (f"{args.precision} tensor-core products (fp32 accumulate), f32 solve"
+                  if args.precision != "fp32" else "f32"),
+        "data": "synthetic", "config": config_dict(spec, args, world),
+        "serial_ms_per_step": head["serial_ms_per_step"],
+        "latency_ms": head["latency_ms"],
+        "stages_ms": head["stages_ms"],
+        "flags": head["flags"],
         "roofline": roofline,
         "step_hbm": {"algorithmic_bytes": ab["step"],
-                     "achieved_gbs": ab["step"] / (total_ms / args.steps * 1e-3) / 1e9,
+                     "achieved_gbs": ab["step"] / (head["serial_ms_per_step"] * 1e-3) / 1e9,
                      "peak_gbs": hbm_peak,
-                     "frac": ab["step"] / (total_ms / args.steps * 1e-3) / 1e9 / hbm_peak},
+                     "frac": ab["step"] / (head["serial_ms_per_step"] * 1e-3) / 1e9 / hbm_peak},
+        "vs_plain_fp32": vs_plain,
+        "variants": {k: strip(v) for k, v in variants.items()},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "serving": serving,
         "noise_estimate": noise,
         "bfp_fronthaul": bfp,
         "learned_denoiser": learned,
-        "gpu_launches": (1 + 2 * detect_chunks(spec)) * args.steps,
+        "gpu_launches": head["gpu_launches"],
         "clocks": clk,
     }
     print(json.dumps(line))

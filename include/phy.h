@@ -111,6 +111,39 @@ typedef struct {
 /* Human-readable name of a status code (static string). */
 const char* phy_status_str(phy_status s);
 
+/*
+ * Failure-detection test hook (no counterpart in the paper). Every device wait in the detection
+ * kernels polls a bounded number of times; a wait that runs out voids the CTA's work: the
+ * tensor-core segment kernel bumps an error word that the solve kernel reads, and the solve
+ * marks each affected RE with flag bit 3 alone. phy_debug_set_wait_polls() sets the poll limit
+ * of the first-level waits of one kernel (PHY_WAIT_SEGMENT_KERNEL: the TMA ring, anchor, MMA
+ * and drain hand-overs of the tensor-core segment kernel; PHY_WAIT_SOLVE_KERNEL: the solve
+ * kernel's Gram-block copies) for every call made afterwards in this process; polls < 0
+ * restores the default (about a second). With polls = 0 those waits give up at once, so a test
+ * can make them run out without any fault: the waits that let copies and MMAs already in flight
+ * land before a CTA ends keep their default limits. Returns PHY_ERR_INVALID_ARG for an unknown
+ * kernel. Thread-safe; not for production use.
+ */
+typedef enum { PHY_WAIT_SEGMENT_KERNEL = 0, PHY_WAIT_SOLVE_KERNEL = 1 } phy_wait_kernel;
+
+phy_status phy_debug_set_wait_polls(int32_t kernel, int64_t polls);
+
+/*
+ * FMA-throughput probe (measurement support, no counterpart in the paper): the measured peak
+ * that the FP32 CUDA-core kernels' roofline fractions are reported against. Enqueues one kernel
+ * of `blocks` CTAs x 256 threads on `stream`; every thread runs `iters` x 256 multiply-adds in
+ * eight independent chains: FP32 (PHY_PROBE_FP32, one fma.rn.f32 each), FP32 pairs
+ * (PHY_PROBE_FP32X2, one fma.rn.f32x2 per two) or FP64 (PHY_PROBE_FP64). CTA 0 writes its 256
+ * thread sums to `sink` (device, 256 floats, or 256 doubles for FP64) so that no work is dead.
+ * *flops_out (host, may be NULL) receives the flops the launch performs (2 per multiply-add);
+ * divide by the launch's CUDA-event time. PHY_ERR_INVALID_ARG for an unknown kind, blocks < 1,
+ * iters < 1 or a NULL sink. Size `blocks` as 8 per SM to fill every SM.
+ */
+typedef enum { PHY_PROBE_FP32 = 0, PHY_PROBE_FP32X2 = 1, PHY_PROBE_FP64 = 2 } phy_probe_kind;
+
+phy_status phy_fma_probe(int32_t kind, int32_t blocks, int32_t iters, void* sink,
+                         double* flops_out, void* stream);
+
 /* Number of LS groups (anchors per DMRS symbol, layer and Rx) for cfg, or -1 if cfg is invalid. */
 int32_t phy_n_groups(const phy_slot_cfg* cfg);
 
@@ -209,11 +242,17 @@ phy_status phy_slot_run_host(const phy_slot_cfg* cfg, const phy_c32* Y_host,
  * scratch space lives in one fixed array of PHY_NOALLOC_SCRATCH_BYTES in the library's device
  * memory: every GPU that loads libphy.so holds that array until the process exits, and the
  * call itself allocates nothing (no cudaMalloc, no cudaFree, no allocating library routine).
- *  - Limit: a configuration whose phy_workspace_size() exceeds PHY_NOALLOC_SCRATCH_BYTES is
- *    rejected with PHY_ERR_NO_MEMORY before anything is enqueued (64 MiB covers 8 cells of
- *    273 PRB with 64 Rx and 16 layers and two DMRS symbols).
+ *  - Limit: the array holds the LS anchors and noise-estimate partial sums of every cell plus
+ *    the detection intermediates of at least one cell; the work then runs in chunks of as many
+ *    cells as fit. A configuration for which even that minimum exceeds
+ *    PHY_NOALLOC_SCRATCH_BYTES is rejected with PHY_ERR_NO_MEMORY before anything is enqueued.
+ *    64 MiB takes 8 cells of 273 PRB with 64 Rx, 16 layers and two DMRS symbols (26.9 MB of
+ *    anchors plus 16 MB per cell of intermediates, in chunks); 32 such cells (107 MB of
+ *    anchors alone) are rejected.
  *  - The first call on each device looks up the array's device address (cudaGetSymbolAddress)
- *    with that device current and caches it; make that first call before any stream capture.
+ *    with that device current and caches it for the life of the process; make that first call
+ *    before any stream capture. The cache does not survive cudaDeviceReset(): do not call this
+ *    entry point after resetting a device it has already run on.
  *  - All calls on a device share the one array and it keeps the previous call's contents (every
  *    value a call reads is written earlier in the same call, so nothing needs clearing). Calls
  *    whose work overlaps on the GPU (different streams, or different host threads) race on it:

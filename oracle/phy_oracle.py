@@ -321,7 +321,8 @@ def detect_res(anchors_cell: np.ndarray, Y_cell: np.ndarray, dmrs_sym: Sequence[
     llr = llr_maxlog(x_t, s2eff, qm)
     ratio = pivot_ratio(gram(H, sigma2))
     flags = (ratio < pivot_min).astype(np.uint8)
-    return dict(x_hat=x_hat, sinr=sinr, llr=llr, flags=flags, x_t=x_t, s2eff=s2eff, H=H)
+    return dict(x_hat=x_hat, sinr=sinr, llr=llr, flags=flags, x_t=x_t, s2eff=s2eff, H=H,
+                pivot_ratio=ratio)
 
 
 def run_slot(Y: np.ndarray, pilots: np.ndarray, sigma2: np.ndarray, dmrs_sym: Sequence[int],
@@ -331,7 +332,8 @@ def run_slot(Y: np.ndarray, pilots: np.ndarray, sigma2: np.ndarray, dmrs_sym: Se
     """The whole receiver for every data RE of every cell (or a sample of REs).
 
     Y [cell][sym][rx][sc]; pilots [cell][dmrs][layer][sc]; sigma2 [cell].
-    Dense outputs: x_hat [cell][dsym][sc][layer], sinr same, llr [...][qm], flags [cell][dsym][sc].
+    Dense outputs: x_hat [cell][dsym][sc][layer], sinr same, llr [...][qm], flags [cell][dsym][sc],
+    pivot_ratio [cell][dsym][sc] (the value the flag thresholds).
     With res = {cell: (j_idx, k_idx)} only those REs (data symbol j, subcarrier k) are computed and
     each output is returned flat in that order per cell (keys 'x_hat_<cell>' etc.).
     """
@@ -347,18 +349,20 @@ def run_slot(Y: np.ndarray, pilots: np.ndarray, sigma2: np.ndarray, dmrs_sym: Se
         sn = np.zeros((n_cells, nj, n_sc, n_layers))
         ll = np.zeros((n_cells, nj, n_sc, n_layers, qm))
         fl = np.zeros((n_cells, nj, n_sc), dtype=np.uint8)
+        pr = np.zeros((n_cells, nj, n_sc))
         ks = np.arange(n_sc)
         for c in range(n_cells):
             for j, t in enumerate(data_sym):
                 r = detect_res(anchors[c], Y[c], dmrs_sym, n_layers, L, qm, float(sigma2[c]), t,
                                ks, pivot_min)
                 xh[c, j], sn[c, j], ll[c, j], fl[c, j] = r["x_hat"], r["sinr"], r["llr"], r["flags"]
-        out.update(x_hat=xh, sinr=sn, llr=ll, flags=fl)
+                pr[c, j] = r["pivot_ratio"]
+        out.update(x_hat=xh, sinr=sn, llr=ll, flags=fl, pivot_ratio=pr)
         return out
     for c, (jj, kk) in res.items():
         jj = np.asarray(jj)
         kk = np.asarray(kk)
-        parts = {key: [] for key in ("x_hat", "sinr", "llr", "flags")}
+        parts = {key: [] for key in ("x_hat", "sinr", "llr", "flags", "pivot_ratio")}
         order = []
         for j in np.unique(jj):
             sel = np.nonzero(jj == j)[0]

@@ -1,5 +1,6 @@
 // C ABI of libphy.so: argument validation, slot geometry, workspace carving, stream enqueue.
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <cstring>
 #include <map>
@@ -22,6 +23,14 @@ int auto_occ(int n_layers) {
   int half = (n_layers + 1) / 2, L = 1;
   while (L < half) L *= 2;
   return L;
+}
+
+// First-level device wait limits set by phy_debug_set_wait_polls (negative: the defaults).
+std::atomic<long long> g_wait_polls[2] = {{-1}, {-1}};
+
+unsigned wait_polls(int kernel, unsigned dflt) {
+  const long long v = g_wait_polls[kernel].load(std::memory_order_relaxed);
+  return v < 0 ? dflt : (unsigned)std::min<long long>(v, 0xFFFFFFFFll);
 }
 
 // Validates cfg and fills g. Returns PHY_OK, PHY_ERR_INVALID_ARG or PHY_ERR_UNSUPPORTED.
@@ -66,6 +75,8 @@ phy_status make_geo(const phy_slot_cfg* c, Geo* g) {
   t.refactor = c->fp64_refactor ? 1 : 0;
   if (c->llr_format != PHY_LLR_F32 && c->llr_format != PHY_LLR_F16) return PHY_ERR_INVALID_ARG;
   t.llr_f16 = c->llr_format == PHY_LLR_F16;
+  t.wait_seg = wait_polls(PHY_WAIT_SEGMENT_KERNEL, phy::kWaitSegDefault);
+  t.wait_solve = wait_polls(PHY_WAIT_SOLVE_KERNEL, phy::kWaitSolveDefault);
   int nd = 0;
   for (int s = 0; s < c->n_sym; ++s) {
     bool is_dmrs = false;
@@ -173,6 +184,13 @@ phy_status slot_run_fit(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32
 }  // namespace phy
 
 extern "C" {
+
+phy_status phy_debug_set_wait_polls(int32_t kernel, int64_t polls) {
+  if (kernel != PHY_WAIT_SEGMENT_KERNEL && kernel != PHY_WAIT_SOLVE_KERNEL)
+    return PHY_ERR_INVALID_ARG;
+  g_wait_polls[kernel].store(polls < 0 ? -1 : (long long)polls, std::memory_order_relaxed);
+  return PHY_OK;
+}
 
 const char* phy_status_str(phy_status s) {
   switch (s) {

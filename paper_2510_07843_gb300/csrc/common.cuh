@@ -13,6 +13,9 @@ namespace phy {
 constexpr int kMaxSym = 14;
 constexpr int kMaxRx = 64;
 constexpr int kMaxLayers = 16;
+// Default first-level wait limits (polls): the tensor-core kernel's polls sleep up to ~1 us each.
+constexpr unsigned kWaitSegDefault = 1u << 20;
+constexpr unsigned kWaitSolveDefault = 1u << 22;
 
 // Everything a kernel needs to know about the slot, resolved on the host from phy_slot_cfg.
 struct Geo {
@@ -27,6 +30,10 @@ struct Geo {
   int refactor; // 1: recompute flagged (ill-conditioned) REs in FP64
   int llr_f16;  // 1: LLR outputs as binary16
   float pivot_min;
+  // Poll limits of the first-level device waits (a wait that runs out is a timeout): in the
+  // tensor-core segment kernel and in the solve kernel. The waits that only let copies and
+  // MMAs already in flight land before a CTA ends keep their own, longer limits.
+  unsigned wait_seg, wait_solve;
   int dsym[kMaxSym];    // data symbol index j -> OFDM symbol t
   float tw[kMaxSym];    // weight of the second DMRS estimate at data symbol j
 };

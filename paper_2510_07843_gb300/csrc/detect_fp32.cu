@@ -420,9 +420,9 @@ __global__ void __launch_bounds__(kSolveThreads)
       b[l + 1] = mk(v.z, v.w);
     }
   }
-  constexpr uint32_t kWait = 1u << 22;
-  bool arrived = tc::mbar_wait(bar, 0, kWait);
-  if (!arrived) arrived = tc::mbar_wait(bar, 0, kWait);  // let copies in flight land
+  bool arrived = tc::mbar_wait(bar, 0, g.wait_solve);
+  // after a timeout, let the copies in flight land before the CTA can end
+  if (!arrived) tc::mbar_wait(bar, 0, kWaitSolveDefault);
   // one decision for the CTA (it has barriers below); a timed-out Gram/matched-filter kernel
   // (its error word) voids every RE as a wait timeout here would
   arrived = __syncthreads_and(arrived && (threadIdx.x != 0 || *prep_err == 0));

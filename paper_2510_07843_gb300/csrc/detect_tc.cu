@@ -51,7 +51,7 @@ constexpr int kBoxWarps = kBoxItems / 32;          // converter warps per box
 constexpr uint32_t kRingBytes = 64 * 1024;         // ring of boxes (FP16/BF16 tiles)
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kColX = 0, kColMf = 128;  // MF accumulator b at kColMf + 128 b
-constexpr uint32_t kWaitIters = 1u << 20;  // polls of up to ~1 us each
+constexpr uint32_t kWaitIters = kWaitSegDefault;  // drains of work in flight (polls of ~1 us)
 
 template <uint32_t FMT>
 struct Layout {
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       bool ok = true;
       for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
         const Item it = item_of(g, w, cell0);
-        if (nitem > 0) ok = tc::mbar_wait_sleep(a_empty, (nitem - 1) & 1, kWaitIters);
+        if (nitem > 0) ok = tc::mbar_wait_sleep(a_empty, (nitem - 1) & 1, g.wait_seg);
         if (!ok) break;
         tc::mbar_arrive_expect_tx(a_full, NC * a_box_bytes);
         const int g1 = seg_g1(g, it.j);
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           const int z = it.cell * g.n_sym + g.dsym[jj];
           for (int b = 0; b < it.nb; ++b) {
             const uint32_t s = nbox % S;
-            if (nbox >= (uint32_t)S) ok = tc::mbar_wait_sleep(empty + s, ((nbox / S) - 1) & 1, kWaitIters);
+            if (nbox >= (uint32_t)S) ok = tc::mbar_wait_sleep(empty + s, ((nbox / S) - 1) & 1, g.wait_seg);
             if (!ok) break;
             tc::mbar_arrive_expect_tx(full + s, y_box_bytes);
             tc::tma_load_3d(ring + s * kStageBytes, &tmY, 2 * (it.lo2 + kBoxSc * b), 0, z, full + s);
@@ -270,8 +270,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const Item it = item_of(g, w, cell0);
       // every MMA of the previous item read CC; its last commit covers them all
       if (ntile > 0) fail |= !tc::mbar_wait_sleep(mf_bar + ((ntile - 1) & 1), ((ntile - 1) >> 1) & 1,
-                                            kWaitIters);
-      fail |= !tc::mbar_wait_sleep(a_full, nitem & 1, kWaitIters);
+                                            g.wait_seg);
+      fail |= !tc::mbar_wait_sleep(a_full, nitem & 1, g.wait_seg);
       ++nitem;
       // ---- CC = [C ; iC] from the anchors of the segment's corners, four antennas per item
 #pragma unroll 2
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (stop) break;
       // ---- X = C^H C, once the drain group has read the previous X
       if (gtid == 0) {
-        if (nitem > 1) fail |= !tc::mbar_wait_sleep(x_free, (nitem - 2) & 1, kWaitIters);
+        if (nitem > 1) fail |= !tc::mbar_wait_sleep(x_free, (nitem - 2) & 1, g.wait_seg);
         tc::fence_after_sync();
         gemm_issue<FMT>(tmem + kColX, cc, cc, tc::instr_desc(FMT, kRows, NXP), x_bar);
       }
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         constexpr uint32_t back = Lay::kYBufs;
         if (ntile >= back)
           fail |= !tc::mbar_wait_sleep(mf_bar + ((ntile - back) & 1), ((ntile - back) >> 1) & 1,
-                                 kWaitIters);
+                                 g.wait_seg);
         // ---- boxes of tile t -> RE-tile operand: kSlots boxes per round, each thread two
         // subcarriers x four antennas of a box (four 16-byte loads, two chunk stores)
         const int nbx = tile_syms(g, it, t) * it.nb;
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         static_assert(S % kSlots == 0, "ring depth must be a multiple of the box slots");
         for (int bx = slot; bx < nbx; bx += kSlots) {
           const uint32_t n = nbox + bx, s = n % S;
-          fail |= !tc::mbar_wait_sleep(full + s, (n / S) & 1, kWaitIters);
+          fail |= !tc::mbar_wait_sleep(full + s, (n / S) & 1, g.wait_seg);
           const float4* raw = reinterpret_cast<const float4*>(ring + s * kStageBytes);
           cf v0[4], v1[4];
 #pragma unroll
@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // ---- V = C^H y, once the drain group has emptied this accumulator buffer
         if (gtid == 0) {
           if (ntile >= 2)
-            fail |= !tc::mbar_wait_sleep(tmem_free + buf, ((ntile - 2) >> 1) & 1, kWaitIters);
+            fail |= !tc::mbar_wait_sleep(tmem_free + buf, ((ntile - 2) >> 1) & 1, g.wait_seg);
           tc::fence_after_sync();
           gemm_issue<FMT>(tmem + kColMf + 128 * buf, yop, cc,
                           tc::instr_desc(FMT, kRows, 2 * NXP), mf_bar + buf);
@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
       const Item it = item_of(g, w, cell0);
       // ---- X -> shared memory (after every drain warp is done with the previous item's X)
-      fail |= !tc::mbar_wait_sleep(x_bar, nitem & 1, kWaitIters);
+      fail |= !tc::mbar_wait_sleep(x_bar, nitem & 1, g.wait_seg);
       tc::fence_after_sync();
       tc::bar_sync<2, 128>();
       {
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       // ---- matched filter of each RE tile: this thread's TMEM lane is its RE row
       for (int t = 0; t < it.ntile; ++t, ++ntile) {
         const uint32_t buf = ntile & 1;
-        fail |= !tc::mbar_wait_sleep(mf_bar + buf, (ntile >> 1) & 1, kWaitIters);
+        fail |= !tc::mbar_wait_sleep(mf_bar + buf, (ntile >> 1) & 1, g.wait_seg);
         tc::fence_after_sync();
         const int row = 32 * quarter + lane;
         const int nrow = tile_syms(g, it, t) * it.W;

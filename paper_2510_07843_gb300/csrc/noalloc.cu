@@ -1,8 +1,9 @@
 // phy_slot_run_noalloc: the whole receiver with its scratch in a fixed device array.
 //
-// phy_slot_run keeps the LS anchors between its two kernels in a caller-provided workspace.
-// This variant keeps them in the file-scope array below instead, so the caller passes only
-// inputs and outputs and nothing is allocated, ever.
+// phy_slot_run keeps its scratch (the LS anchors, the noise-estimate partial sums, the error
+// word and the Gram-block and matched-filter intermediates of a chunk of cells) in a
+// caller-provided workspace. This variant keeps all of it in the file-scope array below
+// instead, so the caller passes only inputs and outputs and nothing is allocated, ever.
 #include <mutex>
 
 #include "../../include/phy.h"
@@ -25,7 +26,8 @@ void* g_addr[kMaxDevices] = {};
 
 // Device address of g_noalloc_scratch on the current device. The host-side name of the array
 // is a stand-in, not a device address, so it is resolved once per device (with that device
-// current) and cached.
+// current) and cached for the life of the process: the cached address belongs to the device's
+// primary context and is stale after cudaDeviceReset (documented in the header).
 cudaError_t scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

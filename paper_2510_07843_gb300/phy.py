@@ -35,6 +35,9 @@ class CSlotCfg(ctypes.Structure):
 _P = ctypes.c_void_p
 _SIGS = {
     "phy_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "phy_debug_set_wait_polls": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64]),
+    "phy_fma_probe": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P,
+                                     ctypes.POINTER(ctypes.c_double), _P]),
     "phy_n_groups": (ctypes.c_int32, [_P]),
     "phy_n_data_symbols": (ctypes.c_int32, [_P]),
     "phy_workspace_size": (ctypes.c_size_t, [_P]),
@@ -245,6 +248,27 @@ def autotune(cfg: SlotConfig, Y, pilots, sigma2, x_hat, sinr, llr, flags, worksp
 def autotune_clear():
     """phy_autotune_clear: forget every tuned configuration."""
     load().phy_autotune_clear()
+
+
+PROBE_KIND = {"fp32": 0, "fp32x2": 1, "fp64": 2}  # phy_probe_kind
+
+
+def fma_probe(kind: str, blocks: int, iters: int, sink, stream=None) -> float:
+    """phy_fma_probe: enqueue the FMA-throughput probe; returns the flops the launch performs."""
+    fl = ctypes.c_double(0.0)
+    _check("phy_fma_probe", load().phy_fma_probe(PROBE_KIND[kind], int(blocks), int(iters),
+                                                 _ptr(sink), ctypes.byref(fl), _stream(stream)))
+    return float(fl.value)
+
+
+WAIT_KERNEL = {"segment": 0, "solve": 1}  # phy_wait_kernel
+
+
+def debug_set_wait_polls(kernel: str, polls: int):
+    """phy_debug_set_wait_polls: first-level device wait limit of one detection kernel for the
+    calls that follow (polls < 0: the default). A failure-detection test hook."""
+    _check("phy_debug_set_wait_polls",
+           load().phy_debug_set_wait_polls(WAIT_KERNEL[kernel], int(polls)))
 
 
 NOISE_MODE = {"freq": 0, "time": 1, "min": 2}  # phy_noise_mode

@@ -189,3 +189,25 @@ def test_noise_tracking_validates_alpha(lib):
         assert lib.phy_slot_run_track(ctypes.byref(c), 2, alpha, fake, fake, fake, None, None,
                                       None, fake, fake, ws, None) == 1
     assert lib.phy_noise_track(ctypes.byref(c), 2, 0.5, fake, fake, fake, fake, 16, None) == 3
+
+
+def test_wait_poll_hook_validates_its_kernel(lib):
+    """phy_debug_set_wait_polls: known kernels accept any limit (and -1 restores the default);
+    an unknown kernel is rejected. No GPU work."""
+    assert lib.phy_debug_set_wait_polls(0, 5) == 0
+    assert lib.phy_debug_set_wait_polls(1, 7) == 0
+    assert lib.phy_debug_set_wait_polls(0, -1) == 0
+    assert lib.phy_debug_set_wait_polls(1, -1) == 0
+    assert lib.phy_debug_set_wait_polls(2, 0) == 1
+    assert lib.phy_debug_set_wait_polls(-1, 0) == 1
+
+
+def test_fma_probe_validates_its_arguments(lib):
+    """phy_fma_probe rejects an unknown kind, empty grids or loops and a NULL sink before it
+    launches anything (no GPU work here)."""
+    sink = ctypes.c_void_p(256)  # never reached: every call below is rejected first
+    fl = ctypes.c_double(0.0)
+    assert lib.phy_fma_probe(3, 1, 1, sink, ctypes.byref(fl), None) == 1
+    assert lib.phy_fma_probe(0, 0, 1, sink, ctypes.byref(fl), None) == 1
+    assert lib.phy_fma_probe(0, 1, 0, sink, ctypes.byref(fl), None) == 1
+    assert lib.phy_fma_probe(0, 1, 1, None, ctypes.byref(fl), None) == 1
