@@ -315,66 +315,64 @@ constexpr size_t solve_scratch_bytes(int NL) {
   return NL == 16 ? (size_t)kScrSlots * kSolveThreads * sizeof(cf) : 0;
 }
 
-// 9..16 layers: after the solve, shared memory holds each thread's x (scratch slots 0..15) and d
-// (floats, [layer][thread]), then the CTA's LLRs [RE][layer][qm], SINRs [RE][layer] and
-// x_hat [RE][layer], each leaving as one block of coalesced stores.
-constexpr size_t kStageX = (size_t)16 * kSolveThreads * sizeof(cf);
-constexpr size_t kStageXd = kStageX + (size_t)16 * kSolveThreads * sizeof(float);
+// 9..16 layers: after the solve, shared memory holds every thread's x and d in RE-major tables
+// padded to 17 entries per RE, and one ok byte per RE (the transposed epilogue's input).
 constexpr size_t solve_stage_bytes(int QM) {
-  return kStageXd + (size_t)kSolveThreads * 16 * ((QM + 1) * sizeof(float) + sizeof(cf));
+  return (size_t)kSolveThreads * 17 * (sizeof(cf) + sizeof(float)) + kSolveThreads;
 }
 
 // Shared memory of the solve kernel: scratch and the Gram blocks of up to max_segs segments (for
-// 9..16 layers at least the output staging), then the mbarrier in the last 16 bytes, which the
-// staging never reaches.
+// 9..16 layers at least the epilogue's tables), then the mbarrier in the last 16 bytes, which the
+// tables never reach.
 __host__ __device__ constexpr size_t solve_smem_bytes(int NL, int QM, int max_segs) {
   const size_t main = solve_scratch_bytes(NL) + (size_t)max_segs * gram_block_bytes(NL);
   const size_t stage = NL == 16 ? solve_stage_bytes(QM) : 0;
   return (main > stage ? main : stage) + 16;
 }
 
-// Cooperative copy of n floats from shared memory to global memory (16-byte stores when dst is
-// 16-byte aligned; src is).
-__device__ __forceinline__ void copy_out(float* dst, const float* src, int n) {
-  int i0 = 0;
-  if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-    const int n4 = n >> 2;
-    for (int i = threadIdx.x; i < n4; i += kSolveThreads)
-      reinterpret_cast<float4*>(dst)[i] = reinterpret_cast<const float4*>(src)[i];
-    i0 = n4 << 2;
-  }
-  for (int i = i0 + threadIdx.x; i < n; i += kSolveThreads) dst[i] = src[i];
-}
-
-// As copy_out, rounding to binary16 with saturation (n even; dst 8-byte aligned for the fast
-// path, which then writes four values per thread and step).
-__device__ __forceinline__ void copy_out_f16(__half* dst, const float* src, int n) {
-  int i0 = 0;
-  const float m = 65504.f;
-  if ((reinterpret_cast<uintptr_t>(dst) & 7) == 0) {
-    const int n4 = n >> 2;
-    for (int i = threadIdx.x; i < n4; i += kSolveThreads) {
-      const float4 v = reinterpret_cast<const float4*>(src)[i];
-      const __half2 a = __floats2half2_rn(fminf(fmaxf(v.x, -m), m), fminf(fmaxf(v.y, -m), m));
-      const __half2 b = __floats2half2_rn(fminf(fmaxf(v.z, -m), m), fminf(fmaxf(v.w, -m), m));
-      uint2 w;
-      w.x = *reinterpret_cast<const uint32_t*>(&a);
-      w.y = *reinterpret_cast<const uint32_t*>(&b);
-      reinterpret_cast<uint2*>(dst)[i] = w;
+// One layer's LLR record (QM values at element index idx, a multiple of QM) to the output:
+// FP32 in 16-byte pieces when QM is a multiple of 4 (the record is then 16-byte aligned), else in
+// pairs; binary16 (rounded to nearest, saturating at +-65504) as one 16- or 8-byte piece for
+// QM = 8 or 4, else in pairs.
+template <int QM>
+__device__ __forceinline__ void store_llr_record(float* base, size_t idx, const float (&v)[QM],
+                                                 bool f16) {
+  if (f16) {
+    const float m = 65504.f;
+    uint32_t w[QM / 2];
+#pragma unroll
+    for (int q = 0; q < QM; q += 2) {
+      const __half2 h = __floats2half2_rn(fminf(fmaxf(v[q], -m), m), fminf(fmaxf(v[q + 1], -m), m));
+      w[q / 2] = *reinterpret_cast<const uint32_t*>(&h);
     }
-    i0 = n4 << 2;
+    __half* hb = reinterpret_cast<__half*>(base) + idx;
+    if constexpr (QM == 8) {
+      *reinterpret_cast<uint4*>(hb) = make_uint4(w[0], w[1], w[2], w[3]);
+    } else if constexpr (QM == 4) {
+      *reinterpret_cast<uint2*>(hb) = make_uint2(w[0], w[1]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < QM / 2; ++q) reinterpret_cast<uint32_t*>(hb)[q] = w[q];
+    }
+  } else if constexpr (QM % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < QM; q += 4)
+      *reinterpret_cast<float4*>(base + idx + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < QM; q += 2)
+      *reinterpret_cast<float2*>(base + idx + q) = make_float2(v[q], v[q + 1]);
   }
-  for (int i = i0 + threadIdx.x; i < n; i += kSolveThreads)
-    dst[i] = __float2half_rn(fminf(fmaxf(src[i], -m), m));
 }
 
 // One CTA per (128 subcarriers, data symbol, cell), one thread per RE. Thread 0 brings the
 // Gram-block 4-tuples of the segments the CTA spans into shared memory with bulk copies
 // (TMA engine, completion counted on an mbarrier); meanwhile every thread loads its matched
 // filter. A barrier timeout, here or in the segment kernel before (its error word), marks the
-// CTA's REs with flag bit 3 and leaves their outputs unwritten. With 9..16 layers the LLRs
-// and SINRs are staged in shared memory and leave as one contiguous block per CTA: per-thread
-// stores of whole records (512 B apart) would keep each warp waiting on the store path.
+// CTA's REs with flag bit 3 and leaves their outputs unwritten. With 9..16 layers the SINR,
+// unbiasing and demapping run transposed, one (RE, layer) item per thread and step, so that a
+// warp's stores cover one contiguous stretch of each output: per-thread stores of whole records
+// (512 B apart) would keep each warp waiting on the store path.
 template <int NL, int QM>
 __global__ void __launch_bounds__(kSolveThreads)
     re_solve_fp32_kernel(Geo g, int cell0, int max_segs, const float4* __restrict__ ygg,
@@ -525,60 +523,46 @@ __global__ void __launch_bounds__(kSolveThreads)
     flags_out[ridx] = flag;
   }
   if constexpr (NL == 16) {
-    // x and d to this thread's scratch slots; once every thread is past the solve, the rest
-    // of shared memory stages the outputs. The per-layer loop is rolled (one copy of the
-    // demapper keeps the code small), its index dynamic, so x and d are read back from shared
-    // memory rather than from a register array. Each thread starts at its own layer, which
-    // spreads the staging stores over the banks.
-    const SmemScratch sc{reinterpret_cast<cf*>(solve_smem) + threadIdx.x};
-    float* dsl = reinterpret_cast<float*>(solve_smem + kStageX) + threadIdx.x;
-    // x goes to this thread's own scratch slots at once; the d slots overlap other threads'
-    // scratch, so d waits until every thread is past the solve
-#pragma unroll
-    for (int l = 0; l < NL; ++l)
-      if (live) sc.st(l, x[l]);
-    __syncthreads();
-#pragma unroll
-    for (int l = 0; l < NL; ++l)
-      if (live) dsl[l * kSolveThreads] = dd[l];
-    float* st_llr = reinterpret_cast<float*>(solve_smem + kStageXd);
-    float* st_sinr = st_llr + kSolveThreads * NL * QM;
-    cf* st_xh = reinterpret_cast<cf*>(st_sinr + kSolveThreads * NL);
+    // Outputs leave in (RE, layer) order: once every thread is past the solve, each stages its
+    // x and d in a padded RE-major table (stride 17: few bank conflicts both ways); then the
+    // CTA's threads take the (RE, layer) items of its 128 REs in turn, consecutive lanes on
+    // consecutive items, so every lane's LLR record (QM values), SINR and x_hat land right after
+    // its neighbour's: the stores of a warp cover one contiguous stretch of each output.
+    constexpr int kXs = NL + 1;
+    cf* xs = reinterpret_cast<cf*>(solve_smem);
+    float* ds = reinterpret_cast<float*>(solve_smem + (size_t)kSolveThreads * kXs * sizeof(cf));
+    unsigned char* oks = reinterpret_cast<unsigned char*>(ds + kSolveThreads * kXs);
+    __syncthreads();  // the scratch and the Gram blocks are dead from here on
     const int r = threadIdx.x;
-    if (live) {
-      int l = r % nl;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      xs[r * kXs + l] = x[l];
+      ds[r * kXs + l] = dd[l];
+    }
+    oks[r] = ok ? 1 : 0;
+    __syncthreads();
+    const int nlive = min(kSolveThreads, g.n_sc - k0);
+    const size_t r0 = ((size_t)cell * nds + jj) * g.n_sc + k0;
 #pragma unroll 1
-      for (int i = 0; i < nl; ++i, l = (l + 1 == nl) ? 0 : l + 1) {
-        const cf xl = sc.ld(l);
-        const LayerOut o = layer_stats(s2, dsl[l * kSolveThreads]);
+    for (int it = threadIdx.x; it < nlive * nl; it += kSolveThreads) {
+      const int re = it / nl, l = it - re * nl;
+      const cf xl = xs[re * kXs + l];
+      const bool okr = oks[re] != 0;
+      const LayerOut o = layer_stats(s2, ds[re * kXs + l]);
+      const size_t li = (r0 + re) * nl + l;
+      if (llr_out) {
         float v[QM];
-        if (ok) {
+        if (okr) {
           qam_llr<QM>(o.inv_mu * xl, o.s2eff, v);
         } else {
 #pragma unroll
           for (int q = 0; q < QM; ++q) v[q] = 0.f;
         }
-        float2* d = reinterpret_cast<float2*>(st_llr + (r * nl + l) * QM);
-#pragma unroll
-        for (int q = 0; q < QM; q += 2) d[q / 2] = make_float2(v[q], v[q + 1]);
-        st_sinr[r * nl + l] = ok ? o.sinr : 0.f;
-        st_xh[r * nl + l] = ok ? xl : mk(0.f, 0.f);
+        store_llr_record<QM>(llr_out, li * QM, v, g.llr_f16);
       }
+      if (sinr_out) sinr_out[li] = okr ? o.sinr : 0.f;
+      if (x_hat) st(x_hat + li, okr ? xl : mk(0.f, 0.f));
     }
-    __syncthreads();
-    // this CTA's live REs are consecutive, so their records form one block in each output
-    const int nlive = min(kSolveThreads, g.n_sc - k0);
-    const size_t r0 = ((size_t)cell * nds + jj) * g.n_sc + k0;
-    if (llr_out) {
-      if (g.llr_f16)
-        copy_out_f16(reinterpret_cast<__half*>(llr_out) + r0 * nl * QM, st_llr, nlive * nl * QM);
-      else
-        copy_out(llr_out + r0 * nl * QM, st_llr, nlive * nl * QM);
-    }
-    if (sinr_out) copy_out(sinr_out + r0 * nl, st_sinr, nlive * nl);
-    if (x_hat)
-      copy_out(reinterpret_cast<float*>(x_hat + r0 * nl), reinterpret_cast<const float*>(st_xh),
-               2 * nlive * nl);
   } else {
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
