@@ -543,9 +543,9 @@ __global__ void __launch_bounds__(kSolveThreads)
     __syncthreads();
     const int nlive = min(kSolveThreads, g.n_sc - k0);
     const size_t r0 = ((size_t)cell * nds + jj) * g.n_sc + k0;
-#pragma unroll 1
+#pragma unroll 2
     for (int it = threadIdx.x; it < nlive * nl; it += kSolveThreads) {
-      const int re = it / nl, l = it - re * nl;
+      const int re = nl == 16 ? (it >> 4) : it / nl, l = it - re * nl;
       const cf xl = xs[re * kXs + l];
       const bool okr = oks[re] != 0;
       const LayerOut o = layer_stats(s2, ds[re * kXs + l]);
