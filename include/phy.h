@@ -265,6 +265,56 @@ phy_status phy_slot_run_noalloc(const phy_slot_cfg* cfg, const phy_c32* Y, const
                                 uint8_t* flags, void* stream);
 
 /*
+ * Batched receiver for serving (no counterpart in the paper, which runs one cell per call): the
+ * whole receiver of phy_slot_run() for up to 64 jobs of different shapes (PRB, antenna, layer,
+ * modulation and DMRS counts, LLR format, FP64 re-computation) in one launch per stage and
+ * layer class, so that a server can batch whatever jobs have arrived. A job is one
+ * phy_slot_run() call's configuration and buffers (device pointers, same layouts and rules;
+ * x_hat, sinr and llr may be NULL). On this path the Gram and matched-filter products run in
+ * FP32 (cfg.precision must be PHY_PREC_FP32) and the cover length is the automatic one
+ * (cfg.occ_len 0 or equal to it); other jobs get PHY_ERR_UNSUPPORTED. Each job's outputs are
+ * bitwise those of phy_slot_run() on that job alone.
+ *  - The job table lives in caller-owned, page-locked, device-mapped host memory of
+ *    phy_batch_table_bytes() bytes (e.g. cudaHostAlloc), zeroed before first use, 8-byte
+ *    aligned; the device keeps a copy in a caller-owned device buffer of the same size, zeroed
+ *    before first use. One table pair per batch in flight.
+ *  - phy_batch_workspace_size(): intermediates of a batch (the sum over its jobs); 0 if a job's
+ *    cfg is invalid or n_jobs is outside 1..64.
+ *  - phy_batch_post() (host only, no CUDA call): validates the jobs, lays out their
+ *    intermediates in `workspace` (device, 256-byte aligned), writes the table into table_host
+ *    and rings its doorbell last. Do not post into a table whose previous batch has not
+ *    finished on the device. PHY_ERR_NO_MEMORY if the workspace is too small.
+ *  - phy_batch_launch(): enqueues on `stream` a gate kernel that polls table_host's doorbell at
+ *    most poll_limit times, about 1 us apart (poll_limit < 0: a million, about a second), copies
+ *    a newly posted table into table_dev and then the stage kernels (LS estimation; per layer
+ *    class the Gram/matched-filter and solve kernels, persistent over the table's items). Its
+ *    arguments do not change between batches, so it may be captured once in a CUDA graph and
+ *    replayed per batch; a launch may also be enqueued before the batch is posted (the gate
+ *    waits for it). If no new table arrives within the limit, the stages run on an empty table
+ *    and the gate records a timeout. PHY_ERR_INVALID_ARG if table_host is not mapped.
+ *  - phy_batch_status(): after the launch has completed on the device, PHY_OK if it ran the last
+ *    posted table, PHY_ERR_TIMEOUT if its gate timed out, PHY_ERR_INVALID_ARG if neither (not
+ *    finished, or nothing launched since the post).
+ */
+typedef struct {
+  phy_slot_cfg cfg;
+  const phy_c32* Y;
+  const phy_c32* pilots;
+  const float* sigma2;
+  phy_c32* x_hat;
+  float* sinr;
+  float* llr;
+  uint8_t* flags;
+} phy_job;
+
+size_t phy_batch_table_bytes(void);
+size_t phy_batch_workspace_size(const phy_job* jobs, int32_t n_jobs);
+phy_status phy_batch_post(const phy_job* jobs, int32_t n_jobs, void* table_host, void* workspace,
+                          size_t workspace_bytes);
+phy_status phy_batch_launch(void* table_host, void* table_dev, int64_t poll_limit, void* stream);
+phy_status phy_batch_status(const void* table_host);
+
+/*
  * Tile autotuner for the detection chunk (no counterpart in the paper). Detection runs in chunks
  * of cells: the Gram/matched-filter kernel writes one chunk's intermediates (about 16 MB per
  * 273-PRB cell at 64x16) and the solve kernel reads them back, so the chunk size trades L2

@@ -183,6 +183,13 @@ phy_status slot_run_fit(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32
 
 }  // namespace phy
 
+namespace phy {
+phy_status make_geo_checked(const phy_slot_cfg* cfg, Geo* g) {
+  const phy_status s = make_geo(cfg, g);
+  return s != PHY_OK ? s : check_shape(*g);
+}
+}  // namespace phy
+
 extern "C" {
 
 phy_status phy_debug_set_wait_polls(int32_t kernel, int64_t polls) {

@@ -13,6 +13,7 @@
 // those of the plain kernel on the decompressed grid. Each warp stages the blocks of its antennas'
 // runs (at most four blocks of 1 + 3w bytes per antenna) in shared memory, one antenna row at a
 // time with the lanes over the row's 32-bit words (coalesced), and each thread unpacks its own.
+#include "batch.cuh"
 #include "bfp.cuh"
 #include "launch.h"
 
@@ -31,12 +32,13 @@ struct BfpGrid {
   float scale;
 };
 
+// One (group, DMRS symbol, cell) work item; the block's threads are its antennas.
 template <int L, bool BFP>
-__global__ void __launch_bounds__(kChestThreads)
-    chest_ls_kernel(Geo g, const phy_c32* __restrict__ Y, BfpGrid bfp,
-                    const phy_c32* __restrict__ P, phy_c32* __restrict__ anchors) {
+__device__ __forceinline__ void chest_body(const Geo& g, int grp, int d, int cell,
+                                           const phy_c32* __restrict__ Y, BfpGrid bfp,
+                                           const phy_c32* __restrict__ P,
+                                           phy_c32* __restrict__ anchors) {
   __shared__ cf pil[kMaxLayers][2 * L];
-  const int grp = blockIdx.x, d = blockIdx.y, cell = blockIdx.z;
   const int r = threadIdx.x;
   const int t = (d == 0) ? g.dmrs0 : g.dmrs1;
   const int s = group_start(g, grp);
@@ -120,6 +122,13 @@ __global__ void __launch_bounds__(kChestThreads)
   }
 }
 
+template <int L, bool BFP>
+__global__ void __launch_bounds__(kChestThreads)
+    chest_ls_kernel(Geo g, const phy_c32* __restrict__ Y, BfpGrid bfp,
+                    const phy_c32* __restrict__ P, phy_c32* __restrict__ anchors) {
+  chest_body<L, BFP>(g, blockIdx.x, blockIdx.y, blockIdx.z, Y, bfp, P, anchors);
+}
+
 template <bool BFP>
 cudaError_t launch_chest_any(const Geo& g, const phy_c32* Y, BfpGrid bfp, const phy_c32* pilots,
                              phy_c32* anchors, cudaStream_t st) {
@@ -138,7 +147,37 @@ cudaError_t launch_chest_any(const Geo& g, const phy_c32* Y, BfpGrid bfp, const 
   return cudaGetLastError();
 }
 
+// Batched form: CTAs stride over the LS items (group, DMRS symbol, cell) of every job in the
+// table; the first item of each job also clears the job's error word for the later stages.
+__global__ void __launch_bounds__(kChestThreads) chest_batch_kernel(const BatchTable* __restrict__ t) {
+  __shared__ Geo sg;
+  const int n = t->n_items[kBatchChest][0];
+  for (int w = blockIdx.x; w < n; w += gridDim.x) {
+    int local;
+    const int jb = batch_find(t, kBatchChest, 0, w, local);
+    const BatchJob& J = t->job[jb];
+    batch_load_geo(sg, J.g);
+    __syncthreads();
+    const int grp = local % sg.G, d = (local / sg.G) % sg.n_dmrs, cell = local / (sg.G * sg.n_dmrs);
+    if (local == 0 && threadIdx.x == 0) *J.err = 0;
+    const BfpGrid none{nullptr, 0, 0, 0.f};
+    switch (sg.L) {
+      case 1: chest_body<1, false>(sg, grp, d, cell, J.Y, none, J.pilots, J.anchors); break;
+      case 2: chest_body<2, false>(sg, grp, d, cell, J.Y, none, J.pilots, J.anchors); break;
+      case 4: chest_body<4, false>(sg, grp, d, cell, J.Y, none, J.pilots, J.anchors); break;
+      case 8: chest_body<8, false>(sg, grp, d, cell, J.Y, none, J.pilots, J.anchors); break;
+      default: chest_body<16, false>(sg, grp, d, cell, J.Y, none, J.pilots, J.anchors); break;
+    }
+    __syncthreads();  // the geometry and the pilot stage are rewritten by the next item
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_chest_batch(const BatchTable* t, int grid, cudaStream_t st) {
+  chest_batch_kernel<<<grid, kChestThreads, 0, st>>>(t);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_chest(const Geo& g, const phy_c32* Y, const phy_c32* pilots, phy_c32* anchors,
                          cudaStream_t st) {

@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cstdlib>
 
+#include "batch.cuh"
 #include "launch.h"
 #include "segment.cuh"
 #include "refactor64.cuh"
@@ -88,11 +89,12 @@ __device__ __forceinline__ void cp_async_wait() {
 // per round: 128 threads per symbol, each group of four lanes one 4-RE x (2 layers x 2 comb
 // groups) register tile with the antennas split four ways (a shuffle reduction at the end).
 // The received-grid tiles of the next round load (cp.async) while this round computes.
+// Work item (segment j, cell lc of the chunk that starts at cell cell0).
 template <int NL>
-__global__ void __launch_bounds__(kPrepThreads)
-    seg_prep_fp32_kernel(Geo g, int wmax, int cell0, const phy_c32* __restrict__ anchors,
-                         const phy_c32* __restrict__ Y, float4* __restrict__ ygg,
-                         cf* __restrict__ bvec) {
+__device__ __forceinline__ void seg_prep_body(const Geo& g, int wmax, int cell0, int j, int lc,
+                                              const phy_c32* __restrict__ anchors,
+                                              const phy_c32* __restrict__ Y,
+                                              float4* __restrict__ ygg, cf* __restrict__ bvec) {
   constexpr int NT = kPrepThreads;
   constexpr int NTRI = NL * (NL + 1) / 2;
   constexpr int LP = NL / 2;  // layer pairs
@@ -100,7 +102,7 @@ __global__ void __launch_bounds__(kPrepThreads)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cf* sm = reinterpret_cast<cf*>(smem_raw);
   const int tid = threadIdx.x;
-  const int j = blockIdx.x, lc = blockIdx.y, cell = cell0 + lc;
+  const int cell = cell0 + lc;
   const int nr = g.n_rx, nl = g.n_layers, nds = g.n_dsym;
   const PrepLayout f = prep_layout(NL, g.n_dmrs, nr, wmax);
   cf* Cs = sm + f.off_C;
@@ -291,6 +293,14 @@ __global__ void __launch_bounds__(kPrepThreads)
   }
 }
 
+template <int NL>
+__global__ void __launch_bounds__(kPrepThreads)
+    seg_prep_fp32_kernel(Geo g, int wmax, int cell0, const phy_c32* __restrict__ anchors,
+                         const phy_c32* __restrict__ Y, float4* __restrict__ ygg,
+                         cf* __restrict__ bvec) {
+  seg_prep_body<NL>(g, wmax, cell0, blockIdx.x, blockIdx.y, anchors, Y, ygg, bvec);
+}
+
 // Thread-private scratch in shared memory, interleaved by thread (conflict-free).
 struct SmemScratch {
   cf* base;  // this thread's slot 0
@@ -299,14 +309,6 @@ struct SmemScratch {
 };
 
 
-
-template <int QM>
-__device__ __forceinline__ void store_llr(float* base, size_t idx, cf xt, float s2eff, bool f16) {
-  float l[QM];
-  qam_llr<QM>(xt, s2eff, l);
-#pragma unroll
-  for (int q = 0; q < QM; q += 2) store_llr_pair(base, idx + q, l[q], l[q + 1], f16);
-}
 
 // Gram-block bytes of one (segment, data symbol): NTRI 4-tuples of complex values.
 constexpr uint32_t gram_block_bytes(int NL) { return (uint32_t)(NL * (NL + 1) / 2) * 32u; }
@@ -365,6 +367,36 @@ __device__ __forceinline__ void store_llr_record(float* base, size_t idx, const 
   }
 }
 
+// LLRs of one layer (unbiased symbol xt, effective noise s2eff), or zeros when !ok, stored as
+// the record of layer index li.
+template <int QM>
+__device__ __forceinline__ void demap_store(float* llr, size_t li, cf xt, float s2eff, bool ok,
+                                            bool f16) {
+  float v[QM];
+  if (ok) {
+    qam_llr<QM>(xt, s2eff, v);
+  } else {
+#pragma unroll
+    for (int q = 0; q < QM; ++q) v[q] = 0.f;
+  }
+  store_llr_record<QM>(llr, li * QM, v, f16);
+}
+// As demap_store for a compile-time QM, or for QM = 0 the run-time qm.
+template <int QM>
+__device__ __forceinline__ void demap_store_q(int qm, float* llr, size_t li, cf xt, float s2eff,
+                                              bool ok, bool f16) {
+  if constexpr (QM > 0) {
+    demap_store<QM>(llr, li, xt, s2eff, ok, f16);
+  } else {
+    switch (qm) {
+      case 2: demap_store<2>(llr, li, xt, s2eff, ok, f16); break;
+      case 4: demap_store<4>(llr, li, xt, s2eff, ok, f16); break;
+      case 6: demap_store<6>(llr, li, xt, s2eff, ok, f16); break;
+      default: demap_store<8>(llr, li, xt, s2eff, ok, f16); break;
+    }
+  }
+}
+
 // One CTA per (128 subcarriers, data symbol, cell), one thread per RE. Thread 0 brings the
 // Gram-block 4-tuples of the segments the CTA spans into shared memory with bulk copies
 // (TMA engine, completion counted on an mbarrier); meanwhile every thread loads its matched
@@ -373,32 +405,30 @@ __device__ __forceinline__ void store_llr_record(float* base, size_t idx, const 
 // unbiasing and demapping run transposed, one (RE, layer) item per thread and step, so that a
 // warp's stores cover one contiguous stretch of each output: per-thread stores of whole records
 // (512 B apart) would keep each warp waiting on the store path.
+// Work item (128 subcarriers from k0 = bx 128, data symbol jj, cell lc of the chunk starting at
+// cell0). The barrier `bar` is initialised and its phase `parity` is the one this item's copies
+// complete. QM = 0 takes the modulation from g.qm. Returns false if the Gram-block copies did not
+// land even after a timeout's second wait (the barrier is then unusable for a later item).
 template <int NL, int QM>
-__global__ void __launch_bounds__(kSolveThreads)
-    re_solve_fp32_kernel(Geo g, int cell0, int max_segs, const float4* __restrict__ ygg,
-                         const cf* __restrict__ bvec, const float* __restrict__ sigma2,
-                         const phy_c32* __restrict__ anchors, const phy_c32* __restrict__ Y,
-                         phy_c32* __restrict__ x_hat, float* __restrict__ sinr_out,
-                         float* __restrict__ llr_out, uint8_t* __restrict__ flags_out,
-                         const unsigned* __restrict__ prep_err) {
+__device__ __forceinline__ bool re_solve_body(
+    const Geo& g, int cell0, int bx, int jj, int lc, uint64_t* bar, uint32_t parity,
+    const float4* __restrict__ ygg, const cf* __restrict__ bvec,
+    const float* __restrict__ sigma2, const phy_c32* __restrict__ anchors,
+    const phy_c32* __restrict__ Y, phy_c32* __restrict__ x_hat, float* __restrict__ sinr_out,
+    float* __restrict__ llr_out, uint8_t* __restrict__ flags_out,
+    const unsigned* __restrict__ prep_err) {
   constexpr int NTRI = NL * (NL + 1) / 2;
   constexpr uint32_t kBlk = gram_block_bytes(NL);
   extern __shared__ __align__(128) unsigned char solve_smem[];
   float4* ys = reinterpret_cast<float4*>(solve_smem + solve_scratch_bytes(NL));
-  uint64_t* bar =
-      reinterpret_cast<uint64_t*>(solve_smem + solve_smem_bytes(NL, QM, max_segs) - 16);
   const int nl = g.n_layers, nds = g.n_dsym;
-  const int jj = blockIdx.y, lc = blockIdx.z, cell = cell0 + lc;
-  const int k0 = blockIdx.x * kSolveThreads;
+  const int qm = QM > 0 ? QM : g.qm;
+  const int cell = cell0 + lc;
+  const int k0 = bx * kSolveThreads;
   const int k = k0 + threadIdx.x;
   const bool live = k < g.n_sc;
   const int s0 = seg_of(g, k0), s1 = seg_of(g, min(k0 + kSolveThreads, g.n_sc) - 1);
   const int nseg = s1 - s0 + 1;  // <= max_segs (host-computed bound)
-  if (threadIdx.x == 0) {
-    tc::mbar_init(bar, 1);
-    tc::mbar_fence_init();
-  }
-  __syncthreads();
   if (threadIdx.x == 0) {
     tc::mbar_arrive_expect_tx(bar, (uint32_t)nseg * kBlk);
     for (int s = 0; s < nseg; ++s)
@@ -418,18 +448,18 @@ __global__ void __launch_bounds__(kSolveThreads)
       b[l + 1] = mk(v.z, v.w);
     }
   }
-  bool arrived = tc::mbar_wait(bar, 0, g.wait_solve);
+  bool arrived = tc::mbar_wait(bar, parity, g.wait_solve);
   // after a timeout, let the copies in flight land before the CTA can end
-  if (!arrived) tc::mbar_wait(bar, 0, kWaitSolveDefault);
+  const bool landed = arrived || tc::mbar_wait(bar, parity, kWaitSolveDefault);
   // one decision for the CTA (it has barriers below); a timed-out Gram/matched-filter kernel
   // (its error word) voids every RE as a wait timeout here would
   arrived = __syncthreads_and(arrived && (threadIdx.x != 0 || *prep_err == 0));
   const size_t ridx = ((size_t)cell * nds + jj) * g.n_sc + (live ? k : k0);
   if (!arrived) {
     if (live) flags_out[ridx] = 8;
-    return;
+    return __syncthreads_and(landed);
   }
-  if (NL != 16 && !live) return;
+  if (NL != 16 && !live) return true;
   const int j = seg_of(g, live ? k : k0);
   const float s2 = sigma2[cell];
   const float be0 = seg_beta(g, j, k, 0), be1 = seg_beta(g, j, k, 1);
@@ -550,16 +580,7 @@ __global__ void __launch_bounds__(kSolveThreads)
       const bool okr = oks[re] != 0;
       const LayerOut o = layer_stats(s2, ds[re * kXs + l]);
       const size_t li = (r0 + re) * nl + l;
-      if (llr_out) {
-        float v[QM];
-        if (okr) {
-          qam_llr<QM>(o.inv_mu * xl, o.s2eff, v);
-        } else {
-#pragma unroll
-          for (int q = 0; q < QM; ++q) v[q] = 0.f;
-        }
-        store_llr_record<QM>(llr_out, li * QM, v, g.llr_f16);
-      }
+      if (llr_out) demap_store_q<QM>(qm, llr_out, li, o.inv_mu * xl, o.s2eff, okr, g.llr_f16);
       if (sinr_out) sinr_out[li] = okr ? o.sinr : 0.f;
       if (x_hat) st(x_hat + li, okr ? xl : mk(0.f, 0.f));
     }
@@ -572,15 +593,111 @@ __global__ void __launch_bounds__(kSolveThreads)
       if (ok) {
         if (x_hat) st(x_hat + li, x[l]);
         if (sinr_out) sinr_out[li] = o.sinr;
-        if (llr_out) store_llr<QM>(llr_out, li * QM, o.inv_mu * x[l], o.s2eff, g.llr_f16);
+        if (llr_out) demap_store_q<QM>(qm, llr_out, li, o.inv_mu * x[l], o.s2eff, true, g.llr_f16);
       } else {
         if (x_hat) st(x_hat + li, mk(0.f, 0.f));
         if (sinr_out) sinr_out[li] = 0.f;
-        if (llr_out)
-          for (int q = 0; q < QM; q += 2) store_llr_pair(llr_out, li * QM + q, 0.f, 0.f, g.llr_f16);
+        if (llr_out) demap_store_q<QM>(qm, llr_out, li, mk(0.f, 0.f), 1.f, false, g.llr_f16);
       }
     }
   }
+  return true;
+}
+
+template <int NL, int QM>
+__global__ void __launch_bounds__(kSolveThreads)
+    re_solve_fp32_kernel(Geo g, int cell0, int max_segs, const float4* __restrict__ ygg,
+                         const cf* __restrict__ bvec, const float* __restrict__ sigma2,
+                         const phy_c32* __restrict__ anchors, const phy_c32* __restrict__ Y,
+                         phy_c32* __restrict__ x_hat, float* __restrict__ sinr_out,
+                         float* __restrict__ llr_out, uint8_t* __restrict__ flags_out,
+                         const unsigned* __restrict__ prep_err) {
+  extern __shared__ __align__(128) unsigned char solve_smem[];
+  uint64_t* bar =
+      reinterpret_cast<uint64_t*>(solve_smem + solve_smem_bytes(NL, QM, max_segs) - 16);
+  if (threadIdx.x == 0) {
+    tc::mbar_init(bar, 1);
+    tc::mbar_fence_init();
+  }
+  __syncthreads();
+  re_solve_body<NL, QM>(g, cell0, blockIdx.x, blockIdx.y, blockIdx.z, bar, 0, ygg, bvec, sigma2,
+                        anchors, Y, x_hat, sinr_out, llr_out, flags_out, prep_err);
+}
+
+// Batched forms (one launch per layer class serves every job of that class in the table).
+// Segment stage: CTAs stride over the (segment, cell) items of the class's jobs.
+template <int NL>
+__global__ void __launch_bounds__(kPrepThreads)
+    seg_prep_batch_kernel(const BatchTable* __restrict__ t) {
+  __shared__ Geo sg;
+  constexpr int cls = batch_class(NL);
+  const int n = t->n_items[kBatchSeg][cls];
+  for (int w = blockIdx.x; w < n; w += gridDim.x) {
+    int local;
+    const BatchJob& J = t->job[batch_find(t, kBatchSeg, cls, w, local)];
+    batch_load_geo(sg, J.g);
+    __syncthreads();
+    seg_prep_body<NL>(sg, J.wmax, 0, local % sg.n_seg, local / sg.n_seg, J.anchors, J.Y, J.ygg,
+                      J.bvec);
+    __syncthreads();
+  }
+}
+
+// Solve stage: CTAs stride over the (128 subcarriers, data symbol, cell) items of the class's
+// jobs; one mbarrier per CTA counts every item's Gram-block copies, item i completing phase
+// i mod 2. The modulation is each job's own (run-time QM).
+template <int NL>
+__global__ void __launch_bounds__(kSolveThreads)
+    re_solve_batch_kernel(const BatchTable* __restrict__ t, int smem_bytes) {
+  extern __shared__ __align__(128) unsigned char solve_smem[];
+  __shared__ Geo sg;
+  constexpr int cls = batch_class(NL);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(solve_smem + smem_bytes - 16);
+  if (threadIdx.x == 0) {
+    tc::mbar_init(bar, 1);
+    tc::mbar_fence_init();
+  }
+  __syncthreads();
+  const int n = t->n_items[kBatchSolve][cls];
+  uint32_t it = 0;
+  for (int w = blockIdx.x; w < n; w += gridDim.x, ++it) {
+    int local;
+    const BatchJob& J = t->job[batch_find(t, kBatchSolve, cls, w, local)];
+    batch_load_geo(sg, J.g);
+    // the previous item's generic accesses to shared memory come before this item's bulk copies
+    if (threadIdx.x == 0) tc::fence_proxy_async();
+    __syncthreads();
+    const int nb = (sg.n_sc + kSolveThreads - 1) / kSolveThreads;
+    const int bx = local % nb, jj = (local / nb) % sg.n_dsym, lc = local / (nb * sg.n_dsym);
+    const bool usable = re_solve_body<NL, 0>(sg, 0, bx, jj, lc, bar, it & 1, J.ygg, J.bvec,
+                                             J.sigma2, J.anchors, J.Y, J.x_hat, J.sinr, J.llr,
+                                             J.flags, J.err);
+    if (!__syncthreads_and(usable)) break;  // copies still in flight: the barrier is unusable
+  }
+}
+
+template <int NL>
+cudaError_t launch_batch_class(const BatchTable* t, int grid_seg, int grid_solve,
+                               size_t smem_seg, size_t smem_solve, cudaStream_t st) {
+  static size_t cfg_seg[kMaxDevices] = {}, cfg_solve[kMaxDevices] = {};
+  const int dev = current_device();
+  if (smem_seg > cfg_seg[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(seg_prep_batch_kernel<NL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_seg);
+    if (e != cudaSuccess) return e;
+    cfg_seg[dev] = smem_seg;
+  }
+  if (smem_solve > cfg_solve[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(re_solve_batch_kernel<NL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_solve);
+    if (e != cudaSuccess) return e;
+    cfg_solve[dev] = smem_solve;
+  }
+  seg_prep_batch_kernel<NL><<<grid_seg, kPrepThreads, smem_seg, st>>>(t);
+  re_solve_batch_kernel<NL><<<grid_solve, kSolveThreads, smem_solve, st>>>(t, (int)smem_solve);
+  return cudaGetLastError();
 }
 
 struct Sizes {
@@ -697,6 +814,107 @@ cudaError_t run_chunks(const Geo& g, int wmax, const Sizes& s, const phy_c32* an
 }
 
 }  // namespace
+
+int nl_class_of(int n_layers) { return nl_class(n_layers); }
+
+// ---------------------------------------------------------------- batched receiver, host side
+int batch_wmax(const Geo& g) { return host_max_segment_width(g); }
+int batch_max_segs(const Geo& g) { return max_segments_per_block(g); }
+size_t batch_ygg_bytes(const Geo& g) { return sizes(g, 1).ygg_per_cell * g.n_cells; }
+size_t batch_bvec_bytes(const Geo& g) { return sizes(g, 1).b_per_cell * g.n_cells; }
+
+namespace {
+
+// Shared memory and persistent grids of one layer class's batched kernels, bounded over every
+// geometry the batched path accepts for that class (automatic cover length, 1..275 PRB, one or
+// two DMRS symbols, up to 64 antennas), so that one captured launch serves any batch.
+struct BatchClassLaunch {
+  size_t smem_seg = 0, smem_solve = 0;
+  int grid_seg = 0, grid_solve = 0;
+};
+
+// Shared-memory bounds of one class (pure host arithmetic, no CUDA call).
+template <int NL>
+BatchClassLaunch batch_class_smem() {
+  static const BatchClassLaunch b = [] {
+    BatchClassLaunch r;
+    const int L = NL <= 2 ? 1 : NL / 2;  // the automatic cover of the class's layer counts
+    int wmax = 1, msegs = 1;
+    for (int prb = 1; prb <= 275; ++prb) {
+      Geo g{};
+      g.n_sc = 12 * prb;
+      g.n_comb = g.n_sc / 2;
+      g.L = L;
+      if (g.n_comb < L) continue;
+      g.G = (g.n_comb + L - 1) / L;
+      g.n_seg = g.G > 1 ? g.G - 1 : 1;
+      wmax = std::max(wmax, host_max_segment_width(g));
+      msegs = std::max(msegs, max_segments_per_block(g));
+    }
+    r.smem_seg = (size_t)prep_layout(NL, 2, kMaxRx, wmax).total * sizeof(cf);
+    r.smem_solve = solve_smem_bytes(NL, 0, msegs);
+    return r;
+  }();
+  return b;
+}
+
+// The bounds plus persistent grids filling every SM at the kernels' occupancy (per device).
+template <int NL>
+BatchClassLaunch batch_class_launch() {
+  static BatchClassLaunch on[kMaxDevices];
+  BatchClassLaunch& b = on[current_device()];
+  if (b.grid_seg > 0) return b;
+  b = batch_class_smem<NL>();
+  const int sms = device_sm_count();
+  int occ = 0;
+  cudaFuncSetAttribute(seg_prep_batch_kernel<NL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)b.smem_seg);
+  cudaFuncSetAttribute(re_solve_batch_kernel<NL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)b.smem_solve);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, seg_prep_batch_kernel<NL>, kPrepThreads,
+                                                    b.smem_seg) != cudaSuccess || occ < 1)
+    occ = 1;
+  b.grid_seg = sms * occ;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, re_solve_batch_kernel<NL>,
+                                                    kSolveThreads, b.smem_solve) != cudaSuccess ||
+      occ < 1)
+    occ = 1;
+  b.grid_solve = sms * occ;
+  return b;
+}
+
+template <int NL>
+cudaError_t launch_batch_nl(const BatchTable* t, cudaStream_t st) {
+  const BatchClassLaunch b = batch_class_launch<NL>();
+  return launch_batch_class<NL>(t, b.grid_seg, b.grid_solve, b.smem_seg, b.smem_solve, st);
+}
+
+}  // namespace
+
+bool batch_geometry_fits(const Geo& g) {
+  const int NL = nl_class(g.n_layers);
+  size_t seg = 0, solve = 0;
+  BatchClassLaunch b;
+  switch (NL) {
+    case 2: b = batch_class_smem<2>(); break;
+    case 4: b = batch_class_smem<4>(); break;
+    case 8: b = batch_class_smem<8>(); break;
+    default: b = batch_class_smem<16>(); break;
+  }
+  seg = b.smem_seg;
+  solve = b.smem_solve;
+  const PrepLayout f = prep_layout(NL, g.n_dmrs, g.n_rx, host_max_segment_width(g));
+  return (size_t)f.total * sizeof(cf) <= seg &&
+         solve_smem_bytes(NL, 0, max_segments_per_block(g)) <= solve;
+}
+
+cudaError_t launch_batch_stages(const BatchTable* t, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = launch_batch_nl<2>(t, st)) != cudaSuccess) return e;
+  if ((e = launch_batch_nl<4>(t, st)) != cudaSuccess) return e;
+  if ((e = launch_batch_nl<8>(t, st)) != cudaSuccess) return e;
+  return launch_batch_nl<16>(t, st);
+}
 
 int host_max_segment_width(const Geo& g) {
   auto start = [&](int grp) { return std::min(g.L * grp, g.n_comb - g.L); };

@@ -109,4 +109,21 @@ cudaError_t launch_detect_h(const Geo& g, const phy_c32* H, const phy_c32* Y, co
 cudaError_t launch_llr(const Geo& g, const phy_c32* x_hat, const float* sinr, float* llr,
                        cudaStream_t st);
 
+// Validated geometry of a configuration (make_geo plus the shape checks of the single-job path).
+phy_status make_geo_checked(const phy_slot_cfg* cfg, Geo* g);
+// Kernel layer class (2, 4, 8 or 16) of a layer count.
+int nl_class_of(int n_layers);
+
+// Batched receiver (batch.cuh holds the table). Per-job intermediate sizes and launch bounds,
+// the batched LS kernel, and the per-class segment and solve kernels.
+struct BatchTable;
+size_t batch_anchor_bytes(const Geo& g);
+size_t batch_ygg_bytes(const Geo& g);
+size_t batch_bvec_bytes(const Geo& g);
+int batch_wmax(const Geo& g);
+int batch_max_segs(const Geo& g);
+bool batch_geometry_fits(const Geo& g);
+cudaError_t launch_chest_batch(const BatchTable* t, int grid, cudaStream_t st);
+cudaError_t launch_batch_stages(const BatchTable* t, cudaStream_t st);
+
 }  // namespace phy

@@ -31,6 +31,13 @@ class CSlotCfg(ctypes.Structure):
                 ("llr_format", ctypes.c_int32)]
 
 
+class CJob(ctypes.Structure):
+    """phy_job: one job of a batched call (configuration and device buffers)."""
+    _fields_ = [("cfg", CSlotCfg), ("Y", ctypes.c_void_p), ("pilots", ctypes.c_void_p),
+                ("sigma2", ctypes.c_void_p), ("x_hat", ctypes.c_void_p),
+                ("sinr", ctypes.c_void_p), ("llr", ctypes.c_void_p), ("flags", ctypes.c_void_p)]
+
+
 # Every entry point declared in include/phy.h, with its ctypes signature.
 _P = ctypes.c_void_p
 _SIGS = {
@@ -52,6 +59,11 @@ _SIGS = {
     "phy_detect_stage": (ctypes.c_int, [_P, ctypes.c_int32] + [_P] * 8 + [ctypes.c_size_t, _P]),
     "phy_autotune": (ctypes.c_int, [_P] * 9 + [ctypes.c_size_t, _P, _P]),
     "phy_autotune_clear": (None, []),
+    "phy_batch_table_bytes": (ctypes.c_size_t, []),
+    "phy_batch_workspace_size": (ctypes.c_size_t, [_P, ctypes.c_int32]),
+    "phy_batch_post": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_size_t]),
+    "phy_batch_launch": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
+    "phy_batch_status": (ctypes.c_int, [_P]),
     "phy_noise_est": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "phy_slot_run_est": (ctypes.c_int, [_P, ctypes.c_int32] + [_P] * 8 + [ctypes.c_size_t, _P]),
     "phy_noise_track": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_float, _P, _P, _P, _P,
@@ -150,6 +162,8 @@ class SlotConfig:
 def _ptr(t) -> Optional[int]:
     if t is None:
         return None
+    if isinstance(t, int):  # a raw device address
+        return t
     if not t.is_contiguous():  # the library indexes dense row-major arrays
         raise ValueError("libphy arguments must be contiguous tensors")
     return t.data_ptr()
@@ -476,3 +490,50 @@ class SlotBuffers:
         if ws == 0:
             raise PhyError("phy_workspace_size", 1)
         self.workspace = torch.empty((ws,), dtype=torch.uint8, device=device)
+
+
+# ---------------------------------------------------------------------------------------------
+# batched receiver (phy_batch_*)
+# ---------------------------------------------------------------------------------------------
+
+BATCH_MAX_JOBS = 64
+
+
+def _jobs_array(jobs):
+    """jobs: sequence of (SlotConfig, Y, pilots, sigma2, x_hat, sinr, llr, flags) tuples."""
+    arr = (CJob * len(jobs))()
+    for i, (cfg, Y, P, s2, x, sn, l, f) in enumerate(jobs):
+        arr[i] = CJob(cfg.c(), _ptr(Y), _ptr(P), _ptr(s2), _ptr(x), _ptr(sn), _ptr(l), _ptr(f))
+    return arr
+
+
+def batch_table_bytes() -> int:
+    return int(load().phy_batch_table_bytes())
+
+
+def batch_workspace_size(jobs) -> int:
+    """phy_batch_workspace_size for jobs given as (cfg, ...) tuples (only cfg is read)."""
+    arr = (CJob * len(jobs))()
+    for i, j in enumerate(jobs):
+        arr[i] = CJob(j[0].c(), None, None, None, None, None, None, None)
+    return int(load().phy_batch_workspace_size(arr, len(jobs)))
+
+
+def batch_post(jobs, table_host, workspace):
+    """phy_batch_post: lays out the batch in `workspace` and rings the doorbell of the pinned
+    host table (a uint8 tensor of batch_table_bytes())."""
+    arr = _jobs_array(jobs)
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check("phy_batch_post", load().phy_batch_post(arr, len(jobs), _ptr(table_host),
+                                                   _ptr(workspace), ws_bytes))
+
+
+def batch_launch(table_host, table_dev, poll_limit: int = -1, stream=None):
+    """phy_batch_launch: gate (bounded wait for the doorbell) and stage kernels on `stream`."""
+    _check("phy_batch_launch", load().phy_batch_launch(_ptr(table_host), _ptr(table_dev),
+                                                       int(poll_limit), _stream(stream)))
+
+
+def batch_status(table_host) -> int:
+    """phy_batch_status as a status code (0 OK, 5 timed out, 1 not finished or not launched)."""
+    return int(load().phy_batch_status(_ptr(table_host)))

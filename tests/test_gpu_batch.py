@@ -1,0 +1,154 @@
+"""Batched receiver on the GPU: jobs of different shapes in one launch per stage and layer
+class, each job's outputs bitwise those of phy_slot_run on that job alone; a captured graph of
+the launch serving changing batches; and the gate's bounded wait running out when the host never
+posts a table."""
+import numpy as np
+import pytest
+
+from paper_2510_07843_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_07843_gb300 import build, phy
+    build.build()
+    phy.load()
+    return torch.device("cuda:0")
+
+
+# (spec, seed, extra cfg) of a heterogeneous batch: every layer class, one and two DMRS
+# symbols, every modulation, both LLR formats, multi-cell jobs, FP64 re-computation enabled
+MIX = [
+    (S.spec_massive_mimo(n_cells=1, n_prb=24), 501, {}),
+    (S.SlotSpec(n_cells=2, n_prb=4, n_rx=4, n_layers=1, qm=2, dmrs_sym=(2,), snr_db=12.0), 502,
+     {}),
+    (S.spec_carrier_273prb(n_prb=40), 503, {"llr_format": "f16"}),
+    (S.SlotSpec(n_prb=17, n_rx=32, n_layers=7, qm=6, dmrs_sym=(3,), snr_db=25.0, n_taps=6), 504,
+     {"fp64_refactor": True}),
+    (S.SlotSpec(n_prb=9, n_rx=64, n_layers=12, qm=8, dmrs_sym=(2, 11), snr_db=30.0), 505, {}),
+    (S.SlotSpec(n_prb=33, n_rx=16, n_layers=3, qm=4, dmrs_sym=(2, 11), snr_db=18.0,
+                doppler_hz=300.0), 506, {}),
+    (S.SlotSpec(n_prb=1, n_rx=2, n_layers=2, qm=2, dmrs_sym=(0,), n_sym=2), 507, {}),
+]
+
+
+def _prepare(dev, entries):
+    """Inputs on the device and two output sets (batched, alone) per job."""
+    import torch
+    from paper_2510_07843_gb300 import phy
+    jobs = []
+    for spec, seed, kw in entries:
+        sl = S.make_slot(spec, seed, keep_h=False)
+        cfg = phy.SlotConfig.from_spec(spec, **kw)
+        inp = [torch.from_numpy(a).to(dev) for a in (sl.Y, sl.pilots, sl.sigma2)]
+        outs = [phy.SlotBuffers(cfg, device=dev, with_inputs=False) for _ in range(2)]
+        for b in outs:
+            b.flags.fill_(0xEE)
+        jobs.append((cfg, inp, outs))
+    return jobs
+
+
+def _tuples(jobs, which=0):
+    return [(cfg, *inp, o[which].x_hat, o[which].sinr, o[which].llr, o[which].flags)
+            for cfg, inp, o in jobs]
+
+
+def _tables(dev):
+    import torch
+    from paper_2510_07843_gb300 import phy
+    n = phy.batch_table_bytes()
+    host = torch.zeros(n, dtype=torch.uint8).pin_memory()
+    devt = torch.zeros(n, dtype=torch.uint8, device=dev)
+    return host, devt
+
+
+def _alone(jobs):
+    from paper_2510_07843_gb300 import phy
+    for cfg, (Y, P, s2), o in jobs:
+        b = o[1]
+        phy.slot_run(cfg, Y, P, s2, b.x_hat, b.sinr, b.llr, b.flags, b.workspace)
+
+
+def _assert_same(jobs):
+    import torch
+    for cfg, _, (a, b) in jobs:
+        for k in ("x_hat", "sinr", "llr", "flags"):
+            assert torch.equal(getattr(a, k), getattr(b, k)), (cfg, k)
+        assert not torch.any(a.flags == 0xEE)
+
+
+def test_mixed_batch_equals_each_job_alone(dev):
+    import torch
+    from paper_2510_07843_gb300 import phy
+    jobs = _prepare(dev, MIX)
+    host, devt = _tables(dev)
+    ws = torch.empty(phy.batch_workspace_size(_tuples(jobs)), dtype=torch.uint8, device=dev)
+    phy.batch_post(_tuples(jobs), host, ws)
+    phy.batch_launch(host, devt)
+    _alone(jobs)
+    torch.cuda.synchronize()
+    assert phy.batch_status(host) == 0
+    _assert_same(jobs)
+
+
+def test_captured_launch_serves_changing_batches(dev):
+    """One CUDA graph of phy_batch_launch, replayed for three different posted batches (the
+    jobs in another order and mix each time)."""
+    import torch
+    from paper_2510_07843_gb300 import phy
+    jobs = _prepare(dev, MIX)
+    host, devt = _tables(dev)
+    ws = torch.empty(phy.batch_workspace_size(_tuples(jobs)), dtype=torch.uint8, device=dev)
+    st = torch.cuda.Stream(device=dev)
+    # a first batch configures the kernels before capture
+    phy.batch_post(_tuples(jobs[:1]), host, ws)
+    phy.batch_launch(host, devt, stream=st)
+    st.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        phy.batch_launch(host, devt, stream=st)
+    _alone(jobs)
+    for order in ([6, 0, 3], [1, 2, 4, 5], list(range(7))[::-1]):
+        sub = [jobs[i] for i in order]
+        for _, _, o in sub:
+            o[0].flags.fill_(0xEE)
+        phy.batch_post(_tuples(sub), host, ws)
+        with torch.cuda.stream(st):
+            g.replay()
+        st.synchronize()
+        torch.cuda.synchronize()
+        assert phy.batch_status(host) == 0
+        _assert_same(sub)
+
+
+def test_gate_times_out_when_nothing_is_posted(dev):
+    """The gate's bounded wait runs out (about 2 ms of polls) when the host never rings: the
+    stages run on an empty table, no output is touched, the status is PHY_ERR_TIMEOUT; the next
+    posted batch runs normally."""
+    import torch
+    from paper_2510_07843_gb300 import phy
+    jobs = _prepare(dev, MIX[:2])
+    host, devt = _tables(dev)
+    ws = torch.empty(phy.batch_workspace_size(_tuples(jobs)), dtype=torch.uint8, device=dev)
+    phy.batch_launch(host, devt, poll_limit=2000)
+    torch.cuda.synchronize()
+    assert phy.batch_status(host) == 5
+    for _, _, o in jobs:
+        assert torch.all(o[0].flags == 0xEE)
+    # a batch that ran, then a launch without a new post: the old table is not run again
+    phy.batch_post(_tuples(jobs), host, ws)
+    phy.batch_launch(host, devt, poll_limit=2000)
+    torch.cuda.synchronize()
+    assert phy.batch_status(host) == 0
+    for _, _, o in jobs:
+        o[0].flags.fill_(0xEE)
+    phy.batch_launch(host, devt, poll_limit=2000)
+    torch.cuda.synchronize()
+    assert phy.batch_status(host) == 5
+    for _, _, o in jobs:
+        assert torch.all(o[0].flags == 0xEE)
