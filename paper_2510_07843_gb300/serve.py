@@ -21,6 +21,8 @@ import time
 from dataclasses import dataclass, field
 from typing import Callable, Dict, List, Optional, Sequence, Tuple
 
+import numpy as np
+
 from . import phy
 
 DEADLINE_S = 0.5e-3  # one 30 kHz slot
@@ -315,3 +317,208 @@ def latency_summary(jobs: Sequence[Job], deadline: float = DEADLINE_S,
         out.update(service_p50_ms=float(np.percentile(sv, 50)),
                    service_p99_ms=float(np.percentile(sv, 99)))
     return out
+
+
+# ---------------------------------------------------------------------------------------------
+# Heterogeneous continuous batching over the batched receiver (phy_batch_*)
+# ---------------------------------------------------------------------------------------------
+
+_ALIGN = 256
+
+
+def _up(v: int) -> int:
+    return (v + _ALIGN - 1) // _ALIGN * _ALIGN
+
+
+@dataclass
+class MixedJob:
+    """One cell's slot with its own shape; inputs are device tensors [1][...] that stay resident
+    until the job completes. The server fills llr and flags (views into its lane arena, valid
+    until that lane's next batch, or copies with keep) and done."""
+    cfg: phy.SlotConfig
+    Y: object
+    pilots: object
+    sigma2: object           # device tensor [1] float32
+    arrival: float = 0.0
+    job_id: int = 0
+    llr: object = None
+    flags: object = None
+    done: float = field(default=float("nan"))
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+    @property
+    def n_res(self) -> int:
+        return self.cfg.n_cells * self.cfg.n_dsym * self.cfg.n_sc
+
+
+def mixed_job_bytes(cfg: phy.SlotConfig) -> int:
+    """Device bytes a job takes in a lane's arena: its intermediates and its LLR and flag
+    outputs (x_hat and SINR are not kept by the server)."""
+    one = (cfg, None, None, None, None, None, None, None)
+    llr_el = 2 if cfg.llr_format == "f16" else 4
+    n_re = cfg.n_cells * cfg.n_dsym * cfg.n_sc
+    return (phy.batch_workspace_size([one]) + _up(n_re * cfg.n_layers * cfg.qm * llr_el)
+            + _up(n_re))
+
+
+class _Lane:
+    """One batch in flight: its arena, its pinned job table and device copy, its stream and the
+    CUDA graph captured on phy_batch_launch for them."""
+
+    def __init__(self, device, arena_bytes: int, poll_limit: int):
+        import torch
+        self.stream = torch.cuda.Stream(device=device)
+        self.arena = torch.empty(arena_bytes, dtype=torch.uint8, device=device)
+        n = phy.batch_table_bytes()
+        self.host = torch.zeros(n, dtype=torch.uint8).pin_memory()
+        self.devt = torch.zeros(n, dtype=torch.uint8, device=device)
+        self.poll_limit = poll_limit
+        self.graph = None
+
+    def capture(self, warm: Sequence["MixedJob"]):
+        """Runs one real batch (configures the kernels), then captures the launch."""
+        import torch
+        self.post(warm)
+        phy.batch_launch(self.host, self.devt, self.poll_limit, stream=self.stream)
+        self.stream.synchronize()
+        if phy.batch_status(self.host) != 0:
+            raise RuntimeError("warm-up batch did not run")
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=self.stream):
+            phy.batch_launch(self.host, self.devt, self.poll_limit, stream=self.stream)
+
+    def post(self, jobs: Sequence["MixedJob"]):
+        """Lays the batch out in the arena (intermediates, then each job's LLRs and flags) and
+        rings the table's doorbell."""
+        import torch
+        tuples = [(j.cfg, j.Y, j.pilots, j.sigma2, None, None, None, None) for j in jobs]
+        off = _up(phy.batch_workspace_size(tuples))
+        ws = self.arena[:off]
+        for i, j in enumerate(jobs):
+            c = j.cfg
+            shape = (c.n_cells, c.n_dsym, c.n_sc, c.n_layers, c.qm)
+            dt = torch.float16 if c.llr_format == "f16" else torch.float32
+            n = int(np.prod(shape)) * (2 if c.llr_format == "f16" else 4)
+            j.llr = self.arena[off:off + n].view(dt).view(shape)
+            off = _up(off + n)
+            nf = c.n_cells * c.n_dsym * c.n_sc
+            j.flags = self.arena[off:off + nf].view(c.n_cells, c.n_dsym, c.n_sc)
+            off = _up(off + nf)
+            tuples[i] = (c, j.Y, j.pilots, j.sigma2, None, None, j.llr, j.flags)
+        if off > self.arena.numel():
+            raise ValueError("batch larger than the lane arena")
+        phy.batch_post(tuples, self.host, ws)
+
+
+class BatchServer:
+    """Continuous batching of jobs of any shape: whatever has arrived goes into the next free
+    lane's batch (arrival order, up to 64 jobs and the lane arena's bytes), served by one replay
+    of the lane's captured graph of the batched receiver. The arenas are sized from the device's
+    free memory when the server starts (admission by device memory). Up to `lanes` batches are
+    in flight at once; a batch's completion is its end event on the GPU clock, mapped to the host
+    clock by an event recorded when serving starts."""
+
+    def __init__(self, device="cuda", lanes: int = 2, memory_fraction: float = 0.25,
+                 max_arena: int = 4 << 30, max_jobs: int = phy.BATCH_MAX_JOBS,
+                 poll_limit: int = -1, clock: Callable[[], float] = time.perf_counter):
+        import torch
+        self.device = torch.device(device)
+        free, _ = torch.cuda.mem_get_info(self.device)
+        self.arena_bytes = int(min(free * memory_fraction / max(1, lanes), max_arena))
+        self.max_jobs = min(max_jobs, phy.BATCH_MAX_JOBS)
+        self.clock = clock
+        self.lanes = [_Lane(self.device, self.arena_bytes, poll_limit) for _ in range(lanes)]
+        self.batches = 0
+        self.batch_sizes: List[int] = []
+        self.service: List[float] = []
+        self._bytes: Dict[Tuple, int] = {}
+
+    def job_bytes(self, cfg: phy.SlotConfig) -> int:
+        k = config_key(cfg) + (("n_cells", cfg.n_cells),)
+        if k not in self._bytes:
+            self._bytes[k] = mixed_job_bytes(cfg)
+        return self._bytes[k]
+
+    def prepare(self, warm: "MixedJob"):
+        """Captures every lane's graph (before timing), warming each on one job."""
+        for ln in self.lanes:
+            ln.capture([warm])
+
+    def _take(self, waiting: "collections.deque") -> List["MixedJob"]:
+        """The longest arrival-order prefix of the waiting jobs that fits one lane."""
+        batch, used = [], 0
+        while waiting and len(batch) < self.max_jobs:
+            b = self.job_bytes(waiting[0].cfg)
+            if b > self.arena_bytes:
+                raise ValueError(f"job {waiting[0].job_id} needs {b} bytes, above the arena")
+            if used + b + _ALIGN > self.arena_bytes:
+                break
+            used += b
+            batch.append(waiting.popleft())
+        return batch
+
+    def run(self, jobs: Sequence["MixedJob"], realtime: bool = True,
+            keep: bool = False) -> List["MixedJob"]:
+        """Serves jobs in arrival order (see SlotServer.run for realtime and the clock)."""
+        import collections
+        import torch
+        pending = sorted(jobs, key=lambda j: j.arrival)
+        waiting: collections.deque = collections.deque()
+        finished: List[MixedJob] = []
+        inflight = collections.deque()  # (lane, start event, end event, batch)
+        free = list(range(len(self.lanes)))
+        torch.cuda.synchronize(self.device)
+        ref = torch.cuda.Event(enable_timing=True)
+        ref.record(self.lanes[0].stream)
+        t0 = self.clock()
+        ref.synchronize()
+
+        def retire(block: bool):
+            while inflight and (block or inflight[0][2].query()):
+                li, e0, e1, batch = inflight.popleft()
+                e1.synchronize()
+                st = phy.batch_status(self.lanes[li].host)
+                if st != 0:
+                    raise RuntimeError(f"batch of {len(batch)} jobs ended with status {st}")
+                t = ref.elapsed_time(e1) * 1e-3
+                self.service.append(e0.elapsed_time(e1) * 1e-3)
+                for j in batch:
+                    j.done = t
+                    if keep:
+                        j.llr, j.flags = j.llr.clone(), j.flags.clone()
+                finished.extend(batch)
+                free.append(li)
+                block = False
+
+        i = 0
+        while i < len(pending) or waiting:
+            now = self.clock() - t0
+            while i < len(pending) and (not realtime or pending[i].arrival <= now):
+                waiting.append(pending[i])
+                i += 1
+            retire(False)
+            if not waiting:
+                if realtime and i < len(pending):
+                    while self.clock() - t0 < pending[i].arrival:
+                        retire(False)
+                continue
+            if not free:
+                retire(True)
+            li = free.pop(0)
+            ln = self.lanes[li]
+            batch = self._take(waiting)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(ln.stream)
+            ln.post(batch)
+            with torch.cuda.stream(ln.stream):
+                ln.graph.replay()
+            e1.record(ln.stream)
+            inflight.append((li, e0, e1, batch))
+            self.batches += 1
+            self.batch_sizes.append(len(batch))
+        while inflight:
+            retire(True)
+        return finished

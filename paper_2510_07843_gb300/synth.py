@@ -103,6 +103,36 @@ def spec_massive_mimo(**kw) -> SlotSpec:
     return SlotSpec(**base)
 
 
+# Serving workload: a stream of per-cell uplink jobs of uneven shapes.
+SERVING_RX = (4, 16, 32, 64)
+SERVING_QM = (2, 4, 6, 8)
+
+
+def spec_serving_job(rng: np.random.Generator) -> SlotSpec:
+    """One job of the serving stream: 4-273 PRB (uniform), 4/16/32/64 Rx, 1-16 layers (uniform,
+    clamped to the antenna count), QPSK to 256-QAM, DMRS 2 and 11, the 23-tap 300 ns PDP with
+    Jakes 100 Hz Doppler, 10-30 dB SNR (uniform)."""
+    n_rx = int(rng.choice(SERVING_RX))
+    return SlotSpec(n_cells=1, n_prb=int(rng.integers(4, 274)), n_rx=n_rx,
+                    n_layers=min(int(rng.integers(1, 17)), n_rx), qm=int(rng.choice(SERVING_QM)),
+                    dmrs_sym=(2, 11), snr_db=float(rng.uniform(10.0, 30.0)), n_taps=23,
+                    delay_spread_s=300e-9, doppler_hz=100.0, rho_rx=0.0)
+
+
+def serving_arrivals(n_cells: int, rate_hz: float, duration_s: float, seed: int):
+    """Poisson arrivals of every cell (exponential gaps of mean 1/rate_hz) within duration_s:
+    a list of (time in seconds, cell), sorted by time."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for c in range(n_cells):
+        t = rng.exponential(1.0 / rate_hz)
+        while t < duration_s:
+            out.append((float(t), c))
+            t += rng.exponential(1.0 / rate_hz)
+    out.sort()
+    return out
+
+
 # ----------------------------------------------------------------------------------------------
 # Transmitter
 # ----------------------------------------------------------------------------------------------

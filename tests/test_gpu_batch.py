@@ -2,6 +2,8 @@
 class, each job's outputs bitwise those of phy_slot_run on that job alone; a captured graph of
 the launch serving changing batches; and the gate's bounded wait running out when the host never
 posts a table."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -152,3 +154,35 @@ def test_gate_times_out_when_nothing_is_posted(dev):
     assert phy.batch_status(host) == 5
     for _, _, o in jobs:
         assert torch.all(o[0].flags == 0xEE)
+
+
+def test_batch_server_mixed_stream_equals_each_job_alone(dev):
+    """The serving loop over the batched receiver: jobs of the serving configuration's shapes
+    (4-273 PRB, 4-64 Rx, 1-16 layers, QPSK-256QAM) arriving as a Poisson stream, continuously
+    batched on two lanes; every job's LLRs and flags equal phy_slot_run on the job alone."""
+    import torch
+    from paper_2510_07843_gb300 import phy, serve
+    rng = np.random.default_rng(77)
+    specs = [S.spec_serving_job(rng) for _ in range(10)]
+    specs = [dataclasses.replace(s, n_prb=min(s.n_prb, 60)) for s in specs]  # test-sized
+    pool = []
+    for i, sp in enumerate(specs):
+        sl = S.make_slot(sp, 900 + i, keep_h=False)
+        cfg = phy.SlotConfig.from_spec(sp)
+        pool.append((cfg, *(torch.from_numpy(a).to(dev) for a in (sl.Y, sl.pilots, sl.sigma2))))
+    arrivals = S.serving_arrivals(8, 2000.0, 0.004, 3)
+    jobs = [serve.MixedJob(pool[k % len(pool)][0], *pool[k % len(pool)][1:], arrival=t,
+                           job_id=k) for k, (t, _) in enumerate(arrivals)]
+    srv = serve.BatchServer(device=dev, lanes=2, memory_fraction=0.05)
+    srv.prepare(jobs[0])
+    done = srv.run(jobs, realtime=False, keep=True)
+    assert len(done) == len(jobs) and srv.batches >= 1 and max(srv.batch_sizes) > 1
+    ref = {}
+    for k, (cfg, Y, P, s2) in enumerate(pool):
+        b = phy.SlotBuffers(cfg, device=dev, with_inputs=False)
+        phy.slot_run(cfg, Y, P, s2, b.x_hat, b.sinr, b.llr, b.flags, b.workspace)
+        ref[k] = b
+    torch.cuda.synchronize()
+    for j in done:
+        r = ref[j.job_id % len(pool)]
+        assert torch.equal(j.llr, r.llr) and torch.equal(j.flags, r.flags), j.job_id

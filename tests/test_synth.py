@@ -107,3 +107,19 @@ def test_denoiser_initial_parameters_are_the_identity_network():
     x = np.random.default_rng(0).standard_normal((2, 2, 14, 12))
     out, _ = O.cnn_forward(p.astype(np.float64), x)
     np.testing.assert_array_equal(out, x)
+
+
+def test_serving_stream_shapes_and_rates():
+    """The serving workload's job shapes stay in their ranges (layers never above antennas) and
+    its arrivals are Poisson at the stated rate per cell (count within 5 sigma)."""
+    import numpy as np
+    rng = np.random.default_rng(0)
+    specs = [S.spec_serving_job(rng) for _ in range(2000)]
+    assert all(4 <= s.n_prb <= 273 and s.n_rx in S.SERVING_RX and 1 <= s.n_layers <= s.n_rx
+               and s.n_layers <= 16 and s.qm in S.SERVING_QM for s in specs)
+    assert {s.n_rx for s in specs} == set(S.SERVING_RX) and min(s.n_prb for s in specs) == 4
+    arr = S.serving_arrivals(32, 2000.0, 0.05, 1)
+    mean = 32 * 2000.0 * 0.05
+    assert abs(len(arr) - mean) < 5 * mean ** 0.5
+    assert all(a[0] <= b[0] for a, b in zip(arr, arr[1:]))
+    assert {c for _, c in arr} == set(range(32))
