@@ -315,7 +315,7 @@ phy_status phy_batch_launch(void* table_host, void* table_dev, int64_t poll_limi
 phy_status phy_batch_status(const void* table_host);
 
 /*
- * Tile autotuner for the detection chunk (no counterpart in the paper). Detection runs in chunks
+ * Tile autotuner (no counterpart in the paper). Detection runs in chunks
  * of cells: the Gram/matched-filter kernel writes one chunk's intermediates (about 16 MB per
  * 273-PRB cell at 64x16) and the solve kernel reads them back, so the chunk size trades L2
  * residency of those intermediates against launch count and tail effects. phy_autotune() runs
@@ -335,6 +335,25 @@ phy_status phy_autotune(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32
                         uint8_t* flags, void* workspace, size_t workspace_bytes, void* stream,
                         int32_t* chunk_out);
 void phy_autotune_clear(void);
+
+/*
+ * The tile shapes behind a configuration's calls, as phy_autotune() chose them or as set here;
+ * 0 means the library default (and chunk 0: the preferred chunk for the workspace).
+ *  - chunk: cells per detection chunk (1..n_cells);
+ *  - solve_width: REs (threads) per CTA of the solve kernel, 128 (default) or 64;
+ *  - ring_stages: depth of the tensor-core segment kernel's ring of 16-subcarrier boxes, the
+ *    format's default (8 stages for FP16/BF16, 6 for TF32) or 12 where its shared-memory map
+ *    still fits (otherwise the default is used).
+ * phy_autotune() searches them in that order (chunk sizes, then the other solve width, then the
+ * deeper ring for FP16/BF16 products), keeping each change only if it is faster. Tiles never
+ * change the arithmetic: every choice gives bitwise the same outputs.
+ * phy_autotune_set_tiles() pins them for cfg's key (PHY_ERR_INVALID_ARG for a value outside the
+ * lists); phy_autotune_tiles() reads them back. Both are thread-safe and host-only.
+ */
+phy_status phy_autotune_set_tiles(const phy_slot_cfg* cfg, int32_t chunk, int32_t solve_width,
+                                  int32_t ring_stages);
+phy_status phy_autotune_tiles(const phy_slot_cfg* cfg, int32_t* chunk, int32_t* solve_width,
+                              int32_t* ring_stages);
 
 /*
  * Noise-variance estimate from the DMRS (the paper treats the noise level as a known input of the

@@ -140,16 +140,16 @@ TuneKey tune_key(const Geo& g) {
                   g.dmrs1, g.L, g.prec, g.refactor}};
 }
 std::mutex g_tune_mu;
-std::map<TuneKey, int> g_tuned;
+std::map<TuneKey, phy::Tile> g_tuned;
 
 }  // namespace
 
 namespace phy {
 
-int tuned_chunk(const Geo& g) {
+Tile tuned_tile(const Geo& g) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_tuned.find(tune_key(g));
-  return it == g_tuned.end() ? 0 : it->second;
+  return it == g_tuned.end() ? Tile{0, 0, 0} : it->second;
 }
 
 size_t min_workspace_bytes(const phy_slot_cfg* cfg) {
@@ -662,9 +662,6 @@ phy_status phy_autotune(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32
   s = check_shape(g);
   if (s != PHY_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
-  std::vector<int> cand;
-  for (int c = 1; c < g.n_cells; c *= 2) cand.push_back(c);
-  cand.push_back(g.n_cells);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return PHY_ERR_CUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -672,16 +669,14 @@ phy_status phy_autotune(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32
     return PHY_ERR_CUDA;
   }
   const TuneKey key = tune_key(g);
-  int best = 0;
-  float best_ms = 0.f;
   phy_status rs = PHY_OK;
-  for (int c : cand) {
-    if (workspace_for_chunk(g, c) > workspace_bytes) continue;
+  // median of three timed runs (after one warm-up) with tile t in force; < 0 on an error
+  auto trial = [&](const phy::Tile& t) -> float {
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
-      g_tuned[key] = c;
+      g_tuned[key] = t;
     }
-    float t[3];
+    float ms[3];
     for (int rep = -1; rep < 3 && rs == PHY_OK; ++rep) {
       if (rep >= 0 && cudaEventRecord(e0, st) != cudaSuccess) rs = PHY_ERR_CUDA;
       if (rs == PHY_OK)
@@ -689,33 +684,75 @@ phy_status phy_autotune(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32
                                workspace_bytes, st);
       if (rep >= 0 && rs == PHY_OK) {
         if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-            cudaEventElapsedTime(&t[rep], e0, e1) != cudaSuccess)
+            cudaEventElapsedTime(&ms[rep], e0, e1) != cudaSuccess)
           rs = PHY_ERR_CUDA;
       }
     }
-    if (rs != PHY_OK) break;
-    std::sort(t, t + 3);
-    if (best == 0 || t[1] < best_ms) {
-      best = c;
-      best_ms = t[1];
+    if (rs != PHY_OK) return -1.f;
+    std::sort(ms, ms + 3);
+    return ms[1];
+  };
+  // coordinate search: cells per chunk with the default tiles, then the solve CTA width, then
+  // (tensor-core products) the ring depth, each keeping the best so far
+  phy::Tile best{0, 128, 0};
+  float best_ms = -1.f;
+  auto consider = [&](const phy::Tile& t) {
+    const float ms = trial(t);
+    if (ms >= 0.f && (best_ms < 0.f || ms < best_ms)) {
+      best = t;
+      best_ms = ms;
     }
-  }
+  };
+  std::vector<int> cand;
+  for (int c = 1; c < g.n_cells; c *= 2) cand.push_back(c);
+  cand.push_back(g.n_cells);
+  for (int c : cand)
+    if (rs == PHY_OK && workspace_for_chunk(g, c) <= workspace_bytes) consider({c, 128, 0});
+  if (rs == PHY_OK && best.chunk > 0) consider({best.chunk, 64, 0});
+  if (rs == PHY_OK && best.chunk > 0 && g.prec != PHY_PREC_FP32 && g.prec != PHY_PREC_TC_TF32)
+    consider({best.chunk, best.solve_w, 12});
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    if (rs == PHY_OK && best > 0)
+    if (rs == PHY_OK && best.chunk > 0)
       g_tuned[key] = best;
     else
       g_tuned.erase(key);
   }
   if (rs != PHY_OK) return rs;
-  // leave the outputs as a plain call with the chosen chunk produces them
+  // leave the outputs as a plain call with the chosen tiles produces them
   rs = phy::slot_run_fit(cfg, Y, pilots, sigma2, x_hat, sinr, llr, flags, workspace,
                          workspace_bytes, st);
   if (rs != PHY_OK) return rs;
   if (cudaStreamSynchronize(st) != cudaSuccess) return PHY_ERR_CUDA;
-  if (chunk_out) *chunk_out = best;
+  if (chunk_out) *chunk_out = best.chunk;
+  return PHY_OK;
+}
+
+phy_status phy_autotune_set_tiles(const phy_slot_cfg* cfg, int32_t chunk, int32_t solve_width,
+                                  int32_t ring_stages) {
+  Geo g;
+  const phy_status s = make_geo(cfg, &g);
+  if (s != PHY_OK) return s;
+  if (chunk < 0 || chunk > g.n_cells || (solve_width != 0 && solve_width != 64 &&
+                                         solve_width != 128) ||
+      (ring_stages != 0 && ring_stages != 12))
+    return PHY_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[tune_key(g)] = phy::Tile{chunk, solve_width, ring_stages};
+  return PHY_OK;
+}
+
+phy_status phy_autotune_tiles(const phy_slot_cfg* cfg, int32_t* chunk, int32_t* solve_width,
+                              int32_t* ring_stages) {
+  Geo g;
+  const phy_status s = make_geo(cfg, &g);
+  if (s != PHY_OK) return s;
+  const phy::Tile t = phy::tuned_tile(g);
+  if (chunk) *chunk = t.chunk;
+  if (solve_width) *solve_width = t.solve_w;
+  if (ring_stages) *ring_stages = t.ring;
   return PHY_OK;
 }
 

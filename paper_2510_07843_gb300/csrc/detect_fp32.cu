@@ -301,11 +301,13 @@ __global__ void __launch_bounds__(kPrepThreads)
   seg_prep_body<NL>(g, wmax, cell0, blockIdx.x, blockIdx.y, anchors, Y, ygg, bvec);
 }
 
-// Thread-private scratch in shared memory, interleaved by thread (conflict-free).
+// Thread-private scratch in shared memory, interleaved by thread (conflict-free) over the W
+// threads of a solve CTA.
+template <int W>
 struct SmemScratch {
   cf* base;  // this thread's slot 0
-  __device__ __forceinline__ void st(int e, cf v) const { base[e * kSolveThreads] = v; }
-  __device__ __forceinline__ cf ld(int e) const { return base[e * kSolveThreads]; }
+  __device__ __forceinline__ void st(int e, cf v) const { base[e * W] = v; }
+  __device__ __forceinline__ cf ld(int e) const { return base[e * W]; }
 };
 
 
@@ -313,22 +315,24 @@ struct SmemScratch {
 // Gram-block bytes of one (segment, data symbol): NTRI 4-tuples of complex values.
 constexpr uint32_t gram_block_bytes(int NL) { return (uint32_t)(NL * (NL + 1) / 2) * 32u; }
 
-constexpr size_t solve_scratch_bytes(int NL) {
-  return NL == 16 ? (size_t)kScrSlots * kSolveThreads * sizeof(cf) : 0;
+// The solve kernel's CTA width W (REs per CTA) is a tile shape the autotuner picks: 128 or 64.
+constexpr size_t solve_scratch_bytes(int NL, int W = kSolveThreads) {
+  return NL == 16 ? (size_t)kScrSlots * W * sizeof(cf) : 0;
 }
 
 // 9..16 layers: after the solve, shared memory holds every thread's x and d in RE-major tables
 // padded to 17 entries per RE, and one ok byte per RE (the transposed epilogue's input).
-constexpr size_t solve_stage_bytes(int QM) {
-  return (size_t)kSolveThreads * 17 * (sizeof(cf) + sizeof(float)) + kSolveThreads;
+constexpr size_t solve_stage_bytes(int W = kSolveThreads) {
+  return (size_t)W * 17 * (sizeof(cf) + sizeof(float)) + W;
 }
 
 // Shared memory of the solve kernel: scratch and the Gram blocks of up to max_segs segments (for
 // 9..16 layers at least the epilogue's tables), then the mbarrier in the last 16 bytes, which the
 // tables never reach.
-__host__ __device__ constexpr size_t solve_smem_bytes(int NL, int QM, int max_segs) {
-  const size_t main = solve_scratch_bytes(NL) + (size_t)max_segs * gram_block_bytes(NL);
-  const size_t stage = NL == 16 ? solve_stage_bytes(QM) : 0;
+__host__ __device__ constexpr size_t solve_smem_bytes(int NL, int QM, int max_segs,
+                                                      int W = kSolveThreads) {
+  const size_t main = solve_scratch_bytes(NL, W) + (size_t)max_segs * gram_block_bytes(NL);
+  const size_t stage = NL == 16 ? solve_stage_bytes(W) : 0;
   return (main > stage ? main : stage) + 16;
 }
 
@@ -409,7 +413,7 @@ __device__ __forceinline__ void demap_store_q(int qm, float* llr, size_t li, cf 
 // cell0). The barrier `bar` is initialised and its phase `parity` is the one this item's copies
 // complete. QM = 0 takes the modulation from g.qm. Returns false if the Gram-block copies did not
 // land even after a timeout's second wait (the barrier is then unusable for a later item).
-template <int NL, int QM>
+template <int NL, int QM, int W = kSolveThreads>
 __device__ __forceinline__ bool re_solve_body(
     const Geo& g, int cell0, int bx, int jj, int lc, uint64_t* bar, uint32_t parity,
     const float4* __restrict__ ygg, const cf* __restrict__ bvec,
@@ -420,14 +424,14 @@ __device__ __forceinline__ bool re_solve_body(
   constexpr int NTRI = NL * (NL + 1) / 2;
   constexpr uint32_t kBlk = gram_block_bytes(NL);
   extern __shared__ __align__(128) unsigned char solve_smem[];
-  float4* ys = reinterpret_cast<float4*>(solve_smem + solve_scratch_bytes(NL));
+  float4* ys = reinterpret_cast<float4*>(solve_smem + solve_scratch_bytes(NL, W));
   const int nl = g.n_layers, nds = g.n_dsym;
   const int qm = QM > 0 ? QM : g.qm;
   const int cell = cell0 + lc;
-  const int k0 = bx * kSolveThreads;
+  const int k0 = bx * W;
   const int k = k0 + threadIdx.x;
   const bool live = k < g.n_sc;
-  const int s0 = seg_of(g, k0), s1 = seg_of(g, min(k0 + kSolveThreads, g.n_sc) - 1);
+  const int s0 = seg_of(g, k0), s1 = seg_of(g, min(k0 + W, g.n_sc) - 1);
   const int nseg = s1 - s0 + 1;  // <= max_segs (host-computed bound)
   if (threadIdx.x == 0) {
     tc::mbar_arrive_expect_tx(bar, (uint32_t)nseg * kBlk);
@@ -525,7 +529,7 @@ __device__ __forceinline__ bool re_solve_body(
           row[k] = (lv && k < nl) ? a : mk(0.f, 0.f);  // l >= 8 > k: never on the diagonal
         }
       };
-      si = solve16(getA, rowA, SmemScratch{reinterpret_cast<cf*>(solve_smem) + threadIdx.x}, b,
+      si = solve16(getA, rowA, SmemScratch<W>{reinterpret_cast<cf*>(solve_smem) + threadIdx.x}, b,
                    x, dd);
     } else {
       si = solve_small<NL>(getA, b, x, dd);
@@ -560,8 +564,8 @@ __device__ __forceinline__ bool re_solve_body(
     // its neighbour's: the stores of a warp cover one contiguous stretch of each output.
     constexpr int kXs = NL + 1;
     cf* xs = reinterpret_cast<cf*>(solve_smem);
-    float* ds = reinterpret_cast<float*>(solve_smem + (size_t)kSolveThreads * kXs * sizeof(cf));
-    unsigned char* oks = reinterpret_cast<unsigned char*>(ds + kSolveThreads * kXs);
+    float* ds = reinterpret_cast<float*>(solve_smem + (size_t)W * kXs * sizeof(cf));
+    unsigned char* oks = reinterpret_cast<unsigned char*>(ds + W * kXs);
     __syncthreads();  // the scratch and the Gram blocks are dead from here on
     const int r = threadIdx.x;
 #pragma unroll
@@ -571,10 +575,10 @@ __device__ __forceinline__ bool re_solve_body(
     }
     oks[r] = ok ? 1 : 0;
     __syncthreads();
-    const int nlive = min(kSolveThreads, g.n_sc - k0);
+    const int nlive = min(W, g.n_sc - k0);
     const size_t r0 = ((size_t)cell * nds + jj) * g.n_sc + k0;
 #pragma unroll 2
-    for (int it = threadIdx.x; it < nlive * nl; it += kSolveThreads) {
+    for (int it = threadIdx.x; it < nlive * nl; it += W) {
       const int re = nl == 16 ? (it >> 4) : it / nl, l = it - re * nl;
       const cf xl = xs[re * kXs + l];
       const bool okr = oks[re] != 0;
@@ -604,8 +608,8 @@ __device__ __forceinline__ bool re_solve_body(
   return true;
 }
 
-template <int NL, int QM>
-__global__ void __launch_bounds__(kSolveThreads)
+template <int NL, int QM, int W>
+__global__ void __launch_bounds__(W)
     re_solve_fp32_kernel(Geo g, int cell0, int max_segs, const float4* __restrict__ ygg,
                          const cf* __restrict__ bvec, const float* __restrict__ sigma2,
                          const phy_c32* __restrict__ anchors, const phy_c32* __restrict__ Y,
@@ -614,13 +618,13 @@ __global__ void __launch_bounds__(kSolveThreads)
                          const unsigned* __restrict__ prep_err) {
   extern __shared__ __align__(128) unsigned char solve_smem[];
   uint64_t* bar =
-      reinterpret_cast<uint64_t*>(solve_smem + solve_smem_bytes(NL, QM, max_segs) - 16);
+      reinterpret_cast<uint64_t*>(solve_smem + solve_smem_bytes(NL, QM, max_segs, W) - 16);
   if (threadIdx.x == 0) {
     tc::mbar_init(bar, 1);
     tc::mbar_fence_init();
   }
   __syncthreads();
-  re_solve_body<NL, QM>(g, cell0, blockIdx.x, blockIdx.y, blockIdx.z, bar, 0, ygg, bvec, sigma2,
+  re_solve_body<NL, QM, W>(g, cell0, blockIdx.x, blockIdx.y, blockIdx.z, bar, 0, ygg, bvec, sigma2,
                         anchors, Y, x_hat, sinr_out, llr_out, flags_out, prep_err);
 }
 
@@ -718,8 +722,8 @@ Sizes sizes(const Geo& g, int chunk) {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-// Most frequency segments any block of kSolveThreads consecutive subcarriers touches.
-int max_segments_per_block(const Geo& g) {
+// Most frequency segments any block of w consecutive subcarriers touches.
+int max_segments_per_block(const Geo& g, int w = kSolveThreads) {
   if (g.G == 1) return 1;
   auto seg = [&](int k) {
     int j = (k - g.L) / (2 * g.L);
@@ -727,8 +731,8 @@ int max_segments_per_block(const Geo& g) {
     return std::min(j, g.n_seg - 1);
   };
   int best = 1;
-  for (int k0 = 0; k0 < g.n_sc; k0 += kSolveThreads)
-    best = std::max(best, seg(std::min(k0 + kSolveThreads, g.n_sc) - 1) - seg(k0) + 1);
+  for (int k0 = 0; k0 < g.n_sc; k0 += w)
+    best = std::max(best, seg(std::min(k0 + w, g.n_sc) - 1) - seg(k0) + 1);
   return best;
 }
 
@@ -737,27 +741,41 @@ size_t scratch_bytes(const Sizes& s, int chunk) {
   return 256 + align256(s.ygg_per_cell * chunk) + align256(s.b_per_cell * chunk);
 }
 
-template <int NL, int QM>
-cudaError_t launch_solve(const Geo& g, int c0, int nc, int max_segs, const float4* ygg,
-                         const cf* bvec, const float* sigma2, const phy_c32* anchors,
-                         const phy_c32* Y, phy_c32* x_hat, float* sinr, float* llr,
-                         uint8_t* flags, const unsigned* err, cudaStream_t st) {
-  const size_t smem = solve_smem_bytes(NL, QM, max_segs);
+template <int NL, int QM, int W>
+cudaError_t launch_solve_w(const Geo& g, int c0, int nc, const float4* ygg, const cf* bvec,
+                           const float* sigma2, const phy_c32* anchors, const phy_c32* Y,
+                           phy_c32* x_hat, float* sinr, float* llr, uint8_t* flags,
+                           const unsigned* err, cudaStream_t st) {
+  const int max_segs = max_segments_per_block(g, W);
+  const size_t smem = solve_smem_bytes(NL, QM, max_segs, W);
   static size_t configured_on[kMaxDevices] = {};
   size_t& configured = configured_on[current_device()];
   if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(re_solve_fp32_kernel<NL, QM>,
+    cudaError_t e = cudaFuncSetAttribute(re_solve_fp32_kernel<NL, QM, W>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(re_solve_fp32_kernel<NL, QM>,
+    e = cudaFuncSetAttribute(re_solve_fp32_kernel<NL, QM, W>,
                              cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  dim3 grid((g.n_sc + kSolveThreads - 1) / kSolveThreads, g.n_dsym, nc);
-  re_solve_fp32_kernel<NL, QM><<<grid, kSolveThreads, smem, st>>>(
+  dim3 grid((g.n_sc + W - 1) / W, g.n_dsym, nc);
+  re_solve_fp32_kernel<NL, QM, W><<<grid, W, smem, st>>>(
       g, c0, max_segs, ygg, bvec, sigma2, anchors, Y, x_hat, sinr, llr, flags, err);
   return cudaGetLastError();
+}
+
+// The solve kernel with CTA width w (128 or 64 REs per CTA).
+template <int NL, int QM>
+cudaError_t launch_solve(const Geo& g, int w, int c0, int nc, const float4* ygg, const cf* bvec,
+                         const float* sigma2, const phy_c32* anchors, const phy_c32* Y,
+                         phy_c32* x_hat, float* sinr, float* llr, uint8_t* flags,
+                         const unsigned* err, cudaStream_t st) {
+  if (w == 64)
+    return launch_solve_w<NL, QM, 64>(g, c0, nc, ygg, bvec, sigma2, anchors, Y, x_hat, sinr, llr,
+                                      flags, err, st);
+  return launch_solve_w<NL, QM, 128>(g, c0, nc, ygg, bvec, sigma2, anchors, Y, x_hat, sinr, llr,
+                                     flags, err, st);
 }
 
 template <int NL>
@@ -797,16 +815,16 @@ cudaError_t run_chunks(const Geo& g, int wmax, const Sizes& s, const phy_c32* an
       if (e != cudaSuccess) return e;
     }
     if (!(stages & kStageSolve)) continue;
-    const int ms = max_segments_per_block(g);
+    const int w = tuned_tile(g).solve_w == 64 ? 64 : kSolveThreads;
     switch (g.qm) {
-      case 2: e = launch_solve<NL, 2>(g, c0, nc, ms, ygg, bvec, sigma2, anchors, Y, x_hat, sinr, llr,
-                                           flags, err, st); break;
-      case 4: e = launch_solve<NL, 4>(g, c0, nc, ms, ygg, bvec, sigma2, anchors, Y, x_hat, sinr, llr,
-                                           flags, err, st); break;
-      case 6: e = launch_solve<NL, 6>(g, c0, nc, ms, ygg, bvec, sigma2, anchors, Y, x_hat, sinr, llr,
-                                           flags, err, st); break;
-      default: e = launch_solve<NL, 8>(g, c0, nc, ms, ygg, bvec, sigma2, anchors, Y, x_hat, sinr, llr,
-                                           flags, err, st); break;
+      case 2: e = launch_solve<NL, 2>(g, w, c0, nc, ygg, bvec, sigma2, anchors, Y, x_hat, sinr,
+                                      llr, flags, err, st); break;
+      case 4: e = launch_solve<NL, 4>(g, w, c0, nc, ygg, bvec, sigma2, anchors, Y, x_hat, sinr,
+                                      llr, flags, err, st); break;
+      case 6: e = launch_solve<NL, 6>(g, w, c0, nc, ygg, bvec, sigma2, anchors, Y, x_hat, sinr,
+                                      llr, flags, err, st); break;
+      default: e = launch_solve<NL, 8>(g, w, c0, nc, ygg, bvec, sigma2, anchors, Y, x_hat, sinr,
+                                       llr, flags, err, st); break;
     }
     if (e != cudaSuccess) return e;
   }
@@ -952,7 +970,7 @@ cudaError_t launch_detect(const Geo& g, const phy_c32* anchors, const phy_c32* Y
   const int wmax = host_max_segment_width(g);
   // the largest chunk of cells (up to the tuned or preferred one) whose intermediates fit the
   // scratch; a single stage needs the whole batch in one chunk
-  const int tuned = tuned_chunk(g);
+  const int tuned = tuned_tile(g).chunk;
   int chunk = stages != (kStageGramMf | kStageSolve) ? g.n_cells
               : tuned > 0                            ? std::min(tuned, g.n_cells)
                                                      : detect_preferred_chunk(g);

@@ -74,8 +74,9 @@ struct Layout {
 constexpr int nxp_of(int nx) { return nx <= 16 ? 16 : (nx + 15) / 16 * 16; }
 constexpr size_t up128(size_t v) { return (v + 127) & ~(size_t)127; }
 
-// Shared-memory map: CC tile | RE tiles | X (FP32) | anchor corners | ring | barriers.
-template <int NL, int NC, uint32_t FMT>
+// Shared-memory map: CC tile | RE tiles | X (FP32) | anchor corners | ring of RS stages |
+// barriers.
+template <int NL, int NC, uint32_t FMT, int RS>
 struct Smem {
   using Lay = Layout<FMT>;
   static constexpr int NXP = nxp_of(NC * NL);
@@ -85,9 +86,9 @@ struct Smem {
   static constexpr size_t kAnch = kXs + up128((size_t)NXP * (NXP + 1) / 2 * 8);  // X, lower
   static constexpr size_t kCorner = up128((size_t)NL * 64 * 8);  // one corner's [l][r] block
   static constexpr size_t kRing = kAnch + NC * kCorner;
-  static constexpr size_t kBars = kRing + (size_t)Lay::kStages * kStageBytes;
+  static constexpr size_t kBars = kRing + (size_t)RS * kStageBytes;
   // full[S], empty[S], anchors full / empty, X done / drained, MF done[2] / drained[2]
-  static constexpr int kNumBars = 2 * Lay::kStages + 8;
+  static constexpr int kNumBars = 2 * RS + 8;
   static constexpr size_t kMisc = kBars + 8 * kNumBars;  // TMEM address, consumed counts
   static constexpr size_t kTotal = kMisc + 16;
 };
@@ -156,15 +157,15 @@ __device__ __forceinline__ int tile_syms(const Geo& g, const Item& it, int t) {
   return min(it.spt, g.n_dsym - t * it.spt);
 }
 
-template <int NL, int NC, uint32_t FMT>
+template <int NL, int NC, uint32_t FMT, int RS>
 __global__ void __launch_bounds__(kTcThreads, 1)
     seg_prep_tc_kernel(const __grid_constant__ CUtensorMap tmY,
                        const __grid_constant__ CUtensorMap tmA, Geo g, int cell0, int nc,
                        float4* __restrict__ ygg, cf* __restrict__ bvec,
                        unsigned* __restrict__ err) {
   using Lay = Layout<FMT>;
-  using Sm = Smem<NL, NC, FMT>;
-  constexpr int S = Lay::kStages;
+  using Sm = Smem<NL, NC, FMT, RS>;
+  constexpr int S = RS;
   constexpr int NX = NC * NL;
   constexpr int NXP = Sm::NXP;
   constexpr int NTRI = NL * (NL + 1) / 2;
@@ -487,19 +488,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 // ---------------------------------------------------------------- host side
-template <int NL, int NC, uint32_t FMT>
+template <int NL, int NC, uint32_t FMT, int RS>
 cudaError_t launch_one(const Geo& g, int c0, int nc, const phy_c32* anchors, const phy_c32* Y,
                        float4* ygg, cf* bvec, unsigned* err, cudaStream_t st) {
-  constexpr size_t smem = Smem<NL, NC, FMT>::kTotal;
+  constexpr size_t smem = Smem<NL, NC, FMT, RS>::kTotal;
   static bool configured_on[kMaxDevices] = {};
   bool& configured = configured_on[current_device()];
   const int num_sms = device_sm_count();
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(seg_prep_tc_kernel<NL, NC, FMT>,
+    cudaError_t e = cudaFuncSetAttribute(seg_prep_tc_kernel<NL, NC, FMT, RS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (std::getenv("PHY_DEBUG"))
-      std::fprintf(stderr, "seg_prep_tc<%d,%d,%u>: smem %zu, SMs %d\n", NL, NC, FMT, smem,
+      std::fprintf(stderr, "seg_prep_tc<%d,%d,%u,%d>: smem %zu, SMs %d\n", NL, NC, FMT, RS, smem,
                    num_sms);
     configured = true;
   }
@@ -518,16 +519,31 @@ cudaError_t launch_one(const Geo& g, int c0, int nc, const phy_c32* anchors, con
     return cudaErrorInvalidValue;
   const int n_work = g.n_seg * nc;
   const int grid = std::min(n_work, num_sms);
-  seg_prep_tc_kernel<NL, NC, FMT><<<grid, kTcThreads, smem, st>>>(tmY, tmA, g, c0, nc, ygg, bvec,
-                                                                  err);
+  seg_prep_tc_kernel<NL, NC, FMT, RS><<<grid, kTcThreads, smem, st>>>(tmY, tmA, g, c0, nc, ygg,
+                                                                      bvec, err);
   return cudaGetLastError();
+}
+
+// Ring depth: the format's default, or a deeper ring of kDeepRing stages (more box bytes in
+// flight per SM) where the shared-memory map still fits; the autotuner picks.
+constexpr int kDeepRing = 12;
+
+template <int NL, int NC, uint32_t FMT>
+cudaError_t launch_ring(const Geo& g, int c0, int nc, const phy_c32* anchors, const phy_c32* Y,
+                        float4* ygg, cf* bvec, unsigned* err, cudaStream_t st) {
+  constexpr int kDef = Layout<FMT>::kStages;
+  if constexpr (FMT != tc::kFmtTF32 && Smem<NL, NC, FMT, kDeepRing>::kTotal <= 227 * 1024) {
+    if (tuned_tile(g).ring == kDeepRing)
+      return launch_one<NL, NC, FMT, kDeepRing>(g, c0, nc, anchors, Y, ygg, bvec, err, st);
+  }
+  return launch_one<NL, NC, FMT, kDef>(g, c0, nc, anchors, Y, ygg, bvec, err, st);
 }
 
 template <int NL, uint32_t FMT>
 cudaError_t launch_nc(const Geo& g, int c0, int nc, const phy_c32* anchors, const phy_c32* Y,
                       float4* ygg, cf* bvec, unsigned* err, cudaStream_t st) {
-  if (g.n_dmrs == 2) return launch_one<NL, 4, FMT>(g, c0, nc, anchors, Y, ygg, bvec, err, st);
-  return launch_one<NL, 2, FMT>(g, c0, nc, anchors, Y, ygg, bvec, err, st);
+  if (g.n_dmrs == 2) return launch_ring<NL, 4, FMT>(g, c0, nc, anchors, Y, ygg, bvec, err, st);
+  return launch_ring<NL, 2, FMT>(g, c0, nc, anchors, Y, ygg, bvec, err, st);
 }
 
 template <uint32_t FMT>

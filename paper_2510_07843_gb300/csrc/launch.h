@@ -36,8 +36,13 @@ size_t fused_fp32_smem_bytes(const Geo& g);
 // Scratch bytes for chunks of `chunk` cells, and the chunk size the library prefers.
 size_t detect_scratch_bytes(const Geo& g, int chunk);
 int detect_preferred_chunk(const Geo& g);
-// Cells per chunk chosen by phy_autotune() for this geometry, or 0 if it was never tuned.
-int tuned_chunk(const Geo& g);
+// Tile shapes phy_autotune() chooses per geometry (each 0 where it was never tuned: the library
+// default): cells per detection chunk, the solve kernel's CTA width (64 or 128 REs) and the
+// tensor-core segment kernel's ring depth (stages of one 16-subcarrier box).
+struct Tile {
+  int chunk, solve_w, ring;
+};
+Tile tuned_tile(const Geo& g);
 
 cudaError_t launch_chest(const Geo& g, const phy_c32* Y, const phy_c32* pilots, phy_c32* anchors,
                          cudaStream_t st);
@@ -97,6 +102,10 @@ cudaError_t cnn_forward(int n, const float* params, const float* x, float* out, 
 cudaError_t cnn_train_step(int n, float* params, float* m, float* v, int step, float lr,
                            const float* x, const float* label, float* grad_out, float* dx_out,
                            float* loss_out, float* ws, cudaStream_t st);
+// The same forward pass on the tensor cores with BF16 operands (cnn_tc.cu); err (device word)
+// is cleared first and counts CTAs whose bounded MMA wait ran out.
+cudaError_t cnn_forward_tc(int n, const float* params, const float* x, float* out, unsigned* err,
+                           cudaStream_t st);
 // Interpolated channel at every symbol H[cell][t][k][r][l]; tiles per (cell, PRB, Rx, layer)
 // from such an H, and the data symbols of tiles back into Hd[cell][dsym][k][r][l].
 cudaError_t launch_interp_all(const Geo& g, const phy_c32* anchors, phy_c32* H, cudaStream_t st);

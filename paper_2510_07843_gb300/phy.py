@@ -59,6 +59,8 @@ _SIGS = {
     "phy_detect_stage": (ctypes.c_int, [_P, ctypes.c_int32] + [_P] * 8 + [ctypes.c_size_t, _P]),
     "phy_autotune": (ctypes.c_int, [_P] * 9 + [ctypes.c_size_t, _P, _P]),
     "phy_autotune_clear": (None, []),
+    "phy_autotune_set_tiles": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "phy_autotune_tiles": (ctypes.c_int, [_P, _P, _P, _P]),
     "phy_batch_table_bytes": (ctypes.c_size_t, []),
     "phy_batch_workspace_size": (ctypes.c_size_t, [_P, ctypes.c_int32]),
     "phy_batch_post": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_size_t]),
@@ -262,6 +264,21 @@ def autotune(cfg: SlotConfig, Y, pilots, sigma2, x_hat, sinr, llr, flags, worksp
 def autotune_clear():
     """phy_autotune_clear: forget every tuned configuration."""
     load().phy_autotune_clear()
+
+
+def autotune_set_tiles(cfg: SlotConfig, chunk: int = 0, solve_width: int = 0, ring: int = 0):
+    """phy_autotune_set_tiles: pin cfg's tile shapes (0: the default)."""
+    c = cfg.c()
+    _check("phy_autotune_set_tiles",
+           load().phy_autotune_set_tiles(ctypes.byref(c), chunk, solve_width, ring))
+
+
+def autotune_tiles(cfg: SlotConfig) -> dict:
+    """phy_autotune_tiles: cfg's tile shapes (chunk, solve_width, ring; 0 = default)."""
+    c = cfg.c()
+    v = [ctypes.c_int32(0) for _ in range(3)]
+    _check("phy_autotune_tiles", load().phy_autotune_tiles(ctypes.byref(c), *map(ctypes.byref, v)))
+    return {"chunk": v[0].value, "solve_width": v[1].value, "ring": v[2].value}
 
 
 PROBE_KIND = {"fp32": 0, "fp32x2": 1, "fp64": 2}  # phy_probe_kind
