@@ -626,7 +626,7 @@ CNN_MACS_FWD = 168 * (32 * 18 + 2 * 32 * 288 + 2 * 288)  # per tile: the four 3x
 CNN_MACS_TRAIN = 2 * CNN_MACS_FWD + 168 * (2 * 288 + 2 * 32 * 288)  # + dW all, dX layers 2-4
 
 
-def cnn_run(dev, st, fp32_peak_tf: float) -> dict:
+def cnn_run(dev, st, fp32_peak_tf: float, bf16_peak_tf: float) -> dict:
     """The learned denoiser: trained on the GPU by the library's kernels on generated slots
     (24 slots of 12 PRB, 32 Rx x 8 layers, 0-30 dB, 0-500 Hz Doppler; 8 epochs of Adam), then
     evaluated on one 273-PRB 32 Rx x 8 layer 64-QAM slot at 5 dB and 300 Hz against LS +
@@ -645,7 +645,6 @@ def cnn_run(dev, st, fp32_peak_tf: float) -> dict:
     train_s = a.elapsed_time(b) * 1e-3
     tiles = tr.step * tr.batch
     ev = D.slot_tiles(D.train_spec(n_prb=273, snr_db=5.0, doppler_hz=300.0), 4000, dev)
-    res = D.evaluate(tr.p, ev, dev)
     n_tiles = phy.cnn_n_tiles(ev.cfg)
     H = torch.empty((1, len(ev.spec.data_sym), ev.spec.n_sc, 32, 8), dtype=torch.complex64,
                     device=dev)
@@ -658,15 +657,52 @@ def cnn_run(dev, st, fp32_peak_tf: float) -> dict:
     b.record(st)
     torch.cuda.synchronize()
     inf_s = a.elapsed_time(b) * 1e-3 / 10
+    # the same slot through the tensor-core forward pass (BF16 operands, FP32 sums), and the
+    # forward pass alone on the slot's tiles for both forms
+    for _ in range(3):
+        phy.cnn_denoise_bf16(ev.cfg, tr.p, ev.anchors, H, ws, stream=st)
+    a.record(st)
+    for _ in range(10):
+        phy.cnn_denoise_bf16(ev.cfg, tr.p, ev.anchors, H, ws, stream=st)
+    b.record(st)
+    torch.cuda.synchronize()
+    inf_tc_s = a.elapsed_time(b) * 1e-3 / 10
+    tiles_in = ev.x
+    tiles_out = torch.empty_like(tiles_in)
+    wsf = torch.empty(phy.cnn_workspace_size(n_tiles), dtype=torch.uint8, device=dev)
+    fwd = {}
+    for name, fn in (("fp32", lambda: phy.cnn_forward(n_tiles, tr.p, tiles_in, tiles_out, wsf,
+                                                      stream=st)),
+                     ("bf16_tensor_core", lambda: phy.cnn_forward_bf16(n_tiles, tr.p, tiles_in,
+                                                                        tiles_out, wsf,
+                                                                        stream=st))):
+        for _ in range(3):
+            fn()
+        a.record(st)
+        for _ in range(10):
+            fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        fwd[name] = a.elapsed_time(b) / 10
     train_tf = tiles * CNN_MACS_TRAIN * 2 / train_s / 1e12
     inf_tf = n_tiles * CNN_MACS_FWD * 2 / inf_s / 1e12
+    fwd_flops = n_tiles * CNN_MACS_FWD * 2
+    res = D.evaluate(tr.p, ev, dev, tensor_cores=True)
     return {"train": {"tiles": int(tiles), "steps": tr.step, "batch": tr.batch,
                       "seconds": train_s, "tiles_per_s": tiles / train_s,
                       "tflops": train_tf, "fp32_peak_frac": train_tf / fp32_peak_tf},
             "denoise_slot": {"tiles": n_tiles, "ms": inf_s * 1e3, "tflops": inf_tf,
                              "fp32_peak_frac": inf_tf / fp32_peak_tf,
+                             "ms_bf16_tensor_core": inf_tc_s * 1e3,
                              "what": "interpolation, tiles, 4 conv layers, untile (273 PRB, "
                                      "32 Rx x 8 layers)"},
+            "forward_only": {"tiles": n_tiles,
+                             "ms": fwd,
+                             "tflops": {k: fwd_flops / (v * 1e-3) / 1e12 for k, v in fwd.items()},
+                             "bf16_peak_frac": fwd_flops / (fwd["bf16_tensor_core"] * 1e-3)
+                             / 1e12 / bf16_peak_tf,
+                             "peak": {"fp32_tflops": fp32_peak_tf, "bf16_tflops": bf16_peak_tf,
+                                      "bf16_source": "MEASURED_PEAKS.json bf16_tflops"}},
             "eval": {"snr_db": 5.0, "doppler_hz": 300.0, **res}}
 
 
@@ -980,7 +1016,7 @@ def run_ours(args, spec, rank, world, local):
         bfp = bfp_run(cfg, spec, slot, buf, st, hbm_peak)
     learned = None
     if not args.no_cnn:
-        learned = cnn_run(dev, st, fl_peak)
+        learned = cnn_run(dev, st, fl_peak, peaks.get("bf16_tflops", 1900.0))
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:

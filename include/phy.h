@@ -502,6 +502,22 @@ phy_status phy_cnn_tiles(const phy_slot_cfg* cfg, const phy_c32* H, float* tiles
 phy_status phy_cnn_untile(const phy_slot_cfg* cfg, const float* tiles, phy_c32* H_data,
                           void* stream);
 size_t phy_cnn_denoise_workspace_size(const phy_slot_cfg* cfg);
+/*
+ * The same network on the tcgen05 tensor cores with BF16 operands and FP32 accumulation: the
+ * weights and every layer's input rounded to nearest BF16, biases, sums and the residual in FP32
+ * (the bfloat16 form of the network). phy_cnn_forward_bf16 takes a workspace of at least 4 bytes
+ * (4-byte aligned) whose first word it clears and then counts CTAs whose bounded wait for the
+ * tensor core ran out (nonzero: the outputs are not valid). phy_cnn_denoise_bf16 is
+ * phy_cnn_denoise with this forward pass (same workspace); its error word sits at byte
+ * phy_cnn_denoise_error_offset(cfg) of the workspace.
+ */
+phy_status phy_cnn_forward_bf16(int32_t n_tiles, const float* params, const float* tiles_in,
+                                float* tiles_out, void* workspace, size_t workspace_bytes,
+                                void* stream);
+phy_status phy_cnn_denoise_bf16(const phy_slot_cfg* cfg, const float* params,
+                                const phy_c32* anchors, phy_c32* H_data, void* workspace,
+                                size_t workspace_bytes, void* stream);
+size_t phy_cnn_denoise_error_offset(const phy_slot_cfg* cfg);
 phy_status phy_cnn_denoise(const phy_slot_cfg* cfg, const float* params, const phy_c32* anchors,
                            phy_c32* H_data, void* workspace, size_t workspace_bytes,
                            void* stream);

@@ -614,6 +614,51 @@ phy_status phy_cnn_denoise(const phy_slot_cfg* cfg, const float* params, const p
   return cuda_status(e);
 }
 
+phy_status phy_cnn_forward_bf16(int32_t n_tiles, const float* params, const float* tiles_in,
+                                float* tiles_out, void* workspace, size_t workspace_bytes,
+                                void* stream) {
+  if (n_tiles < 0 || !params || (n_tiles > 0 && (!tiles_in || !tiles_out)) || !workspace)
+    return PHY_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace) % 4) return PHY_ERR_INVALID_ARG;
+  if (workspace_bytes < sizeof(unsigned)) return PHY_ERR_NO_MEMORY;
+  return cuda_status(phy::cnn_forward_tc(n_tiles, params, tiles_in, tiles_out,
+                                         (unsigned*)workspace, (cudaStream_t)stream));
+}
+
+phy_status phy_cnn_denoise_bf16(const phy_slot_cfg* cfg, const float* params,
+                                const phy_c32* anchors, phy_c32* H_data, void* workspace,
+                                size_t workspace_bytes, void* stream) {
+  Geo g;
+  phy_status s = check_tiles(cfg, &g);
+  if (s != PHY_OK) return s;
+  if (!params || !anchors || !H_data || !workspace) return PHY_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace) % kAlign) return PHY_ERR_INVALID_ARG;
+  if (workspace_bytes < phy_cnn_denoise_workspace_size(cfg)) return PHY_ERR_NO_MEMORY;
+  const int n = g.n_cells * (g.n_sc / 12) * g.n_rx * g.n_layers;
+  const size_t h = (size_t)g.n_cells * g.n_sym * g.n_sc * g.n_rx * g.n_layers * sizeof(phy_c32);
+  char* ws = static_cast<char*>(workspace);
+  phy_c32* H = (phy_c32*)ws;
+  float* t_in = (float*)(ws + align_up(h));
+  float* t_out = (float*)(ws + align_up(h) + align_up((size_t)n * 2 * 168 * sizeof(float)));
+  // the error word sits where the FP32 pass keeps its scratch
+  unsigned* err =
+      (unsigned*)(ws + align_up(h) + 2 * align_up((size_t)n * 2 * 168 * sizeof(float)));
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = phy::launch_interp_all(g, anchors, H, st);
+  if (e == cudaSuccess) e = phy::launch_tiles_from_h(g, H, t_in, st);
+  if (e == cudaSuccess) e = phy::cnn_forward_tc(n, params, t_in, t_out, err, st);
+  if (e == cudaSuccess) e = phy::launch_tiles_to_h(g, t_out, H_data, st);
+  return cuda_status(e);
+}
+
+size_t phy_cnn_denoise_error_offset(const phy_slot_cfg* cfg) {
+  Geo g;
+  if (check_tiles(cfg, &g) != PHY_OK) return 0;
+  const int n = g.n_cells * (g.n_sc / 12) * g.n_rx * g.n_layers;
+  const size_t h = (size_t)g.n_cells * g.n_sym * g.n_sc * g.n_rx * g.n_layers * sizeof(phy_c32);
+  return align_up(h) + 2 * align_up((size_t)n * 2 * 168 * sizeof(float));
+}
+
 phy_status phy_slot_run_host(const phy_slot_cfg* cfg, const phy_c32* Y_host,
                              const phy_c32* pilots_host, const float* sigma2_host,
                              float* llr_host, uint8_t* flags_host, phy_c32* Y, phy_c32* pilots,

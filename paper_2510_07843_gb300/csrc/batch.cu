@@ -148,10 +148,12 @@ extern "C" phy_status phy_batch_post(const phy_job* jobs, int32_t n_jobs, void* 
     J.max_segs = phy::batch_max_segs(g);
     // items per stage: LS (group, DMRS symbol, cell) over all jobs; segment (segment, cell) and
     // solve (128 subcarriers, data symbol, cell) per layer class
-    const int cls = phy::batch_class(phy::nl_class_of(g.n_layers));
-    const int items[phy::kBatchStages] = {
-        g.G * g.n_dmrs * g.n_cells, g.n_seg * g.n_cells,
-        ((g.n_sc + 127) / 128) * g.n_dsym * g.n_cells};
+    const int nlc = phy::nl_class_of(g.n_layers), cls = phy::batch_class(nlc);
+    // up to four layers: the direct form, no segment stage
+    const bool direct = phy::batch_direct_class(nlc) != 0;
+    const int items[phy::kBatchStages] = {g.G * g.n_dmrs * g.n_cells,
+                                          direct ? 0 : g.n_seg * g.n_cells,
+                                          ((g.n_sc + 127) / 128) * g.n_dsym * g.n_cells};
     for (int stg = 0; stg < phy::kBatchStages; ++stg) {
       const int c = stg == phy::kBatchChest ? 0 : cls;
       int& nj = t->n_class_jobs[stg][c];

@@ -628,6 +628,158 @@ __global__ void __launch_bounds__(W)
                         anchors, Y, x_hat, sinr_out, llr_out, flags_out, prep_err);
 }
 
+// ---------------------------------------------------------------- direct form, up to 4 layers
+// With up to four layers the cover is at most 2 and the anchors change every 2L <= 4
+// subcarriers, so a segment's corner cross-Gram is shared by too few REs to pay for a CTA. Here
+// one thread takes one RE (subcarrier k, data symbol t) of one cell: per antenna it interpolates
+// its channel row from the four corner anchors of its segment (frequency per comb, then time)
+// and accumulates A = H^H H and b = H^H y directly, the plain definition. The solve, SINR, LLRs
+// and the FP64 re-computation are those of the solve kernel. QM = 0 takes the modulation from
+// g.qm.
+template <int NL, int QM>
+__device__ __forceinline__ void direct_body(const Geo& g, int k, int t, int cell,
+                                            const phy_c32* __restrict__ anchors,
+                                            const phy_c32* __restrict__ Y,
+                                            const float* __restrict__ sigma2,
+                                            phy_c32* __restrict__ x_hat,
+                                            float* __restrict__ sinr_out,
+                                            float* __restrict__ llr_out,
+                                            uint8_t* __restrict__ flags_out) {
+  static_assert(NL <= 4, "the direct form keeps its sums in registers");
+  constexpr int NTRI = NL * (NL + 1) / 2;
+  const int nr = g.n_rx, nl = g.n_layers, nds = g.n_dsym, nd = g.n_dmrs;
+  const int qm = QM > 0 ? QM : g.qm;
+  const int j = seg_of(g, k), g1 = seg_g1(g, j);
+  const float bw[2] = {seg_beta(g, j, k, 0), seg_beta(g, j, k, 1)};
+  const float tau = nd == 2 ? g.tw[t] : 0.f;
+  cf A[NTRI], bv[NL];
+#pragma unroll
+  for (int e = 0; e < NTRI; ++e) A[e] = mk(0.f, 0.f);
+#pragma unroll
+  for (int l = 0; l < NL; ++l) bv[l] = mk(0.f, 0.f);
+  const size_t a_d = (size_t)g.G * nl * nr;  // one DMRS symbol's anchors
+  const phy_c32* a0 = anchors + ((size_t)cell * nd * g.G + j) * nl * nr;
+  const phy_c32* a1 = anchors + ((size_t)cell * nd * g.G + g1) * nl * nr;
+  const phy_c32* yk = Y + (((size_t)cell * g.n_sym + g.dsym[t]) * nr) * g.n_sc + k;
+#pragma unroll 4
+  for (int r = 0; r < nr; ++r) {
+    cf h[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      h[l] = mk(0.f, 0.f);
+      if (l < nl) {
+        const float w1 = bw[l & 1], w0 = 1.f - w1;
+        const cf c0 = ld(a0 + (size_t)l * nr + r), c1 = ld(a1 + (size_t)l * nr + r);
+        cf v = mk(fmaf(w1, c1.x, w0 * c0.x), fmaf(w1, c1.y, w0 * c0.y));
+        if (nd == 2) {
+          const cf e0 = ld(a0 + a_d + (size_t)l * nr + r);
+          const cf e1 = ld(a1 + a_d + (size_t)l * nr + r);
+          const cf u = mk(fmaf(w1, e1.x, w0 * e0.x), fmaf(w1, e1.y, w0 * e0.y));
+          v = mk(fmaf(tau, u.x - v.x, v.x), fmaf(tau, u.y - v.y, v.y));
+        }
+        h[l] = v;
+      }
+    }
+    const cf y = ld(yk + (size_t)r * g.n_sc);
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+#pragma unroll
+      for (int m = 0; m <= l; ++m) A[tri(l, m)] = cfma_cj(h[l], h[m], A[tri(l, m)]);
+      bv[l] = cfma_cj(h[l], y, bv[l]);
+    }
+  }
+  const float s2 = sigma2[cell];
+  auto getA = [&](int l, int m) -> cf {
+    if (l >= nl || m >= nl) return (l == m) ? mk(1.f, 0.f) : mk(0.f, 0.f);
+    // A holds sum conj(h_l) h_m: entry (l, m) of H^H H
+    cf a = A[tri(l, m)];
+    if (l == m) {
+      a.x += s2;
+      a.y = 0.f;
+    }
+    return a;
+  };
+  cf b[NL], x[NL];
+  float dd[NL];
+  bool fin = true;
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    b[l] = l < nl ? bv[l] : mk(0.f, 0.f);
+    fin = fin && finite_cf(b[l]);
+  }
+  const SolveInfo si = solve_small<NL>(getA, b, x, dd);
+  fin = fin && si.fin;
+  bool ok = si.ok && fin;
+  uint8_t flag = 0;
+  if (!fin) flag |= 4;
+  if (!si.ok || si.pmin < g.pivot_min * si.pmax) flag |= 1;
+  if (g.refactor && (flag & 1) && fin) {
+    Refactor64Out r64;
+    refactor_fp64(g, anchors, Y, cell, t, k, j, s2, &r64);
+    if (r64.ok) {
+#pragma unroll
+      for (int l = 0; l < NL; ++l) {
+        if (l < nl) {
+          x[l] = r64.x[l];
+          dd[l] = r64.d[l];
+        }
+      }
+      ok = true;
+      flag |= 2;
+    }
+  }
+  const size_t ridx = ((size_t)cell * nds + t) * g.n_sc + k;
+  flags_out[ridx] = flag;
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    if (l >= nl) continue;
+    const LayerOut o = layer_stats(s2, dd[l]);
+    const size_t li = ridx * nl + l;
+    if (x_hat) st(x_hat + li, ok ? x[l] : mk(0.f, 0.f));
+    if (sinr_out) sinr_out[li] = ok ? o.sinr : 0.f;
+    if (llr_out)
+      demap_store_q<QM>(qm, llr_out, li, ok ? o.inv_mu * x[l] : mk(0.f, 0.f), o.s2eff, ok,
+                        g.llr_f16);
+  }
+}
+
+constexpr int kDirectThreads = 128;
+
+template <int NL, int QM>
+__global__ void __launch_bounds__(kDirectThreads)
+    direct_fp32_kernel(Geo g, const phy_c32* __restrict__ anchors, const phy_c32* __restrict__ Y,
+                       const float* __restrict__ sigma2, phy_c32* __restrict__ x_hat,
+                       float* __restrict__ sinr_out, float* __restrict__ llr_out,
+                       uint8_t* __restrict__ flags_out) {
+  const int k = blockIdx.x * kDirectThreads + threadIdx.x;
+  if (k < g.n_sc)
+    direct_body<NL, QM>(g, k, blockIdx.y, blockIdx.z, anchors, Y, sigma2, x_hat, sinr_out,
+                        llr_out, flags_out);
+}
+
+// Batched direct form: CTAs stride over the (128 subcarriers, data symbol, cell) items of the
+// class's jobs.
+template <int NL>
+__global__ void __launch_bounds__(kDirectThreads)
+    direct_batch_kernel(const BatchTable* __restrict__ t) {
+  __shared__ Geo sg;
+  constexpr int cls = batch_class(NL);
+  const int n = t->n_items[kBatchSolve][cls];
+  for (int w = blockIdx.x; w < n; w += gridDim.x) {
+    int local;
+    const BatchJob& J = t->job[batch_find(t, kBatchSolve, cls, w, local)];
+    batch_load_geo(sg, J.g);
+    __syncthreads();
+    const int nb = (sg.n_sc + kDirectThreads - 1) / kDirectThreads;
+    const int k = (local % nb) * kDirectThreads + threadIdx.x;
+    const int jj = (local / nb) % sg.n_dsym, cell = local / (nb * sg.n_dsym);
+    if (k < sg.n_sc)
+      direct_body<NL, 0>(sg, k, jj, cell, J.anchors, J.Y, J.sigma2, J.x_hat, J.sinr, J.llr,
+                         J.flags);
+    __syncthreads();
+  }
+}
+
 // Batched forms (one launch per layer class serves every job of that class in the table).
 // Segment stage: CTAs stride over the (segment, cell) items of the class's jobs.
 template <int NL>
@@ -779,6 +931,20 @@ cudaError_t launch_solve(const Geo& g, int w, int c0, int nc, const float4* ygg,
 }
 
 template <int NL>
+cudaError_t launch_direct(const Geo& g, const phy_c32* anchors, const phy_c32* Y,
+                          const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
+                          uint8_t* flags, cudaStream_t st) {
+  dim3 grid((g.n_sc + kDirectThreads - 1) / kDirectThreads, g.n_dsym, g.n_cells);
+  switch (g.qm) {
+    case 2: direct_fp32_kernel<NL, 2><<<grid, kDirectThreads, 0, st>>>(g, anchors, Y, sigma2, x_hat, sinr, llr, flags); break;
+    case 4: direct_fp32_kernel<NL, 4><<<grid, kDirectThreads, 0, st>>>(g, anchors, Y, sigma2, x_hat, sinr, llr, flags); break;
+    case 6: direct_fp32_kernel<NL, 6><<<grid, kDirectThreads, 0, st>>>(g, anchors, Y, sigma2, x_hat, sinr, llr, flags); break;
+    default: direct_fp32_kernel<NL, 8><<<grid, kDirectThreads, 0, st>>>(g, anchors, Y, sigma2, x_hat, sinr, llr, flags); break;
+  }
+  return cudaGetLastError();
+}
+
+template <int NL>
 cudaError_t run_chunks(const Geo& g, int wmax, const Sizes& s, const phy_c32* anchors,
                        const phy_c32* Y, const float* sigma2, phy_c32* x_hat, float* sinr,
                        float* llr, uint8_t* flags, void* scratch, int stages, cudaStream_t st) {
@@ -834,6 +1000,7 @@ cudaError_t run_chunks(const Geo& g, int wmax, const Sizes& s, const phy_c32* an
 }  // namespace
 
 int nl_class_of(int n_layers) { return nl_class(n_layers); }
+int batch_direct_class(int nl_cls) { return nl_cls <= 4 ? 1 : 0; }
 
 // ---------------------------------------------------------------- batched receiver, host side
 int batch_wmax(const Geo& g) { return host_max_segment_width(g); }
@@ -903,6 +1070,10 @@ BatchClassLaunch batch_class_launch() {
 
 template <int NL>
 cudaError_t launch_batch_nl(const BatchTable* t, cudaStream_t st) {
+  if constexpr (NL <= 4) {  // the direct form: everything in one kernel
+    direct_batch_kernel<NL><<<device_sm_count() * 8, kDirectThreads, 0, st>>>(t);
+    return cudaGetLastError();
+  }
   const BatchClassLaunch b = batch_class_launch<NL>();
   return launch_batch_class<NL>(t, b.grid_seg, b.grid_solve, b.smem_seg, b.smem_solve, st);
 }
@@ -979,6 +1150,12 @@ cudaError_t launch_detect(const Geo& g, const phy_c32* anchors, const phy_c32* Y
   if (scratch_bytes(s, chunk) > scratch_bytes_avail) return cudaErrorInvalidValue;
   // a single stage is only meaningful when the whole batch is one chunk
   if (stages != (kStageGramMf | kStageSolve) && chunk != g.n_cells) return cudaErrorInvalidValue;
+  // FP32 products with up to four layers: the direct form does everything in the solve stage
+  if (g.prec == PHY_PREC_FP32 && s.NL <= 4) {
+    if (!(stages & kStageSolve)) return cudaSuccess;
+    return s.NL == 2 ? launch_direct<2>(g, anchors, Y, sigma2, x_hat, sinr, llr, flags, st)
+                     : launch_direct<4>(g, anchors, Y, sigma2, x_hat, sinr, llr, flags, st);
+  }
   switch (s.NL) {
     case 2:
       return run_chunks<2>(g, wmax, s, anchors, Y, sigma2, x_hat, sinr, llr, flags, scratch,

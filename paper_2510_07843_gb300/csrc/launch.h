@@ -122,6 +122,8 @@ cudaError_t launch_llr(const Geo& g, const phy_c32* x_hat, const float* sinr, fl
 phy_status make_geo_checked(const phy_slot_cfg* cfg, Geo* g);
 // Kernel layer class (2, 4, 8 or 16) of a layer count.
 int nl_class_of(int n_layers);
+// 1 if that class runs the direct per-subcarrier form with FP32 products (no segment stage).
+int batch_direct_class(int nl_cls);
 
 // Batched receiver (batch.cuh holds the table). Per-job intermediate sizes and launch bounds,
 // the batched LS kernel, and the per-class segment and solve kernels.

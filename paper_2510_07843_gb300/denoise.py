@@ -139,9 +139,11 @@ def channel_mse(H_data, H_true_data) -> float:
     return float((H_data - H_true_data).abs().pow(2).mean().item())
 
 
-def evaluate(params_dev, st: SlotTiles, dev) -> Dict[str, float]:
+def evaluate(params_dev, st: SlotTiles, dev, tensor_cores: bool = False) -> Dict[str, float]:
     """Channel MSE at the data symbols and uncoded BER of LMMSE detection on the LS +
-    interpolation channel and on the denoised one (explicit-channel detector, same demapper)."""
+    interpolation channel and on the denoised one (explicit-channel detector, same demapper);
+    with tensor_cores also for the network run on the tensor cores with BF16 operands
+    (phy_cnn_denoise_bf16, keys mse_cnn_bf16 and ber_cnn_bf16)."""
     import torch
     spec, cfg = st.spec, st.cfg
     dshape = (spec.n_cells, len(spec.data_sym), spec.n_sc, spec.n_rx, spec.n_layers)
@@ -153,8 +155,17 @@ def evaluate(params_dev, st: SlotTiles, dev) -> Dict[str, float]:
     H_true = torch.empty_like(H_ls)
     phy.cnn_untile(cfg, st.label, H_true)
     out = {"mse_ls": channel_mse(H_ls, H_true), "mse_cnn": channel_mse(H_cnn, H_true)}
+    chans = [("ls", H_ls), ("cnn", H_cnn), ("genie", H_true)]
+    if tensor_cores:
+        H_tc = torch.empty_like(H_ls)
+        phy.cnn_denoise_bf16(cfg, params_dev, st.anchors, H_tc, ws)
+        off = phy.cnn_denoise_error_offset(cfg)
+        if int(ws[off:off + 4].view(torch.int32).item()) != 0:
+            raise RuntimeError("tensor-core denoiser: a bounded wait ran out")
+        out["mse_cnn_bf16"] = channel_mse(H_tc, H_true)
+        chans.append(("cnn_bf16", H_tc))
     bits = torch.from_numpy(st.slot.bits).to(dev)
-    for name, H in (("ls", H_ls), ("cnn", H_cnn), ("genie", H_true)):
+    for name, H in chans:
         n_re = spec.n_cells * len(spec.data_sym) * spec.n_sc
         x_hat = torch.empty((n_re, spec.n_layers), dtype=torch.complex64, device=dev)
         sinr = torch.empty((n_re, spec.n_layers), dtype=torch.float32, device=dev)

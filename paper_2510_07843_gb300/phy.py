@@ -92,6 +92,10 @@ _SIGS = {
     "phy_cnn_untile": (ctypes.c_int, [_P, _P, _P, _P]),
     "phy_cnn_denoise_workspace_size": (ctypes.c_size_t, [_P]),
     "phy_cnn_denoise": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "phy_cnn_forward_bf16": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, ctypes.c_size_t,
+                                            _P]),
+    "phy_cnn_denoise_bf16": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "phy_cnn_denoise_error_offset": (ctypes.c_size_t, [_P]),
 }
 
 STAGE_GRAM_MF, STAGE_SOLVE = 0, 1
@@ -438,6 +442,29 @@ def cnn_denoise(cfg: SlotConfig, params, anchors, H_data, workspace, stream=None
     _check("phy_cnn_denoise",
            load().phy_cnn_denoise(ctypes.byref(c), _ptr(params), _ptr(anchors), _ptr(H_data),
                                   _ptr(workspace), ws_bytes, _stream(stream)))
+
+
+def cnn_forward_bf16(n_tiles: int, params, tiles_in, tiles_out, workspace, stream=None):
+    """phy_cnn_forward_bf16: the denoiser on the tensor cores (BF16 operands, FP32 sums);
+    workspace word 0 then holds the timed-out CTA count (0 when the outputs are valid)."""
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check("phy_cnn_forward_bf16",
+           load().phy_cnn_forward_bf16(n_tiles, _ptr(params), _ptr(tiles_in), _ptr(tiles_out),
+                                       _ptr(workspace), ws_bytes, _stream(stream)))
+
+
+def cnn_denoise_bf16(cfg: SlotConfig, params, anchors, H_data, workspace, stream=None):
+    """phy_cnn_denoise_bf16: phy_cnn_denoise with the tensor-core forward pass."""
+    c = cfg.c()
+    ws_bytes = workspace.numel() * workspace.element_size()
+    _check("phy_cnn_denoise_bf16",
+           load().phy_cnn_denoise_bf16(ctypes.byref(c), _ptr(params), _ptr(anchors), _ptr(H_data),
+                                       _ptr(workspace), ws_bytes, _stream(stream)))
+
+
+def cnn_denoise_error_offset(cfg: SlotConfig) -> int:
+    c = cfg.c()
+    return int(load().phy_cnn_denoise_error_offset(ctypes.byref(c)))
 
 
 def noise_track(cfg: SlotConfig, mode: str, alpha: float, anchors, pilots, sigma2_state,

@@ -48,6 +48,9 @@ def _items(cfg):
     n_seg = max(G - 1, 1)
     nds = cfg.n_sym - len(cfg.dmrs_sym)
     nlc = next(c for c in (2, 4, 8, 16) if cfg.n_layers <= c)
+    if nlc <= 4:  # the direct form: no segment stage
+        return ((G * len(cfg.dmrs_sym) * cfg.n_cells, 0, -(-n_sc // 128) * nds * cfg.n_cells),
+                (2, 4, 8, 16).index(nlc))
     return ((G * len(cfg.dmrs_sym) * cfg.n_cells, n_seg * cfg.n_cells,
              -(-n_sc // 128) * nds * cfg.n_cells), (2, 4, 8, 16).index(nlc))
 

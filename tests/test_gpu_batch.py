@@ -80,7 +80,11 @@ def _assert_same(jobs):
     import torch
     for cfg, _, (a, b) in jobs:
         for k in ("x_hat", "sinr", "llr", "flags"):
-            assert torch.equal(getattr(a, k), getattr(b, k)), (cfg, k)
+            va, vb = getattr(a, k), getattr(b, k)
+            if not torch.equal(va, vb):
+                bad = (va != vb).nonzero()[:5].tolist()
+                raise AssertionError((cfg, k, bad, va.flatten()[:16].tolist(),
+                                      vb.flatten()[:16].tolist()))
         assert not torch.any(a.flags == 0xEE)
 
 

@@ -153,23 +153,53 @@ def test_interpolated_channel_and_tiles(dev):
 def test_trained_denoiser_beats_ls_interpolation(dev):
     """Trained on the GPU by the library's own kernels (16 generated slots of 12 PRB, 32 Rx x 8
     layers, SNR 0-30 dB, Doppler 0-500 Hz; 8 epochs of Adam), the network lowers the channel MSE
-    of LS + interpolation on held-out slots at 0 and 5 dB and does not lose BER. An untrained
-    (identity) network reproduces LS + interpolation exactly. Measured when the bounds were set:
-    MSE 0.162 -> 0.134 at 0 dB and 0.074 -> 0.066 at 5 dB; BER 16.8% -> 15.6% and 9.45% ->
-    8.97%."""
+    of LS + interpolation on held-out slots at 0 and 5 dB and does not lose BER, both in FP32 and
+    run on the tensor cores with BF16 operands; at 20 dB, where the gain is small, neither form
+    may lose. An untrained (identity) network reproduces LS + interpolation exactly. Measured
+    when the bounds were set: MSE 0.162 -> 0.134 at 0 dB and 0.074 -> 0.066 at 5 dB; BER 16.8%
+    -> 15.6% and 9.45% -> 8.97%."""
     import torch
     from paper_2510_07843_gb300 import denoise as D
     x, y = D.training_set(n_slots=16, n_prb=12, seed=11, dev=dev)
     tr = D.Trainer(D.init_params(0), batch=256, dev=dev, lr=2e-3)
     ident = tr.p.clone()
     held = {snr: D.slot_tiles(D.train_spec(n_prb=24, snr_db=snr, doppler_hz=300.0), 999, dev)
-            for snr in (0.0, 5.0)}
+            for snr in (0.0, 5.0, 20.0)}
     r0 = D.evaluate(ident, held[0.0], dev)
     assert r0["mse_cnn"] == r0["mse_ls"] and r0["ber_cnn"] == r0["ber_ls"]
     for ep in range(8):
         tr.epoch(x, y, seed=ep)
-    for snr, bound in ((0.0, 0.9), (5.0, 0.95)):
-        r = D.evaluate(tr.p, held[snr], dev)
+    for snr, bound in ((0.0, 0.9), (5.0, 0.95), (20.0, 1.0)):
+        r = D.evaluate(tr.p, held[snr], dev, tensor_cores=True)
         print(snr, r)
-        assert r["mse_cnn"] < bound * r["mse_ls"]
-        assert r["ber_cnn"] <= r["ber_ls"]
+        for form in ("cnn", "cnn_bf16"):
+            assert r[f"mse_{form}"] < bound * r["mse_ls"], (snr, form, r)
+            assert r[f"ber_{form}"] <= r["ber_ls"], (snr, form, r)
+
+
+@pytest.mark.parametrize("n", [1, 5, 300, 1203])
+def test_tensor_core_forward_matches_the_bf16_oracle(dev, n):
+    """phy_cnn_forward_bf16 (tcgen05, BF16 operands, FP32 sums) against the oracle's bfloat16
+    form (weights and each layer's input rounded to BF16, exact sums). The two differ only by
+    FP32 summation (about 1e-6 relative) and the rare activation whose FP32 and FP64 values round
+    to neighbouring BF16 numbers (one BF16 step, 2^-8 relative, in that activation): bar 2e-3 of
+    the network's correction (output minus input), against the BF16 effect itself (the FP32
+    network differs from the BF16 one by far more, which the test prints). Tile counts cover a
+    partial last group of four tiles and several groups per CTA."""
+    import torch
+    from paper_2510_07843_gb300 import phy
+    p, x, _ = random_net(100 + n, n)
+    out = torch.full((n, 2, 14, 12), float("nan"), dtype=torch.float32, device=dev)
+    ws = torch.full((64,), 7, dtype=torch.int32, device=dev)
+    phy.cnn_forward_bf16(n, T(p, dev), T(x, dev), out, ws)
+    torch.cuda.synchronize()
+    assert int(ws[0].item()) == 0  # no bounded wait ran out
+    got = out.cpu().numpy().astype(np.float64)
+    want16, _ = O.cnn_forward(p.astype(np.float64), x.astype(np.float64), operands="bf16")
+    want32, _ = O.cnn_forward(p.astype(np.float64), x.astype(np.float64))
+    corr = want16 - x
+    e = float(np.linalg.norm(got - want16) / np.linalg.norm(corr))
+    e16 = float(np.linalg.norm(want32 - want16) / np.linalg.norm(corr))
+    print(f"tensor-core forward n={n}: vs bf16 oracle {e:.2e}, bf16 vs fp32 oracle {e16:.2e}")
+    assert np.all(np.isfinite(got))
+    assert e <= 2e-3 and e < e16 / 4
