@@ -884,7 +884,8 @@ def serving_mixed_run(dev, slots: int = 100, n_cells: int = 32, rate_hz: float =
     """The serving configuration: uplink jobs of 32 cells arriving as Poisson streams at 2000
     slots/s per cell, each of its own shape (4-273 PRB, 4/16/32/64 Rx, 1-16 layers, QPSK to
     256-QAM, 23-tap 300 ns TDL with Jakes 100 Hz), served by continuous heterogeneous batching
-    (BatchServer over the batched receiver, FP32 products) for `slots` 0.5 ms slots in real
+    (BatchServer over the batched receiver: FP16 tensor-core products for jobs of 5 or more
+    layers, the direct FP32 form below that) for `slots` 0.5 ms slots in real
     time. Job inputs come from a pool of `pool_size` distinct seeded jobs resident on the device
     (arrivals pick pool entries uniformly). Latency is per job, arrival to completion seen by
     the host; throughput counts the REs of every served job over the run's span."""
@@ -895,7 +896,9 @@ def serving_mixed_run(dev, slots: int = 100, n_cells: int = 32, rate_hz: float =
     for i in range(pool_size):
         sp = S.spec_serving_job(rng)
         sl = S.make_slot(sp, 7000 + i, keep_h=False)
-        cfg = phy.SlotConfig.from_spec(sp)
+        # FP16 tensor-core products where they are dense (5 or more layers), the direct FP32
+        # form below that
+        cfg = phy.SlotConfig.from_spec(sp, precision="fp16" if sp.n_layers > 4 else "fp32")
         pool.append((cfg, *(torch.from_numpy(a).to(dev) for a in (sl.Y, sl.pilots, sl.sigma2))))
     duration = slots * serve.DEADLINE_S
     arrivals = S.serving_arrivals(n_cells, rate_hz, duration, seed + 1)
@@ -914,7 +917,8 @@ def serving_mixed_run(dev, slots: int = 100, n_cells: int = 32, rate_hz: float =
     span = max(j.done for j in done) - min(j.arrival for j in done)
     out.update(workload=f"{n_cells} cells, Poisson {rate_hz:g} slots/s per cell for {slots} "
                         f"slots of 0.5 ms; per job 4-273 PRB, 4/16/32/64 Rx, 1-16 layers, "
-                        f"QPSK-256QAM; pool of {pool_size} distinct resident jobs; FP32 products",
+                        f"QPSK-256QAM; pool of {pool_size} distinct resident jobs; FP16 "
+                        f"tensor-core products for 5-16 layers, FP32 for 1-4",
                res_per_s=n_res / span, offered_res_per_s=n_res / duration, res=int(n_res),
                batches=srv.batches, mean_batch=float(np.mean(srv.batch_sizes)),
                max_batch=int(max(srv.batch_sizes)), lanes=lanes,

@@ -271,18 +271,21 @@ phy_status phy_slot_run_noalloc(const phy_slot_cfg* cfg, const phy_c32* Y, const
  * layer class, so that a server can batch whatever jobs have arrived. A job is one
  * phy_slot_run() call's configuration and buffers (device pointers, same layouts and rules;
  * x_hat, sinr and llr may be NULL). On this path the Gram and matched-filter products run in
- * FP32 (cfg.precision must be PHY_PREC_FP32) and the cover length is the automatic one
+ * FP32 (cfg.precision PHY_PREC_FP32) or on the tensor cores with FP16 operands
+ * (PHY_PREC_TC_FP16, two DMRS symbols, even n_rx); the cover length is the automatic one
  * (cfg.occ_len 0 or equal to it); other jobs get PHY_ERR_UNSUPPORTED. Each job's outputs are
  * bitwise those of phy_slot_run() on that job alone.
  *  - The job table lives in caller-owned, page-locked, device-mapped host memory of
- *    phy_batch_table_bytes() bytes (e.g. cudaHostAlloc), zeroed before first use, 8-byte
- *    aligned; the device keeps a copy in a caller-owned device buffer of the same size, zeroed
- *    before first use. One table pair per batch in flight.
+ *    phy_batch_table_bytes() bytes (e.g. cudaHostAlloc), zeroed before first use, 128-byte
+ *    aligned (the TMA tensor maps it holds need that); the device keeps a copy in a
+ *    caller-owned device buffer of the same size, zeroed before first use, 128-byte aligned.
+ *    One table pair per batch in flight.
  *  - phy_batch_workspace_size(): intermediates of a batch (the sum over its jobs); 0 if a job's
  *    cfg is invalid or n_jobs is outside 1..64.
- *  - phy_batch_post() (host only, no CUDA call): validates the jobs, lays out their
- *    intermediates in `workspace` (device, 256-byte aligned), writes the table into table_host
- *    and rings its doorbell last. Do not post into a table whose previous batch has not
+ *  - phy_batch_post() (host only; for tensor-core jobs it encodes their TMA tensor maps, a
+ *    driver call that touches no device): validates the jobs, lays out their intermediates in
+ *    `workspace` (device, 256-byte aligned), writes the table into table_host and rings its
+ *    doorbell last. Do not post into a table whose previous batch has not
  *    finished on the device. PHY_ERR_NO_MEMORY if the workspace is too small.
  *  - phy_batch_launch(): enqueues on `stream` a gate kernel that polls table_host's doorbell at
  *    most poll_limit times, about 1 us apart (poll_limit < 0: a million, about a second), copies

@@ -102,7 +102,8 @@ extern "C" phy_status phy_batch_post(const phy_job* jobs, int32_t n_jobs, void* 
                                      void* workspace, size_t workspace_bytes) {
   if (!jobs || !table_host || n_jobs < 1 || n_jobs > phy::kBatchMaxJobs)
     return PHY_ERR_INVALID_ARG;
-  if (reinterpret_cast<uintptr_t>(table_host) % 8 || reinterpret_cast<uintptr_t>(workspace) % 256)
+  if (reinterpret_cast<uintptr_t>(table_host) % alignof(BatchTable) ||
+      reinterpret_cast<uintptr_t>(workspace) % 256)
     return PHY_ERR_INVALID_ARG;
   BatchTable* t = static_cast<BatchTable*>(table_host);
   // everything but the doorbell words is rebuilt
@@ -116,12 +117,18 @@ extern "C" phy_status phy_batch_post(const phy_job* jobs, int32_t n_jobs, void* 
     phy::Geo g;
     const phy_status s = phy::make_geo_checked(&jb.cfg, &g);
     if (s != PHY_OK) return s;
-    // the batched path: FP32 products, automatic cover length, shapes within the captured
-    // launches' shared memory
+    // the batched path: FP32 or FP16 tensor-core products, automatic cover length, shapes
+    // within the captured launches' shared memory; tensor-core jobs need two DMRS symbols and
+    // the tensor-core kernel's shape rules
     int auto_l = 1;
     while (auto_l < (g.n_layers + 1) / 2) auto_l *= 2;
-    if (g.prec != PHY_PREC_FP32 || g.L != auto_l || !phy::batch_geometry_fits(g))
+    const int nlc = phy::nl_class_of(g.n_layers), cls = phy::batch_class(nlc);
+    const bool tc = g.prec == PHY_PREC_TC_FP16;
+    const bool direct = !tc && phy::batch_direct_class(nlc) != 0;
+    if ((g.prec != PHY_PREC_FP32 && !tc) || g.L != auto_l) return PHY_ERR_UNSUPPORTED;
+    if (tc && (g.n_dmrs != 2 || !phy::seg_prep_tc_supported(g) || !phy::batch_solve_fits(g)))
       return PHY_ERR_UNSUPPORTED;
+    if (!tc && !direct && !phy::batch_geometry_fits(g)) return PHY_ERR_UNSUPPORTED;
     if (!jb.Y || !jb.pilots || !jb.sigma2 || !jb.flags) return PHY_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(jb.Y) % 16) return PHY_ERR_INVALID_ARG;
     const size_t need = phy::job_workspace(g);
@@ -146,15 +153,18 @@ extern "C" phy_status phy_batch_post(const phy_job* jobs, int32_t n_jobs, void* 
     used += need;
     J.wmax = phy::batch_wmax(g);
     J.max_segs = phy::batch_max_segs(g);
-    // items per stage: LS (group, DMRS symbol, cell) over all jobs; segment (segment, cell) and
-    // solve (128 subcarriers, data symbol, cell) per layer class
-    const int nlc = phy::nl_class_of(g.n_layers), cls = phy::batch_class(nlc);
-    // up to four layers: the direct form, no segment stage
-    const bool direct = phy::batch_direct_class(nlc) != 0;
+    if (tc && !phy::encode_tc_maps(g, J.anchors, jb.Y, &J.tmY, &J.tmA))
+      return PHY_ERR_INVALID_ARG;
+    // items per stage: LS (group, DMRS symbol, cell) over all jobs; per layer class the segment
+    // stage (FP32 or tensor-core: segment, cell) and the solve or, for the direct form, that
+    // form (128 subcarriers, data symbol, cell)
+    const int res = ((g.n_sc + 127) / 128) * g.n_dsym * g.n_cells;
+    const int seg_items = g.n_seg * g.n_cells;
     const int items[phy::kBatchStages] = {g.G * g.n_dmrs * g.n_cells,
-                                          direct ? 0 : g.n_seg * g.n_cells,
-                                          ((g.n_sc + 127) / 128) * g.n_dsym * g.n_cells};
+                                          !tc && !direct ? seg_items : 0, tc ? seg_items : 0,
+                                          direct ? 0 : res, direct ? res : 0};
     for (int stg = 0; stg < phy::kBatchStages; ++stg) {
+      if (stg != phy::kBatchChest && items[stg] == 0) continue;
       const int c = stg == phy::kBatchChest ? 0 : cls;
       int& nj = t->n_class_jobs[stg][c];
       t->job_of[stg][c][nj] = (unsigned char)i;
@@ -173,7 +183,8 @@ extern "C" phy_status phy_batch_post(const phy_job* jobs, int32_t n_jobs, void* 
 
 extern "C" phy_status phy_batch_launch(void* table_host, void* table_dev, int64_t poll_limit,
                                        void* stream) {
-  if (!table_host || !table_dev || reinterpret_cast<uintptr_t>(table_dev) % 8)
+  if (!table_host || !table_dev || reinterpret_cast<uintptr_t>(table_dev) % alignof(BatchTable) ||
+      reinterpret_cast<uintptr_t>(table_host) % alignof(BatchTable))
     return PHY_ERR_INVALID_ARG;
   void* mapped = nullptr;
   if (cudaHostGetDevicePointer(&mapped, table_host, 0) != cudaSuccess || !mapped) {

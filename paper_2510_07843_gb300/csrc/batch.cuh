@@ -9,19 +9,33 @@
 // kernels, on that job's geometry and buffers.
 #pragma once
 
+#include <cuda.h>
+
 #include "common.cuh"
 
 namespace phy {
 
 constexpr int kBatchMaxJobs = 64;
 constexpr int kBatchClasses = 4;  // layer classes 2, 4, 8, 16 (the kernels' NL)
-enum BatchStage : int { kBatchChest = 0, kBatchSeg = 1, kBatchSolve = 2, kBatchStages = 3 };
+// Stages: LS estimation (every job, class 0), FP32 segment kernel, tensor-core segment kernel
+// (FP16 products), per-RE solve (after either segment kernel), direct form (FP32, <= 4 layers).
+enum BatchStage : int {
+  kBatchChest = 0,
+  kBatchSeg = 1,
+  kBatchSegTc = 2,
+  kBatchSolve = 3,
+  kBatchDirect = 4,
+  kBatchStages = 5
+};
 
 __host__ __device__ constexpr int batch_class(int nl_class) {
   return nl_class <= 2 ? 0 : nl_class <= 4 ? 1 : nl_class <= 8 ? 2 : 3;
 }
 
 struct BatchJob {
+  // tensor maps of the job's grid and anchors (jobs with tensor-core products; encoded by the
+  // host into the table, read by TMA from the device copy)
+  CUtensorMap tmY, tmA;
   Geo g;
   const phy_c32* Y;
   const phy_c32* pilots;

@@ -764,10 +764,10 @@ __global__ void __launch_bounds__(kDirectThreads)
     direct_batch_kernel(const BatchTable* __restrict__ t) {
   __shared__ Geo sg;
   constexpr int cls = batch_class(NL);
-  const int n = t->n_items[kBatchSolve][cls];
+  const int n = t->n_items[kBatchDirect][cls];
   for (int w = blockIdx.x; w < n; w += gridDim.x) {
     int local;
-    const BatchJob& J = t->job[batch_find(t, kBatchSolve, cls, w, local)];
+    const BatchJob& J = t->job[batch_find(t, kBatchDirect, cls, w, local)];
     batch_load_geo(sg, J.g);
     __syncthreads();
     const int nb = (sg.n_sc + kDirectThreads - 1) / kDirectThreads;
@@ -830,30 +830,6 @@ __global__ void __launch_bounds__(kSolveThreads)
                                              J.flags, J.err);
     if (!__syncthreads_and(usable)) break;  // copies still in flight: the barrier is unusable
   }
-}
-
-template <int NL>
-cudaError_t launch_batch_class(const BatchTable* t, int grid_seg, int grid_solve,
-                               size_t smem_seg, size_t smem_solve, cudaStream_t st) {
-  static size_t cfg_seg[kMaxDevices] = {}, cfg_solve[kMaxDevices] = {};
-  const int dev = current_device();
-  if (smem_seg > cfg_seg[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(seg_prep_batch_kernel<NL>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_seg);
-    if (e != cudaSuccess) return e;
-    cfg_seg[dev] = smem_seg;
-  }
-  if (smem_solve > cfg_solve[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(re_solve_batch_kernel<NL>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_solve);
-    if (e != cudaSuccess) return e;
-    cfg_solve[dev] = smem_solve;
-  }
-  seg_prep_batch_kernel<NL><<<grid_seg, kPrepThreads, smem_seg, st>>>(t);
-  re_solve_batch_kernel<NL><<<grid_solve, kSolveThreads, smem_solve, st>>>(t, (int)smem_solve);
-  return cudaGetLastError();
 }
 
 struct Sizes {
@@ -1068,14 +1044,23 @@ BatchClassLaunch batch_class_launch() {
   return b;
 }
 
+// One layer class: the direct form (FP32, <= 4 layers), the FP32 segment kernel (>= 5
+// layers), the tensor-core segment kernel (FP16 jobs), then the solve of every job that went
+// through a segment kernel. Empty stages exit at once.
 template <int NL>
 cudaError_t launch_batch_nl(const BatchTable* t, cudaStream_t st) {
-  if constexpr (NL <= 4) {  // the direct form: everything in one kernel
-    direct_batch_kernel<NL><<<device_sm_count() * 8, kDirectThreads, 0, st>>>(t);
-    return cudaGetLastError();
-  }
   const BatchClassLaunch b = batch_class_launch<NL>();
-  return launch_batch_class<NL>(t, b.grid_seg, b.grid_solve, b.smem_seg, b.smem_solve, st);
+  if constexpr (NL <= 4) {
+    direct_batch_kernel<NL><<<device_sm_count() * 8, kDirectThreads, 0, st>>>(t);
+  } else {
+    seg_prep_batch_kernel<NL><<<b.grid_seg, kPrepThreads, b.smem_seg, st>>>(t);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if ((e = launch_seg_prep_tc_batch(t, NL, st)) != cudaSuccess) return e;
+  re_solve_batch_kernel<NL><<<b.grid_solve, kSolveThreads, b.smem_solve, st>>>(
+      t, (int)b.smem_solve);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -1095,6 +1080,18 @@ bool batch_geometry_fits(const Geo& g) {
   const PrepLayout f = prep_layout(NL, g.n_dmrs, g.n_rx, host_max_segment_width(g));
   return (size_t)f.total * sizeof(cf) <= seg &&
          solve_smem_bytes(NL, 0, max_segments_per_block(g)) <= solve;
+}
+
+bool batch_solve_fits(const Geo& g) {
+  const int NL = nl_class(g.n_layers);
+  BatchClassLaunch b;
+  switch (NL) {
+    case 2: b = batch_class_smem<2>(); break;
+    case 4: b = batch_class_smem<4>(); break;
+    case 8: b = batch_class_smem<8>(); break;
+    default: b = batch_class_smem<16>(); break;
+  }
+  return solve_smem_bytes(NL, 0, max_segments_per_block(g)) <= b.smem_solve;
 }
 
 cudaError_t launch_batch_stages(const BatchTable* t, cudaStream_t st) {

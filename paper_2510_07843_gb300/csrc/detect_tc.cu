@@ -29,6 +29,7 @@
 #include <cstdio>
 #include <cstdlib>
 
+#include "batch.cuh"
 #include "launch.h"
 #include "segment.cuh"
 #include "tc.cuh"
@@ -157,12 +158,46 @@ __device__ __forceinline__ int tile_syms(const Geo& g, const Item& it, int t) {
   return min(it.spt, g.n_dsym - t * it.spt);
 }
 
-template <int NL, int NC, uint32_t FMT, int RS>
-__global__ void __launch_bounds__(kTcThreads, 1)
-    seg_prep_tc_kernel(const __grid_constant__ CUtensorMap tmY,
-                       const __grid_constant__ CUtensorMap tmA, Geo g, int cell0, int nc,
-                       float4* __restrict__ ygg, cf* __restrict__ bvec,
-                       unsigned* __restrict__ err) {
+// Where a work item's job lives: its geometry, tensor maps, outputs and error word, and the
+// item's index within the job.
+struct TcView {
+  const Geo* g;
+  const CUtensorMap* tmY;
+  const CUtensorMap* tmA;
+  float4* ygg;
+  cf* bvec;
+  unsigned* err;
+  int w, cell0;
+};
+// One job: (segment, cell) items of the chunk starting at cell0; maps are kernel parameters.
+struct TcSingle {
+  static constexpr bool kBatched = false;
+  const Geo* g;
+  const CUtensorMap* tmY;
+  const CUtensorMap* tmA;
+  float4* ygg;
+  cf* bvec;
+  unsigned* err;
+  int cell0, nc;
+  __device__ int n_work() const { return g->n_seg * nc; }
+  __device__ TcView at(int w) const { return TcView{g, tmY, tmA, ygg, bvec, err, w, cell0}; }
+};
+// The batched receiver's tensor-core jobs of one layer class; maps are in the device table.
+struct TcBatch {
+  static constexpr bool kBatched = true;
+  const BatchTable* t;
+  int cls;
+  __device__ int n_work() const { return t->n_items[kBatchSegTc][cls]; }
+  __device__ TcView at(int w) const {
+    int local;
+    const BatchJob& J = t->job[batch_find(t, kBatchSegTc, cls, w, local)];
+    return TcView{&J.g, &J.tmY, &J.tmA, J.ygg, J.bvec, J.err, local, 0};
+  }
+};
+
+// The kernel body over the work items of a source (TcSingle or TcBatch).
+template <int NL, int NC, uint32_t FMT, int RS, class Src>
+__device__ __forceinline__ void seg_prep_tc_body(const Src& src) {
   using Lay = Layout<FMT>;
   using Sm = Smem<NL, NC, FMT, RS>;
   constexpr int S = RS;
@@ -187,10 +222,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint32_t* misc = reinterpret_cast<uint32_t*>(smem + Sm::kMisc);  // TMEM address
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nr = g.n_rx, nl = g.n_layers, nds = g.n_dsym;
-  const int n_work = g.n_seg * nc;
-  const uint32_t y_box_bytes = (uint32_t)nr * kBoxSc * 8;
-  const uint32_t a_box_bytes = (uint32_t)nl * nr * 8;
+  const int n_work = src.n_work();
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
@@ -219,14 +251,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (lane == 0) {
       bool ok = true;
       for (int w = blockIdx.x; w < n_work && ok; w += gridDim.x) {
-        const Item it = item_of(g, w, cell0);
+        const TcView v = src.at(w);
+        const Geo& g = *v.g;
+        const Item it = item_of(g, v.w, v.cell0);
+        const int nds = g.n_dsym;
+        const uint32_t y_box_bytes = (uint32_t)g.n_rx * kBoxSc * 8;
+        const uint32_t a_box_bytes = (uint32_t)g.n_layers * g.n_rx * 8;
+        if constexpr (Src::kBatched) {  // maps written through the generic proxy (the table copy)
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(v.tmY)
+                       : "memory");
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(v.tmA)
+                       : "memory");
+        }
         if (nitem > 0) ok = tc::mbar_wait_sleep(a_empty, (nitem - 1) & 1, g.wait_seg);
         if (!ok) break;
         tc::mbar_arrive_expect_tx(a_full, NC * a_box_bytes);
         const int g1 = seg_g1(g, it.j);
         for (int corner = 0; corner < NC; ++corner) {
           const int d = corner >> 1, grp = (corner & 1) ? g1 : it.j;
-          tc::tma_load_3d(anch + corner * Sm::kCorner, &tmA, 0, 0,
+          tc::tma_load_3d(anch + corner * Sm::kCorner, v.tmA, 0, 0,
                           (it.cell * g.n_dmrs + d) * g.G + grp, a_full);
         }
         ++nitem;
@@ -237,7 +280,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (nbox >= (uint32_t)S) ok = tc::mbar_wait_sleep(empty + s, ((nbox / S) - 1) & 1, g.wait_seg);
             if (!ok) break;
             tc::mbar_arrive_expect_tx(full + s, y_box_bytes);
-            tc::tma_load_3d(ring + s * kStageBytes, &tmY, 2 * (it.lo2 + kBoxSc * b), 0, z, full + s);
+            tc::tma_load_3d(ring + s * kStageBytes, v.tmY, 2 * (it.lo2 + kBoxSc * b), 0, z,
+                            full + s);
             ++nbox;
           }
         }
@@ -267,8 +311,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (warp < kConvWarps) {
     uint32_t nbox = 0, nitem = 0, ntile = 0;  // boxes, anchor sets and RE tiles consumed
     uint32_t x_count = 0, mf_count[2] = {0, 0};  // MMA commits per barrier
+    unsigned* err = nullptr;                     // the current item's error word
     for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
-      const Item it = item_of(g, w, cell0);
+      const TcView v = src.at(w);
+      const Geo& g = *v.g;
+      const Item it = item_of(g, v.w, v.cell0);
+      const int nr = g.n_rx, nl = g.n_layers;
+      err = v.err;
       // every MMA of the previous item read CC; its last commit covers them all
       if (ntile > 0) fail |= !tc::mbar_wait_sleep(mf_bar + ((ntile - 1) & 1), ((ntile - 1) >> 1) & 1,
                                             g.wait_seg);
@@ -375,7 +424,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (stop) break;
     }
     if (gtid == 0) {
-      if (stop) atomicAdd(err, 1u);
+      if (stop && err) atomicAdd(err, 1u);
       // MMAs still running (only after a timeout) must finish before tensor memory is released
       if (x_count) tc::mbar_wait_sleep(x_bar, (x_count - 1) & 1, kWaitIters);
       for (int b = 0; b < 2; ++b)
@@ -383,8 +432,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
   } else {
     uint32_t nitem = 0, ntile = 0;
+    unsigned* err = nullptr;
     for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
-      const Item it = item_of(g, w, cell0);
+      const TcView v = src.at(w);
+      const Geo& g = *v.g;
+      const Item it = item_of(g, v.w, v.cell0);
+      const int nds = g.n_dsym;
+      float4* ygg = v.ygg;
+      cf* bvec = v.bvec;
+      err = v.err;
       // ---- X -> shared memory (after every drain warp is done with the previous item's X)
       fail |= !tc::mbar_wait_sleep(x_bar, nitem & 1, g.wait_seg);
       tc::fence_after_sync();
@@ -477,7 +533,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       stop = tc::bar_or<2, 128>(fail);
       if (stop) break;
     }
-    if (gtid == 0 && stop) atomicAdd(err, 1u);
+    if (gtid == 0 && stop && err) atomicAdd(err, 1u);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -487,7 +543,44 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
+template <int NL, int NC, uint32_t FMT, int RS>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    seg_prep_tc_kernel(const __grid_constant__ CUtensorMap tmY,
+                       const __grid_constant__ CUtensorMap tmA, const __grid_constant__ Geo g,
+                       int cell0, int nc, float4* __restrict__ ygg, cf* __restrict__ bvec,
+                       unsigned* __restrict__ err) {
+  const TcSingle src{&g, &tmY, &tmA, ygg, bvec, err, cell0, nc};
+  seg_prep_tc_body<NL, NC, FMT, RS>(src);
+}
+
+// Batched form: the FP16 tensor-core jobs of one layer class (two DMRS symbols) in the table.
+template <int NL>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    seg_prep_tc_batch_kernel(const BatchTable* __restrict__ t) {
+  const TcBatch src{t, batch_class(NL)};
+  seg_prep_tc_body<NL, 4, tc::kFmtF16, Layout<tc::kFmtF16>::kStages>(src);
+}
+
 // ---------------------------------------------------------------- host side
+}  // namespace
+
+// Received grid: (2 n_sc floats, n_rx, n_cells n_sym), box = kBoxSc subcarriers x all antennas.
+// Anchors: (2 n_rx floats, n_layers, n_cells n_dmrs G), box = one corner's [layer][antenna].
+bool encode_tc_maps(const Geo& g, const phy_c32* anchors, const phy_c32* Y, CUtensorMap* tmY,
+                    CUtensorMap* tmA) {
+  const cuuint64_t ydim[3] = {(cuuint64_t)2 * g.n_sc, (cuuint64_t)g.n_rx,
+                              (cuuint64_t)g.n_cells * g.n_sym};
+  const cuuint64_t ystr[2] = {(cuuint64_t)8 * g.n_sc, (cuuint64_t)8 * g.n_sc * g.n_rx};
+  const cuuint32_t ybox[3] = {2 * kBoxSc, (cuuint32_t)g.n_rx, 1};
+  const cuuint64_t adim[3] = {(cuuint64_t)2 * g.n_rx, (cuuint64_t)g.n_layers,
+                              (cuuint64_t)g.n_cells * g.n_dmrs * g.G};
+  const cuuint64_t astr[2] = {(cuuint64_t)8 * g.n_rx, (cuuint64_t)8 * g.n_rx * g.n_layers};
+  const cuuint32_t abox[3] = {(cuuint32_t)2 * g.n_rx, (cuuint32_t)g.n_layers, 1};
+  return make_map(tmY, Y, ydim, ystr, ybox) && make_map(tmA, anchors, adim, astr, abox);
+}
+
+namespace {
+
 template <int NL, int NC, uint32_t FMT, int RS>
 cudaError_t launch_one(const Geo& g, int c0, int nc, const phy_c32* anchors, const phy_c32* Y,
                        float4* ygg, cf* bvec, unsigned* err, cudaStream_t st) {
@@ -507,16 +600,7 @@ cudaError_t launch_one(const Geo& g, int c0, int nc, const phy_c32* anchors, con
   // Received grid: (2 n_sc floats, n_rx, n_cells n_sym), box = kBoxSc subcarriers x all antennas.
   // Anchors: (2 n_rx floats, n_layers, n_cells n_dmrs G), box = one corner's [layer][antenna].
   CUtensorMap tmY, tmA;
-  const cuuint64_t ydim[3] = {(cuuint64_t)2 * g.n_sc, (cuuint64_t)g.n_rx,
-                              (cuuint64_t)g.n_cells * g.n_sym};
-  const cuuint64_t ystr[2] = {(cuuint64_t)8 * g.n_sc, (cuuint64_t)8 * g.n_sc * g.n_rx};
-  const cuuint32_t ybox[3] = {2 * kBoxSc, (cuuint32_t)g.n_rx, 1};
-  const cuuint64_t adim[3] = {(cuuint64_t)2 * g.n_rx, (cuuint64_t)g.n_layers,
-                              (cuuint64_t)g.n_cells * g.n_dmrs * g.G};
-  const cuuint64_t astr[2] = {(cuuint64_t)8 * g.n_rx, (cuuint64_t)8 * g.n_rx * g.n_layers};
-  const cuuint32_t abox[3] = {(cuuint32_t)2 * g.n_rx, (cuuint32_t)g.n_layers, 1};
-  if (!make_map(&tmY, Y, ydim, ystr, ybox) || !make_map(&tmA, anchors, adim, astr, abox))
-    return cudaErrorInvalidValue;
+  if (!encode_tc_maps(g, anchors, Y, &tmY, &tmA)) return cudaErrorInvalidValue;
   const int n_work = g.n_seg * nc;
   const int grid = std::min(n_work, num_sms);
   seg_prep_tc_kernel<NL, NC, FMT, RS><<<grid, kTcThreads, smem, st>>>(tmY, tmA, g, c0, nc, ygg,
@@ -557,7 +641,31 @@ cudaError_t launch_fmt(const Geo& g, int NL, int c0, int nc, const phy_c32* anch
   }
 }
 
+template <int NL>
+cudaError_t launch_tc_batch_nl(const BatchTable* t, cudaStream_t st) {
+  constexpr size_t smem = Smem<NL, 4, tc::kFmtF16, Layout<tc::kFmtF16>::kStages>::kTotal;
+  static bool configured_on[kMaxDevices] = {};
+  bool& configured = configured_on[current_device()];
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(seg_prep_tc_batch_kernel<NL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  seg_prep_tc_batch_kernel<NL><<<device_sm_count(), kTcThreads, smem, st>>>(t);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_seg_prep_tc_batch(const BatchTable* t, int nl_cls, cudaStream_t st) {
+  switch (nl_cls) {
+    case 2: return launch_tc_batch_nl<2>(t, st);
+    case 4: return launch_tc_batch_nl<4>(t, st);
+    case 8: return launch_tc_batch_nl<8>(t, st);
+    default: return launch_tc_batch_nl<16>(t, st);
+  }
+}
 
 bool seg_prep_tc_supported(const Geo& g) {
   // tensor-map rules: 16-byte strides and inner box extents (even antenna count); tiles of

@@ -136,5 +136,13 @@ int batch_max_segs(const Geo& g);
 bool batch_geometry_fits(const Geo& g);
 cudaError_t launch_chest_batch(const BatchTable* t, int grid, cudaStream_t st);
 cudaError_t launch_batch_stages(const BatchTable* t, cudaStream_t st);
+// TMA tensor maps of the tensor-core segment kernel for a geometry's grid and anchors.
+bool encode_tc_maps(const Geo& g, const phy_c32* anchors, const phy_c32* Y, CUtensorMap* tmY,
+                    CUtensorMap* tmA);
+// Whether the batched solve (after either segment kernel) and, for FP32 products, the batched
+// FP32 segment kernel fit the captured launches' shared memory for g.
+bool batch_solve_fits(const Geo& g);
+// The batched tensor-core segment kernel (FP16 products, two DMRS symbols) of one layer class.
+cudaError_t launch_seg_prep_tc_batch(const BatchTable* t, int nl_cls, cudaStream_t st);
 
 }  // namespace phy

@@ -24,9 +24,12 @@ def _job(cfg, base=FAKE):
 
 
 def _table():
+    """A zeroed host table, 128-byte aligned (a view into a larger buffer)."""
     n = phy.batch_table_bytes()
-    assert n % 8 == 0
-    return np.zeros(n // 8, dtype=np.uint64)
+    assert n % 128 == 0
+    raw = np.zeros(n // 8 + 16, dtype=np.uint64)
+    off = (-raw.ctypes.data % 128) // 8
+    return raw[off:off + n // 8]
 
 
 def _post(jobs, table, ws_bytes=1 << 40):
@@ -69,13 +72,16 @@ def test_post_writes_the_table_and_rings_the_doorbell(lib):
     assert _post([_job(c) for c in MIX], t) == 0
     w = _words(t)
     assert w[0] == 1 and w[2] == 0 and w[3] == len(MIX)  # seq bumped, status pending, n_jobs
-    n_items = w[4:16].reshape(3, 4)
-    want = np.zeros((3, 4), dtype=np.int64)
+    n_items = w[4:24].reshape(5, 4)  # stages: LS, FP32 segment, tensor-core segment, solve, direct
+    want = np.zeros((5, 4), dtype=np.int64)
     for c in MIX:
         (ls, seg, solve), cls = _items(c)
         want[0, 0] += ls
-        want[1, cls] += seg
-        want[2, cls] += solve
+        if cls <= 1:
+            want[4, cls] += solve
+        else:
+            want[1, cls] += seg
+            want[3, cls] += solve
     assert np.array_equal(n_items, want)
     assert _post([_job(MIX[0])], t) == 0 and w[0] == 2  # every post rings again
 
@@ -90,7 +96,8 @@ def test_workspace_size_is_the_sum_over_jobs(lib):
 
 
 @pytest.mark.parametrize("bad,code", [
-    (dict(precision="fp16"), 2),          # the batched path computes its products in FP32
+    (dict(precision="bf16"), 2),          # products in FP32 or FP16 on this path
+    (dict(precision="fp16", dmrs_sym=(2,)), 2),  # tensor-core jobs need two DMRS symbols
     (dict(occ_len=16, n_layers=16), 2),   # forced cover length other than the automatic one
     (dict(n_layers=17), 1),
     (dict(qm=5), 1),
@@ -111,6 +118,7 @@ def test_post_rejects_bad_counts_and_pointers(lib):
     assert lib.phy_batch_post(many, 65, t.ctypes.data, FAKE, 1 << 30) == 1
     assert lib.phy_batch_post(arr, 1, None, FAKE, 1 << 30) == 1
     assert lib.phy_batch_post(arr, 1, t.ctypes.data, FAKE + 8, 1 << 30) == 1  # workspace align
+    assert lib.phy_batch_post(arr, 1, t.ctypes.data + 8, FAKE, 1 << 30) == 1  # table align
     assert _post([_job(MIX[1], base=FAKE + 8)], t) == 1  # grid not 16-byte aligned
     assert lib.phy_batch_status(None) == 1
     assert lib.phy_batch_status(ctypes.c_void_p(t.ctypes.data)) == 1  # nothing ran

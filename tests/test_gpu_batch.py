@@ -24,7 +24,8 @@ def dev():
 
 
 # (spec, seed, extra cfg) of a heterogeneous batch: every layer class, one and two DMRS
-# symbols, every modulation, both LLR formats, multi-cell jobs, FP64 re-computation enabled
+# symbols, every modulation, both LLR formats, multi-cell jobs, FP64 re-computation enabled,
+# FP32 and FP16 tensor-core products
 MIX = [
     (S.spec_massive_mimo(n_cells=1, n_prb=24), 501, {}),
     (S.SlotSpec(n_cells=2, n_prb=4, n_rx=4, n_layers=1, qm=2, dmrs_sym=(2,), snr_db=12.0), 502,
@@ -36,6 +37,14 @@ MIX = [
     (S.SlotSpec(n_prb=33, n_rx=16, n_layers=3, qm=4, dmrs_sym=(2, 11), snr_db=18.0,
                 doppler_hz=300.0), 506, {}),
     (S.SlotSpec(n_prb=1, n_rx=2, n_layers=2, qm=2, dmrs_sym=(0,), n_sym=2), 507, {}),
+    # FP16 tensor-core products: every layer class
+    (S.spec_massive_mimo(n_cells=2, n_prb=10), 508, {"precision": "fp16"}),
+    (S.SlotSpec(n_prb=23, n_rx=32, n_layers=6, qm=6, dmrs_sym=(2, 11), snr_db=25.0), 509,
+     {"precision": "fp16", "llr_format": "f16"}),
+    (S.SlotSpec(n_prb=14, n_rx=16, n_layers=4, qm=4, dmrs_sym=(2, 11), snr_db=20.0), 510,
+     {"precision": "fp16"}),
+    (S.SlotSpec(n_prb=5, n_rx=4, n_layers=1, qm=2, dmrs_sym=(2, 11), snr_db=15.0), 511,
+     {"precision": "fp16"}),
 ]
 
 
@@ -119,7 +128,7 @@ def test_captured_launch_serves_changing_batches(dev):
     with torch.cuda.graph(g, stream=st):
         phy.batch_launch(host, devt, stream=st)
     _alone(jobs)
-    for order in ([6, 0, 3], [1, 2, 4, 5], list(range(7))[::-1]):
+    for order in ([6, 0, 3, 8], [1, 2, 4, 5, 10], [7, 9], list(range(len(MIX)))[::-1]):
         sub = [jobs[i] for i in order]
         for _, _, o in sub:
             o[0].flags.fill_(0xEE)
