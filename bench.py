@@ -879,7 +879,7 @@ def time_variant(spec, precision, refactor, llr, args, slot, dev, world, fl_peak
     return rec, cfg, buf, st
 
 
-def serving_mixed_run(dev, slots: int = 100, n_cells: int = 32, rate_hz: float = 2000.0,
+def serving_mixed_run(dev, slots: int = 100, n_cells=(32, 16), rate_hz: float = 2000.0,
                       pool_size: int = 48, lanes: int = 2, seed: int = 5) -> dict:
     """The serving configuration: uplink jobs of 32 cells arriving as Poisson streams at 2000
     slots/s per cell, each of its own shape (4-273 PRB, 4/16/32/64 Rx, 1-16 layers, QPSK to
@@ -901,30 +901,33 @@ def serving_mixed_run(dev, slots: int = 100, n_cells: int = 32, rate_hz: float =
         cfg = phy.SlotConfig.from_spec(sp, precision="fp16" if sp.n_layers > 4 else "fp32")
         pool.append((cfg, *(torch.from_numpy(a).to(dev) for a in (sl.Y, sl.pilots, sl.sigma2))))
     duration = slots * serve.DEADLINE_S
-    arrivals = S.serving_arrivals(n_cells, rate_hz, duration, seed + 1)
-    pick = rng.integers(0, pool_size, len(arrivals))
-    jobs = [serve.MixedJob(*pool[p], arrival=t, job_id=k)
-            for k, ((t, _), p) in enumerate(zip(arrivals, pick))]
     srv = serve.BatchServer(device=dev, lanes=lanes)
-    srv.prepare(jobs[0])
-    # a short untimed stream first (kernels warm, lanes in use), then the measured one
+    srv.prepare(serve.MixedJob(*pool[0], arrival=0.0, job_id=-1))
+    # a short untimed stream first (kernels warm, lanes in use), then the measured ones
     srv.run([serve.MixedJob(*pool[p], arrival=0.0, job_id=-1) for p in range(min(8, pool_size))],
             realtime=False)
-    srv.batches, srv.batch_sizes, srv.service = 0, [], []
-    done = srv.run(jobs, realtime=True)
-    out = serve.latency_summary(done, service=srv.service)
-    n_res = sum(j.n_res for j in done)
-    span = max(j.done for j in done) - min(j.arrival for j in done)
-    out.update(workload=f"{n_cells} cells, Poisson {rate_hz:g} slots/s per cell for {slots} "
-                        f"slots of 0.5 ms; per job 4-273 PRB, 4/16/32/64 Rx, 1-16 layers, "
-                        f"QPSK-256QAM; pool of {pool_size} distinct resident jobs; FP16 "
-                        f"tensor-core products for 5-16 layers, FP32 for 1-4",
-               res_per_s=n_res / span, offered_res_per_s=n_res / duration, res=int(n_res),
-               batches=srv.batches, mean_batch=float(np.mean(srv.batch_sizes)),
-               max_batch=int(max(srv.batch_sizes)), lanes=lanes,
-               arena_bytes_per_lane=srv.arena_bytes,
-               api="phy_batch_post / phy_batch_launch (captured graph per lane)")
-    return out
+    runs = []
+    for cells in n_cells:
+        arrivals = S.serving_arrivals(cells, rate_hz, duration, seed + cells)
+        pick = rng.integers(0, pool_size, len(arrivals))
+        jobs = [serve.MixedJob(*pool[p], arrival=t, job_id=k)
+                for k, ((t, _), p) in enumerate(zip(arrivals, pick))]
+        srv.batches, srv.batch_sizes, srv.service = 0, [], []
+        done = srv.run(jobs, realtime=True)
+        out = serve.latency_summary(done, service=srv.service)
+        n_res = sum(j.n_res for j in done)
+        span = max(j.done for j in done) - min(j.arrival for j in done)
+        out.update(cells=cells, res_per_s=n_res / span, offered_res_per_s=n_res / duration,
+                   res=int(n_res), batches=srv.batches,
+                   mean_batch=float(np.mean(srv.batch_sizes)),
+                   max_batch=int(max(srv.batch_sizes)))
+        runs.append(out)
+    return {"workload": f"Poisson {rate_hz:g} slots/s per cell for {slots} slots of 0.5 ms; per "
+                        f"job 4-273 PRB, 4/16/32/64 Rx, 1-16 layers, QPSK-256QAM; pool of "
+                        f"{pool_size} distinct resident jobs; FP16 tensor-core products for 5-16 "
+                        f"layers, FP32 for 1-4; the configuration's 32 cells, then 16",
+            "runs": runs, "lanes": lanes, "arena_bytes_per_lane": srv.arena_bytes,
+            "api": "phy_batch_post / phy_batch_launch (captured graph per lane)"}
 
 
 def run_ours(args, spec, rank, world, local):
