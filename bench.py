@@ -439,8 +439,8 @@ def main():
 def aux_probe(spec, reps: int) -> int:
     """Times the auxiliary paths alone (CUDA events, `reps` calls each after two warm-up calls):
     the noise estimate and the 9-bit BFP decoder on `spec` (use --cells to size it), the
-    denoiser forward pass on 16,384 tiles and its training step on 1,024 tiles. Small enough to
-    run under ncu; prints one JSON line."""
+    denoiser forward pass (FP32, then BF16 on the tensor cores) on 16,384 tiles and its training
+    step on 1,024 tiles. Small enough to run under ncu; prints one JSON line."""
     import torch
     from paper_2510_07843_gb300 import denoise as D
     from paper_2510_07843_gb300 import phy
@@ -479,6 +479,11 @@ def aux_probe(spec, reps: int) -> int:
     y = torch.empty_like(x)
     ws = torch.empty(phy.cnn_workspace_size(n), dtype=torch.uint8, device=dev)
     out["cnn_forward_us_16384_tiles"] = timed(lambda: phy.cnn_forward(n, p, x, y, ws))
+    err = torch.zeros(64, dtype=torch.int32, device=dev)
+    out["cnn_forward_bf16_tc_us_16384_tiles"] = timed(
+        lambda: phy.cnn_forward_bf16(n, p, x, y, err))
+    if int(err[0].item()) != 0:
+        raise RuntimeError("tensor-core denoiser forward: a bounded wait ran out")
     nb = 1024
     m, v, g = torch.zeros_like(p), torch.zeros_like(p), torch.zeros_like(p)
     wsb = torch.empty(phy.cnn_workspace_size(nb), dtype=torch.uint8, device=dev)
@@ -771,6 +776,12 @@ def time_variant(spec, precision, refactor, llr, args, slot, dev, world, fl_peak
                 e2.record(st)
             phy.detect_anchors(cfg, *args_, stream=st)
 
+    # tile shapes (cells per chunk, solve CTA width, tensor-core ring depth) chosen by the
+    # library's autotuner on these buffers, before anything is timed; outputs do not depend on them
+    phy.autotune_clear()
+    phy.autotune(cfg, buf.Y, buf.pilots, buf.sigma2, buf.x_hat, buf.sinr, buf.llr, buf.flags,
+                 buf.workspace, stream=st)
+    tiles = phy.autotune_tiles(cfg)
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
@@ -863,7 +874,7 @@ def time_variant(spec, precision, refactor, llr, args, slot, dev, world, fl_peak
         r["frac"] = r["achieved"] / r["peak"]
     dominant = solve_roof if solve_ms >= gram_ms else gram_roof
     timed_ms = pipe_ms if pipe_ms is not None else serial_ms
-    rec = {"precision": precision, "fp64_refactor": bool(refactor),
+    rec = {"precision": precision, "fp64_refactor": bool(refactor), "tiles": tiles,
            "value": whole_job_rate(world, n_re, args.steps, timed_ms), "unit": "REs/s",
            "ms_per_step": timed_ms / args.steps,
            "serial_ms_per_step": serial_ms / args.steps,
@@ -912,7 +923,7 @@ def serving_mixed_run(dev, slots: int = 100, n_cells=(32, 16), rate_hz: float = 
         pick = rng.integers(0, pool_size, len(arrivals))
         jobs = [serve.MixedJob(*pool[p], arrival=t, job_id=k)
                 for k, ((t, _), p) in enumerate(zip(arrivals, pick))]
-        srv.batches, srv.batch_sizes, srv.service = 0, [], []
+        srv.batches, srv.batch_sizes, srv.service, srv.host_post = 0, [], [], []
         done = srv.run(jobs, realtime=True)
         out = serve.latency_summary(done, service=srv.service)
         n_res = sum(j.n_res for j in done)
@@ -920,7 +931,8 @@ def serving_mixed_run(dev, slots: int = 100, n_cells=(32, 16), rate_hz: float = 
         out.update(cells=cells, res_per_s=n_res / span, offered_res_per_s=n_res / duration,
                    res=int(n_res), batches=srv.batches,
                    mean_batch=float(np.mean(srv.batch_sizes)),
-                   max_batch=int(max(srv.batch_sizes)))
+                   max_batch=int(max(srv.batch_sizes)),
+                   host_post_us_p50=float(np.median(srv.host_post)) * 1e6)
         runs.append(out)
     return {"workload": f"Poisson {rate_hz:g} slots/s per cell for {slots} slots of 0.5 ms; per "
                         f"job 4-273 PRB, 4/16/32/64 Rx, 1-16 layers, QPSK-256QAM; pool of "
@@ -1050,7 +1062,8 @@ def run_ours(args, spec, rank, world, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": (f"{args.precision} tensor-core products (fp32 accumulate), f32 solve"
                   if args.precision != "fp32" else "f32"),
-        "data": "synthetic", "config": config_dict(spec, args, world),
+        "data": "synthetic", "config": dict(config_dict(spec, args, world),
+                                            tiles=dict(head["tiles"], chosen_by="phy_autotune")),
         "serial_ms_per_step": head["serial_ms_per_step"],
         "latency_ms": head["latency_ms"],
         "stages_ms": head["stages_ms"],

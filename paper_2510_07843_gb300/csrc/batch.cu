@@ -155,12 +155,14 @@ extern "C" phy_status phy_batch_post(const phy_job* jobs, int32_t n_jobs, void* 
     J.max_segs = phy::batch_max_segs(g);
     if (tc && !phy::encode_tc_maps(g, J.anchors, jb.Y, &J.tmY, &J.tmA))
       return PHY_ERR_INVALID_ARG;
-    // items per stage: LS (group, DMRS symbol, cell) over all jobs; per layer class the segment
+    // items per stage: LS (chunk of groups, DMRS symbol, cell) over all jobs; per layer class the segment
     // stage (FP32 or tensor-core: segment, cell) and the solve or, for the direct form, that
     // form (128 subcarriers, data symbol, cell)
     const int res = ((g.n_sc + 127) / 128) * g.n_dsym * g.n_cells;
     const int seg_items = g.n_seg * g.n_cells;
-    const int items[phy::kBatchStages] = {g.G * g.n_dmrs * g.n_cells,
+    const int gp = phy::chest_batch_groups(g.n_rx);
+    if (gp * g.n_layers * 2 * g.L > phy::kChestBatchPilots) return PHY_ERR_UNSUPPORTED;
+    const int items[phy::kBatchStages] = {(g.G + gp - 1) / gp * g.n_dmrs * g.n_cells,
                                           !tc && !direct ? seg_items : 0, tc ? seg_items : 0,
                                           direct ? 0 : res, direct ? res : 0};
     for (int stg = 0; stg < phy::kBatchStages; ++stg) {
@@ -200,7 +202,7 @@ extern "C" phy_status phy_batch_launch(void* table_host, void* table_dev, int64_
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return PHY_ERR_CUDA;
   const BatchTable* t = static_cast<const BatchTable*>(table_dev);
-  if ((e = phy::launch_chest_batch(t, phy::device_sm_count() * 16, st)) != cudaSuccess)
+  if ((e = phy::launch_chest_batch(t, phy::device_sm_count() * 8, st)) != cudaSuccess)
     return PHY_ERR_CUDA;
   if ((e = phy::launch_batch_stages(t, st)) != cudaSuccess) return PHY_ERR_CUDA;
   return PHY_OK;

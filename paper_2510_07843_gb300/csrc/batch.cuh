@@ -32,6 +32,16 @@ __host__ __device__ constexpr int batch_class(int nl_class) {
   return nl_class <= 2 ? 0 : nl_class <= 4 ? 1 : nl_class <= 8 ? 2 : 3;
 }
 
+// LS items of the batched path: a CTA of kChestBatchThreads threads takes chest_batch_groups
+// consecutive anchor groups of one (DMRS symbol, cell), one thread per (group, antenna) with the
+// antennas padded to a power of two, so that jobs with few antennas still fill the CTA.
+constexpr int kChestBatchThreads = 128;
+constexpr int kChestBatchPilots = 2048;  // staged pilots: groups x layers x 2L (bounded below)
+__host__ __device__ constexpr int chest_batch_groups(int n_rx) {
+  return n_rx <= 1 ? 128 : n_rx <= 2 ? 64 : n_rx <= 4 ? 32 : n_rx <= 8 ? 16 : n_rx <= 16 ? 8
+       : n_rx <= 32 ? 4 : 2;
+}
+
 struct BatchJob {
   // tensor maps of the job's grid and anchors (jobs with tensor-core products; encoded by the
   // host into the table, read by TMA from the device copy)

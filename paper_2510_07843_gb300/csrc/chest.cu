@@ -147,10 +147,68 @@ cudaError_t launch_chest_any(const Geo& g, const phy_c32* Y, BfpGrid bfp, const 
   return cudaGetLastError();
 }
 
-// Batched form: CTAs stride over the LS items (group, DMRS symbol, cell) of every job in the
-// table; the first item of each job also clears the job's error word for the later stages.
-__global__ void __launch_bounds__(kChestThreads) chest_batch_kernel(const BatchTable* __restrict__ t) {
+// Batched LS item: `gp` consecutive groups of one (DMRS symbol, cell), thread (group, antenna);
+// the arithmetic per anchor is chest_body's, so both give the same bits. pil: staged pilots
+// [group][layer][2L].
+template <int L>
+__device__ __forceinline__ void chest_multi_body(const Geo& g, int grp0, int gp, int d, int cell,
+                                                 const phy_c32* __restrict__ Y,
+                                                 const phy_c32* __restrict__ P,
+                                                 phy_c32* __restrict__ anchors,
+                                                 cf* __restrict__ pil) {
+  const int nrp = kChestBatchThreads / gp;
+  const int r = threadIdx.x % nrp, gi = threadIdx.x / nrp, grp = grp0 + gi;
+  const int t = (d == 0) ? g.dmrs0 : g.dmrs1;
+  const int nl = g.n_layers;
+  const bool live = r < g.n_rx && grp < g.G;
+  cf y[2 * L];
+  if (live) {
+    const int k0 = 2 * group_start(g, grp);  // even: the run starts on a 16-byte boundary
+    const phy_c32* yrow = Y + ((size_t)(cell * g.n_sym + t) * g.n_rx + r) * g.n_sc + k0;
+    if constexpr (L >= 2) {
+      const float4* y4 = reinterpret_cast<const float4*>(yrow);
+#pragma unroll
+      for (int i = 0; i < L; ++i) {
+        const float4 v = __ldg(y4 + i);
+        y[2 * i] = mk(v.x, v.y);
+        y[2 * i + 1] = mk(v.z, v.w);
+      }
+    } else {
+      y[0] = ld(yrow);
+      y[1] = ld(yrow + 1);
+    }
+  }
+  const int ngl = min(gp, g.G - grp0);
+  const phy_c32* pbase = P + (size_t)(cell * g.n_dmrs + d) * nl * g.n_sc;
+  for (int e = threadIdx.x; e < ngl * nl * 2 * L; e += blockDim.x) {
+    const int i = e % (2 * L), q = e / (2 * L);
+    const int l = q % nl, gj = q / nl;
+    pil[(gj * nl + l) * 2 * L + i] =
+        ld(pbase + (size_t)l * g.n_sc + 2 * group_start(g, grp0 + gj) + i);
+  }
+  __syncthreads();
+  if (!live) return;
+  phy_c32* out = anchors + (((size_t)(cell * g.n_dmrs + d) * g.G + grp) * nl) * g.n_rx;
+  const float inv_l = 1.f / (float)L;
+  for (int l = 0; l < nl; ++l) {
+    const int c = l & 1;
+    const cf* pl = pil + (gi * nl + l) * 2 * L;
+    cf acc = mk(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+      const cf yv = c ? y[2 * i + 1] : y[2 * i];
+      acc = cfma_cj(pl[2 * i + c], yv, acc);
+    }
+    st(out + (size_t)l * g.n_rx + r, inv_l * acc);
+  }
+}
+
+// Batched form: CTAs stride over the LS items (group chunk, DMRS symbol, cell) of every job in
+// the table; the first item of each job also clears the job's error word for the later stages.
+__global__ void __launch_bounds__(kChestBatchThreads)
+    chest_batch_kernel(const BatchTable* __restrict__ t) {
   __shared__ Geo sg;
+  __shared__ cf pil[kChestBatchPilots];
   const int n = t->n_items[kBatchChest][0];
   for (int w = blockIdx.x; w < n; w += gridDim.x) {
     int local;
@@ -158,15 +216,15 @@ __global__ void __launch_bounds__(kChestThreads) chest_batch_kernel(const BatchT
     const BatchJob& J = t->job[jb];
     batch_load_geo(sg, J.g);
     __syncthreads();
-    const int grp = local % sg.G, d = (local / sg.G) % sg.n_dmrs, cell = local / (sg.G * sg.n_dmrs);
+    const int gp = chest_batch_groups(sg.n_rx), nch = (sg.G + gp - 1) / gp;
+    const int grp0 = (local % nch) * gp, d = (local / nch) % sg.n_dmrs;
+    const int cell = local / (nch * sg.n_dmrs);
     if (local == 0 && threadIdx.x == 0) *J.err = 0;
-    const BfpGrid none{nullptr, 0, 0, 0.f};
     switch (sg.L) {
-      case 1: chest_body<1, false>(sg, grp, d, cell, J.Y, none, J.pilots, J.anchors); break;
-      case 2: chest_body<2, false>(sg, grp, d, cell, J.Y, none, J.pilots, J.anchors); break;
-      case 4: chest_body<4, false>(sg, grp, d, cell, J.Y, none, J.pilots, J.anchors); break;
-      case 8: chest_body<8, false>(sg, grp, d, cell, J.Y, none, J.pilots, J.anchors); break;
-      default: chest_body<16, false>(sg, grp, d, cell, J.Y, none, J.pilots, J.anchors); break;
+      case 1: chest_multi_body<1>(sg, grp0, gp, d, cell, J.Y, J.pilots, J.anchors, pil); break;
+      case 2: chest_multi_body<2>(sg, grp0, gp, d, cell, J.Y, J.pilots, J.anchors, pil); break;
+      case 4: chest_multi_body<4>(sg, grp0, gp, d, cell, J.Y, J.pilots, J.anchors, pil); break;
+      default: chest_multi_body<8>(sg, grp0, gp, d, cell, J.Y, J.pilots, J.anchors, pil); break;
     }
     __syncthreads();  // the geometry and the pilot stage are rewritten by the next item
   }
@@ -175,7 +233,7 @@ __global__ void __launch_bounds__(kChestThreads) chest_batch_kernel(const BatchT
 }  // namespace
 
 cudaError_t launch_chest_batch(const BatchTable* t, int grid, cudaStream_t st) {
-  chest_batch_kernel<<<grid, kChestThreads, 0, st>>>(t);
+  chest_batch_kernel<<<grid, kChestBatchThreads, 0, st>>>(t);
   return cudaGetLastError();
 }
 

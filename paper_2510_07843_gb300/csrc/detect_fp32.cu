@@ -636,58 +636,105 @@ __global__ void __launch_bounds__(W)
 // and accumulates A = H^H H and b = H^H y directly, the plain definition. The solve, SINR, LLRs
 // and the FP64 re-computation are those of the solve kernel. QM = 0 takes the modulation from
 // g.qm.
+//
+// A CTA takes 128 consecutive subcarriers of one symbol. Their segments span at most
+// 127 / (2L) + 3 anchor groups, so the CTA stages those groups' anchors in shared memory,
+// kDirectRc antennas at a time, as [DMRS][layer][antenna][group]: a warp's 32 subcarriers read
+// equal (broadcast) or consecutive groups, one wavefront per load, where reading the anchors from
+// global memory touched one cache line per distinct segment. Global reads of the stage run over
+// antennas (contiguous in the anchor layout).
+constexpr int kDirectThreads = 128;
+constexpr int kDirectRc = 16;  // antennas per staged chunk
+// Anchor groups a CTA can need, for the smallest cover of the class (L >= NL / 2), odd so that
+// the staging stores (stride: one antenna row of groups) spread over the banks.
+template <int NL>
+__host__ __device__ constexpr int direct_groups() {
+  return (127 / NL + 3) | 1;
+}
+template <int NL>
+__host__ __device__ constexpr int direct_stage_elems() {
+  return 2 * NL * kDirectRc * direct_groups<NL>();
+}
+
 template <int NL, int QM>
-__device__ __forceinline__ void direct_body(const Geo& g, int k, int t, int cell,
-                                            const phy_c32* __restrict__ anchors,
-                                            const phy_c32* __restrict__ Y,
-                                            const float* __restrict__ sigma2,
-                                            phy_c32* __restrict__ x_hat,
-                                            float* __restrict__ sinr_out,
-                                            float* __restrict__ llr_out,
-                                            uint8_t* __restrict__ flags_out) {
+__device__ __forceinline__ void direct_cta(const Geo& g, int k0, int t, int cell,
+                                           const phy_c32* __restrict__ anchors,
+                                           const phy_c32* __restrict__ Y,
+                                           const float* __restrict__ sigma2,
+                                           phy_c32* __restrict__ x_hat,
+                                           float* __restrict__ sinr_out,
+                                           float* __restrict__ llr_out,
+                                           uint8_t* __restrict__ flags_out,
+                                           cf* __restrict__ stage) {
   static_assert(NL <= 4, "the direct form keeps its sums in registers");
   constexpr int NTRI = NL * (NL + 1) / 2;
+  constexpr int NGP = direct_groups<NL>();
   const int nr = g.n_rx, nl = g.n_layers, nds = g.n_dsym, nd = g.n_dmrs;
   const int qm = QM > 0 ? QM : g.qm;
-  const int j = seg_of(g, k), g1 = seg_g1(g, j);
-  const float bw[2] = {seg_beta(g, j, k, 0), seg_beta(g, j, k, 1)};
+  const int k = k0 + (int)threadIdx.x;
+  const bool live = k < g.n_sc;
+  const int kc = live ? k : g.n_sc - 1;
+  const int j = seg_of(g, kc), g1 = seg_g1(g, j);
+  // groups [gA, gB] cover every segment pair of the CTA's subcarriers (seg_of is monotone)
+  const int gA = seg_of(g, k0);
+  const int gB = seg_g1(g, seg_of(g, min(k0 + kDirectThreads - 1, g.n_sc - 1)));
+  const int ng = gB - gA + 1;  // <= NGP since L >= NL / 2 (host-checked)
+  const int lj = j - gA, lg1 = g1 - gA;
+  const float bw[2] = {seg_beta(g, j, kc, 0), seg_beta(g, j, kc, 1)};
   const float tau = nd == 2 ? g.tw[t] : 0.f;
   cf A[NTRI], bv[NL];
 #pragma unroll
   for (int e = 0; e < NTRI; ++e) A[e] = mk(0.f, 0.f);
 #pragma unroll
   for (int l = 0; l < NL; ++l) bv[l] = mk(0.f, 0.f);
-  const size_t a_d = (size_t)g.G * nl * nr;  // one DMRS symbol's anchors
-  const phy_c32* a0 = anchors + ((size_t)cell * nd * g.G + j) * nl * nr;
-  const phy_c32* a1 = anchors + ((size_t)cell * nd * g.G + g1) * nl * nr;
-  const phy_c32* yk = Y + (((size_t)cell * g.n_sym + g.dsym[t]) * nr) * g.n_sc + k;
+  const phy_c32* acell = anchors + (size_t)cell * nd * g.G * nl * nr;  // [d][group][l][r]
+  const phy_c32* yk = Y + (((size_t)cell * g.n_sym + g.dsym[t]) * nr) * g.n_sc + kc;
+  for (int r0 = 0; r0 < nr; r0 += kDirectRc) {
+    const int rc = min(kDirectRc, nr - r0);
+    __syncthreads();  // every thread is done with the previous chunk
+    const int n_st = nd * ng * nl * rc;
+    for (int e = threadIdx.x; e < n_st; e += kDirectThreads) {
+      const int rr = e % rc;
+      int q = e / rc;
+      const int l = q % nl;
+      q /= nl;
+      const int gl = q % ng, d = q / ng;
+      stage[((d * NL + l) * kDirectRc + rr) * NGP + gl] =
+          ld(acell + ((size_t)(d * g.G + gA + gl) * nl + l) * nr + r0 + rr);
+    }
+    __syncthreads();
+    if (live) {
 #pragma unroll 4
-  for (int r = 0; r < nr; ++r) {
-    cf h[NL];
+      for (int rr = 0; rr < rc; ++rr) {
+        cf h[NL];
 #pragma unroll
-    for (int l = 0; l < NL; ++l) {
-      h[l] = mk(0.f, 0.f);
-      if (l < nl) {
-        const float w1 = bw[l & 1], w0 = 1.f - w1;
-        const cf c0 = ld(a0 + (size_t)l * nr + r), c1 = ld(a1 + (size_t)l * nr + r);
-        cf v = mk(fmaf(w1, c1.x, w0 * c0.x), fmaf(w1, c1.y, w0 * c0.y));
-        if (nd == 2) {
-          const cf e0 = ld(a0 + a_d + (size_t)l * nr + r);
-          const cf e1 = ld(a1 + a_d + (size_t)l * nr + r);
-          const cf u = mk(fmaf(w1, e1.x, w0 * e0.x), fmaf(w1, e1.y, w0 * e0.y));
-          v = mk(fmaf(tau, u.x - v.x, v.x), fmaf(tau, u.y - v.y, v.y));
+        for (int l = 0; l < NL; ++l) {
+          h[l] = mk(0.f, 0.f);
+          if (l < nl) {
+            const float w1 = bw[l & 1], w0 = 1.f - w1;
+            const cf* s0 = stage + (l * kDirectRc + rr) * NGP;
+            const cf c0 = s0[lj], c1 = s0[lg1];
+            cf v = mk(fmaf(w1, c1.x, w0 * c0.x), fmaf(w1, c1.y, w0 * c0.y));
+            if (nd == 2) {
+              const cf* s1 = s0 + NL * kDirectRc * NGP;
+              const cf e0 = s1[lj], e1 = s1[lg1];
+              const cf u = mk(fmaf(w1, e1.x, w0 * e0.x), fmaf(w1, e1.y, w0 * e0.y));
+              v = mk(fmaf(tau, u.x - v.x, v.x), fmaf(tau, u.y - v.y, v.y));
+            }
+            h[l] = v;
+          }
         }
-        h[l] = v;
+        const cf y = ld(yk + (size_t)(r0 + rr) * g.n_sc);
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+#pragma unroll
+          for (int m = 0; m <= l; ++m) A[tri(l, m)] = cfma_cj(h[l], h[m], A[tri(l, m)]);
+          bv[l] = cfma_cj(h[l], y, bv[l]);
+        }
       }
     }
-    const cf y = ld(yk + (size_t)r * g.n_sc);
-#pragma unroll
-    for (int l = 0; l < NL; ++l) {
-#pragma unroll
-      for (int m = 0; m <= l; ++m) A[tri(l, m)] = cfma_cj(h[l], h[m], A[tri(l, m)]);
-      bv[l] = cfma_cj(h[l], y, bv[l]);
-    }
   }
+  if (!live) return;
   const float s2 = sigma2[cell];
   auto getA = [&](int l, int m) -> cf {
     if (l >= nl || m >= nl) return (l == m) ? mk(1.f, 0.f) : mk(0.f, 0.f);
@@ -743,18 +790,15 @@ __device__ __forceinline__ void direct_body(const Geo& g, int k, int t, int cell
   }
 }
 
-constexpr int kDirectThreads = 128;
-
 template <int NL, int QM>
 __global__ void __launch_bounds__(kDirectThreads)
     direct_fp32_kernel(Geo g, const phy_c32* __restrict__ anchors, const phy_c32* __restrict__ Y,
                        const float* __restrict__ sigma2, phy_c32* __restrict__ x_hat,
                        float* __restrict__ sinr_out, float* __restrict__ llr_out,
                        uint8_t* __restrict__ flags_out) {
-  const int k = blockIdx.x * kDirectThreads + threadIdx.x;
-  if (k < g.n_sc)
-    direct_body<NL, QM>(g, k, blockIdx.y, blockIdx.z, anchors, Y, sigma2, x_hat, sinr_out,
-                        llr_out, flags_out);
+  __shared__ cf stage[direct_stage_elems<NL>()];
+  direct_cta<NL, QM>(g, blockIdx.x * kDirectThreads, blockIdx.y, blockIdx.z, anchors, Y, sigma2,
+                     x_hat, sinr_out, llr_out, flags_out, stage);
 }
 
 // Batched direct form: CTAs stride over the (128 subcarriers, data symbol, cell) items of the
@@ -763,6 +807,7 @@ template <int NL>
 __global__ void __launch_bounds__(kDirectThreads)
     direct_batch_kernel(const BatchTable* __restrict__ t) {
   __shared__ Geo sg;
+  __shared__ cf stage[direct_stage_elems<NL>()];
   constexpr int cls = batch_class(NL);
   const int n = t->n_items[kBatchDirect][cls];
   for (int w = blockIdx.x; w < n; w += gridDim.x) {
@@ -771,11 +816,10 @@ __global__ void __launch_bounds__(kDirectThreads)
     batch_load_geo(sg, J.g);
     __syncthreads();
     const int nb = (sg.n_sc + kDirectThreads - 1) / kDirectThreads;
-    const int k = (local % nb) * kDirectThreads + threadIdx.x;
+    const int k0 = (local % nb) * kDirectThreads;
     const int jj = (local / nb) % sg.n_dsym, cell = local / (nb * sg.n_dsym);
-    if (k < sg.n_sc)
-      direct_body<NL, 0>(sg, k, jj, cell, J.anchors, J.Y, J.sigma2, J.x_hat, J.sinr, J.llr,
-                         J.flags);
+    direct_cta<NL, 0>(sg, k0, jj, cell, J.anchors, J.Y, J.sigma2, J.x_hat, J.sinr, J.llr,
+                      J.flags, stage);
     __syncthreads();
   }
 }
@@ -910,6 +954,7 @@ template <int NL>
 cudaError_t launch_direct(const Geo& g, const phy_c32* anchors, const phy_c32* Y,
                           const float* sigma2, phy_c32* x_hat, float* sinr, float* llr,
                           uint8_t* flags, cudaStream_t st) {
+  if (2 * g.L < NL) return cudaErrorInvalidValue;  // the anchor stage is sized for L >= NL / 2
   dim3 grid((g.n_sc + kDirectThreads - 1) / kDirectThreads, g.n_dsym, g.n_cells);
   switch (g.qm) {
     case 2: direct_fp32_kernel<NL, 2><<<grid, kDirectThreads, 0, st>>>(g, anchors, Y, sigma2, x_hat, sinr, llr, flags); break;

@@ -551,6 +551,21 @@ def _jobs_array(jobs):
     return arr
 
 
+# Raw job records for callers that fill them without ctypes objects (a serving loop's hot path):
+# the configuration block, then the seven buffer addresses as 64-bit words.
+JOB_BYTES = ctypes.sizeof(CJob)
+JOB_ADDR_OFFSET = CJob.Y.offset
+assert JOB_BYTES == JOB_ADDR_OFFSET + 7 * 8 and JOB_ADDR_OFFSET == ctypes.sizeof(CSlotCfg)
+
+
+def batch_post_records(records, n_jobs: int, table_host: int, workspace: int,
+                       workspace_bytes: int) -> int:
+    """phy_batch_post on `n_jobs` raw phy_job records (a ctypes char array of JOB_BYTES each)
+    and raw addresses; returns the status code."""
+    return int(load().phy_batch_post(records, int(n_jobs), table_host, workspace,
+                                     workspace_bytes))
+
+
 def batch_table_bytes() -> int:
     return int(load().phy_batch_table_bytes())
 

@@ -17,6 +17,7 @@ Everything on the device runs in libphy.so; this module only schedules and marsh
 from __future__ import annotations
 
 import dataclasses
+import struct
 import time
 from dataclasses import dataclass, field
 from typing import Callable, Dict, List, Optional, Sequence, Tuple
@@ -341,9 +342,13 @@ class MixedJob:
     sigma2: object           # device tensor [1] float32
     arrival: float = 0.0
     job_id: int = 0
-    llr: object = None
-    flags: object = None
     done: float = field(default=float("nan"))
+    _out: object = field(default=None, repr=False)    # (arena, LLR offset, flag offset)
+    _views: object = field(default=None, repr=False)  # (llr, flags) once built or kept
+
+    def __post_init__(self):
+        # input addresses, taken once (the inputs stay where they are until the job is done)
+        self._addr = (phy._ptr(self.Y), phy._ptr(self.pilots), phy._ptr(self.sigma2))
 
     @property
     def latency(self) -> float:
@@ -353,15 +358,50 @@ class MixedJob:
     def n_res(self) -> int:
         return self.cfg.n_cells * self.cfg.n_dsym * self.cfg.n_sc
 
+    def _results(self):
+        if self._views is None and self._out is not None:
+            import torch
+            arena, lo, fo = self._out
+            c = self.cfg
+            n_re = c.n_cells * c.n_dsym * c.n_sc
+            dt, el = (torch.float16, 2) if c.llr_format == "f16" else (torch.float32, 4)
+            n = n_re * c.n_layers * c.qm * el
+            llr = arena[lo:lo + n].view(dt).view(c.n_cells, c.n_dsym, c.n_sc, c.n_layers, c.qm)
+            self._views = (llr, arena[fo:fo + n_re].view(c.n_cells, c.n_dsym, c.n_sc))
+        return self._views
+
+    @property
+    def llr(self):
+        v = self._results()
+        return None if v is None else v[0]
+
+    @property
+    def flags(self):
+        v = self._results()
+        return None if v is None else v[1]
+
+
+class _JobLayout:
+    """Per-configuration constants of the batched path: the phy_slot_cfg record and the bytes a
+    job takes (intermediates, LLRs, flags)."""
+    __slots__ = ("cfg", "record", "ws", "llr", "flags", "total")
+
+    def __init__(self, cfg: phy.SlotConfig):
+        self.cfg = cfg
+        self.record = bytes(cfg.c())
+        self.ws = phy.batch_workspace_size([(cfg, None, None, None, None, None, None, None)])
+        if self.ws == 0:
+            raise ValueError(f"configuration not accepted by the batched receiver: {cfg}")
+        n_re = cfg.n_cells * cfg.n_dsym * cfg.n_sc
+        self.llr = n_re * cfg.n_layers * cfg.qm * (2 if cfg.llr_format == "f16" else 4)
+        self.flags = n_re
+        self.total = self.ws + _up(self.llr) + _up(self.flags)
+
 
 def mixed_job_bytes(cfg: phy.SlotConfig) -> int:
     """Device bytes a job takes in a lane's arena: its intermediates and its LLR and flag
     outputs (x_hat and SINR are not kept by the server)."""
-    one = (cfg, None, None, None, None, None, None, None)
-    llr_el = 2 if cfg.llr_format == "f16" else 4
-    n_re = cfg.n_cells * cfg.n_dsym * cfg.n_sc
-    return (phy.batch_workspace_size([one]) + _up(n_re * cfg.n_layers * cfg.qm * llr_el)
-            + _up(n_re))
+    return _JobLayout(cfg).total
 
 
 class _Lane:
@@ -369,19 +409,25 @@ class _Lane:
     CUDA graph captured on phy_batch_launch for them."""
 
     def __init__(self, device, arena_bytes: int, poll_limit: int):
+        import ctypes
         import torch
         self.stream = torch.cuda.Stream(device=device)
         self.arena = torch.empty(arena_bytes, dtype=torch.uint8, device=device)
+        self.base = self.arena.data_ptr()
         n = phy.batch_table_bytes()
         self.host = torch.zeros(n, dtype=torch.uint8).pin_memory()
+        self.host_addr = self.host.data_ptr()
         self.devt = torch.zeros(n, dtype=torch.uint8, device=device)
         self.poll_limit = poll_limit
         self.graph = None
+        # the job records of a batch, filled in place (no ctypes objects per job)
+        self.records = (ctypes.c_char * (phy.BATCH_MAX_JOBS * phy.JOB_BYTES))()
+        self.rec_view = memoryview(self.records).cast("B")
 
-    def capture(self, warm: Sequence["MixedJob"]):
+    def capture(self, warm: Sequence["MixedJob"], layout):
         """Runs one real batch (configures the kernels), then captures the launch."""
         import torch
-        self.post(warm)
+        self.post(warm, layout)
         phy.batch_launch(self.host, self.devt, self.poll_limit, stream=self.stream)
         self.stream.synchronize()
         if phy.batch_status(self.host) != 0:
@@ -390,27 +436,40 @@ class _Lane:
         with torch.cuda.graph(self.graph, stream=self.stream):
             phy.batch_launch(self.host, self.devt, self.poll_limit, stream=self.stream)
 
-    def post(self, jobs: Sequence["MixedJob"]):
-        """Lays the batch out in the arena (intermediates, then each job's LLRs and flags) and
-        rings the table's doorbell."""
-        import torch
-        tuples = [(j.cfg, j.Y, j.pilots, j.sigma2, None, None, None, None) for j in jobs]
-        off = _up(phy.batch_workspace_size(tuples))
-        ws = self.arena[:off]
-        for i, j in enumerate(jobs):
-            c = j.cfg
-            shape = (c.n_cells, c.n_dsym, c.n_sc, c.n_layers, c.qm)
-            dt = torch.float16 if c.llr_format == "f16" else torch.float32
-            n = int(np.prod(shape)) * (2 if c.llr_format == "f16" else 4)
-            j.llr = self.arena[off:off + n].view(dt).view(shape)
-            off = _up(off + n)
-            nf = c.n_cells * c.n_dsym * c.n_sc
-            j.flags = self.arena[off:off + nf].view(c.n_cells, c.n_dsym, c.n_sc)
-            off = _up(off + nf)
-            tuples[i] = (c, j.Y, j.pilots, j.sigma2, None, None, j.llr, j.flags)
-        if off > self.arena.numel():
+    def post(self, jobs: Sequence["MixedJob"], layout):
+        """Lays the batch out in the arena (intermediates, then each job's LLRs and flags),
+        writes the job records and rings the table's doorbell. layout(cfg) -> _JobLayout."""
+        lays = [layout(j.cfg) for j in jobs]
+        ws, outs, end = write_records(self.rec_view, lays, [j._addr for j in jobs], self.base)
+        if end > self.arena.numel():
             raise ValueError("batch larger than the lane arena")
-        phy.batch_post(tuples, self.host, ws)
+        for j, o in zip(jobs, outs):
+            j._out, j._views = (self.arena,) + o, None
+        st = phy.batch_post_records(self.records, len(jobs), self.host_addr, self.base, ws)
+        if st != 0:
+            raise RuntimeError(f"phy_batch_post failed: {phy.STATUS.get(st, st)}")
+
+
+_ADDR = struct.Struct("<7Q")
+
+
+def write_records(rec, lays: Sequence[_JobLayout], addrs, base: int):
+    """Writes the phy_job records of a batch into `rec` (a writable byte buffer) for an arena at
+    device address `base`: the intermediates first (phy_batch_post lays them out from `base`),
+    then per job its LLRs and flags. addrs: per job the (Y, pilots, sigma2) addresses. Returns
+    the intermediates' bytes, per job the (LLR, flag) arena offsets, and the end offset."""
+    ws = _up(sum(l.ws for l in lays))
+    off, jb, ao, pack = ws, phy.JOB_BYTES, phy.JOB_ADDR_OFFSET, _ADDR.pack_into
+    outs = []
+    for i, (l, (y, p, s2)) in enumerate(zip(lays, addrs)):
+        lo = off
+        fo = _up(lo + l.llr)
+        off = _up(fo + l.flags)
+        o = i * jb
+        rec[o:o + ao] = l.record
+        pack(rec, o + ao, y or 0, p or 0, s2 or 0, 0, 0, base + lo, base + fo)
+        outs.append((lo, fo))
+    return ws, outs, off
 
 
 class BatchServer:
@@ -434,18 +493,24 @@ class BatchServer:
         self.batches = 0
         self.batch_sizes: List[int] = []
         self.service: List[float] = []
-        self._bytes: Dict[Tuple, int] = {}
+        self.host_post: List[float] = []  # host seconds per batch: records, table, doorbell
+        self._layouts: Dict[int, _JobLayout] = {}
+
+    def _layout(self, cfg: phy.SlotConfig) -> _JobLayout:
+        """The configuration's layout, cached by object (configurations are shared by the jobs
+        of one stream; the cache keeps each object alive, so its id is not reused)."""
+        lay = self._layouts.get(id(cfg))
+        if lay is None or lay.cfg is not cfg:
+            lay = self._layouts[id(cfg)] = _JobLayout(cfg)
+        return lay
 
     def job_bytes(self, cfg: phy.SlotConfig) -> int:
-        k = config_key(cfg) + (("n_cells", cfg.n_cells),)
-        if k not in self._bytes:
-            self._bytes[k] = mixed_job_bytes(cfg)
-        return self._bytes[k]
+        return self._layout(cfg).total
 
     def prepare(self, warm: "MixedJob"):
         """Captures every lane's graph (before timing), warming each on one job."""
         for ln in self.lanes:
-            ln.capture([warm])
+            ln.capture([warm], self._layout)
 
     def _take(self, waiting: "collections.deque") -> List["MixedJob"]:
         """The longest arrival-order prefix of the waiting jobs that fits one lane."""
@@ -488,7 +553,8 @@ class BatchServer:
                 for j in batch:
                     j.done = t
                     if keep:
-                        j.llr, j.flags = j.llr.clone(), j.flags.clone()
+                        j._views = (j.llr.clone(), j.flags.clone())
+                        j._out = None
                 finished.extend(batch)
                 free.append(li)
                 block = False
@@ -511,8 +577,10 @@ class BatchServer:
             ln = self.lanes[li]
             batch = self._take(waiting)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            h0 = self.clock()
+            ln.post(batch, self._layout)
+            self.host_post.append(self.clock() - h0)
             e0.record(ln.stream)
-            ln.post(batch)
             with torch.cuda.stream(ln.stream):
                 ln.graph.replay()
             e1.record(ln.stream)

@@ -51,11 +51,15 @@ def _items(cfg):
     n_seg = max(G - 1, 1)
     nds = cfg.n_sym - len(cfg.dmrs_sym)
     nlc = next(c for c in (2, 4, 8, 16) if cfg.n_layers <= c)
+    # LS items take 128 / (n_rx padded to a power of two) groups each
+    nrp = 1
+    while nrp < cfg.n_rx:
+        nrp *= 2
+    ls = -(-G // (128 // nrp)) * len(cfg.dmrs_sym) * cfg.n_cells
     if nlc <= 4:  # the direct form: no segment stage
-        return ((G * len(cfg.dmrs_sym) * cfg.n_cells, 0, -(-n_sc // 128) * nds * cfg.n_cells),
-                (2, 4, 8, 16).index(nlc))
-    return ((G * len(cfg.dmrs_sym) * cfg.n_cells, n_seg * cfg.n_cells,
-             -(-n_sc // 128) * nds * cfg.n_cells), (2, 4, 8, 16).index(nlc))
+        return ((ls, 0, -(-n_sc // 128) * nds * cfg.n_cells), (2, 4, 8, 16).index(nlc))
+    return ((ls, n_seg * cfg.n_cells, -(-n_sc // 128) * nds * cfg.n_cells),
+            (2, 4, 8, 16).index(nlc))
 
 
 MIX = [phy.SlotConfig(n_cells=1, n_prb=273, n_rx=64, n_layers=16, qm=8, dmrs_sym=(2, 11)),

@@ -210,3 +210,32 @@ def test_noise_tracking_jobs_batch_apart(monkeypatch):
     for _, ids in log:
         assert len({ids_i % 2 for ids_i in ids}) == 1, ids
     assert sorted(len(b) for _, b in log) == [1, 1, 2, 2]
+
+
+def test_batch_records_match_the_ctypes_jobs():
+    """The serving loop writes phy_job records into a byte buffer; each record equals the
+    ctypes phy_job of the same configuration and addresses, and the outputs follow the
+    intermediates in the arena, 256-byte aligned and disjoint."""
+    import ctypes
+    import numpy as np
+    from paper_2510_07843_gb300 import synth as S
+    phy.load()
+    rng = np.random.default_rng(3)
+    cfgs = [phy.SlotConfig.from_spec(S.spec_serving_job(rng)) for _ in range(12)]
+    lays = [serve._JobLayout(c) for c in cfgs]
+    addrs = [(1 << 32) + 4096 * i for i in range(12)]
+    base = 1 << 40
+    rec = bytearray(12 * phy.JOB_BYTES)
+    ws, outs, end = serve.write_records(memoryview(rec), lays, [(a, a + 16, a + 32) for a in addrs],
+                                        base)
+    assert sum(l.ws for l in lays) == phy.batch_workspace_size([(c,) + (None,) * 7 for c in cfgs])
+    assert ws == serve._up(sum(l.ws for l in lays))
+    spans = []
+    for i, (c, a, (lo, fo)) in enumerate(zip(cfgs, addrs, outs)):
+        want = phy._jobs_array([(c, a, a + 16, a + 32, None, None, base + lo, base + fo)])
+        assert bytes(rec[i * phy.JOB_BYTES:(i + 1) * phy.JOB_BYTES]) == bytes(want[0])
+        assert lo % 256 == 0 and fo % 256 == 0 and lo >= ws
+        spans += [(lo, lo + lays[i].llr), (fo, fo + lays[i].flags)]
+    spans.sort()
+    assert all(b[0] >= a[1] for a, b in zip(spans, spans[1:])) and spans[-1][1] <= end
+    assert ctypes.sizeof(phy.CJob) == phy.JOB_BYTES
