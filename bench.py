@@ -420,6 +420,9 @@ def main():
                     help="skip training and evaluating the learned channel denoiser")
     ap.add_argument("--aux-probe", type=int, default=0, metavar="REPS",
                     help="only time the auxiliary paths (noise estimate, BFP decoder, denoiser)")
+    ap.add_argument("--batch-probe", type=int, default=0, metavar="JOBS",
+                    help="only time batches of JOBS jobs of the serving mix through the batched "
+                         "receiver (1 to 64; small enough to run under ncu)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -433,6 +436,8 @@ def main():
         return run_reference(args, spec, rank, world)
     if args.aux_probe:
         return aux_probe(spec, args.aux_probe)
+    if args.batch_probe:
+        return batch_probe(args.batch_probe, max(args.steps, 1))
     return run_ours(args, spec, rank, world, local)
 
 
@@ -890,6 +895,55 @@ def time_variant(spec, precision, refactor, llr, args, slot, dev, world, fl_peak
     return rec, cfg, buf, st
 
 
+def serving_pool(dev, pool_size: int = 48, seed: int = 5):
+    """Distinct seeded jobs of the serving configuration, resident on the device: FP16
+    tensor-core products for 5 or more layers, the direct FP32 form below that."""
+    import torch
+    from paper_2510_07843_gb300 import phy
+    rng = np.random.default_rng(seed)
+    pool = []
+    for i in range(pool_size):
+        sp = S.spec_serving_job(rng)
+        sl = S.make_slot(sp, 7000 + i, keep_h=False)
+        cfg = phy.SlotConfig.from_spec(sp, precision="fp16" if sp.n_layers > 4 else "fp32")
+        pool.append((cfg, *(torch.from_numpy(a).to(dev) for a in (sl.Y, sl.pilots, sl.sigma2))))
+    return pool
+
+
+def batch_probe(n_jobs: int, reps: int) -> int:
+    """Times `reps` batches of `n_jobs` jobs of the serving mix (consecutive pool entries) through
+    one lane of the batching server (post, then a replay of the captured batched receiver), after
+    one warm-up batch; prints one JSON line with the GPU time per batch (CUDA events)."""
+    import torch
+    from paper_2510_07843_gb300 import build, phy, serve
+    if not 1 <= n_jobs <= phy.BATCH_MAX_JOBS:
+        raise SystemExit(f"--batch-probe takes 1 to {phy.BATCH_MAX_JOBS} jobs")
+    build.build()
+    dev = torch.device("cuda:0")
+    pool = serving_pool(dev)
+    srv = serve.BatchServer(device=dev, lanes=1)
+    srv.prepare(serve.MixedJob(*pool[0]))
+    ln = srv.lanes[0]
+    ms, res = [], 0
+    for rep in range(reps + 1):
+        jobs = [serve.MixedJob(*pool[(rep * n_jobs + k) % len(pool)]) for k in range(n_jobs)]
+        ln.post(jobs, srv._layout)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ln.stream)
+        with torch.cuda.stream(ln.stream):
+            ln.graph.replay()
+        e1.record(ln.stream)
+        torch.cuda.synchronize()
+        if phy.batch_status(ln.host) != 0:
+            raise RuntimeError("batch did not complete")
+        if rep > 0:
+            ms.append(e0.elapsed_time(e1))
+            res += sum(j.n_res for j in jobs)
+    print(json.dumps({"batch_jobs": n_jobs, "batches": reps, "ms_per_batch_p50":
+                      float(np.median(ms)), "res_per_s": res / (sum(ms) * 1e-3)}))
+    return 0
+
+
 def serving_mixed_run(dev, slots: int = 100, n_cells=(32, 16), rate_hz: float = 2000.0,
                       pool_size: int = 48, lanes: int = 2, seed: int = 5) -> dict:
     """The serving configuration: uplink jobs of 32 cells arriving as Poisson streams at 2000
@@ -900,17 +954,9 @@ def serving_mixed_run(dev, slots: int = 100, n_cells=(32, 16), rate_hz: float = 
     time. Job inputs come from a pool of `pool_size` distinct seeded jobs resident on the device
     (arrivals pick pool entries uniformly). Latency is per job, arrival to completion seen by
     the host; throughput counts the REs of every served job over the run's span."""
-    import torch
-    from paper_2510_07843_gb300 import phy, serve
+    from paper_2510_07843_gb300 import serve
     rng = np.random.default_rng(seed)
-    pool = []
-    for i in range(pool_size):
-        sp = S.spec_serving_job(rng)
-        sl = S.make_slot(sp, 7000 + i, keep_h=False)
-        # FP16 tensor-core products where they are dense (5 or more layers), the direct FP32
-        # form below that
-        cfg = phy.SlotConfig.from_spec(sp, precision="fp16" if sp.n_layers > 4 else "fp32")
-        pool.append((cfg, *(torch.from_numpy(a).to(dev) for a in (sl.Y, sl.pilots, sl.sigma2))))
+    pool = serving_pool(dev, pool_size, seed)
     duration = slots * serve.DEADLINE_S
     srv = serve.BatchServer(device=dev, lanes=lanes)
     srv.prepare(serve.MixedJob(*pool[0], arrival=0.0, job_id=-1))

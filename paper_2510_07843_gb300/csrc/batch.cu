@@ -202,7 +202,7 @@ extern "C" phy_status phy_batch_launch(void* table_host, void* table_dev, int64_
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return PHY_ERR_CUDA;
   const BatchTable* t = static_cast<const BatchTable*>(table_dev);
-  if ((e = phy::launch_chest_batch(t, phy::device_sm_count() * 8, st)) != cudaSuccess)
+  if ((e = phy::launch_chest_batch(t, st)) != cudaSuccess)
     return PHY_ERR_CUDA;
   if ((e = phy::launch_batch_stages(t, st)) != cudaSuccess) return PHY_ERR_CUDA;
   return PHY_OK;

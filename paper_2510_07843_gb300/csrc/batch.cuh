@@ -95,6 +95,36 @@ __device__ __forceinline__ int batch_find(const BatchTable* __restrict__ t, int 
   return t->job_of[stage][cls][lo];
 }
 
+// A CTA's shared-memory copy of one (stage, class) prefix table, so that finding an item's job
+// is a search in shared memory instead of a chain of dependent global loads per item.
+struct BatchIndex {
+  int n;                           // jobs of the class
+  int start[kBatchMaxJobs + 1];    // prefix offsets of their items
+  unsigned char job[kBatchMaxJobs];
+};
+
+// Every thread of the block calls it; a barrier must follow before the copy is read.
+__device__ __forceinline__ void batch_index_load(BatchIndex& s, const BatchTable* __restrict__ t,
+                                                 int stage, int cls) {
+  const int n = t->n_class_jobs[stage][cls];
+  if (threadIdx.x == 0) s.n = n;
+  for (int i = threadIdx.x; i <= n; i += blockDim.x) s.start[i] = t->start[stage][cls][i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s.job[i] = t->job_of[stage][cls][i];
+}
+
+__device__ __forceinline__ int batch_find(const BatchIndex& s, int w, int& local) {
+  int lo = 0, hi = s.n - 1;
+  while (lo < hi) {  // last i with start[i] <= w
+    const int mid = (lo + hi + 1) >> 1;
+    if (s.start[mid] <= w)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  local = w - s.start[lo];
+  return s.job[lo];
+}
+
 // Cooperative copy of a job's geometry into shared memory (every thread of the block calls it;
 // a barrier must follow before the copy is read).
 __device__ __forceinline__ void batch_load_geo(Geo& dst, const Geo& src) {

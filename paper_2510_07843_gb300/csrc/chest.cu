@@ -156,8 +156,8 @@ __device__ __forceinline__ void chest_multi_body(const Geo& g, int grp0, int gp,
                                                  const phy_c32* __restrict__ P,
                                                  phy_c32* __restrict__ anchors,
                                                  cf* __restrict__ pil) {
-  const int nrp = kChestBatchThreads / gp;
-  const int r = threadIdx.x % nrp, gi = threadIdx.x / nrp, grp = grp0 + gi;
+  const int lg = __ffs(kChestBatchThreads / gp) - 1;  // log2 of the padded antenna count
+  const int r = threadIdx.x & ((1 << lg) - 1), gi = threadIdx.x >> lg, grp = grp0 + gi;
   const int t = (d == 0) ? g.dmrs0 : g.dmrs1;
   const int nl = g.n_layers;
   const bool live = r < g.n_rx && grp < g.G;
@@ -180,11 +180,12 @@ __device__ __forceinline__ void chest_multi_body(const Geo& g, int grp0, int gp,
   }
   const int ngl = min(gp, g.G - grp0);
   const phy_c32* pbase = P + (size_t)(cell * g.n_dmrs + d) * nl * g.n_sc;
-  for (int e = threadIdx.x; e < ngl * nl * 2 * L; e += blockDim.x) {
-    const int i = e % (2 * L), q = e / (2 * L);
-    const int l = q % nl, gj = q / nl;
-    pil[(gj * nl + l) * 2 * L + i] =
-        ld(pbase + (size_t)l * g.n_sc + 2 * group_start(g, grp0 + gj) + i);
+  for (int l = 0; l < nl; ++l) {  // per layer: the chunk's groups, 2L pilots each
+    const phy_c32* prow = pbase + (size_t)l * g.n_sc;
+    for (int e = threadIdx.x; e < ngl * 2 * L; e += blockDim.x) {
+      const int gj = e / (2 * L), i = e % (2 * L);
+      pil[(gj * nl + l) * 2 * L + i] = ld(prow + 2 * group_start(g, grp0 + gj) + i);
+    }
   }
   __syncthreads();
   if (!live) return;
@@ -209,12 +210,22 @@ __global__ void __launch_bounds__(kChestBatchThreads)
     chest_batch_kernel(const BatchTable* __restrict__ t) {
   __shared__ Geo sg;
   __shared__ cf pil[kChestBatchPilots];
+  __shared__ BatchIndex ix;
   const int n = t->n_items[kBatchChest][0];
+  // items strided over the CTAs (a job's items spread over the grid: balanced whatever the mix
+  // of light and heavy jobs); a CTA keeps the geometry while consecutive items share a job
+  if ((int)blockIdx.x >= n) return;
+  batch_index_load(ix, t, kBatchChest, 0);
+  __syncthreads();
+  int cur = -1;
   for (int w = blockIdx.x; w < n; w += gridDim.x) {
     int local;
-    const int jb = batch_find(t, kBatchChest, 0, w, local);
+    const int jb = batch_find(ix, w, local);
     const BatchJob& J = t->job[jb];
-    batch_load_geo(sg, J.g);
+    if (jb != cur) {  // uniform over the block
+      batch_load_geo(sg, J.g);
+      cur = jb;
+    }
     __syncthreads();
     const int gp = chest_batch_groups(sg.n_rx), nch = (sg.G + gp - 1) / gp;
     const int grp0 = (local % nch) * gp, d = (local / nch) % sg.n_dmrs;
@@ -232,7 +243,20 @@ __global__ void __launch_bounds__(kChestBatchThreads)
 
 }  // namespace
 
-cudaError_t launch_chest_batch(const BatchTable* t, int grid, cudaStream_t st) {
+cudaError_t launch_chest_batch(const BatchTable* t, cudaStream_t st) {
+  // two waves of CTAs: those that finish early take the next ones
+  static int grid_on[kMaxDevices] = {};
+  int& grid = grid_on[current_device()];
+  if (grid == 0) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, chest_batch_kernel,
+                                                      kChestBatchThreads, 0) != cudaSuccess ||
+        occ < 1) {
+      cudaGetLastError();
+      occ = 1;
+    }
+    grid = 2 * device_sm_count() * occ;
+  }
   chest_batch_kernel<<<grid, kChestBatchThreads, 0, st>>>(t);
   return cudaGetLastError();
 }

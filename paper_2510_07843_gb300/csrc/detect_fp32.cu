@@ -19,6 +19,7 @@
 // The two kernels run per chunk of cells so that the intermediates stay small (L2-sized).
 #include <algorithm>
 #include <cstdlib>
+#include <mutex>
 
 #include "batch.cuh"
 #include "launch.h"
@@ -689,50 +690,67 @@ __device__ __forceinline__ void direct_cta(const Geo& g, int k0, int t, int cell
   for (int l = 0; l < NL; ++l) bv[l] = mk(0.f, 0.f);
   const phy_c32* acell = anchors + (size_t)cell * nd * g.G * nl * nr;  // [d][group][l][r]
   const phy_c32* yk = Y + (((size_t)cell * g.n_sym + g.dsym[t]) * nr) * g.n_sc + kc;
+  // this thread's received values of a chunk of antennas (zero past the last antenna)
+  auto load_y = [&](int r0, cf(&dst)[kDirectRc]) {
+#pragma unroll
+    for (int rr = 0; rr < kDirectRc; ++rr)
+      dst[rr] = (live && r0 + rr < nr) ? ld(yk + (size_t)(r0 + rr) * g.n_sc) : mk(0.f, 0.f);
+  };
+  // staging threads: 16 antennas (lanes of a half-warp) x 8 (DMRS, group) rows at a time
+  constexpr int kQ = kDirectThreads / kDirectRc;
+  const int rr_t = (int)threadIdx.x % kDirectRc, qs = (int)threadIdx.x / kDirectRc;
+  cf yv[kDirectRc];
+  load_y(0, yv);
   for (int r0 = 0; r0 < nr; r0 += kDirectRc) {
     const int rc = min(kDirectRc, nr - r0);
     __syncthreads();  // every thread is done with the previous chunk
-    const int n_st = nd * ng * nl * rc;
-    for (int e = threadIdx.x; e < n_st; e += kDirectThreads) {
-      const int rr = e % rc;
-      int q = e / rc;
-      const int l = q % nl;
-      q /= nl;
-      const int gl = q % ng, d = q / ng;
-      stage[((d * NL + l) * kDirectRc + rr) * NGP + gl] =
-          ld(acell + ((size_t)(d * g.G + gA + gl) * nl + l) * nr + r0 + rr);
+    if (rr_t < rc) {
+      for (int q = qs; q < nd * ng; q += kQ) {
+        const int d = q >= ng ? 1 : 0, gl = q - d * ng;  // nd <= 2
+        const phy_c32* src = acell + ((size_t)(d * g.G + gA + gl) * nl) * nr + r0 + rr_t;
+        cf* dst = stage + ((d * NL) * kDirectRc + rr_t) * NGP + gl;
+#pragma unroll
+        for (int l = 0; l < NL; ++l)
+          if (l < nl) dst[l * kDirectRc * NGP] = ld(src + (size_t)l * nr);
+      }
     }
     __syncthreads();
+    cf yn[kDirectRc];
+    load_y(r0 + kDirectRc, yn);  // the next chunk's values load while this one is consumed
     if (live) {
-#pragma unroll 4
-      for (int rr = 0; rr < rc; ++rr) {
-        cf h[NL];
 #pragma unroll
-        for (int l = 0; l < NL; ++l) {
-          h[l] = mk(0.f, 0.f);
-          if (l < nl) {
-            const float w1 = bw[l & 1], w0 = 1.f - w1;
-            const cf* s0 = stage + (l * kDirectRc + rr) * NGP;
-            const cf c0 = s0[lj], c1 = s0[lg1];
-            cf v = mk(fmaf(w1, c1.x, w0 * c0.x), fmaf(w1, c1.y, w0 * c0.y));
-            if (nd == 2) {
-              const cf* s1 = s0 + NL * kDirectRc * NGP;
-              const cf e0 = s1[lj], e1 = s1[lg1];
-              const cf u = mk(fmaf(w1, e1.x, w0 * e0.x), fmaf(w1, e1.y, w0 * e0.y));
-              v = mk(fmaf(tau, u.x - v.x, v.x), fmaf(tau, u.y - v.y, v.y));
+      for (int rr = 0; rr < kDirectRc; ++rr) {
+        if (rr < rc) {
+          cf h[NL];
+#pragma unroll
+          for (int l = 0; l < NL; ++l) {
+            h[l] = mk(0.f, 0.f);
+            if (l < nl) {
+              const float w1 = bw[l & 1], w0 = 1.f - w1;
+              const cf* s0 = stage + (l * kDirectRc + rr) * NGP;
+              const cf c0 = s0[lj], c1 = s0[lg1];
+              cf v = mk(fmaf(w1, c1.x, w0 * c0.x), fmaf(w1, c1.y, w0 * c0.y));
+              if (nd == 2) {
+                const cf* s1 = s0 + NL * kDirectRc * NGP;
+                const cf e0 = s1[lj], e1 = s1[lg1];
+                const cf u = mk(fmaf(w1, e1.x, w0 * e0.x), fmaf(w1, e1.y, w0 * e0.y));
+                v = mk(fmaf(tau, u.x - v.x, v.x), fmaf(tau, u.y - v.y, v.y));
+              }
+              h[l] = v;
             }
-            h[l] = v;
           }
-        }
-        const cf y = ld(yk + (size_t)(r0 + rr) * g.n_sc);
+          const cf y = yv[rr];
 #pragma unroll
-        for (int l = 0; l < NL; ++l) {
+          for (int l = 0; l < NL; ++l) {
 #pragma unroll
-          for (int m = 0; m <= l; ++m) A[tri(l, m)] = cfma_cj(h[l], h[m], A[tri(l, m)]);
-          bv[l] = cfma_cj(h[l], y, bv[l]);
+            for (int m = 0; m <= l; ++m) A[tri(l, m)] = cfma_cj(h[l], h[m], A[tri(l, m)]);
+            bv[l] = cfma_cj(h[l], y, bv[l]);
+          }
         }
       }
     }
+#pragma unroll
+    for (int rr = 0; rr < kDirectRc; ++rr) yv[rr] = yn[rr];
   }
   if (!live) return;
   const float s2 = sigma2[cell];
@@ -808,12 +826,23 @@ __global__ void __launch_bounds__(kDirectThreads)
     direct_batch_kernel(const BatchTable* __restrict__ t) {
   __shared__ Geo sg;
   __shared__ cf stage[direct_stage_elems<NL>()];
+  __shared__ BatchIndex ix;
   constexpr int cls = batch_class(NL);
   const int n = t->n_items[kBatchDirect][cls];
+  // items strided over the CTAs (a job's items spread over the grid: balanced whatever the mix
+  // of light and heavy jobs); a CTA keeps the geometry while consecutive items share a job
+  if ((int)blockIdx.x >= n) return;
+  batch_index_load(ix, t, kBatchDirect, cls);
+  __syncthreads();
+  int cur = -1;
   for (int w = blockIdx.x; w < n; w += gridDim.x) {
     int local;
-    const BatchJob& J = t->job[batch_find(t, kBatchDirect, cls, w, local)];
-    batch_load_geo(sg, J.g);
+    const int jb = batch_find(ix, w, local);
+    const BatchJob& J = t->job[jb];
+    if (jb != cur) {  // uniform over the block
+      batch_load_geo(sg, J.g);
+      cur = jb;
+    }
     __syncthreads();
     const int nb = (sg.n_sc + kDirectThreads - 1) / kDirectThreads;
     const int k0 = (local % nb) * kDirectThreads;
@@ -830,11 +859,15 @@ template <int NL>
 __global__ void __launch_bounds__(kPrepThreads)
     seg_prep_batch_kernel(const BatchTable* __restrict__ t) {
   __shared__ Geo sg;
+  __shared__ BatchIndex ix;
   constexpr int cls = batch_class(NL);
   const int n = t->n_items[kBatchSeg][cls];
+  if ((int)blockIdx.x >= n) return;
+  batch_index_load(ix, t, kBatchSeg, cls);
+  __syncthreads();
   for (int w = blockIdx.x; w < n; w += gridDim.x) {
     int local;
-    const BatchJob& J = t->job[batch_find(t, kBatchSeg, cls, w, local)];
+    const BatchJob& J = t->job[batch_find(ix, w, local)];
     batch_load_geo(sg, J.g);
     __syncthreads();
     seg_prep_body<NL>(sg, J.wmax, 0, local % sg.n_seg, local / sg.n_seg, J.anchors, J.Y, J.ygg,
@@ -851,18 +884,21 @@ __global__ void __launch_bounds__(kSolveThreads)
     re_solve_batch_kernel(const BatchTable* __restrict__ t, int smem_bytes) {
   extern __shared__ __align__(128) unsigned char solve_smem[];
   __shared__ Geo sg;
+  __shared__ BatchIndex ix;
   constexpr int cls = batch_class(NL);
+  const int n = t->n_items[kBatchSolve][cls];
+  if ((int)blockIdx.x >= n) return;
   uint64_t* bar = reinterpret_cast<uint64_t*>(solve_smem + smem_bytes - 16);
   if (threadIdx.x == 0) {
     tc::mbar_init(bar, 1);
     tc::mbar_fence_init();
   }
+  batch_index_load(ix, t, kBatchSolve, cls);
   __syncthreads();
-  const int n = t->n_items[kBatchSolve][cls];
   uint32_t it = 0;
   for (int w = blockIdx.x; w < n; w += gridDim.x, ++it) {
     int local;
-    const BatchJob& J = t->job[batch_find(t, kBatchSolve, cls, w, local)];
+    const BatchJob& J = t->job[batch_find(ix, w, local)];
     batch_load_geo(sg, J.g);
     // the previous item's generic accesses to shared memory come before this item's bulk copies
     if (threadIdx.x == 0) tc::fence_proxy_async();
@@ -1036,7 +1072,7 @@ namespace {
 // two DMRS symbols, up to 64 antennas), so that one captured launch serves any batch.
 struct BatchClassLaunch {
   size_t smem_seg = 0, smem_solve = 0;
-  int grid_seg = 0, grid_solve = 0;
+  int grid_seg = 0, grid_solve = 0, grid_direct = 0;
 };
 
 // Shared-memory bounds of one class (pure host arithmetic, no CUDA call).
@@ -1086,6 +1122,14 @@ BatchClassLaunch batch_class_launch() {
       occ < 1)
     occ = 1;
   b.grid_solve = sms * occ;
+  if constexpr (NL <= 4) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, direct_batch_kernel<NL>,
+                                                      kDirectThreads, 0) != cudaSuccess ||
+        occ < 1)
+      occ = 1;
+    b.grid_direct = 2 * sms * occ;  // two waves: CTAs that finish early take the next ones
+  }
+  cudaGetLastError();
   return b;
 }
 
@@ -1096,7 +1140,7 @@ template <int NL>
 cudaError_t launch_batch_nl(const BatchTable* t, cudaStream_t st) {
   const BatchClassLaunch b = batch_class_launch<NL>();
   if constexpr (NL <= 4) {
-    direct_batch_kernel<NL><<<device_sm_count() * 8, kDirectThreads, 0, st>>>(t);
+    direct_batch_kernel<NL><<<b.grid_direct, kDirectThreads, 0, st>>>(t);
   } else {
     seg_prep_batch_kernel<NL><<<b.grid_seg, kPrepThreads, b.smem_seg, st>>>(t);
   }
@@ -1139,12 +1183,63 @@ bool batch_solve_fits(const Geo& g) {
   return solve_smem_bytes(NL, 0, max_segments_per_block(g)) <= b.smem_solve;
 }
 
+namespace {
+
+// Side streams on which the batched receiver runs three of its four layer classes next to the
+// fourth (per device, created on the first launch that is not being captured; a launch captured
+// before that runs the classes one after another on the caller's stream).
+struct BatchFork {
+  cudaStream_t s[3] = {};
+  cudaEvent_t fork = nullptr, join[3] = {};
+  bool ok = false;
+};
+std::mutex g_fork_mu;  // one fork/join sequence at a time (the events are shared)
+
+BatchFork& batch_fork(bool may_create) {
+  static BatchFork on[kMaxDevices];
+  BatchFork& f = on[current_device()];
+  if (f.ok || !may_create) return f;
+  bool ok = cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < 3 && ok; ++i)
+    ok = cudaStreamCreateWithFlags(&f.s[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&f.join[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) cudaGetLastError();
+  f.ok = ok;
+  return f;
+}
+
+}  // namespace
+
+// The layer classes are independent once the LS stage is done: each runs its chain (direct
+// form, or segment kernels then solve) on its own stream, forked from and joined back into the
+// caller's, so that a batch's critical path is its longest chain, not the sum of the four.
 cudaError_t launch_batch_stages(const BatchTable* t, cudaStream_t st) {
+  std::lock_guard<std::mutex> lock(g_fork_mu);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    cs = cudaStreamCaptureStatusActive;
+  }
+  BatchFork& f = batch_fork(cs == cudaStreamCaptureStatusNone);
   cudaError_t e;
-  if ((e = launch_batch_nl<2>(t, st)) != cudaSuccess) return e;
-  if ((e = launch_batch_nl<4>(t, st)) != cudaSuccess) return e;
-  if ((e = launch_batch_nl<8>(t, st)) != cudaSuccess) return e;
-  return launch_batch_nl<16>(t, st);
+  if (!f.ok) {
+    if ((e = launch_batch_nl<2>(t, st)) != cudaSuccess) return e;
+    if ((e = launch_batch_nl<4>(t, st)) != cudaSuccess) return e;
+    if ((e = launch_batch_nl<8>(t, st)) != cudaSuccess) return e;
+    return launch_batch_nl<16>(t, st);
+  }
+  if ((e = cudaEventRecord(f.fork, st)) != cudaSuccess) return e;
+  for (int i = 0; i < 3; ++i)
+    if ((e = cudaStreamWaitEvent(f.s[i], f.fork, 0)) != cudaSuccess) return e;
+  if ((e = launch_batch_nl<2>(t, f.s[0])) != cudaSuccess) return e;
+  if ((e = launch_batch_nl<4>(t, f.s[1])) != cudaSuccess) return e;
+  if ((e = launch_batch_nl<8>(t, f.s[2])) != cudaSuccess) return e;
+  if ((e = launch_batch_nl<16>(t, st)) != cudaSuccess) return e;
+  for (int i = 0; i < 3; ++i) {
+    if ((e = cudaEventRecord(f.join[i], f.s[i])) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(st, f.join[i], 0)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 int host_max_segment_width(const Geo& g) {

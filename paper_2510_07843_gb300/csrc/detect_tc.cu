@@ -17,8 +17,9 @@
 //    tensor copies (one box = 16 subcarriers x all antennas of one data symbol) and the anchors
 //    of the next segment's corners, running ahead of the consumers by up to the ring's depth;
 //  - eight converter warps turn anchors into the CC operand and boxes into the RE-tile operand
-//    (conversion to the MMA type and K-major core-matrix order); one of their threads issues
-//    the MMAs;
+//    (conversion to the MMA type and K-major core-matrix order);
+//  - one warp issues the MMAs as operands become ready, so that conversion never waits on MMA
+//    issue;
 //  - four drain warps fold X into the Gram blocks and the accumulators into the matched filter.
 // RE tiles are whole data symbols of the segment (floor(128 / W) of them), double-buffered in
 // shared and tensor memory, so that converting one tile overlaps the MMA of the previous one
@@ -41,7 +42,8 @@ namespace {
 constexpr int kConvWarps = 8;   // converters: anchors -> CC, boxes -> RE tiles, MMA issue
 constexpr int kDrainWarps = 4;  // drain: X -> Gram blocks, accumulators -> matched filter
 constexpr int kConv = 32 * kConvWarps;
-constexpr int kProducerWarp = kConvWarps + kDrainWarps;
+constexpr int kMmaWarp = kConvWarps + kDrainWarps;  // issues every MMA of the CTA
+constexpr int kProducerWarp = kMmaWarp + 1;
 constexpr int kTcThreads = 32 * (kProducerWarp + 1);
 constexpr int kRows = 128;                 // UMMA M and rows of every operand tile
 constexpr int kK = 128;                    // K elements per operand row: (re, im) x 64 antennas
@@ -88,8 +90,9 @@ struct Smem {
   static constexpr size_t kCorner = up128((size_t)NL * 64 * 8);  // one corner's [l][r] block
   static constexpr size_t kRing = kAnch + NC * kCorner;
   static constexpr size_t kBars = kRing + (size_t)RS * kStageBytes;
-  // full[S], empty[S], anchors full / empty, X done / drained, MF done[2] / drained[2]
-  static constexpr int kNumBars = 2 * RS + 8;
+  // full[S], empty[S], anchors full / empty, X done / drained, MF done[2] / drained[2],
+  // CC converted, RE tile converted[2]
+  static constexpr int kNumBars = 2 * RS + 11;
   static constexpr size_t kMisc = kBars + 8 * kNumBars;  // TMEM address, consumed counts
   static constexpr size_t kTotal = kMisc + 16;
 };
@@ -219,6 +222,8 @@ __device__ __forceinline__ void seg_prep_tc_body(const Src& src) {
   uint64_t* x_free = a_full + 3;
   uint64_t* mf_bar = a_full + 4;     // [2]
   uint64_t* tmem_free = a_full + 6;  // [2]
+  uint64_t* cc_ready = a_full + 8;
+  uint64_t* tile_ready = a_full + 9;  // [2]
   uint32_t* misc = reinterpret_cast<uint32_t*>(smem + Sm::kMisc);  // TMEM address
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -236,7 +241,9 @@ __device__ __forceinline__ void seg_prep_tc_body(const Src& src) {
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(mf_bar + b, 1);
       tc::mbar_init(tmem_free + b, 4);
+      tc::mbar_init(tile_ready + b, kConvWarps);  // arrivals: the converter warps
     }
+    tc::mbar_init(cc_ready, kConvWarps);
     tc::mbar_fence_init();
   }
   if (warp == 0) tc::tmem_alloc(misc, kTmemCols);
@@ -310,8 +317,7 @@ __device__ __forceinline__ void seg_prep_tc_body(const Src& src) {
 
   if (warp < kConvWarps) {
     uint32_t nbox = 0, nitem = 0, ntile = 0;  // boxes, anchor sets and RE tiles consumed
-    uint32_t x_count = 0, mf_count[2] = {0, 0};  // MMA commits per barrier
-    unsigned* err = nullptr;                     // the current item's error word
+    unsigned* err = nullptr;                   // the current item's error word
     for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
       const TcView v = src.at(w);
       const Geo& g = *v.g;
@@ -323,10 +329,12 @@ __device__ __forceinline__ void seg_prep_tc_body(const Src& src) {
                                             g.wait_seg);
       fail |= !tc::mbar_wait_sleep(a_full, nitem & 1, g.wait_seg);
       ++nitem;
-      // ---- CC = [C ; iC] from the anchors of the segment's corners, four antennas per item
+      // ---- CC = [C ; iC] from the anchors of the segment's corners, four antennas per item.
+      // A warp takes 8 rows x 4 antenna quads: its 16-byte stores fill whole 128-byte core
+      // matrix rows (no bank conflicts), its anchor loads spread over the banks.
 #pragma unroll 2
       for (int e = gtid; e < NXP * 16; e += kConv) {
-        const int rq = e & 15, c = e >> 4;
+        const int rq = (e >> 3) & 15, c = ((e >> 7) << 3) | (e & 7);
         const int corner = c / NL, l = c % NL;
         cf v[4];
         const float2* src =
@@ -351,18 +359,14 @@ __device__ __forceinline__ void seg_prep_tc_body(const Src& src) {
         store_quad<FMT>(cc, c, rq, v);
         store_quad<FMT>(cc, NXP + c, rq, iv);
       }
+      tc::fence_proxy_async();  // the generic stores before the MMAs' async-proxy reads
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(a_empty);
-      tc::fence_proxy_async();
+      if (lane == 0) {
+        tc::mbar_arrive(a_empty);
+        tc::mbar_arrive(cc_ready);
+      }
       stop = tc::bar_or<1, kConv>(fail);
       if (stop) break;
-      // ---- X = C^H C, once the drain group has read the previous X
-      if (gtid == 0) {
-        if (nitem > 1) fail |= !tc::mbar_wait_sleep(x_free, (nitem - 2) & 1, g.wait_seg);
-        tc::fence_after_sync();
-        gemm_issue<FMT>(tmem + kColX, cc, cc, tc::instr_desc(FMT, kRows, NXP), x_bar);
-      }
-      ++x_count;
       for (int t = 0; t < it.ntile; ++t, ++ntile) {
         const uint32_t buf = ntile & 1;
         unsigned char* yop =
@@ -409,27 +413,54 @@ __device__ __forceinline__ void seg_prep_tc_body(const Src& src) {
         }
         nbox += nbx;
         tc::fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(tile_ready + buf);
         stop = tc::bar_or<1, kConv>(fail);
         if (stop) break;
-        // ---- V = C^H y, once the drain group has emptied this accumulator buffer
-        if (gtid == 0) {
-          if (ntile >= 2)
-            fail |= !tc::mbar_wait_sleep(tmem_free + buf, ((ntile - 2) >> 1) & 1, g.wait_seg);
-          tc::fence_after_sync();
-          gemm_issue<FMT>(tmem + kColMf + 128 * buf, yop, cc,
-                          tc::instr_desc(FMT, kRows, 2 * NXP), mf_bar + buf);
-        }
-        ++mf_count[buf];
       }
       if (stop) break;
     }
-    if (gtid == 0) {
-      if (stop && err) atomicAdd(err, 1u);
+    if (gtid == 0 && stop && err) atomicAdd(err, 1u);
+  } else if (warp == kMmaWarp) {
+    // ------------------------------------------------------------ MMA issue
+    // X = C^H C once CC is converted and the drain has read the previous X; V = C^H y per RE
+    // tile once the tile is converted and the drain has emptied the accumulator buffer.
+    uint32_t nitem = 0, ntile = 0, x_count = 0, mf_count[2] = {0, 0};
+    unsigned* err = nullptr;
+    if (lane == 0) {
+      for (int w = blockIdx.x; w < n_work && !fail; w += gridDim.x) {
+        const TcView v = src.at(w);
+        const Geo& g = *v.g;
+        const Item it = item_of(g, v.w, v.cell0);
+        err = v.err;
+        fail |= !tc::mbar_wait_sleep(cc_ready, nitem & 1, g.wait_seg);
+        if (nitem > 0) fail |= !tc::mbar_wait_sleep(x_free, (nitem - 1) & 1, g.wait_seg);
+        ++nitem;
+        if (fail) break;
+        tc::fence_after_sync();
+        gemm_issue<FMT>(tmem + kColX, cc, cc, tc::instr_desc(FMT, kRows, NXP), x_bar);
+        ++x_count;
+        for (int t = 0; t < it.ntile && !fail; ++t, ++ntile) {
+          const uint32_t buf = ntile & 1;
+          const unsigned char* yop =
+              smem + Sm::kYop + (size_t)(Lay::kYBufs == 2 ? buf : 0) * Lay::kTileBytes;
+          fail |= !tc::mbar_wait_sleep(tile_ready + buf, (ntile >> 1) & 1, g.wait_seg);
+          if (ntile >= 2)
+            fail |= !tc::mbar_wait_sleep(tmem_free + buf, ((ntile - 2) >> 1) & 1, g.wait_seg);
+          if (fail) break;
+          tc::fence_after_sync();
+          gemm_issue<FMT>(tmem + kColMf + 128 * buf, yop, cc,
+                          tc::instr_desc(FMT, kRows, 2 * NXP), mf_bar + buf);
+          ++mf_count[buf];
+        }
+      }
+      if (fail && err) atomicAdd(err, 1u);
       // MMAs still running (only after a timeout) must finish before tensor memory is released
       if (x_count) tc::mbar_wait_sleep(x_bar, (x_count - 1) & 1, kWaitIters);
       for (int b = 0; b < 2; ++b)
         if (mf_count[b]) tc::mbar_wait_sleep(mf_bar + b, (mf_count[b] - 1) & 1, kWaitIters);
     }
+    __syncwarp();
   } else {
     uint32_t nitem = 0, ntile = 0;
     unsigned* err = nullptr;
