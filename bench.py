@@ -423,6 +423,9 @@ def main():
     ap.add_argument("--batch-probe", type=int, default=0, metavar="JOBS",
                     help="only time batches of JOBS jobs of the serving mix through the batched "
                          "receiver (1 to 64; small enough to run under ncu)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default tile shapes (no tuning launches before the timing; "
+                         "for launch-list captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -784,8 +787,9 @@ def time_variant(spec, precision, refactor, llr, args, slot, dev, world, fl_peak
     # tile shapes (cells per chunk, solve CTA width, tensor-core ring depth) chosen by the
     # library's autotuner on these buffers, before anything is timed; outputs do not depend on them
     phy.autotune_clear()
-    phy.autotune(cfg, buf.Y, buf.pilots, buf.sigma2, buf.x_hat, buf.sinr, buf.llr, buf.flags,
-                 buf.workspace, stream=st)
+    if not args.no_autotune:
+        phy.autotune(cfg, buf.Y, buf.pilots, buf.sigma2, buf.x_hat, buf.sinr, buf.llr, buf.flags,
+                     buf.workspace, stream=st)
     tiles = phy.autotune_tiles(cfg)
     for _ in range(max(args.warmup, 3)):
         step()
@@ -1109,7 +1113,9 @@ def run_ours(args, spec, rank, world, local):
         "dtype": (f"{args.precision} tensor-core products (fp32 accumulate), f32 solve"
                   if args.precision != "fp32" else "f32"),
         "data": "synthetic", "config": dict(config_dict(spec, args, world),
-                                            tiles=dict(head["tiles"], chosen_by="phy_autotune")),
+                                            tiles=dict(head["tiles"], chosen_by=(
+                                                "defaults" if args.no_autotune
+                                                else "phy_autotune"))),
         "serial_ms_per_step": head["serial_ms_per_step"],
         "latency_ms": head["latency_ms"],
         "stages_ms": head["stages_ms"],
