@@ -346,9 +346,9 @@ void phy_autotune_clear(void);
  *  - solve_width: REs (threads) per CTA of the solve kernel, 128 (default) or 64;
  *  - ring_stages: depth of the tensor-core segment kernel's ring of 16-subcarrier boxes, the
  *    format's default (8 stages for FP16/BF16, 6 for TF32) or 12 where its shared-memory map
- *    still fits (otherwise the default is used).
+ *    still fits (otherwise the default is used, and phy_autotune_tiles() reads back 0).
  * phy_autotune() searches them in that order (chunk sizes, then the other solve width, then the
- * deeper ring for FP16/BF16 products), keeping each change only if it is faster. Tiles never
+ * deeper ring for FP16/BF16 products where it fits), keeping each change only if it is faster. Tiles never
  * change the arithmetic: every choice gives bitwise the same outputs.
  * phy_autotune_set_tiles() pins them for cfg's key (PHY_ERR_INVALID_ARG for a value outside the
  * lists); phy_autotune_tiles() reads them back. Both are thread-safe and host-only.

@@ -754,7 +754,7 @@ phy_status phy_autotune(const phy_slot_cfg* cfg, const phy_c32* Y, const phy_c32
   for (int c : cand)
     if (rs == PHY_OK && workspace_for_chunk(g, c) <= workspace_bytes) consider({c, 128, 0});
   if (rs == PHY_OK && best.chunk > 0) consider({best.chunk, 64, 0});
-  if (rs == PHY_OK && best.chunk > 0 && g.prec != PHY_PREC_FP32 && g.prec != PHY_PREC_TC_TF32)
+  if (rs == PHY_OK && best.chunk > 0 && phy::tc_deep_ring_fits(g))
     consider({best.chunk, best.solve_w, 12});
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -797,7 +797,8 @@ phy_status phy_autotune_tiles(const phy_slot_cfg* cfg, int32_t* chunk, int32_t* 
   const phy::Tile t = phy::tuned_tile(g);
   if (chunk) *chunk = t.chunk;
   if (solve_width) *solve_width = t.solve_w;
-  if (ring_stages) *ring_stages = t.ring;
+  // the ring the kernel runs with: a pinned deeper ring that does not fit reads back as 0
+  if (ring_stages) *ring_stages = t.ring == 12 && !phy::tc_deep_ring_fits(g) ? 0 : t.ring;
   return PHY_OK;
 }
 

@@ -698,6 +698,22 @@ cudaError_t launch_seg_prep_tc_batch(const BatchTable* t, int nl_cls, cudaStream
   }
 }
 
+bool tc_deep_ring_fits(const Geo& g) {
+  if (g.prec != PHY_PREC_TC_FP16 && g.prec != PHY_PREC_TC_BF16) return false;
+  const int nc = g.n_dmrs == 2 ? 4 : 2;
+  auto fits = [](size_t total) { return total <= 227 * 1024; };
+  switch (nl_class_of(g.n_layers)) {
+    case 2: return fits(nc == 4 ? Smem<2, 4, tc::kFmtF16, kDeepRing>::kTotal
+                                : Smem<2, 2, tc::kFmtF16, kDeepRing>::kTotal);
+    case 4: return fits(nc == 4 ? Smem<4, 4, tc::kFmtF16, kDeepRing>::kTotal
+                                : Smem<4, 2, tc::kFmtF16, kDeepRing>::kTotal);
+    case 8: return fits(nc == 4 ? Smem<8, 4, tc::kFmtF16, kDeepRing>::kTotal
+                                : Smem<8, 2, tc::kFmtF16, kDeepRing>::kTotal);
+    default: return fits(nc == 4 ? Smem<16, 4, tc::kFmtF16, kDeepRing>::kTotal
+                                 : Smem<16, 2, tc::kFmtF16, kDeepRing>::kTotal);
+  }
+}
+
 bool seg_prep_tc_supported(const Geo& g) {
   // tensor-map rules: 16-byte strides and inner box extents (even antenna count); tiles of
   // whole data symbols (segments of at most 64 subcarriers, always the case for covers <= 16)

@@ -74,6 +74,8 @@ bool make_map(CUtensorMap* m, const void* base, const cuuint64_t (&dim)[3],
 // Tensor-core segment kernel (same outputs as the FP32 one) for g.prec != PHY_PREC_FP32.
 // Needs an even antenna count and 16-byte aligned anchors and grid (TMA tensor maps).
 bool seg_prep_tc_supported(const Geo& g);
+// Whether the tensor-core segment kernel's deeper ring (12 stages) fits shared memory for g.
+bool tc_deep_ring_fits(const Geo& g);
 cudaError_t launch_seg_prep_tc(const Geo& g, int NL, int c0, int nc, const phy_c32* anchors,
                                const phy_c32* Y, float4* ygg, cf* bvec, unsigned* err,
                                cudaStream_t st);

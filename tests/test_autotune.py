@@ -56,7 +56,16 @@ def test_tile_pins_are_validated_and_read_back():
     phy.autotune_clear()
     assert phy.autotune_tiles(cfg) == {"chunk": 0, "solve_width": 0, "ring": 0}
     phy.autotune_set_tiles(cfg, 2, 64, 12)
-    assert phy.autotune_tiles(cfg) == {"chunk": 2, "solve_width": 64, "ring": 12}
+    # the deeper ring reads back only where it applies: tensor-core products whose
+    # shared-memory map still fits it (8 layers yes; FP32 products or 16 layers no)
+    assert phy.autotune_tiles(cfg) == {"chunk": 2, "solve_width": 64, "ring": 0}
+    tc8 = phy.SlotConfig(n_cells=2, n_prb=12, n_rx=64, n_layers=8, qm=8, dmrs_sym=(2, 11),
+                         precision="fp16")
+    tc16 = phy.SlotConfig(n_cells=2, n_prb=12, n_rx=64, n_layers=16, qm=8, dmrs_sym=(2, 11),
+                          precision="fp16")
+    for c, ring in ((tc8, 12), (tc16, 0)):
+        phy.autotune_set_tiles(c, 1, 128, 12)
+        assert phy.autotune_tiles(c) == {"chunk": 1, "solve_width": 128, "ring": ring}
     for bad in ((5, 0, 0), (-1, 0, 0), (0, 96, 0), (0, 0, 10)):
         with pytest.raises(phy.PhyError):
             phy.autotune_set_tiles(cfg, *bad)
