@@ -423,6 +423,10 @@ def main():
     ap.add_argument("--batch-probe", type=int, default=0, metavar="JOBS",
                     help="only time batches of JOBS jobs of the serving mix through the batched "
                          "receiver (1 to 64; small enough to run under ncu)")
+    ap.add_argument("--cnn-slots", type=int, default=24,
+                    help="generated 12-PRB training slots for the denoiser (3,072 tiles each; "
+                         "651 slots = 2.0 M tiles)")
+    ap.add_argument("--cnn-epochs", type=int, default=8)
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default tile shapes (no tuning launches before the timing; "
                          "for launch-list captures)")
@@ -639,19 +643,24 @@ CNN_MACS_FWD = 168 * (32 * 18 + 2 * 32 * 288 + 2 * 288)  # per tile: the four 3x
 CNN_MACS_TRAIN = 2 * CNN_MACS_FWD + 168 * (2 * 288 + 2 * 32 * 288)  # + dW all, dX layers 2-4
 
 
-def cnn_run(dev, st, fp32_peak_tf: float, bf16_peak_tf: float) -> dict:
+def cnn_run(dev, st, fp32_peak_tf: float, bf16_peak_tf: float, slots: int = 24,
+            epochs: int = 8) -> dict:
     """The learned denoiser: trained on the GPU by the library's kernels on generated slots
-    (24 slots of 12 PRB, 32 Rx x 8 layers, 0-30 dB, 0-500 Hz Doppler; 8 epochs of Adam), then
-    evaluated on one 273-PRB 32 Rx x 8 layer 64-QAM slot at 5 dB and 300 Hz against LS +
-    interpolation (channel MSE, uncoded BER of LMMSE detection). Times by CUDA events."""
+    (`slots` slots of 12 PRB, 32 Rx x 8 layers = 3,072 tiles each, 0-30 dB, 0-500 Hz Doppler;
+    `epochs` epochs of Adam), then evaluated on one 273-PRB 32 Rx x 8 layer 64-QAM slot at 5 dB
+    and 300 Hz against LS + interpolation (channel MSE, uncoded BER of LMMSE detection), and with
+    more than 24 training slots also at 0 and 20 dB. Times by CUDA events."""
     import torch
     from paper_2510_07843_gb300 import denoise as D
     from paper_2510_07843_gb300 import phy
-    x, y = D.training_set(n_slots=24, n_prb=12, seed=11, dev=dev)
+    workers = 0 if slots <= 24 else max(1, min(16, len(os.sched_getaffinity(0))))
+    g0 = time.perf_counter()
+    x, y = D.training_set(n_slots=slots, n_prb=12, seed=11, dev=dev, workers=workers)
+    gen_s = time.perf_counter() - g0
     tr = D.Trainer(D.init_params(0), batch=256, dev=dev, lr=2e-3)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(st)
-    for ep in range(8):
+    for ep in range(epochs):
         tr.epoch(x, y, seed=ep)
     b.record(st)
     torch.cuda.synchronize()
@@ -701,7 +710,15 @@ def cnn_run(dev, st, fp32_peak_tf: float, bf16_peak_tf: float) -> dict:
     inf_tf = n_tiles * CNN_MACS_FWD * 2 / inf_s / 1e12
     fwd_flops = n_tiles * CNN_MACS_FWD * 2
     res = D.evaluate(tr.p, ev, dev, tensor_cores=True)
+    more = {}
+    if slots > 24:
+        for snr in (0.0, 20.0):
+            evs = D.slot_tiles(D.train_spec(n_prb=273, snr_db=snr, doppler_hz=300.0),
+                               4000 + int(snr), dev)
+            more[f"{snr:g}dB"] = D.evaluate(tr.p, evs, dev, tensor_cores=True)
     return {"train": {"tiles": int(tiles), "steps": tr.step, "batch": tr.batch,
+                      "set_tiles": int(x.shape[0]), "epochs": epochs,
+                      "generation_s": gen_s, "generation_workers": workers,
                       "seconds": train_s, "tiles_per_s": tiles / train_s,
                       "tflops": train_tf, "fp32_peak_frac": train_tf / fp32_peak_tf},
             "denoise_slot": {"tiles": n_tiles, "ms": inf_s * 1e3, "tflops": inf_tf,
@@ -716,7 +733,8 @@ def cnn_run(dev, st, fp32_peak_tf: float, bf16_peak_tf: float) -> dict:
                              / 1e12 / bf16_peak_tf,
                              "peak": {"fp32_tflops": fp32_peak_tf, "bf16_tflops": bf16_peak_tf,
                                       "bf16_source": "MEASURED_PEAKS.json bf16_tflops"}},
-            "eval": {"snr_db": 5.0, "doppler_hz": 300.0, **res}}
+            "eval": {"snr_db": 5.0, "doppler_hz": 300.0, **res},
+            **({"eval_more": more} if more else {})}
 
 
 def serving_run(spec, precision, dev, buf, slots=100, llr="f32", streams=2):
@@ -1085,7 +1103,8 @@ def run_ours(args, spec, rank, world, local):
         bfp = bfp_run(cfg, spec, slot, buf, st, hbm_peak)
     learned = None
     if not args.no_cnn:
-        learned = cnn_run(dev, st, fl_peak, peaks.get("bf16_tflops", 1900.0))
+        learned = cnn_run(dev, st, fl_peak, peaks.get("bf16_tflops", 1900.0),
+                          slots=args.cnn_slots, epochs=args.cnn_epochs)
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:

@@ -56,9 +56,15 @@ class SlotTiles:
     sigma2: "object"
 
 
-def slot_tiles(spec: S.SlotSpec, seed: int, dev) -> SlotTiles:
+def _make_slot(args):
+    """Process-pool entry: one generated slot (numpy only)."""
+    spec, seed = args
+    return S.make_slot(spec, seed, keep_h=True)
+
+
+def slot_tiles(spec: S.SlotSpec, seed: int, dev, slot: Optional[S.Slot] = None) -> SlotTiles:
     import torch
-    sl = S.make_slot(spec, seed, keep_h=True)
+    sl = slot if slot is not None else S.make_slot(spec, seed, keep_h=True)
     cfg = phy.SlotConfig.from_spec(spec)
     Y = torch.from_numpy(sl.Y).to(dev)
     P = torch.from_numpy(sl.pilots).to(dev)
@@ -82,17 +88,29 @@ def slot_tiles(spec: S.SlotSpec, seed: int, dev) -> SlotTiles:
 
 
 def training_set(n_slots: int, n_prb: int, seed: int, dev, snr_range=(0.0, 30.0),
-                 doppler_range=(0.0, 500.0)):
-    """Tiles of n_slots slots with SNR and Doppler drawn uniformly (seeded), concatenated."""
+                 doppler_range=(0.0, 500.0), workers: int = 0):
+    """Tiles of n_slots slots with SNR and Doppler drawn uniformly (seeded), concatenated. With
+    workers > 0 the slots are generated (numpy) in that many spawned processes, in chunks, and
+    tiled on the device as they arrive; the tiles are the same either way."""
     import torch
     rng = np.random.default_rng(seed)
-    xs, ys = [], []
+    specs = []
     for i in range(n_slots):
         snr, doppler = float(rng.uniform(*snr_range)), float(rng.uniform(*doppler_range))
-        spec = train_spec(n_prb, snr, doppler)
-        st = slot_tiles(spec, seed * 1000 + i, dev)
-        xs.append(st.x)
-        ys.append(st.label)
+        specs.append((train_spec(n_prb, snr, doppler), seed * 1000 + i))
+    xs, ys = [], []
+    if workers > 0:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            for (spec, sd), sl in zip(specs, pool.imap(_make_slot, specs, chunksize=4)):
+                st = slot_tiles(spec, sd, dev, slot=sl)
+                xs.append(st.x)
+                ys.append(st.label)
+    else:
+        for spec, sd in specs:
+            st = slot_tiles(spec, sd, dev)
+            xs.append(st.x)
+            ys.append(st.label)
     return torch.cat(xs), torch.cat(ys)
 
 
