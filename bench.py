@@ -623,11 +623,39 @@ def bfp_run(cfg, spec, slot, buf, st, hbm_peak: float, iq_width: int = 9, reps: 
     ch = c.cpu().pin_memory()
     Ph = buf.pilots.cpu().pin_memory()
     sh = buf.sigma2.cpu().pin_memory()
-    lh = torch.empty(buf.llr.shape, dtype=buf.llr.dtype).pin_memory()
-    fh = torch.empty(buf.flags.shape, dtype=torch.uint8).pin_memory()
-    e2e_ms = timed(lambda: phy.slot_run_bfp_host(cfg, ch, iq_width, scale, Ph, sh, lh, fh, c, Yd,
-                                                 buf.pilots, buf.sigma2, buf.x_hat, buf.sinr,
-                                                 buf.llr, buf.flags, buf.workspace, stream=st))
+    # the steps rotate over E2E_SETS streams with their own device and pinned output buffers,
+    # as the grid-fed end-to-end measurement does
+    esets = []
+    for i in range(E2E_SETS):
+        b_ = buf if i == 0 else phy.SlotBuffers(cfg, device=buf.Y.device)
+        s_ = st if i == 0 else torch.cuda.Stream(device=buf.Y.device)
+        esets.append((b_, s_, torch.empty_like(c), torch.empty_like(Yd),
+                      torch.empty(buf.llr.shape, dtype=buf.llr.dtype).pin_memory(),
+                      torch.empty(buf.flags.shape, dtype=torch.uint8).pin_memory()))
+    lh, fh = esets[0][4], esets[0][5]
+
+    def e2e_step(i):
+        b_, s_, cd, yd, lh_, fh_ = esets[i % len(esets)]
+        phy.slot_run_bfp_host(cfg, ch, iq_width, scale, Ph, sh, lh_, fh_, cd, yd, b_.pilots,
+                              b_.sigma2, b_.x_hat, b_.sinr, b_.llr, b_.flags, b_.workspace,
+                              stream=s_)
+
+    for i in range(2 * len(esets)):
+        e2e_step(i)
+    torch.cuda.synchronize()
+    k2 = max(reps, 3 * len(esets))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _, s_, *_ in esets[1:]:
+        s_.wait_event(a)
+    for i in range(k2):
+        e2e_step(i)
+    for _, s_, *_ in esets[1:]:
+        st.wait_stream(s_)
+    b.record(st)
+    torch.cuda.synchronize()
+    e2e_ms = a.elapsed_time(b) / k2
+    del esets
     n_re = spec.n_cells * len(spec.data_sym) * spec.n_sc
     return {"iq_width": iq_width, "stream_mb": c.numel() / 1e6,
             "decompress_us": dec_ms * 1e3, "decompress_gbs": gbs,

@@ -338,6 +338,40 @@ def test_fp64_refactor_of_ill_conditioned_res(dev):
     assert e64 <= bound and e64 < e32 / 10
 
 
+def test_host_buffer_entry_point_on_concurrent_streams(dev):
+    """phy_slot_run_host (pinned host inputs in, host LLRs and flags out) equals phy_slot_run on
+    device buffers, bit for bit, also when three calls on three streams with their own device
+    buffers overlap, as the benchmark's end-to-end steps do."""
+    import torch
+    from paper_2510_07843_gb300 import phy
+    spec = S.spec_massive_mimo(n_cells=2, n_prb=8)
+    sl = S.make_slot(spec, 3300, keep_h=False)
+    cfg = phy.SlotConfig.from_spec(spec, precision="fp16")
+    ref = phy.SlotBuffers(cfg, device=dev)
+    ref.Y.copy_(torch.from_numpy(sl.Y))
+    ref.pilots.copy_(torch.from_numpy(sl.pilots))
+    ref.sigma2.copy_(torch.from_numpy(sl.sigma2))
+    phy.slot_run(cfg, ref.Y, ref.pilots, ref.sigma2, ref.x_hat, ref.sinr, ref.llr, ref.flags,
+                 ref.workspace)
+    torch.cuda.synchronize()
+    Yh = torch.from_numpy(sl.Y).pin_memory()
+    Ph = torch.from_numpy(sl.pilots).pin_memory()
+    sh = torch.from_numpy(sl.sigma2).pin_memory()
+    sets = []
+    for i in range(3):
+        b = phy.SlotBuffers(cfg, device=dev)
+        lh = torch.full(ref.llr.shape, float("nan"), dtype=ref.llr.dtype).pin_memory()
+        fh = torch.full(ref.flags.shape, 255, dtype=torch.uint8).pin_memory()
+        sets.append((b, torch.cuda.Stream(device=dev), lh, fh))
+    for rep in range(2):
+        for b, st, lh, fh in sets:
+            phy.slot_run_host(cfg, Yh, Ph, sh, lh, fh, b.Y, b.pilots, b.sigma2, b.x_hat, b.sinr,
+                              b.llr, b.flags, b.workspace, stream=st)
+    torch.cuda.synchronize()
+    for b, st, lh, fh in sets:
+        assert torch.equal(lh, ref.llr.cpu()) and torch.equal(fh, ref.flags.cpu())
+
+
 def test_llr_binary16_output_is_the_rounded_fp32_output(dev):
     """cfg.llr_format = f16: every LLR is the FP32 value rounded to nearest binary16, saturating
     at +-65504; through the full receiver and through the stand-alone demapper."""
