@@ -289,8 +289,9 @@ phy_status phy_slot_run_noalloc(const phy_slot_cfg* cfg, const phy_c32* Y, const
  *    finished on the device. PHY_ERR_NO_MEMORY if the workspace is too small.
  *  - phy_batch_launch(): enqueues on `stream` a gate kernel that polls table_host's doorbell at
  *    most poll_limit times, about 1 us apart (poll_limit < 0: a million, about a second), copies
- *    a newly posted table into table_dev and then the stage kernels (LS estimation; per layer
- *    class the Gram/matched-filter and solve kernels, persistent over the table's items). Its
+ *    a newly posted table into table_dev and then the stage kernels (LS estimation; the noise
+ *    estimate of the jobs that track it; per layer class, on forked streams joined back into
+ *    `stream`, the Gram/matched-filter and solve kernels, persistent over the table's items). Its
  *    arguments do not change between batches, so it may be captured once in a CUDA graph and
  *    replayed per batch; a launch may also be enqueued before the batch is posted (the gate
  *    waits for it). If no new table arrives within the limit, the stages run on an empty table
@@ -308,6 +309,14 @@ typedef struct {
   float* sinr;
   float* llr;
   uint8_t* flags;
+  /* Noise level tracked on the device across slots (optional): with noise_state non-NULL the
+   * job ignores sigma2 and runs as phy_slot_run_track() with (noise_mode, noise_alpha) on that
+   * state (n_cells floats, device, kept by the caller between slots): the batch estimates each
+   * cell's noise variance from this slot's DMRS, blends it into the state and detects with the
+   * updated state. Tracking jobs of one batch must not share state (PHY_ERR_INVALID_ARG). */
+  float* noise_state;
+  float noise_alpha;   /* 0 < alpha <= 1 when noise_state is set */
+  int32_t noise_mode;  /* phy_noise_mode */
 } phy_job;
 
 size_t phy_batch_table_bytes(void);

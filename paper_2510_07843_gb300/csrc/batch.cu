@@ -27,7 +27,8 @@ constexpr size_t kAlign = 256;
 size_t up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
 size_t job_workspace(const Geo& g) {
-  return up(batch_anchor_bytes(g)) + up(batch_ygg_bytes(g)) + up(batch_bvec_bytes(g)) + kAlign;
+  return up(batch_anchor_bytes(g)) + up(batch_ygg_bytes(g)) + up(batch_bvec_bytes(g)) +
+         up((size_t)g.n_cells * noise_blocks(g) * sizeof(float4)) + kAlign;
 }
 
 __device__ __forceinline__ uint32_t ld_acquire_sys(const uint32_t* p) {
@@ -129,7 +130,22 @@ extern "C" phy_status phy_batch_post(const phy_job* jobs, int32_t n_jobs, void* 
     if (tc && (g.n_dmrs != 2 || !phy::seg_prep_tc_supported(g) || !phy::batch_solve_fits(g)))
       return PHY_ERR_UNSUPPORTED;
     if (!tc && !direct && !phy::batch_geometry_fits(g)) return PHY_ERR_UNSUPPORTED;
-    if (!jb.Y || !jb.pilots || !jb.sigma2 || !jb.flags) return PHY_ERR_INVALID_ARG;
+    const bool track = jb.noise_state != nullptr;
+    if (!jb.Y || !jb.pilots || (!jb.sigma2 && !track) || !jb.flags) return PHY_ERR_INVALID_ARG;
+    if (track) {
+      if (!(jb.noise_alpha > 0.f && jb.noise_alpha <= 1.f) || jb.noise_mode < PHY_NOISE_FREQ ||
+          jb.noise_mode > PHY_NOISE_MIN || (jb.noise_mode == PHY_NOISE_TIME && g.n_dmrs != 2))
+        return PHY_ERR_INVALID_ARG;
+      // tracking jobs of one batch update their states concurrently: no shared cells
+      const uintptr_t a0 = reinterpret_cast<uintptr_t>(jb.noise_state);
+      const uintptr_t a1 = a0 + (uintptr_t)g.n_cells * sizeof(float);
+      for (int k = 0; k < i; ++k) {
+        if (!jobs[k].noise_state) continue;
+        const uintptr_t b0 = reinterpret_cast<uintptr_t>(jobs[k].noise_state);
+        const uintptr_t b1 = b0 + (uintptr_t)t->job[k].g.n_cells * sizeof(float);
+        if (a0 < b1 && b0 < a1) return PHY_ERR_INVALID_ARG;
+      }
+    }
     if (reinterpret_cast<uintptr_t>(jb.Y) % 16) return PHY_ERR_INVALID_ARG;
     const size_t need = phy::job_workspace(g);
     if (!workspace || used + need > workspace_bytes) return PHY_ERR_NO_MEMORY;
@@ -137,7 +153,10 @@ extern "C" phy_status phy_batch_post(const phy_job* jobs, int32_t n_jobs, void* 
     J.g = g;
     J.Y = jb.Y;
     J.pilots = jb.pilots;
-    J.sigma2 = jb.sigma2;
+    J.sigma2 = track ? jb.noise_state : jb.sigma2;  // detection reads the updated state
+    J.noise_alpha = track ? jb.noise_alpha : 0.f;
+    J.noise_mode = jb.noise_mode;
+    J.noise_blocks = phy::noise_blocks(g);
     J.x_hat = jb.x_hat;
     J.sinr = jb.sinr;
     J.llr = jb.llr;
@@ -149,6 +168,8 @@ extern "C" phy_status phy_batch_post(const phy_job* jobs, int32_t n_jobs, void* 
     p += phy::up(phy::batch_ygg_bytes(g));
     J.bvec = reinterpret_cast<phy::cf*>(p);
     p += phy::up(phy::batch_bvec_bytes(g));
+    J.noise_part = reinterpret_cast<float4*>(p);
+    p += phy::up((size_t)g.n_cells * J.noise_blocks * sizeof(float4));
     J.err = reinterpret_cast<unsigned*>(p);
     used += need;
     J.wmax = phy::batch_wmax(g);
@@ -164,10 +185,14 @@ extern "C" phy_status phy_batch_post(const phy_job* jobs, int32_t n_jobs, void* 
     if (gp * g.n_layers * 2 * g.L > phy::kChestBatchPilots) return PHY_ERR_UNSUPPORTED;
     const int items[phy::kBatchStages] = {(g.G + gp - 1) / gp * g.n_dmrs * g.n_cells,
                                           !tc && !direct ? seg_items : 0, tc ? seg_items : 0,
-                                          direct ? 0 : res, direct ? res : 0};
+                                          direct ? 0 : res, direct ? res : 0,
+                                          track ? J.noise_blocks * g.n_cells : 0,
+                                          track ? g.n_cells : 0};
     for (int stg = 0; stg < phy::kBatchStages; ++stg) {
       if (stg != phy::kBatchChest && items[stg] == 0) continue;
-      const int c = stg == phy::kBatchChest ? 0 : cls;
+      const bool per_job = stg == phy::kBatchChest || stg == phy::kBatchNoisePart ||
+                           stg == phy::kBatchNoiseFinal;  // one class for every job
+      const int c = per_job ? 0 : cls;
       int& nj = t->n_class_jobs[stg][c];
       t->job_of[stg][c][nj] = (unsigned char)i;
       t->start[stg][c][nj] = t->n_items[stg][c];
@@ -202,7 +227,8 @@ extern "C" phy_status phy_batch_launch(void* table_host, void* table_dev, int64_
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return PHY_ERR_CUDA;
   const BatchTable* t = static_cast<const BatchTable*>(table_dev);
-  if ((e = phy::launch_chest_batch(t, st)) != cudaSuccess)
+  if ((e = phy::launch_chest_batch(t, st)) != cudaSuccess ||
+      (e = phy::launch_noise_batch(t, st)) != cudaSuccess)
     return PHY_ERR_CUDA;
   if ((e = phy::launch_batch_stages(t, st)) != cudaSuccess) return PHY_ERR_CUDA;
   return PHY_OK;

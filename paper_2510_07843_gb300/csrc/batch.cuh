@@ -18,14 +18,18 @@ namespace phy {
 constexpr int kBatchMaxJobs = 64;
 constexpr int kBatchClasses = 4;  // layer classes 2, 4, 8, 16 (the kernels' NL)
 // Stages: LS estimation (every job, class 0), FP32 segment kernel, tensor-core segment kernel
-// (FP16 products), per-RE solve (after either segment kernel), direct form (FP32, <= 4 layers).
+// (FP16 products), per-RE solve (after either segment kernel), direct form (FP32, <= 4 layers),
+// and for jobs that track their noise level on the device the estimate's partial sums and its
+// per-cell reduction into the state (class 0, between LS estimation and detection).
 enum BatchStage : int {
   kBatchChest = 0,
   kBatchSeg = 1,
   kBatchSegTc = 2,
   kBatchSolve = 3,
   kBatchDirect = 4,
-  kBatchStages = 5
+  kBatchNoisePart = 5,
+  kBatchNoiseFinal = 6,
+  kBatchStages = 7
 };
 
 __host__ __device__ constexpr int batch_class(int nl_class) {
@@ -58,6 +62,9 @@ struct BatchJob {
   float4* ygg;
   cf* bvec;
   unsigned* err;
+  float4* noise_part;  // the noise estimate's partial sums (jobs that track their noise level)
+  float noise_alpha;   // > 0: sigma2 is the job's per-cell state, updated before detection
+  int noise_mode, noise_blocks;
   int wmax, max_segs;
 };
 

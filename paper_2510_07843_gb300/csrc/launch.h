@@ -137,6 +137,9 @@ int batch_wmax(const Geo& g);
 int batch_max_segs(const Geo& g);
 bool batch_geometry_fits(const Geo& g);
 cudaError_t launch_chest_batch(const BatchTable* t, cudaStream_t st);
+// The noise estimate of the jobs that track their noise level (partial sums, then per cell).
+cudaError_t launch_noise_batch(const BatchTable* t, cudaStream_t st);
+int noise_blocks(const Geo& g);  // partial-sum blocks per cell
 cudaError_t launch_batch_stages(const BatchTable* t, cudaStream_t st);
 // TMA tensor maps of the tensor-core segment kernel for a geometry's grid and anchors.
 bool encode_tc_maps(const Geo& g, const phy_c32* anchors, const phy_c32* Y, CUtensorMap* tmY,

@@ -22,6 +22,7 @@
 // result does not depend on scheduling.
 #include <math.h>
 
+#include "batch.cuh"
 #include "launch.h"
 
 namespace phy {
@@ -52,21 +53,22 @@ __device__ __forceinline__ int div_small(int a, int b, float inv_b) {
   return q;
 }
 
-__global__ void __launch_bounds__(kNoiseThreads)
-    noise_partial_kernel(Geo g, const phy_c32* __restrict__ anchors,
-                         const phy_c32* __restrict__ pilots, float4* __restrict__ part) {
-  const int cell = blockIdx.y;
+// Partial sums of block `blk` (of n_blk) of one cell's anchor entries; every thread of the CTA
+// calls it. red: CTA scratch of kNoiseThreads / 32 float4.
+__device__ __forceinline__ void noise_partial_body(const Geo& g, int cell, int blk, int n_blk,
+                                                   const phy_c32* __restrict__ anchors,
+                                                   const phy_c32* __restrict__ pilots,
+                                                   float4* __restrict__ part,
+                                                   float4* __restrict__ red) {
   const int nl = g.n_layers, nr = g.n_rx;
   const int per_grp = nl * nr;                  // entries between neighbouring groups
   const int per_d = g.G * per_grp;              // entries of one DMRS symbol
   const phy_c32* A0 = anchors + (size_t)cell * g.n_dmrs * per_d;
   const phy_c32* A1 = A0 + (g.n_dmrs == 2 ? per_d : 0);
-  const int i0 = blockIdx.x * kNoiseEntries;
+  const int i0 = blk * kNoiseEntries;
   const int i1 = min(i0 + kNoiseEntries, per_d);
   const float inv_grp = 1.f / (float)per_grp;
   float ef = 0.f, et = 0.f, gf = 0.f, gt = 0.f;
-  // the final kernel may launch now and wait for this grid's completion (programmatic launch)
-  asm volatile("griddepcontrol.launch_dependents;");
 
   // ---- residual energies, entry i = (group * nl + layer) * nr + antenna
 #pragma unroll
@@ -124,7 +126,6 @@ __global__ void __launch_bounds__(kNoiseThreads)
   }
 
   // ---- CTA sums in a fixed order
-  __shared__ float4 red[kNoiseThreads / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     ef += __shfl_xor_sync(0xffffffffu, ef, o);
@@ -143,17 +144,25 @@ __global__ void __launch_bounds__(kNoiseThreads)
       s.z += red[w].z;
       s.w += red[w].w;
     }
-    part[(size_t)cell * gridDim.x + blockIdx.x] = s;
+    part[(size_t)cell * n_blk + blk] = s;
   }
 }
 
 __global__ void __launch_bounds__(kNoiseThreads)
-    noise_final_kernel(Geo g, int mode, float alpha, int n_part, const float4* __restrict__ part,
-                       float* __restrict__ sigma2_out) {
-  const int cell = blockIdx.x;
-  __shared__ double red[4][kNoiseThreads];
-  // launched programmatically behind the partial kernel: wait until its sums are complete
-  asm volatile("griddepcontrol.wait;" ::: "memory");
+    noise_partial_kernel(Geo g, const phy_c32* __restrict__ anchors,
+                         const phy_c32* __restrict__ pilots, float4* __restrict__ part) {
+  __shared__ float4 red[kNoiseThreads / 32];
+  // the final kernel may launch now and wait for this grid's completion (programmatic launch)
+  asm volatile("griddepcontrol.launch_dependents;");
+  noise_partial_body(g, blockIdx.y, blockIdx.x, gridDim.x, anchors, pilots, part, red);
+}
+
+// One cell's estimate from its n_part partial sums (and, with alpha < 1, its blend into the
+// cell's state); every thread of the CTA calls it. red: CTA scratch of 4 x kNoiseThreads doubles.
+__device__ __forceinline__ void noise_final_body(const Geo& g, int cell, int mode, float alpha,
+                                                 int n_part, const float4* __restrict__ part,
+                                                 float* __restrict__ sigma2_out,
+                                                 double (*red)[kNoiseThreads]) {
   double s[4] = {0.0, 0.0, 0.0, 0.0};
   for (int i = threadIdx.x; i < n_part; i += kNoiseThreads) {
     const float4 v = part[(size_t)cell * n_part + i];
@@ -189,12 +198,74 @@ __global__ void __launch_bounds__(kNoiseThreads)
   }
 }
 
+__global__ void __launch_bounds__(kNoiseThreads)
+    noise_final_kernel(Geo g, int mode, float alpha, int n_part, const float4* __restrict__ part,
+                       float* __restrict__ sigma2_out) {
+  __shared__ double red[4][kNoiseThreads];
+  // launched programmatically behind the partial kernel: wait until its sums are complete
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  noise_final_body(g, blockIdx.x, mode, alpha, n_part, part, sigma2_out, red);
+}
+
 int n_parts(const Geo& g) {
   const int per_d = g.G * g.n_layers * g.n_rx;
   return (per_d + kNoiseEntries - 1) / kNoiseEntries;
 }
 
+// Batched forms: CTAs stride over the (block, cell) items, then the cells, of the jobs in the
+// table that track their noise level; the job's sigma2 pointer is its state.
+__global__ void __launch_bounds__(kNoiseThreads)
+    noise_partial_batch_kernel(const BatchTable* __restrict__ t) {
+  __shared__ Geo sg;
+  __shared__ BatchIndex ix;
+  __shared__ float4 red[kNoiseThreads / 32];
+  const int n = t->n_items[kBatchNoisePart][0];
+  if ((int)blockIdx.x >= n) return;
+  batch_index_load(ix, t, kBatchNoisePart, 0);
+  __syncthreads();
+  for (int w = blockIdx.x; w < n; w += gridDim.x) {
+    int local;
+    const BatchJob& J = t->job[batch_find(ix, w, local)];
+    batch_load_geo(sg, J.g);
+    __syncthreads();
+    noise_partial_body(sg, local / J.noise_blocks, local % J.noise_blocks, J.noise_blocks,
+                       J.anchors, J.pilots, J.noise_part, red);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kNoiseThreads)
+    noise_final_batch_kernel(const BatchTable* __restrict__ t) {
+  __shared__ Geo sg;
+  __shared__ BatchIndex ix;
+  __shared__ double red[4][kNoiseThreads];
+  const int n = t->n_items[kBatchNoiseFinal][0];
+  if ((int)blockIdx.x >= n) return;
+  batch_index_load(ix, t, kBatchNoiseFinal, 0);
+  __syncthreads();
+  for (int w = blockIdx.x; w < n; w += gridDim.x) {
+    int local;
+    const BatchJob& J = t->job[batch_find(ix, w, local)];
+    batch_load_geo(sg, J.g);
+    __syncthreads();
+    noise_final_body(sg, local, J.noise_mode, J.noise_alpha, J.noise_blocks, J.noise_part,
+                     const_cast<float*>(J.sigma2), red);
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+int noise_blocks(const Geo& g) { return n_parts(g); }
+
+cudaError_t launch_noise_batch(const BatchTable* t, cudaStream_t st) {
+  const int grid = 2 * device_sm_count();
+  noise_partial_batch_kernel<<<grid, kNoiseThreads, 0, st>>>(t);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  noise_final_batch_kernel<<<grid, kNoiseThreads, 0, st>>>(t);
+  return cudaGetLastError();
+}
 
 size_t noise_scratch_bytes(const Geo& g) {
   return (size_t)g.n_cells * n_parts(g) * sizeof(float4);

@@ -32,10 +32,13 @@ class CSlotCfg(ctypes.Structure):
 
 
 class CJob(ctypes.Structure):
-    """phy_job: one job of a batched call (configuration and device buffers)."""
+    """phy_job: one job of a batched call (configuration, device buffers and the optional
+    device-side noise tracking)."""
     _fields_ = [("cfg", CSlotCfg), ("Y", ctypes.c_void_p), ("pilots", ctypes.c_void_p),
                 ("sigma2", ctypes.c_void_p), ("x_hat", ctypes.c_void_p),
-                ("sinr", ctypes.c_void_p), ("llr", ctypes.c_void_p), ("flags", ctypes.c_void_p)]
+                ("sinr", ctypes.c_void_p), ("llr", ctypes.c_void_p), ("flags", ctypes.c_void_p),
+                ("noise_state", ctypes.c_void_p), ("noise_alpha", ctypes.c_float),
+                ("noise_mode", ctypes.c_int32)]
 
 
 # Every entry point declared in include/phy.h, with its ctypes signature.
@@ -544,10 +547,15 @@ BATCH_MAX_JOBS = 64
 
 
 def _jobs_array(jobs):
-    """jobs: sequence of (SlotConfig, Y, pilots, sigma2, x_hat, sinr, llr, flags) tuples."""
+    """jobs: sequence of (SlotConfig, Y, pilots, sigma2, x_hat, sinr, llr, flags) tuples, each
+    optionally followed by (noise_state, noise_alpha, noise_mode) for device-side noise
+    tracking (mode a NOISE_MODE key or code)."""
     arr = (CJob * len(jobs))()
-    for i, (cfg, Y, P, s2, x, sn, l, f) in enumerate(jobs):
-        arr[i] = CJob(cfg.c(), _ptr(Y), _ptr(P), _ptr(s2), _ptr(x), _ptr(sn), _ptr(l), _ptr(f))
+    for i, j in enumerate(jobs):
+        cfg, Y, P, s2, x, sn, l, f = j[:8]
+        st, alpha, mode = (j[8], j[9], j[10]) if len(j) >= 11 else (None, 0.0, "min")
+        arr[i] = CJob(cfg.c(), _ptr(Y), _ptr(P), _ptr(s2), _ptr(x), _ptr(sn), _ptr(l), _ptr(f),
+                      _ptr(st), float(alpha), NOISE_MODE.get(mode, mode))
     return arr
 
 
@@ -555,7 +563,8 @@ def _jobs_array(jobs):
 # the configuration block, then the seven buffer addresses as 64-bit words.
 JOB_BYTES = ctypes.sizeof(CJob)
 JOB_ADDR_OFFSET = CJob.Y.offset
-assert JOB_BYTES == JOB_ADDR_OFFSET + 7 * 8 and JOB_ADDR_OFFSET == ctypes.sizeof(CSlotCfg)
+assert JOB_ADDR_OFFSET == ctypes.sizeof(CSlotCfg) and CJob.noise_state.offset == JOB_ADDR_OFFSET + 56
+assert JOB_BYTES == JOB_ADDR_OFFSET + 8 * 8 + 8
 
 
 def batch_post_records(records, n_jobs: int, table_host: int, workspace: int,

@@ -1,16 +1,23 @@
 """Serving slot loop: continuous batching of uplink receiver jobs on one GPU.
 
-A job is one cell's slot (received grid, DMRS pilots, noise variance) with its receiver
-configuration (a SlotConfig with n_cells = 1). Cells are independent, so jobs with equal
-configurations batch by placing their cells side by side in one phy_slot_run call. The server
-keeps, per (configuration, batch size), persistent device buffers and a CUDA graph of the
-whole receiver captured on them; a batch copies its jobs' inputs into the buffers, replays the
-graph and copies each job's LLRs and flags out; when a batch's inputs already sit side by side
-in device memory (consecutive cells of one resident input), a receiver captured on those
-addresses reads them in place instead. Batch sizes are powers of two up to a limit
-that the configuration's device memory (buffers plus workspace) sets against a budget, so
-admission is by device memory. Latency is measured per job from its arrival to the host seeing
-its batch complete, against the slot deadline.
+Two servers, both measuring latency per job from its arrival to the host seeing its batch
+complete, against the slot deadline.
+
+SlotServer batches jobs of equal configuration: a job is one cell's slot (received grid, DMRS
+pilots, noise variance) with its receiver configuration (a SlotConfig with n_cells = 1). Cells
+are independent, so jobs with equal configurations batch by placing their cells side by side in
+one phy_slot_run call. The server keeps, per (configuration, batch size), persistent device
+buffers and a CUDA graph of the whole receiver captured on them; a batch copies its jobs' inputs
+into the buffers, replays the graph and copies each job's LLRs and flags out; when a batch's
+inputs already sit side by side in device memory (consecutive cells of one resident input), a
+receiver captured on those addresses reads them in place instead. Batch sizes are powers of two
+up to a limit that the configuration's device memory (buffers plus workspace) sets against a
+budget, so admission is by device memory.
+
+BatchServer batches jobs of any shape together through the batched receiver (phy_batch_post /
+phy_batch_launch): whatever has arrived goes into the next free lane's batch, up to 64 jobs and
+the lane arena's bytes (arenas sized from the device's free memory), served by one replay of the
+lane's captured graph.
 
 Everything on the device runs in libphy.so; this module only schedules and marshals.
 """
@@ -342,13 +349,20 @@ class MixedJob:
     sigma2: object           # device tensor [1] float32
     arrival: float = 0.0
     job_id: int = 0
+    # the cell's noise level tracked on the device (phy_job.noise_state): a device tensor of
+    # n_cells floats kept by the caller from slot to slot; sigma2 is then not read
+    noise_state: object = None
+    noise_alpha: float = 0.0
+    noise_mode: str = "min"
     done: float = field(default=float("nan"))
     _out: object = field(default=None, repr=False)    # (arena, LLR offset, flag offset)
     _views: object = field(default=None, repr=False)  # (llr, flags) once built or kept
 
     def __post_init__(self):
         # input addresses, taken once (the inputs stay where they are until the job is done)
-        self._addr = (phy._ptr(self.Y), phy._ptr(self.pilots), phy._ptr(self.sigma2))
+        self._addr = (phy._ptr(self.Y), phy._ptr(self.pilots), phy._ptr(self.sigma2),
+                      phy._ptr(self.noise_state), float(self.noise_alpha),
+                      phy.NOISE_MODE.get(self.noise_mode, self.noise_mode))
 
     @property
     def latency(self) -> float:
@@ -450,24 +464,29 @@ class _Lane:
             raise RuntimeError(f"phy_batch_post failed: {phy.STATUS.get(st, st)}")
 
 
-_ADDR = struct.Struct("<7Q")
+# the phy_job fields after the configuration: eight addresses, noise_alpha, noise_mode
+_ADDR = struct.Struct("<8Qfi")
 
 
 def write_records(rec, lays: Sequence[_JobLayout], addrs, base: int):
     """Writes the phy_job records of a batch into `rec` (a writable byte buffer) for an arena at
     device address `base`: the intermediates first (phy_batch_post lays them out from `base`),
-    then per job its LLRs and flags. addrs: per job the (Y, pilots, sigma2) addresses. Returns
-    the intermediates' bytes, per job the (LLR, flag) arena offsets, and the end offset."""
+    then per job its LLRs and flags. addrs: per job the (Y, pilots, sigma2) addresses, optionally
+    followed by (noise_state, noise_alpha, noise_mode code). Returns the intermediates' bytes,
+    per job the (LLR, flag) arena offsets, and the end offset."""
     ws = _up(sum(l.ws for l in lays))
     off, jb, ao, pack = ws, phy.JOB_BYTES, phy.JOB_ADDR_OFFSET, _ADDR.pack_into
     outs = []
-    for i, (l, (y, p, s2)) in enumerate(zip(lays, addrs)):
+    for i, (l, a) in enumerate(zip(lays, addrs)):
+        y, p, s2 = a[:3]
+        st, alpha, mode = a[3:6] if len(a) >= 6 else (None, 0.0, 2)
         lo = off
         fo = _up(lo + l.llr)
         off = _up(fo + l.flags)
         o = i * jb
         rec[o:o + ao] = l.record
-        pack(rec, o + ao, y or 0, p or 0, s2 or 0, 0, 0, base + lo, base + fo)
+        pack(rec, o + ao, y or 0, p or 0, s2 or 0, 0, 0, base + lo, base + fo, st or 0,
+             alpha, mode)
         outs.append((lo, fo))
     return ws, outs, off
 
@@ -512,17 +531,28 @@ class BatchServer:
         for ln in self.lanes:
             ln.capture([warm], self._layout)
 
-    def _take(self, waiting: "collections.deque") -> List["MixedJob"]:
-        """The longest arrival-order prefix of the waiting jobs that fits one lane."""
-        batch, used = [], 0
+    def _take(self, waiting: "collections.deque", busy=frozenset()) -> List["MixedJob"]:
+        """The arrival-order jobs that fit one lane: up to max_jobs and the arena's bytes. A job
+        that tracks its noise level waits (keeping its place) while a batch in flight, or an
+        earlier job of this batch, updates the same state: one cell's slots then update its
+        state in arrival order."""
+        batch, used, states, skipped = [], 0, set(busy), []
         while waiting and len(batch) < self.max_jobs:
-            b = self.job_bytes(waiting[0].cfg)
+            j = waiting[0]
+            st = j._addr[3]
+            if st is not None and st in states:
+                skipped.append(waiting.popleft())
+                continue
+            b = self.job_bytes(j.cfg)
             if b > self.arena_bytes:
-                raise ValueError(f"job {waiting[0].job_id} needs {b} bytes, above the arena")
+                raise ValueError(f"job {j.job_id} needs {b} bytes, above the arena")
             if used + b + _ALIGN > self.arena_bytes:
                 break
             used += b
+            if st is not None:
+                states.add(st)
             batch.append(waiting.popleft())
+        waiting.extendleft(reversed(skipped))
         return batch
 
     def run(self, jobs: Sequence["MixedJob"], realtime: bool = True,
@@ -573,9 +603,15 @@ class BatchServer:
                 continue
             if not free:
                 retire(True)
+            busy = frozenset(j._addr[3] for f in inflight for j in f[3] if j._addr[3] is not None)
+            batch = self._take(waiting, busy)
+            if not batch:  # every waiting job waits for a state in flight
+                if not inflight:
+                    raise ValueError(f"job {waiting[0].job_id} does not fit a lane's arena")
+                retire(True)
+                continue
             li = free.pop(0)
             ln = self.lanes[li]
-            batch = self._take(waiting)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             h0 = self.clock()
             ln.post(batch, self._layout)

@@ -76,8 +76,9 @@ def test_post_writes_the_table_and_rings_the_doorbell(lib):
     assert _post([_job(c) for c in MIX], t) == 0
     w = _words(t)
     assert w[0] == 1 and w[2] == 0 and w[3] == len(MIX)  # seq bumped, status pending, n_jobs
-    n_items = w[4:24].reshape(5, 4)  # stages: LS, FP32 segment, tensor-core segment, solve, direct
-    want = np.zeros((5, 4), dtype=np.int64)
+    # stages: LS, FP32 segment, tensor-core segment, solve, direct, noise partial sums, noise
+    n_items = w[4:32].reshape(7, 4)
+    want = np.zeros((7, 4), dtype=np.int64)
     for c in MIX:
         (ls, seg, solve), cls = _items(c)
         want[0, 0] += ls
@@ -126,3 +127,48 @@ def test_post_rejects_bad_counts_and_pointers(lib):
     assert _post([_job(MIX[1], base=FAKE + 8)], t) == 1  # grid not 16-byte aligned
     assert lib.phy_batch_status(None) == 1
     assert lib.phy_batch_status(ctypes.c_void_p(t.ctypes.data)) == 1  # nothing ran
+
+
+def _noise_blocks(cfg):
+    """Partial-sum blocks per cell of the noise estimate: 1024 anchor entries each."""
+    n_sc = 12 * cfg.n_prb
+    L = 1
+    while L < (cfg.n_layers + 1) // 2:
+        L *= 2
+    G = -(-(n_sc // 2) // L)
+    return -(-(G * cfg.n_layers * cfg.n_rx) // 1024)
+
+
+def _job_track(cfg, state, alpha=0.5, mode="min"):
+    return (cfg, FAKE, FAKE, None, None, None, FAKE, FAKE, state, alpha, mode)
+
+
+def test_noise_tracking_jobs_add_the_noise_stages(lib):
+    """Jobs with a device noise state add (partial-sum block, cell) and cell items to the two
+    noise stages; other jobs add none, and a tracking job needs no sigma2."""
+    t = _table()
+    jobs = [_job(MIX[1]), _job_track(MIX[0], FAKE + 4096), _job_track(MIX[3], FAKE + 8192,
+                                                                    mode="freq")]
+    assert _post(jobs, t) == 0
+    n_items = _words(t)[4:32].reshape(7, 4)
+    assert n_items[5, 0] == sum(_noise_blocks(c) * c.n_cells for c in (MIX[0], MIX[3]))
+    assert n_items[6, 0] == MIX[0].n_cells + MIX[3].n_cells
+    assert n_items[5:, 1:].sum() == 0
+
+
+@pytest.mark.parametrize("alpha,mode,code", [(0.0, "min", 1), (1.5, "min", 1), (0.5, 3, 1),
+                                             (0.5, "time", 1), (1.0, "freq", 0)])
+def test_noise_tracking_fields_are_validated(lib, alpha, mode, code):
+    one_dmrs = phy.SlotConfig(n_cells=1, n_prb=20, n_rx=16, n_layers=4, qm=4, dmrs_sym=(2,))
+    t = _table()
+    assert _post([_job_track(one_dmrs, FAKE, alpha, mode)], t) == code
+
+
+def test_tracking_jobs_may_not_share_state(lib):
+    two = phy.SlotConfig(n_cells=2, n_prb=20, n_rx=16, n_layers=4, qm=4, dmrs_sym=(2, 11))
+    one = phy.SlotConfig(n_cells=1, n_prb=20, n_rx=16, n_layers=4, qm=4, dmrs_sym=(2, 11))
+    t = _table()
+    # the first job's state covers FAKE and FAKE + 4: a second state at FAKE + 4 overlaps it
+    assert _post([_job_track(two, FAKE), _job_track(one, FAKE + 4)], t) == 1
+    assert _words(t)[0] == 0
+    assert _post([_job_track(two, FAKE), _job_track(one, FAKE + 8)], t) == 0

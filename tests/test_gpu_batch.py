@@ -199,3 +199,89 @@ def test_batch_server_mixed_stream_equals_each_job_alone(dev):
     for j in done:
         r = ref[j.job_id % len(pool)]
         assert torch.equal(j.llr, r.llr) and torch.equal(j.flags, r.flags), j.job_id
+
+
+# (index into MIX, mode, alpha, prior state or None for a state set to 3x the true level) of the
+# jobs that track their noise level on the device; a prior of 0 is an unset state
+TRACK = [(0, "min", 0.5, 0.0), (2, "freq", 0.25, None), (3, "freq", 1.0, 0.0),
+         (8, "time", 0.5, None), (9, "min", 0.75, 0.0)]
+
+
+def test_noise_tracking_in_the_batch_equals_slot_run_track(dev):
+    """Jobs with a device noise state (phy_job.noise_state) next to plain ones: over two batches
+    each tracking job's outputs and state equal phy_slot_run_track on the job alone with the
+    same state, bit for bit, and the plain jobs still equal phy_slot_run."""
+    import torch
+    from paper_2510_07843_gb300 import phy
+    jobs = _prepare(dev, MIX)
+    host, devt = _tables(dev)
+    track = {i: (mode, alpha) for i, mode, alpha, _ in TRACK}
+    states = {}
+    for i, _, _, prior in TRACK:
+        s2 = jobs[i][1][2]
+        init = torch.full_like(s2, 0.0) if prior == 0.0 else 3.0 * s2
+        states[i] = (init.clone(), init.clone())  # (batched, alone)
+    for rnd in range(2):
+        tuples = []
+        for i, (cfg, inp, o) in enumerate(jobs):
+            t = (cfg, *inp, o[0].x_hat, o[0].sinr, o[0].llr, o[0].flags)
+            if i in track:
+                t = t + (states[i][0], track[i][1], track[i][0])
+            tuples.append(t)
+        ws = torch.empty(phy.batch_workspace_size(tuples), dtype=torch.uint8, device=dev)
+        for _, _, o in jobs:
+            o[0].flags.fill_(0xEE)
+        phy.batch_post(tuples, host, ws)
+        phy.batch_launch(host, devt)
+        for i, (cfg, (Y, P, s2), o) in enumerate(jobs):
+            b = o[1]
+            if i in track:
+                phy.slot_run_track(cfg, track[i][0], track[i][1], Y, P, states[i][1], b.x_hat,
+                                   b.sinr, b.llr, b.flags, b.workspace)
+            else:
+                phy.slot_run(cfg, Y, P, s2, b.x_hat, b.sinr, b.llr, b.flags, b.workspace)
+        torch.cuda.synchronize()
+        assert phy.batch_status(host) == 0
+        _assert_same(jobs)
+        for i in track:
+            a, b = states[i]
+            assert torch.equal(a, b), (rnd, i, a.tolist(), b.tolist())
+            assert torch.all(torch.isfinite(a)) and torch.all(a > 0)
+
+
+def test_batch_server_tracks_each_cells_noise_in_arrival_order(dev):
+    """Four cells, three slots each, every job tracking its cell's noise level: the server never
+    puts two slots of one cell in one batch or in two batches in flight, so each cell's state
+    follows its slots in arrival order; outputs and final states equal per-cell sequences of
+    phy_slot_run_track."""
+    import torch
+    from paper_2510_07843_gb300 import phy, serve
+    specs = [S.SlotSpec(n_prb=12, n_rx=16, n_layers=4, qm=4, dmrs_sym=(2, 11), snr_db=15.0),
+             S.SlotSpec(n_prb=8, n_rx=32, n_layers=8, qm=6, dmrs_sym=(2, 11), snr_db=22.0),
+             S.SlotSpec(n_prb=20, n_rx=4, n_layers=2, qm=2, dmrs_sym=(2, 11), snr_db=10.0),
+             S.SlotSpec(n_prb=6, n_rx=64, n_layers=16, qm=8, dmrs_sym=(2, 11), snr_db=28.0)]
+    slots = []  # (cell, cfg, inputs) in arrival order: slot r of every cell, then r + 1
+    for r in range(3):
+        for c, sp in enumerate(specs):
+            sl = S.make_slot(sp, 1200 + 10 * c + r, keep_h=False)
+            cfg = phy.SlotConfig.from_spec(sp, precision="fp16" if sp.n_layers > 4 else "fp32")
+            slots.append((c, cfg, [torch.from_numpy(a).to(dev) for a in (sl.Y, sl.pilots,
+                                                                         sl.sigma2)]))
+    state = [torch.zeros(1, device=dev) for _ in specs]
+    jobs = [serve.MixedJob(cfg, *inp, arrival=0.0, job_id=k, noise_state=state[c],
+                           noise_alpha=0.5, noise_mode="min")
+            for k, (c, cfg, inp) in enumerate(slots)]
+    srv = serve.BatchServer(device=dev, lanes=2, memory_fraction=0.05)
+    srv.prepare(serve.MixedJob(slots[0][1], *slots[0][2]))
+    done = srv.run(jobs, realtime=False, keep=True)
+    assert len(done) == len(jobs)
+    ref_state = [torch.zeros(1, device=dev) for _ in specs]
+    by_id = {j.job_id: j for j in done}
+    for k, (c, cfg, (Y, P, s2)) in enumerate(slots):
+        b = phy.SlotBuffers(cfg, device=dev, with_inputs=False)
+        phy.slot_run_track(cfg, "min", 0.5, Y, P, ref_state[c], b.x_hat, b.sinr, b.llr, b.flags,
+                           b.workspace)
+        torch.cuda.synchronize()
+        assert torch.equal(by_id[k].llr, b.llr) and torch.equal(by_id[k].flags, b.flags), k
+    for c in range(len(specs)):
+        assert torch.equal(state[c], ref_state[c]), (c, state[c].tolist(), ref_state[c].tolist())

@@ -226,13 +226,18 @@ def test_batch_records_match_the_ctypes_jobs():
     addrs = [(1 << 32) + 4096 * i for i in range(12)]
     base = 1 << 40
     rec = bytearray(12 * phy.JOB_BYTES)
-    ws, outs, end = serve.write_records(memoryview(rec), lays, [(a, a + 16, a + 32) for a in addrs],
+    # every third job tracks its noise level on the device (a state address, alpha, mode)
+    tracked = [(a + 48, 0.25, 1) if i % 3 == 0 else (None, 0.0, 2) for i, a in enumerate(addrs)]
+    ws, outs, end = serve.write_records(memoryview(rec), lays,
+                                        [(a, a + 16, a + 32) + tr for a, tr in zip(addrs, tracked)],
                                         base)
     assert sum(l.ws for l in lays) == phy.batch_workspace_size([(c,) + (None,) * 7 for c in cfgs])
     assert ws == serve._up(sum(l.ws for l in lays))
     spans = []
     for i, (c, a, (lo, fo)) in enumerate(zip(cfgs, addrs, outs)):
-        want = phy._jobs_array([(c, a, a + 16, a + 32, None, None, base + lo, base + fo)])
+        st, alpha, mode = tracked[i]
+        want = phy._jobs_array([(c, a, a + 16, a + 32, None, None, base + lo, base + fo, st,
+                                 alpha, mode)])
         assert bytes(rec[i * phy.JOB_BYTES:(i + 1) * phy.JOB_BYTES]) == bytes(want[0])
         assert lo % 256 == 0 and fo % 256 == 0 and lo >= ws
         spans += [(lo, lo + lays[i].llr), (fo, fo + lays[i].flags)]
