@@ -1003,8 +1003,11 @@ def serving_mixed_run(dev, slots: int = 100, n_cells=(32, 16), rate_hz: float = 
     (BatchServer over the batched receiver: FP16 tensor-core products for jobs of 5 or more
     layers, the direct FP32 form below that) for `slots` 0.5 ms slots in real
     time. Job inputs come from a pool of `pool_size` distinct seeded jobs resident on the device
-    (arrivals pick pool entries uniformly). Latency is per job, arrival to completion seen by
-    the host; throughput counts the REs of every served job over the run's span."""
+    (arrivals pick pool entries uniformly). Each cell keeps its noise level on the device
+    across its slots (phy_job.noise_state, alpha 0.5, the smaller of the two DMRS estimates), so
+    a cell's next slot waits for its previous one. Latency is per job, arrival to completion
+    seen by the host; throughput counts the REs of every served job over the run's span."""
+    import torch
     from paper_2510_07843_gb300 import serve
     rng = np.random.default_rng(seed)
     pool = serving_pool(dev, pool_size, seed)
@@ -1018,8 +1021,10 @@ def serving_mixed_run(dev, slots: int = 100, n_cells=(32, 16), rate_hz: float = 
     for cells in n_cells:
         arrivals = S.serving_arrivals(cells, rate_hz, duration, seed + cells)
         pick = rng.integers(0, pool_size, len(arrivals))
-        jobs = [serve.MixedJob(*pool[p], arrival=t, job_id=k)
-                for k, ((t, _), p) in enumerate(zip(arrivals, pick))]
+        state = torch.zeros(cells, dtype=torch.float32, device=dev)  # unset: first slot sets it
+        jobs = [serve.MixedJob(*pool[p], arrival=t, job_id=k, noise_state=state[c:c + 1],
+                               noise_alpha=0.5, noise_mode="min")
+                for k, ((t, c), p) in enumerate(zip(arrivals, pick))]
         srv.batches, srv.batch_sizes, srv.service, srv.host_post = 0, [], [], []
         done = srv.run(jobs, realtime=True)
         out = serve.latency_summary(done, service=srv.service)
@@ -1034,7 +1039,8 @@ def serving_mixed_run(dev, slots: int = 100, n_cells=(32, 16), rate_hz: float = 
     return {"workload": f"Poisson {rate_hz:g} slots/s per cell for {slots} slots of 0.5 ms; per "
                         f"job 4-273 PRB, 4/16/32/64 Rx, 1-16 layers, QPSK-256QAM; pool of "
                         f"{pool_size} distinct resident jobs; FP16 tensor-core products for 5-16 "
-                        f"layers, FP32 for 1-4; the configuration's 32 cells, then 16",
+                        f"layers, FP32 for 1-4; noise level tracked per cell on the device; "
+                        f"the configuration's 32 cells, then 16",
             "runs": runs, "lanes": lanes, "arena_bytes_per_lane": srv.arena_bytes,
             "api": "phy_batch_post / phy_batch_launch (captured graph per lane)"}
 
