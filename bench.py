@@ -1003,13 +1003,14 @@ def serving_mixed_run(dev, slots: int = 100, n_cells=(32, 16), rate_hz: float = 
     (BatchServer over the batched receiver: FP16 tensor-core products for jobs of 5 or more
     layers, the direct FP32 form below that) for `slots` 0.5 ms slots in real
     time. Job inputs come from a pool of `pool_size` distinct seeded jobs resident on the device
-    (arrivals pick pool entries uniformly). Each cell keeps its noise level on the device
-    across its slots (phy_job.noise_state, alpha 0.5, the smaller of the two DMRS estimates), so
-    a cell's next slot waits for its previous one. Latency is per job, arrival to completion
-    seen by the host; throughput counts the REs of every served job over the run's span."""
+    (arrivals pick pool entries uniformly). Each load runs twice: with every cell keeping its
+    noise level on the device across its slots (phy_job.noise_state, alpha 0.5, the smaller of
+    the two DMRS estimates; a cell's next slot then waits for its previous one, since its
+    detection uses the state that slot updated), and with the noise levels given. Latency is
+    per job, arrival to completion seen by the host; throughput counts the REs of every served
+    job over the run's span."""
     import torch
     from paper_2510_07843_gb300 import serve
-    rng = np.random.default_rng(seed)
     pool = serving_pool(dev, pool_size, seed)
     duration = slots * serve.DEADLINE_S
     srv = serve.BatchServer(device=dev, lanes=lanes)
@@ -1018,19 +1019,21 @@ def serving_mixed_run(dev, slots: int = 100, n_cells=(32, 16), rate_hz: float = 
     srv.run([serve.MixedJob(*pool[p], arrival=0.0, job_id=-1) for p in range(min(8, pool_size))],
             realtime=False)
     runs = []
-    for cells in n_cells:
+    for cells, track in [(c, tr) for c in n_cells for tr in (True, False)]:
         arrivals = S.serving_arrivals(cells, rate_hz, duration, seed + cells)
-        pick = rng.integers(0, pool_size, len(arrivals))
+        pick = np.random.default_rng(seed + 100 + cells).integers(0, pool_size, len(arrivals))
         state = torch.zeros(cells, dtype=torch.float32, device=dev)  # unset: first slot sets it
-        jobs = [serve.MixedJob(*pool[p], arrival=t, job_id=k, noise_state=state[c:c + 1],
-                               noise_alpha=0.5, noise_mode="min")
+        jobs = [serve.MixedJob(*pool[p], arrival=t, job_id=k,
+                               noise_state=state[c:c + 1] if track else None,
+                               noise_alpha=0.5 if track else 0.0, noise_mode="min")
                 for k, ((t, c), p) in enumerate(zip(arrivals, pick))]
         srv.batches, srv.batch_sizes, srv.service, srv.host_post = 0, [], [], []
         done = srv.run(jobs, realtime=True)
         out = serve.latency_summary(done, service=srv.service)
         n_res = sum(j.n_res for j in done)
         span = max(j.done for j in done) - min(j.arrival for j in done)
-        out.update(cells=cells, res_per_s=n_res / span, offered_res_per_s=n_res / duration,
+        out.update(cells=cells, noise_state_on_device=track,
+                   res_per_s=n_res / span, offered_res_per_s=n_res / duration,
                    res=int(n_res), batches=srv.batches,
                    mean_batch=float(np.mean(srv.batch_sizes)),
                    max_batch=int(max(srv.batch_sizes)),
@@ -1039,8 +1042,8 @@ def serving_mixed_run(dev, slots: int = 100, n_cells=(32, 16), rate_hz: float = 
     return {"workload": f"Poisson {rate_hz:g} slots/s per cell for {slots} slots of 0.5 ms; per "
                         f"job 4-273 PRB, 4/16/32/64 Rx, 1-16 layers, QPSK-256QAM; pool of "
                         f"{pool_size} distinct resident jobs; FP16 tensor-core products for 5-16 "
-                        f"layers, FP32 for 1-4; noise level tracked per cell on the device; "
-                        f"the configuration's 32 cells, then 16",
+                        f"layers, FP32 for 1-4; the configuration's 32 cells, then 16, each "
+                        f"with and without the noise level tracked per cell on the device",
             "runs": runs, "lanes": lanes, "arena_bytes_per_lane": srv.arena_bytes,
             "api": "phy_batch_post / phy_batch_launch (captured graph per lane)"}
 

@@ -148,18 +148,22 @@ __global__ void __launch_bounds__(kCnnThreads, 1)
         tc::fence_after_sync();
         const int N = nout_of(l), K = kin_of(l);
         const uint32_t idesc = tc::instr_desc(tc::kFmtBF16, 128, N);
-        const uint32_t a0 = tc::smem_u32(src), b0 = tc::smem_u32(sm + w_off(l));
         const uint32_t lbo_a = kRowsP * 16, lbo_b = N * 16;
+        // descriptors built once; each MMA's operands are fixed byte offsets from them
+        const uint64_t da0 = tc::smem_desc(tc::smem_u32(src), lbo_a, 128);
+        const uint64_t db0 = tc::smem_desc(tc::smem_u32(sm + w_off(l)), lbo_b, 128);
 #pragma unroll 1
         for (int m = 0; m < kMTiles; ++m) {
-#pragma unroll 1
+#pragma unroll
           for (int t = 0; t < 9; ++t) {
             const int row0 = kGuard + m * 128 + (t / 3 - 1) * kPadC + (t % 3 - 1);
-            for (int ks = 0; ks < K / 16; ++ks) {
-              const uint64_t da = tc::smem_desc(a0 + row0 * 16 + ks * 2 * lbo_a, lbo_a, 128);
-              const uint64_t db =
-                  tc::smem_desc(b0 + t * N * K * 2 + ks * 2 * lbo_b, lbo_b, 128);
-              tc::mma<tc::kFmtBF16>(tmem + m * 32, da, db, idesc, (t | ks) != 0 ? 1u : 0u);
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+              if (ks < K / 16) {
+                const uint64_t da = tc::desc_advance(da0, row0 * 16 + ks * 2 * lbo_a);
+                const uint64_t db = tc::desc_advance(db0, t * N * K * 2 + ks * 2 * lbo_b);
+                tc::mma<tc::kFmtBF16>(tmem + m * 32, da, db, idesc, (t | ks) != 0 ? 1u : 0u);
+              }
             }
           }
         }

@@ -128,12 +128,14 @@ __device__ __forceinline__ void gemm_issue(uint32_t tmem, const unsigned char* a
                                            const unsigned char* b, uint32_t idesc,
                                            uint64_t* bar) {
   using Lay = Layout<FMT>;
-  const uint32_t a0 = tc::smem_u32(a), b0 = tc::smem_u32(b);
-#pragma unroll 1
+  // descriptors built once; each K step is a fixed byte offset from them
+  const uint64_t da = tc::smem_desc(tc::smem_u32(a), Lay::kLbo, Lay::kSbo);
+  const uint64_t db = tc::smem_desc(tc::smem_u32(b), Lay::kLbo, Lay::kSbo);
+#pragma unroll
   for (int s = 0; s < Lay::kKSteps; ++s) {
     const uint32_t step = (uint32_t)s * 2u * Lay::kLbo;
-    tc::mma<FMT>(tmem, tc::smem_desc(a0 + step, Lay::kLbo, Lay::kSbo),
-                 tc::smem_desc(b0 + step, Lay::kLbo, Lay::kSbo), idesc, s > 0 ? 1u : 0u);
+    tc::mma<FMT>(tmem, tc::desc_advance(da, step), tc::desc_advance(db, step), idesc,
+                 s > 0 ? 1u : 0u);
   }
   tc::mma_commit(bar);
 }

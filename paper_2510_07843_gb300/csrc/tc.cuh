@@ -149,6 +149,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   return d;
 }
 
+// The descriptor of an operand `bytes` (a multiple of 16) further on: the start-address field
+// is the low 14 bits (address >> 4) and shared-memory addresses stay below 2^18, so adding to the
+// whole word never carries into the other fields. Cheaper than rebuilding the descriptor, which
+// matters in the single thread that issues a long run of MMAs.
+__device__ __forceinline__ uint64_t desc_advance(uint64_t desc, uint32_t bytes) {
+  return desc + (uint64_t)(bytes >> 4);
+}
+
 // Instruction descriptor for kind::f16 / kind::tf32 with FP32 accumulation, both operands
 // K-major, dense: [4,6) D format (1 = F32), [7,10) A format, [10,13) B format (kind::f16:
 // 0 = F16, 1 = BF16; kind::tf32: 2 = TF32), [15] / [16] A / B major (0 = K), [17,23) N >> 3,
