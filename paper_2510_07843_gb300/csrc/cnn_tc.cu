@@ -8,7 +8,10 @@
 // of 8 rows x 16 bytes with consecutive rows 16 bytes apart. A shift by s rows is then just a
 // descriptor start 16 s bytes further on: each tap's operand is read in place by the MMA, with
 // no im2col copy. For every 128-row M tile the nine taps (times C_in / 16 K steps) accumulate
-// into one TMEM accumulator of C_out columns; the epilogue adds the bias, applies the ReLU,
+// into one TMEM accumulator of C_out columns; the four warps issue the M tiles' MMAs in turn
+// (each with descriptors built once and advanced by byte offsets) and commit each tile to its
+// own mbarrier, so each tile's epilogue starts as soon as its accumulator is complete; the
+// epilogue adds the bias, applies the ReLU,
 // rounds to BF16 and writes the interior rows of the next layer's matrix (the padding rows stay
 // zero). The last layer adds the FP32 input tile (the residual) and writes FP32 tiles.
 //
@@ -62,8 +65,11 @@ constexpr size_t kOffW1 = kOffW0 + w_bytes(0);
 constexpr size_t kOffW2 = kOffW1 + w_bytes(1);
 constexpr size_t kOffW3 = kOffW2 + w_bytes(2);
 constexpr size_t kOffBias = kOffW3 + w_bytes(3);  // 4 x 32 floats
-constexpr size_t kOffBar = kOffBias + 4 * 32 * 4;
-constexpr size_t kOffMisc = kOffBar + 16;
+constexpr size_t kOffXres = kOffBias + 4 * 32 * 4;  // the group's FP32 input tiles
+constexpr int kGroupIn = kTilesPerGroup * 2 * kTilePos;   // input values of a group
+constexpr int kInPerThread = (kGroupIn + kCnnThreads - 1) / kCnnThreads;
+constexpr size_t kOffBar = kOffXres + (size_t)kGroupIn * 4;  // one mbarrier per M tile
+constexpr size_t kOffMisc = kOffBar + 8 * ((kMTiles + 1) / 2 * 2);
 constexpr size_t kSmem = kOffMisc + 16;
 static_assert(kSmem <= 227 * 1024, "shared memory map too large");
 __host__ __device__ constexpr size_t w_off(int l) {
@@ -116,7 +122,7 @@ __global__ void __launch_bounds__(kCnnThreads, 1)
     for (int c = tid; c < 32; c += kCnnThreads) bias[l * 32 + c] = c < cout_of(l) ? P[boff_of(l) + c] : 0.f;
   }
   if (tid == 0) {
-    tc::mbar_init(bar, 1);
+    for (int m = 0; m < kMTiles; ++m) tc::mbar_init(bar + m, 1);
     tc::mbar_fence_init();
   }
   if (warp == 0) tc::tmem_alloc(misc, kTmemCols);
@@ -129,22 +135,44 @@ __global__ void __launch_bounds__(kCnnThreads, 1)
   uint32_t phase = 0;
   bool ok = true;
   const int n_groups = (n_tiles + kTilesPerGroup - 1) / kTilesPerGroup;
+  float* xres = reinterpret_cast<float*>(sm + kOffXres);
+  // a group's input tiles (contiguous [tile][channel][position]) in registers: the next group's
+  // are loaded while this one is computed
+  float xin[kInPerThread];
+  auto load_group = [&](int grp) {
+    const size_t base = (size_t)grp * kGroupIn, total = (size_t)n_tiles * 2 * kTilePos;
+#pragma unroll
+    for (int u = 0; u < kInPerThread; ++u) {
+      const int e = tid + u * kCnnThreads;
+      xin[u] = (e < kGroupIn && base + e < total) ? __ldg(x + base + e) : 0.f;
+    }
+  };
+  if ((int)blockIdx.x < n_groups) load_group(blockIdx.x);
   for (int grp = blockIdx.x; grp < n_groups && ok; grp += gridDim.x) {
     const int t0 = grp * kTilesPerGroup;
-    // the input tiles, rounded to BF16, as the first layer's 16-channel operand (channels 0, 1)
-    for (int e = tid; e < kTilesPerGroup * 2 * kTilePos; e += kCnnThreads) {
-      const int t = e / (2 * kTilePos), c = (e / kTilePos) & 1, q = e % kTilePos;
-      const int i = q / kTileCols, j = q - i * kTileCols;
-      const float v = t0 + t < n_tiles ? x[((size_t)(t0 + t) * 2 + c) * kTilePos + q] : 0.f;
-      *reinterpret_cast<unsigned short*>(actB + kmaj(kRowsP, act_row(t, i, j), c)) = bf16_bits(v);
+    // the input tiles, rounded to BF16, as the first layer's 16-channel operand (channels 0, 1),
+    // and in FP32 for the residual
+#pragma unroll
+    for (int u = 0; u < kInPerThread; ++u) {
+      const int e = tid + u * kCnnThreads;
+      if (e < kGroupIn) {
+        const int t = e / (2 * kTilePos), c = (e / kTilePos) & 1, q = e % kTilePos;
+        const int i = q / kTileCols, j = q - i * kTileCols;
+        *reinterpret_cast<unsigned short*>(actB + kmaj(kRowsP, act_row(t, i, j), c)) =
+            bf16_bits(xin[u]);
+        xres[e] = xin[u];
+      }
     }
+    if (grp + (int)gridDim.x < n_groups) load_group(grp + gridDim.x);
 #pragma unroll 1
     for (int l = 0; l < 4; ++l) {
       const unsigned char* src = (l & 1) ? actA : actB;
       unsigned char* dst = (l & 1) ? actB : actA;
       tc::fence_proxy_async();  // the operand written above is read by the tensor core
       __syncthreads();
-      if (tid == 0) {
+      // lane 0 of each warp issues the MMAs of every fourth M tile (issue is the bottleneck of a
+      // run of small N = 32 MMAs from one thread)
+      if (lane == 0) {
         tc::fence_after_sync();
         const int N = nout_of(l), K = kin_of(l);
         const uint32_t idesc = tc::instr_desc(tc::kFmtBF16, 128, N);
@@ -153,7 +181,7 @@ __global__ void __launch_bounds__(kCnnThreads, 1)
         const uint64_t da0 = tc::smem_desc(tc::smem_u32(src), lbo_a, 128);
         const uint64_t db0 = tc::smem_desc(tc::smem_u32(sm + w_off(l)), lbo_b, 128);
 #pragma unroll 1
-        for (int m = 0; m < kMTiles; ++m) {
+        for (int m = warp; m < kMTiles; m += kCnnThreads / 32) {
 #pragma unroll
           for (int t = 0; t < 9; ++t) {
             const int row0 = kGuard + m * 128 + (t / 3 - 1) * kPadC + (t % 3 - 1);
@@ -166,18 +194,18 @@ __global__ void __launch_bounds__(kCnnThreads, 1)
               }
             }
           }
+          // M tile m's accumulator is complete once every MMA this thread issued so far is:
+          // its epilogue starts while the tensor core works on the other tiles
+          tc::mma_commit(bar + m);
         }
-        tc::mma_commit(bar);
       }
-      bool done = tc::mbar_wait(bar, phase, kWait);
-      if (!done) done = tc::mbar_wait(bar, phase, kWait);  // let MMAs in flight finish
-      phase ^= 1u;
-      ok = __syncthreads_and(done);
-      if (!ok) break;
-      tc::fence_after_sync();
       // epilogue: this thread's TMEM lane is its row of each M tile
+      bool done = true;
 #pragma unroll 1
       for (int m = 0; m < kMTiles; ++m) {
+        done = __all_sync(0xffffffffu, tc::mbar_wait(bar + m, phase, kWait));  // warp-uniform
+        if (!done) break;
+        tc::fence_after_sync();
         float v[32];
         tc::tmem_ld32(tmem + lane_base + m * 32, v);
         const int p = m * 128 + 32 * (warp & 3) + lane;  // position in the group
@@ -201,11 +229,16 @@ __global__ void __launch_bounds__(kCnnThreads, 1)
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
             const size_t o = ((size_t)(t0 + t) * 2 + c) * kTilePos + q0;
-            out[o] = x[o] + (v[c] + bias[3 * 32 + c]);
+            out[o] = xres[(t * 2 + c) * kTilePos + q0] + (v[c] + bias[3 * 32 + c]);
           }
         }
       }
+      if (!done)  // MMAs in flight finish before anything else happens
+        for (int m = 0; m < kMTiles; ++m) tc::mbar_wait(bar + m, phase, kWait);
+      phase ^= 1u;
       tc::fence_before_sync();  // TMEM reads done before the next layer's MMAs overwrite it
+      ok = __syncthreads_and(done);
+      if (!ok) break;
     }
   }
   tc::fence_before_sync();
