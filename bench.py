@@ -695,6 +695,15 @@ def cnn_run(dev, st, fp32_peak_tf: float, bf16_peak_tf: float, slots: int = 24,
     torch.cuda.synchronize()
     train_s = a.elapsed_time(b) * 1e-3
     tiles = tr.step * tr.batch
+    # the same schedule with the mixed-precision step (tensor-core BF16 forward, FP32 backward
+    # and master weights)
+    trm = D.Trainer(D.init_params(0), batch=256, dev=dev, lr=2e-3, bf16=True)
+    a.record(st)
+    for ep in range(epochs):
+        trm.epoch(x, y, seed=ep)
+    b.record(st)
+    torch.cuda.synchronize()
+    train_mixed_s = a.elapsed_time(b) * 1e-3
     ev = D.slot_tiles(D.train_spec(n_prb=273, snr_db=5.0, doppler_hz=300.0), 4000, dev)
     n_tiles = phy.cnn_n_tiles(ev.cfg)
     H = torch.empty((1, len(ev.spec.data_sym), ev.spec.n_sc, 32, 8), dtype=torch.complex64,
@@ -739,6 +748,7 @@ def cnn_run(dev, st, fp32_peak_tf: float, bf16_peak_tf: float, slots: int = 24,
     inf_tf = n_tiles * CNN_MACS_FWD * 2 / inf_s / 1e12
     fwd_flops = n_tiles * CNN_MACS_FWD * 2
     res = D.evaluate(tr.p, ev, dev, tensor_cores=True)
+    res_mixed = D.evaluate(trm.p, ev, dev)
     more = {}
     if slots > 24:
         for snr in (0.0, 20.0):
@@ -749,7 +759,14 @@ def cnn_run(dev, st, fp32_peak_tf: float, bf16_peak_tf: float, slots: int = 24,
                       "set_tiles": int(x.shape[0]), "epochs": epochs,
                       "generation_s": gen_s, "generation_workers": workers,
                       "seconds": train_s, "tiles_per_s": tiles / train_s,
-                      "tflops": train_tf, "fp32_peak_frac": train_tf / fp32_peak_tf},
+                      "tflops": train_tf, "fp32_peak_frac": train_tf / fp32_peak_tf,
+                      "mixed_precision": {"seconds": train_mixed_s,
+                                          "tiles_per_s": trm.step * trm.batch / train_mixed_s,
+                                          "what": "phy_cnn_train_step_bf16: BF16 forward on "
+                                                  "the tensor cores, FP32 backward and Adam",
+                                          "eval_5db": {k: res_mixed[k] for k in
+                                                       ("mse_ls", "mse_cnn", "ber_ls",
+                                                        "ber_cnn")}}},
             "denoise_slot": {"tiles": n_tiles, "ms": inf_s * 1e3, "tflops": inf_tf,
                              "fp32_peak_frac": inf_tf / fp32_peak_tf,
                              "ms_bf16_tensor_core": inf_tc_s * 1e3,

@@ -530,6 +530,22 @@ phy_status phy_cnn_denoise_bf16(const phy_slot_cfg* cfg, const float* params,
                                 const phy_c32* anchors, phy_c32* H_data, void* workspace,
                                 size_t workspace_bytes, void* stream);
 size_t phy_cnn_denoise_error_offset(const phy_slot_cfg* cfg);
+/*
+ * Mixed-precision training step: phy_cnn_train_step with its forward pass on the tensor cores
+ * (the BF16 form above), which also keeps the activations the next layers read (BF16 values) for
+ * the backward pass; the loss, the gradients and the Adam update of the FP32 master parameters
+ * stay FP32 on the CUDA cores. The gradients are those of the BF16 network (weights and layer
+ * inputs rounded in the forward pass, the backward pass through them in FP32). Same arguments
+ * and workspace as phy_cnn_train_step; the forward pass's error word (nonzero: a bounded wait
+ * for the tensor core ran out and the step's results are not valid) sits at byte
+ * phy_cnn_train_error_offset(n_tiles) of the workspace.
+ */
+phy_status phy_cnn_train_step_bf16(int32_t n_tiles, float* params, float* adam_m, float* adam_v,
+                                   int32_t step, float lr, const float* tiles_in,
+                                   const float* tiles_label, float* grad, float* grad_in,
+                                   float* loss, void* workspace, size_t workspace_bytes,
+                                   void* stream);
+size_t phy_cnn_train_error_offset(int32_t n_tiles);
 phy_status phy_cnn_denoise(const phy_slot_cfg* cfg, const float* params, const phy_c32* anchors,
                            phy_c32* H_data, void* workspace, size_t workspace_bytes,
                            void* stream);

@@ -540,6 +540,25 @@ phy_status phy_cnn_train_step(int32_t n_tiles, float* params, float* adam_m, flo
                                          (cudaStream_t)stream));
 }
 
+phy_status phy_cnn_train_step_bf16(int32_t n_tiles, float* params, float* adam_m, float* adam_v,
+                                   int32_t step, float lr, const float* tiles_in,
+                                   const float* tiles_label, float* grad, float* grad_in,
+                                   float* loss, void* workspace, size_t workspace_bytes,
+                                   void* stream) {
+  if (n_tiles < 1 || !params || !tiles_in || !tiles_label || !grad || !workspace)
+    return PHY_ERR_INVALID_ARG;
+  if (step > 0 && (!adam_m || !adam_v || !(lr >= 0.f))) return PHY_ERR_INVALID_ARG;
+  if (((uintptr_t)workspace) % kAlign) return PHY_ERR_INVALID_ARG;
+  if (workspace_bytes < phy_cnn_workspace_size(n_tiles)) return PHY_ERR_NO_MEMORY;
+  return cuda_status(phy::cnn_train_step(n_tiles, params, adam_m, adam_v, step, lr, tiles_in,
+                                         tiles_label, grad, grad_in, loss, (float*)workspace,
+                                         (cudaStream_t)stream, true));
+}
+
+size_t phy_cnn_train_error_offset(int32_t n_tiles) {
+  return n_tiles < 1 ? 0 : phy::cnn_train_error_float(n_tiles) * sizeof(float);
+}
+
 namespace {
 phy_status check_tiles(const phy_slot_cfg* cfg, Geo* g) {
   phy_status s = make_geo(cfg, g);

@@ -390,8 +390,10 @@ cudaError_t launch_tiles_to_h(const Geo& g, const float* tiles, phy_c32* Hd, cud
 // partials of the persistent CTAs and the loss partials.
 size_t cnn_scratch_floats(int n) {
   const size_t big = (size_t)n * 32 * kTP, small = (size_t)n * 2 * kTP;
-  return 3 * big + 2 * small + 2 * big + kPartFloats + 1024;
+  return 3 * big + 2 * small + 2 * big + kPartFloats + 1024 + 64;  // + the error word's block
 }
+
+size_t cnn_train_error_float(int n) { return cnn_scratch_floats(n) - 64; }
 
 cudaError_t cnn_forward(int n, const float* P, const float* x, float* out, float* ws,
                         cudaStream_t st) {
@@ -406,7 +408,7 @@ cudaError_t cnn_forward(int n, const float* P, const float* x, float* out, float
 
 cudaError_t cnn_train_step(int n, float* P, float* m, float* v, int step, float lr,
                            const float* x, const float* label, float* grad_out, float* dx_out,
-                           float* loss_out, float* ws, cudaStream_t st) {
+                           float* loss_out, float* ws, cudaStream_t st, bool tc_forward) {
   const size_t big = (size_t)n * 32 * kTP, small = (size_t)n * 2 * kTP;
   float *a1 = ws, *a2 = a1 + big, *a3 = a2 + big;
   float* out = a3 + big;
@@ -415,7 +417,14 @@ cudaError_t cnn_train_step(int n, float* P, float* m, float* v, int step, float 
   float* part = dzB + big;
   float* lpart = part + kPartFloats;
   float* g = grad_out;
-  cudaError_t e = cnn_forward(n, P, x, out, ws, st);
+  // forward: FP32 on the CUDA cores, or BF16 operands on the tensor cores (the activations it
+  // keeps are the BF16 values the next layer read; the backward pass stays FP32 on the FP32
+  // master weights)
+  cudaError_t e =
+      tc_forward ? cnn_forward_tc(n, P, x, out,
+                                  reinterpret_cast<unsigned*>(ws + cnn_train_error_float(n)), st,
+                                  a1)
+                 : cnn_forward(n, P, x, out, ws, st);
   if (e) return e;
   const long long total = (long long)small;
   const int lg = (int)std::min<long long>(1024, (total + kCnnThreads - 1) / kCnnThreads);

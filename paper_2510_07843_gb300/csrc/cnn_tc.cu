@@ -96,7 +96,8 @@ __device__ __forceinline__ int act_row(int t, int i, int j) {
 // Persistent CTAs (one per SM) over groups of four tiles.
 __global__ void __launch_bounds__(kCnnThreads, 1)
     cnn_forward_tc_kernel(int n_tiles, const float* __restrict__ P, const float* __restrict__ x,
-                          float* __restrict__ out, unsigned* __restrict__ err) {
+                          float* __restrict__ out, unsigned* __restrict__ err,
+                          float* __restrict__ acts) {
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* actA = sm + kOffA;
   unsigned char* actB = sm + kOffB;
@@ -211,7 +212,14 @@ __global__ void __launch_bounds__(kCnnThreads, 1)
         const int p = m * 128 + 32 * (warp & 3) + lane;  // position in the group
         const int t = p / kPadPos, q = p - t * kPadPos, pr = q / kPadC, pc = q - pr * kPadC;
         if (pr < 1 || pr > kTileRows || pc < 1 || pc > kTileCols) continue;
+        const int q0 = (pr - 1) * kTileCols + (pc - 1);
         if (l < 3) {
+          // the layer's output as the next layer reads it (BF16), also kept in FP32 for a
+          // backward pass when acts is set: acts[l][tile][channel][position]
+          float* keep = (acts && t0 + t < n_tiles)
+                            ? acts + (size_t)l * n_tiles * 32 * kTilePos +
+                                  (size_t)(t0 + t) * 32 * kTilePos + q0
+                            : nullptr;
 #pragma unroll
           for (int c8 = 0; c8 < 4; ++c8) {
             uint32_t w[4];
@@ -219,13 +227,17 @@ __global__ void __launch_bounds__(kCnnThreads, 1)
             for (int h = 0; h < 4; ++h) {
               const float a = fmaxf(v[c8 * 8 + 2 * h] + bias[l * 32 + c8 * 8 + 2 * h], 0.f);
               const float b = fmaxf(v[c8 * 8 + 2 * h + 1] + bias[l * 32 + c8 * 8 + 2 * h + 1], 0.f);
-              w[h] = (uint32_t)bf16_bits(a) | ((uint32_t)bf16_bits(b) << 16);
+              const unsigned short ba = bf16_bits(a), bb = bf16_bits(b);
+              w[h] = (uint32_t)ba | ((uint32_t)bb << 16);
+              if (keep) {
+                keep[(size_t)(c8 * 8 + 2 * h) * kTilePos] = __uint_as_float((uint32_t)ba << 16);
+                keep[(size_t)(c8 * 8 + 2 * h + 1) * kTilePos] = __uint_as_float((uint32_t)bb << 16);
+              }
             }
             *reinterpret_cast<uint4*>(dst + kmaj(kRowsP, kGuard + p, c8 * 8)) =
                 make_uint4(w[0], w[1], w[2], w[3]);
           }
         } else if (t0 + t < n_tiles) {
-          const int q0 = (pr - 1) * kTileCols + (pc - 1);
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
             const size_t o = ((size_t)(t0 + t) * 2 + c) * kTilePos + q0;
@@ -255,7 +267,7 @@ __global__ void __launch_bounds__(kCnnThreads, 1)
 size_t cnn_tc_smem_bytes() { return kSmem; }
 
 cudaError_t cnn_forward_tc(int n, const float* P, const float* x, float* out, unsigned* err,
-                           cudaStream_t st) {
+                           cudaStream_t st, float* acts) {
   static bool configured_on[kMaxDevices] = {};
   bool& configured = configured_on[current_device()];
   if (!configured) {
@@ -269,7 +281,7 @@ cudaError_t cnn_forward_tc(int n, const float* P, const float* x, float* out, un
   if (n <= 0) return cudaSuccess;
   const int groups = (n + kTilesPerGroup - 1) / kTilesPerGroup;
   const int grid = groups < device_sm_count() ? groups : device_sm_count();
-  cnn_forward_tc_kernel<<<grid, kCnnThreads, kSmem, st>>>(n, P, x, out, err);
+  cnn_forward_tc_kernel<<<grid, kCnnThreads, kSmem, st>>>(n, P, x, out, err, acts);
   return cudaGetLastError();
 }
 

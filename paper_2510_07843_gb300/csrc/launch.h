@@ -101,13 +101,19 @@ int cnn_param_count();
 size_t cnn_scratch_floats(int n_tiles);
 cudaError_t cnn_forward(int n, const float* params, const float* x, float* out, float* ws,
                         cudaStream_t st);
+// With tc_forward the forward pass runs on the tensor cores (cnn_forward_tc, keeping its BF16
+// activations for the FP32 backward pass) and its error word is the workspace's float at
+// cnn_train_error_float(n).
 cudaError_t cnn_train_step(int n, float* params, float* m, float* v, int step, float lr,
                            const float* x, const float* label, float* grad_out, float* dx_out,
-                           float* loss_out, float* ws, cudaStream_t st);
+                           float* loss_out, float* ws, cudaStream_t st, bool tc_forward = false);
+size_t cnn_train_error_float(int n_tiles);
 // The same forward pass on the tensor cores with BF16 operands (cnn_tc.cu); err (device word)
-// is cleared first and counts CTAs whose bounded MMA wait ran out.
+// is cleared first and counts CTAs whose bounded MMA wait ran out. With acts set, the outputs
+// of the first three layers (as the next layer reads them, rounded to BF16) are also written in
+// FP32 to acts[layer][tile][channel][position].
 cudaError_t cnn_forward_tc(int n, const float* params, const float* x, float* out, unsigned* err,
-                           cudaStream_t st);
+                           cudaStream_t st, float* acts = nullptr);
 // Interpolated channel at every symbol H[cell][t][k][r][l]; tiles per (cell, PRB, Rx, layer)
 // from such an H, and the data symbols of tiles back into Hd[cell][dsym][k][r][l].
 cudaError_t launch_interp_all(const Geo& g, const phy_c32* anchors, phy_c32* H, cudaStream_t st);

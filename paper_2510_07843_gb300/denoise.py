@@ -115,10 +115,11 @@ def training_set(n_slots: int, n_prb: int, seed: int, dev, snr_range=(0.0, 30.0)
 
 
 class Trainer:
-    """Adam on the device through phy_cnn_train_step; batches are contiguous slices of a
-    shuffled copy of the tile set."""
+    """Adam on the device through phy_cnn_train_step (with bf16: phy_cnn_train_step_bf16, the
+    forward pass on the tensor cores with BF16 operands, FP32 backward and master weights);
+    batches are contiguous slices of a shuffled copy of the tile set."""
 
-    def __init__(self, params: np.ndarray, batch: int, dev, lr: float = 1e-3):
+    def __init__(self, params: np.ndarray, batch: int, dev, lr: float = 1e-3, bf16: bool = False):
         import torch
         self.dev = dev
         self.batch = batch
@@ -130,6 +131,8 @@ class Trainer:
         self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
         self.ws = torch.empty(phy.cnn_workspace_size(batch), dtype=torch.uint8, device=dev)
         self.step = 0
+        self.bf16 = bf16
+        self.err_at = phy.cnn_train_error_offset(batch)
 
     def epoch(self, x, y, seed: int, max_steps: Optional[int] = None) -> List[float]:
         import torch
@@ -144,10 +147,16 @@ class Trainer:
             sl = slice(b * self.batch, (b + 1) * self.batch)
             self.step += 1
             phy.cnn_train_step(self.batch, self.p, self.m, self.v, self.step, self.lr, xs[sl],
-                               ys[sl], self.g, None, self.loss, self.ws)
+                               ys[sl], self.g, None, self.loss, self.ws, bf16=self.bf16)
             if b % 50 == 0 or b == nb - 1:
                 losses.append(float(self.loss.item()))
+                if self.bf16 and self.error_word() != 0:
+                    raise RuntimeError("tensor-core forward pass: a bounded wait ran out")
         return losses
+
+    def error_word(self) -> int:
+        import torch
+        return int(self.ws[self.err_at:self.err_at + 4].view(torch.int32).item())
 
     def params(self) -> np.ndarray:
         return self.p.cpu().numpy()

@@ -89,6 +89,10 @@ _SIGS = {
     "phy_cnn_train_step": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, ctypes.c_int32,
                                           ctypes.c_float, _P, _P, _P, _P, _P, _P,
                                           ctypes.c_size_t, _P]),
+    "phy_cnn_train_step_bf16": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, ctypes.c_int32,
+                                               ctypes.c_float, _P, _P, _P, _P, _P, _P,
+                                               ctypes.c_size_t, _P]),
+    "phy_cnn_train_error_offset": (ctypes.c_size_t, [ctypes.c_int32]),
     "phy_cnn_n_tiles": (ctypes.c_int32, [_P]),
     "phy_interp_channel": (ctypes.c_int, [_P, _P, _P, _P]),
     "phy_cnn_tiles": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -399,14 +403,21 @@ def cnn_forward(n_tiles: int, params, tiles_in, tiles_out, workspace, stream=Non
 
 
 def cnn_train_step(n_tiles: int, params, adam_m, adam_v, step: int, lr: float, tiles_in,
-                   tiles_label, grad, grad_in=None, loss=None, workspace=None, stream=None):
-    """phy_cnn_train_step: loss, gradients and (step >= 1) one Adam update, on the device."""
+                   tiles_label, grad, grad_in=None, loss=None, workspace=None, stream=None,
+                   bf16: bool = False):
+    """phy_cnn_train_step (or, with bf16, phy_cnn_train_step_bf16: the forward pass on the
+    tensor cores): loss, gradients and (step >= 1) one Adam update, on the device."""
     ws_bytes = workspace.numel() * workspace.element_size()
-    _check("phy_cnn_train_step",
-           load().phy_cnn_train_step(n_tiles, _ptr(params), _ptr(adam_m), _ptr(adam_v), step, lr,
-                                     _ptr(tiles_in), _ptr(tiles_label), _ptr(grad),
-                                     _ptr(grad_in), _ptr(loss), _ptr(workspace), ws_bytes,
-                                     _stream(stream)))
+    name = "phy_cnn_train_step_bf16" if bf16 else "phy_cnn_train_step"
+    _check(name, getattr(load(), name)(n_tiles, _ptr(params), _ptr(adam_m), _ptr(adam_v), step,
+                                       lr, _ptr(tiles_in), _ptr(tiles_label), _ptr(grad),
+                                       _ptr(grad_in), _ptr(loss), _ptr(workspace), ws_bytes,
+                                       _stream(stream)))
+
+
+def cnn_train_error_offset(n_tiles: int) -> int:
+    """Byte offset of the mixed-precision step's error word in its workspace."""
+    return int(load().phy_cnn_train_error_offset(n_tiles))
 
 
 def cnn_n_tiles(cfg: SlotConfig) -> int:

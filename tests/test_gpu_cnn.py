@@ -203,3 +203,59 @@ def test_tensor_core_forward_matches_the_bf16_oracle(dev, n):
     print(f"tensor-core forward n={n}: vs bf16 oracle {e:.2e}, bf16 vs fp32 oracle {e16:.2e}")
     assert np.all(np.isfinite(got))
     assert e <= 2e-3 and e < e16 / 4
+
+
+@pytest.mark.parametrize("n", [5, 300])
+def test_mixed_precision_gradients_match_the_bf16_oracle(dev, n):
+    """phy_cnn_train_step_bf16: the forward pass on the tensor cores (BF16 operands) keeps the
+    BF16 activations the next layers read, and the FP32 backward pass through them gives the
+    gradients of the oracle's bfloat16 network (its activations rounded to BF16 as the kernel
+    stores them, then the exact backward pass). Bars as for the tensor-core forward pass: 2e-3
+    relative per parameter tensor, against the gap to the FP32 network's gradients (printed)."""
+    import torch
+    from paper_2510_07843_gb300 import phy
+    p, x, y = random_net(200 + n, n)
+    g = torch.zeros(19682, dtype=torch.float32, device=dev)
+    gx = torch.zeros((n, 2, 14, 12), dtype=torch.float32, device=dev)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    ws = torch.full((phy.cnn_workspace_size(n),), 7, dtype=torch.uint8, device=dev)
+    pd = T(p, dev)
+    phy.cnn_train_step(n, pd, None, None, 0, 0.0, T(x, dev), T(y, dev), g, gx, loss, ws,
+                       bf16=True)
+    torch.cuda.synchronize()
+    off = phy.cnn_train_error_offset(n)
+    assert int(ws[off:off + 4].view(torch.int32).item()) == 0  # no bounded wait ran out
+    p64, x64, y64 = p.astype(np.float64), x.astype(np.float64), y.astype(np.float64)
+    out16, acts16 = O.cnn_forward(p64, x64, operands="bf16")
+    acts_r = [acts16[0]] + [O.round_bf16(a) for a in acts16[1:]]
+    want_g, want_gx = O.cnn_backward(p64, acts_r, out16, y64)
+    out32, acts32 = O.cnn_forward(p64, x64)
+    g32, _ = O.cnn_backward(p64, acts32, out32, y64)
+    assert float(loss.item()) == pytest.approx(O.cnn_loss(out16, y64), rel=1e-3)
+    gg = g.cpu().numpy()
+    offs = np.cumsum([0] + [int(np.prod(s)) for s in O.cnn_param_shapes()])
+    for a, b in zip(offs[:-1], offs[1:]):
+        e, e16 = rel(gg[a:b], want_g[a:b]), rel(g32[a:b], want_g[a:b])
+        print(f"mixed-precision grad [{a}:{b}] vs bf16 oracle {e:.2e} (FP32 network {e16:.2e})")
+        assert e <= 2e-3, (a, b, e)
+    assert rel(gx.cpu().numpy(), want_gx) <= 2e-3
+    assert torch.equal(pd, T(p, dev))  # step 0: no update
+
+
+def test_mixed_precision_training_learns_as_fp32(dev):
+    """Trained with the mixed-precision step (tensor-core BF16 forward, FP32 backward and master
+    weights) on the same generated slots and schedule as the FP32 trainer, the network beats LS +
+    interpolation at 5 dB and ends within 3% of the FP32-trained network's channel MSE."""
+    from paper_2510_07843_gb300 import denoise as D
+    x, y = D.training_set(n_slots=8, n_prb=12, seed=13, dev=dev)
+    held = D.slot_tiles(D.train_spec(n_prb=24, snr_db=5.0, doppler_hz=300.0), 998, dev)
+    res = {}
+    for bf16 in (False, True):
+        tr = D.Trainer(D.init_params(0), batch=256, dev=dev, lr=2e-3, bf16=bf16)
+        for ep in range(6):
+            tr.epoch(x, y, seed=ep)
+        res[bf16] = D.evaluate(tr.p, held, dev, tensor_cores=True)
+        print("bf16" if bf16 else "fp32", res[bf16])
+    m32, m16 = res[False]["mse_cnn"], res[True]["mse_cnn"]
+    assert m16 < 0.95 * res[True]["mse_ls"]
+    assert m16 <= 1.03 * m32, (m16, m32)
