@@ -313,12 +313,78 @@ struct SmemScratch {
 
 
 
+// The solver's 8x8 L21/T matrix of one thread in that scratch, entry (i, j) at slot 8 i + j.
+template <int W>
+struct SmemRows {
+  SmemScratch<W> s;
+  __device__ __forceinline__ void st_row(int i, const cf (&r)[8]) const {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s.st(kScrL21 + 8 * i + j, r[j]);
+  }
+  __device__ __forceinline__ void ld_row(int i, cf (&r)[8]) const {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) r[j] = s.ld(kScrL21 + 8 * i + j);
+  }
+  __device__ __forceinline__ void ld_col(int c, cf (&r)[8]) const {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) r[i] = s.ld(kScrL21 + 8 * i + c);
+  }
+  __device__ __forceinline__ void sync_st() const {}
+};
+
+// The same matrix in tensor memory: the thread's own TMEM lane (lane quarter of its warp),
+// 128 columns, entry (i, j) in columns 16 i + 2 j (real) and 16 i + 2 j + 1 (imaginary). Loads
+// and stores are warp-collective (each access first reconverges the warp); a row is one
+// 16-column access, a column eight 2-column ones.
+struct TmemRows {
+  uint32_t base;  // TMEM address of column 0 at the warp's first lane
+  __device__ __forceinline__ void st_row(int i, const cf (&r)[8]) const {
+    float v[16];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      v[2 * j] = r[j].x;
+      v[2 * j + 1] = r[j].y;
+    }
+    __syncwarp();
+    tc::tmem_st16(base + 16u * i, v);
+  }
+  __device__ __forceinline__ void ld_row(int i, cf (&r)[8]) const {
+    float v[16];
+    __syncwarp();
+    tc::tmem_ld16(base + 16u * i, v);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) r[j] = mk(v[2 * j], v[2 * j + 1]);
+  }
+  __device__ __forceinline__ void ld_col(int c, cf (&r)[8]) const {
+    float v[16];
+    __syncwarp();
+    tc::tmem_ld2x8(base + 2u * c, v);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) r[i] = mk(v[2 * i], v[2 * i + 1]);
+  }
+  __device__ __forceinline__ void sync_st() const {
+    __syncwarp();
+    tc::tmem_wait_st();
+  }
+};
+
 // Gram-block bytes of one (segment, data symbol): NTRI 4-tuples of complex values.
 constexpr uint32_t gram_block_bytes(int NL) { return (uint32_t)(NL * (NL + 1) / 2) * 32u; }
 
+// 9..16 layers with 128-RE CTAs keep the solver's L21/T matrices in tensor memory (128 columns
+// per CTA; this kernel issues no MMAs), which leaves shared memory to the Gram blocks and one
+// 8-vector per thread: three CTAs (12 warps) fit an SM where the shared-memory form fits two.
+// 64-RE CTAs keep the shared-memory form.
+constexpr bool solve_uses_tmem(int NL, int W) { return NL == 16 && W == 128; }
+constexpr uint32_t kSolveTmemCols = 128;
+constexpr int kSolveCarveoutSlack = 2;  // percent above the exact need
+constexpr int solve_min_ctas(int NL, int W) { return solve_uses_tmem(NL, W) ? 3 : 1; }
+
 // The solve kernel's CTA width W (REs per CTA) is a tile shape the autotuner picks: 128 or 64.
 constexpr size_t solve_scratch_bytes(int NL, int W = kSolveThreads) {
-  return NL == 16 ? (size_t)kScrSlots * W * sizeof(cf) : 0;
+  return NL != 16                  ? 0
+         : solve_uses_tmem(NL, W) ? (size_t)8 * W * sizeof(cf)
+                                  : (size_t)kScrSlots * W * sizeof(cf);
 }
 
 // 9..16 layers: after the solve, shared memory holds every thread's x and d in RE-major tables
@@ -328,8 +394,8 @@ constexpr size_t solve_stage_bytes(int W = kSolveThreads) {
 }
 
 // Shared memory of the solve kernel: scratch and the Gram blocks of up to max_segs segments (for
-// 9..16 layers at least the epilogue's tables), then the mbarrier in the last 16 bytes, which the
-// tables never reach.
+// 9..16 layers at least the epilogue's tables), then the mbarrier and the tensor-memory address
+// in the last 16 bytes, which the tables never reach.
 __host__ __device__ constexpr size_t solve_smem_bytes(int NL, int QM, int max_segs,
                                                       int W = kSolveThreads) {
   const size_t main = solve_scratch_bytes(NL, W) + (size_t)max_segs * gram_block_bytes(NL);
@@ -412,11 +478,12 @@ __device__ __forceinline__ void demap_store_q(int qm, float* llr, size_t li, cf 
 // (512 B apart) would keep each warp waiting on the store path.
 // Work item (128 subcarriers from k0 = bx 128, data symbol jj, cell lc of the chunk starting at
 // cell0). The barrier `bar` is initialised and its phase `parity` is the one this item's copies
-// complete. QM = 0 takes the modulation from g.qm. Returns false if the Gram-block copies did not
-// land even after a timeout's second wait (the barrier is then unusable for a later item).
+// complete; `tmem` is the CTA's tensor-memory allocation when solve_uses_tmem(NL, W). QM = 0
+// takes the modulation from g.qm. Returns false if the Gram-block copies did not land even after
+// a timeout's second wait (the barrier is then unusable for a later item).
 template <int NL, int QM, int W = kSolveThreads>
 __device__ __forceinline__ bool re_solve_body(
-    const Geo& g, int cell0, int bx, int jj, int lc, uint64_t* bar, uint32_t parity,
+    const Geo& g, int cell0, int bx, int jj, int lc, uint64_t* bar, uint32_t parity, uint32_t tmem,
     const float4* __restrict__ ygg, const cf* __restrict__ bvec,
     const float* __restrict__ sigma2, const phy_c32* __restrict__ anchors,
     const phy_c32* __restrict__ Y, phy_c32* __restrict__ x_hat, float* __restrict__ sinr_out,
@@ -467,7 +534,8 @@ __device__ __forceinline__ bool re_solve_body(
   if (NL != 16 && !live) return true;
   const int j = seg_of(g, live ? k : k0);
   const float s2 = sigma2[cell];
-  const float be0 = seg_beta(g, j, k, 0), be1 = seg_beta(g, j, k, 1);
+  const int kc = live ? k : k0;
+  const float be0 = seg_beta(g, j, kc, 0), be1 = seg_beta(g, j, kc, 1);
   const float4* yp = ys + (size_t)(j - s0) * NTRI * 2;
   // weight products w_g(comb l) w_g'(comb m) for the four comb pairs (cl, cm), built once
   float cw[2][2][4];
@@ -501,10 +569,12 @@ __device__ __forceinline__ bool re_solve_body(
     return a;
   };
   bool ok = false;
-  if (live) {
+  // every thread of a warp takes part in the 9..16-layer solve (its tensor-memory accesses are
+  // warp-collective); a thread past the carrier's end solves its block's first RE and discards it
+  if (live || NL == 16) {
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
-      if (l >= nl) b[l] = mk(0.f, 0.f);
+      if (l >= nl || !live) b[l] = mk(0.f, 0.f);
       fin = fin && finite_cf(b[l]);
     }
     SolveInfo si;
@@ -530,8 +600,15 @@ __device__ __forceinline__ bool re_solve_body(
           row[k] = (lv && k < nl) ? a : mk(0.f, 0.f);  // l >= 8 > k: never on the diagonal
         }
       };
-      si = solve16(getA, rowA, SmemScratch<W>{reinterpret_cast<cf*>(solve_smem) + threadIdx.x}, b,
-                   x, dd);
+      cf* sb = reinterpret_cast<cf*>(solve_smem) + threadIdx.x;
+      if constexpr (solve_uses_tmem(NL, W)) {
+        // the warp's lane quarter of the allocation: lane field 32 (warp mod 4) << 16
+        const TmemRows rows{tmem + (((threadIdx.x >> 5) & 3u) << 21)};
+        si = solve16(getA, rowA, SmemScratch<W>{sb}, rows, b, x, dd);
+      } else {
+        si = solve16(getA, rowA, SmemScratch<W>{sb + kScrV * W}, SmemRows<W>{SmemScratch<W>{sb}},
+                     b, x, dd);
+      }
     } else {
       si = solve_small<NL>(getA, b, x, dd);
     }
@@ -540,7 +617,7 @@ __device__ __forceinline__ bool re_solve_body(
     uint8_t flag = 0;
     if (!fin) flag |= 4;
     if (!si.ok || si.pmin < g.pivot_min * si.pmax) flag |= 1;
-    if (g.refactor && (flag & 1) && fin) {
+    if (live && g.refactor && (flag & 1) && fin) {
       Refactor64Out r64;
       refactor_fp64(g, anchors, Y, cell, jj, k, j, s2, &r64);
       if (r64.ok) {
@@ -555,7 +632,7 @@ __device__ __forceinline__ bool re_solve_body(
         flag |= 2;
       }
     }
-    flags_out[ridx] = flag;
+    if (live) flags_out[ridx] = flag;
   }
   if constexpr (NL == 16) {
     // Outputs leave in (RE, layer) order: once every thread is past the solve, each stages its
@@ -609,8 +686,35 @@ __device__ __forceinline__ bool re_solve_body(
   return true;
 }
 
+// The CTA's tensor memory for the solver (solve_uses_tmem): warp 0 allocates kSolveTmemCols
+// columns into *slot before the CTA's first barrier, and releases them after its last one.
+template <bool kTm>
+__device__ __forceinline__ uint32_t solve_tmem_acquire(uint32_t* slot) {
+  if constexpr (kTm) {
+    if (threadIdx.x < 32) tc::tmem_alloc(slot, kSolveTmemCols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    return *slot;
+  } else {
+    __syncthreads();
+    return 0;
+  }
+}
+template <bool kTm>
+__device__ __forceinline__ void solve_tmem_release(uint32_t tmem) {
+  if constexpr (kTm) {
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      tc::fence_after_sync();
+      tc::tmem_dealloc(tmem, kSolveTmemCols);
+    }
+  }
+}
+
 template <int NL, int QM, int W>
-__global__ void __launch_bounds__(W)
+__global__ void __launch_bounds__(W, solve_min_ctas(NL, W))
     re_solve_fp32_kernel(Geo g, int cell0, int max_segs, const float4* __restrict__ ygg,
                          const cf* __restrict__ bvec, const float* __restrict__ sigma2,
                          const phy_c32* __restrict__ anchors, const phy_c32* __restrict__ Y,
@@ -618,15 +722,17 @@ __global__ void __launch_bounds__(W)
                          float* __restrict__ llr_out, uint8_t* __restrict__ flags_out,
                          const unsigned* __restrict__ prep_err) {
   extern __shared__ __align__(128) unsigned char solve_smem[];
-  uint64_t* bar =
-      reinterpret_cast<uint64_t*>(solve_smem + solve_smem_bytes(NL, QM, max_segs, W) - 16);
+  unsigned char* top = solve_smem + solve_smem_bytes(NL, QM, max_segs, W);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(top - 16);
   if (threadIdx.x == 0) {
     tc::mbar_init(bar, 1);
     tc::mbar_fence_init();
   }
-  __syncthreads();
-  re_solve_body<NL, QM, W>(g, cell0, blockIdx.x, blockIdx.y, blockIdx.z, bar, 0, ygg, bvec, sigma2,
-                        anchors, Y, x_hat, sinr_out, llr_out, flags_out, prep_err);
+  constexpr bool kTm = solve_uses_tmem(NL, W);
+  const uint32_t tmem = solve_tmem_acquire<kTm>(reinterpret_cast<uint32_t*>(top - 8));
+  re_solve_body<NL, QM, W>(g, cell0, blockIdx.x, blockIdx.y, blockIdx.z, bar, 0, tmem, ygg, bvec,
+                           sigma2, anchors, Y, x_hat, sinr_out, llr_out, flags_out, prep_err);
+  solve_tmem_release<kTm>(tmem);
 }
 
 // ---------------------------------------------------------------- direct form, up to 4 layers
@@ -880,7 +986,7 @@ __global__ void __launch_bounds__(kPrepThreads)
 // jobs; one mbarrier per CTA counts every item's Gram-block copies, item i completing phase
 // i mod 2. The modulation is each job's own (run-time QM).
 template <int NL>
-__global__ void __launch_bounds__(kSolveThreads)
+__global__ void __launch_bounds__(kSolveThreads, solve_min_ctas(NL, kSolveThreads))
     re_solve_batch_kernel(const BatchTable* __restrict__ t, int smem_bytes) {
   extern __shared__ __align__(128) unsigned char solve_smem[];
   __shared__ Geo sg;
@@ -894,7 +1000,9 @@ __global__ void __launch_bounds__(kSolveThreads)
     tc::mbar_fence_init();
   }
   batch_index_load(ix, t, kBatchSolve, cls);
-  __syncthreads();
+  constexpr bool kTm = solve_uses_tmem(NL, kSolveThreads);
+  const uint32_t tmem =
+      solve_tmem_acquire<kTm>(reinterpret_cast<uint32_t*>(solve_smem + smem_bytes - 8));
   uint32_t it = 0;
   for (int w = blockIdx.x; w < n; w += gridDim.x, ++it) {
     int local;
@@ -905,11 +1013,12 @@ __global__ void __launch_bounds__(kSolveThreads)
     __syncthreads();
     const int nb = (sg.n_sc + kSolveThreads - 1) / kSolveThreads;
     const int bx = local % nb, jj = (local / nb) % sg.n_dsym, lc = local / (nb * sg.n_dsym);
-    const bool usable = re_solve_body<NL, 0>(sg, 0, bx, jj, lc, bar, it & 1, J.ygg, J.bvec,
+    const bool usable = re_solve_body<NL, 0>(sg, 0, bx, jj, lc, bar, it & 1, tmem, J.ygg, J.bvec,
                                              J.sigma2, J.anchors, J.Y, J.x_hat, J.sinr, J.llr,
                                              J.flags, J.err);
     if (!__syncthreads_and(usable)) break;  // copies still in flight: the barrier is unusable
   }
+  solve_tmem_release<kTm>(tmem);
 }
 
 struct Sizes {
@@ -949,6 +1058,21 @@ size_t scratch_bytes(const Sizes& s, int chunk) {
   return 256 + align256(s.ygg_per_cell * chunk) + align256(s.b_per_cell * chunk);
 }
 
+// Shared-memory carveout (percent of the SM's maximum) that holds min_ctas CTAs of `smem` bytes
+// (plus the 1 KB the runtime reserves per CTA): the rest of the SM's on-chip memory stays L1
+// cache, which holds the register spills of the 12-warp form. Shared-memory-bound forms take all.
+int solve_carveout(size_t smem, int min_ctas) {
+  if (min_ctas <= 1) return 100;
+  static int per_sm[kMaxDevices] = {};
+  int& cap = per_sm[current_device()];
+  if (cap == 0 && (cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerMultiprocessor,
+                                          current_device()) != cudaSuccess ||
+                   cap <= 0))
+    cap = 228 * 1024;
+  const size_t need = (size_t)min_ctas * (smem + 1024);
+  return std::min(100, (int)((100 * need + cap - 1) / cap) + kSolveCarveoutSlack);
+}
+
 template <int NL, int QM, int W>
 cudaError_t launch_solve_w(const Geo& g, int c0, int nc, const float4* ygg, const cf* bvec,
                            const float* sigma2, const phy_c32* anchors, const phy_c32* Y,
@@ -958,12 +1082,13 @@ cudaError_t launch_solve_w(const Geo& g, int c0, int nc, const float4* ygg, cons
   const size_t smem = solve_smem_bytes(NL, QM, max_segs, W);
   static size_t configured_on[kMaxDevices] = {};
   size_t& configured = configured_on[current_device()];
-  if (smem > 48 * 1024 && smem > configured) {
+  if (smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(re_solve_fp32_kernel<NL, QM, W>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(re_solve_fp32_kernel<NL, QM, W>,
-                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                             solve_carveout(smem, solve_min_ctas(NL, W)));
     if (e != cudaSuccess) return e;
     configured = smem;
   }
@@ -1113,6 +1238,8 @@ BatchClassLaunch batch_class_launch() {
                        (int)b.smem_seg);
   cudaFuncSetAttribute(re_solve_batch_kernel<NL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)b.smem_solve);
+  cudaFuncSetAttribute(re_solve_batch_kernel<NL>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       solve_carveout(b.smem_solve, solve_min_ctas(NL, kSolveThreads)));
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, seg_prep_batch_kernel<NL>, kPrepThreads,
                                                     b.smem_seg) != cudaSuccess || occ < 1)
     occ = 1;

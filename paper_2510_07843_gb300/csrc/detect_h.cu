@@ -15,6 +15,24 @@ struct LocalScratch {
   __device__ __forceinline__ cf ld(int e) const { return base[e]; }
 };
 
+// The solver's 8x8 L21/T matrix in the same thread-local array, entry (i, j) at 8 i + j.
+struct LocalRows {
+  cf* base;
+  __device__ __forceinline__ void st_row(int i, const cf (&r)[8]) const {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) base[8 * i + j] = r[j];
+  }
+  __device__ __forceinline__ void ld_row(int i, cf (&r)[8]) const {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) r[j] = base[8 * i + j];
+  }
+  __device__ __forceinline__ void ld_col(int c, cf (&r)[8]) const {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) r[i] = base[8 * i + c];
+  }
+  __device__ __forceinline__ void sync_st() const {}
+};
+
 template <int NL>
 __global__ void __launch_bounds__(128) detect_h_kernel(Geo g, const phy_c32* __restrict__ H,
                                                        const phy_c32* __restrict__ Y,
@@ -73,7 +91,7 @@ __global__ void __launch_bounds__(128) detect_h_kernel(Geo g, const phy_c32* __r
 #pragma unroll
           for (int k = 0; k < 8; ++k) row[k] = a[tri(li, k)];
     };
-    si = solve16(getA, rowA, LocalScratch{scratch}, b, x, dd);
+    si = solve16(getA, rowA, LocalScratch{scratch + kScrV}, LocalRows{scratch + kScrL21}, b, x, dd);
   } else {
     si = solve_small<NL>(getA, b, x, dd);
   }

@@ -10,9 +10,9 @@
 // Up to 8 layers the packed lower triangle lives in registers. For 9..16 layers the matrix is
 // split into 8x8 blocks, A = [A11 A12; A21 A22]:
 //   L11 = chol(A11), M = L11^-1, L21 = A21 M^H, S = A22 - L21 L21^H, L22 = chol(S), N = L22^-1,
-//   L^-1 = [M 0; -N L21 M  N],
-// so z = L^-1 b = [M b1; N (b2 - L21 z1)], x = L^-H z = [M^H (z1 - L21^H x2); N^H z2], and the
-// column norms of L^-1 give d: block 2 from N, block 1 from M and N T with T = L21 M.
+//   L^-1 = [M 0; -N T  N] with T = L21 M,
+// so z = L^-1 b = [M b1; N (b2 - L21 z1)], x = L^-H z = [M^H z1 - T^H x2; N^H z2], and the
+// column norms of L^-1 give d: block 2 from N, block 1 from M and N T.
 #pragma once
 
 #include "common.cuh"
@@ -142,18 +142,24 @@ __device__ __forceinline__ SolveInfo solve_small(GetA getA, const cf (&b)[N], cf
   return si;
 }
 
-// 9..16 layers: two 8x8 blocks. Scr is a thread-private scratch of kScrSlots complex values
-// (ld(e) / st(e, v)) holding L21 (later overwritten by T = L21 M) and two 8-vectors. M and the
-// Schur factor stay in registers. The large repeated pieces (rows of L21 and T, the Schur
-// update, the columns of N T) are runtime loops over small unrolled bodies: the kernel's code
-// then fits the instruction cache, which the fully unrolled form did not.
+// 9..16 layers: two 8x8 blocks. The thread's 8x8 L21 (later overwritten by T = L21 M) lives
+// off registers in `rows`, which stores and loads it a row or a column at a time
+// (st_row(i, r) / ld_row(i, r) / ld_col(c, col), then sync_st() once a pass of stores must be
+// visible to the next pass's loads), and an 8-vector lives in the thread-private scratch `vs`
+// (ld(e) / st(e, v), e < 8). M and the Schur complement are in registers, but never both
+// factored at once: everything that needs M (L21, T, M^H z1, the column norms of M) is done
+// before the Schur complement is factored, so M is dead by then and x1 comes from T as
+// x1 = M^H z1 - T^H x2. The large repeated pieces (rows of L21 and T, the Schur update, the
+// columns of N T) are runtime loops over small unrolled bodies: the kernel's code then fits the
+// instruction cache, which the fully unrolled form did not. Every thread of a warp must take
+// part (the tensor-memory form of `rows` is warp-collective).
 constexpr int kScrL21 = 0, kScrV = 64, kScrSlots = 72;
 
 // rowA(l, row) fills row[k] = A(l, k), k = 0..7, for a row l >= 8 known only at run time (the
 // runtime-row form of getA, for the rolled L21 loop).
-template <class GetA, class RowA, class Scr>
-__device__ __forceinline__ SolveInfo solve16(GetA getA, RowA rowA, Scr scr, const cf (&b)[16],
-                                             cf (&x)[16], float (&d)[16]) {
+template <class GetA, class RowA, class Vec, class Rows>
+__device__ __forceinline__ SolveInfo solve16(GetA getA, RowA rowA, Vec vs, Rows rows,
+                                             const cf (&b)[16], cf (&x)[16], float (&d)[16]) {
   constexpr int B = 8;
   SolveInfo si{true, true, 3.0e38f, 0.f};
   // ---- block 1: L11, z1 = L11^-1 b1, M = L11^-1
@@ -168,7 +174,7 @@ __device__ __forceinline__ SolveInfo solve16(GetA getA, RowA rowA, Scr scr, cons
 #pragma unroll
   for (int i = 0; i < B; ++i) {
     b1[i] = b[i];
-    scr.st(kScrV + i, b[B + i]);
+    vs.st(i, b[B + i]);
   }
   fwd_packed<B>(m, r1, b1, z1);
   inv_packed<B>(m, r1);
@@ -176,21 +182,36 @@ __device__ __forceinline__ SolveInfo solve16(GetA getA, RowA rowA, Scr scr, cons
   // ---- L21 = A21 M^H row by row; v = b2 - L21 z1
 #pragma unroll 1
   for (int i = 0; i < B; ++i) {
-    cf row[B];
+    cf row[B], l21[B];
     rowA(B + i, row);
-    cf acc = scr.ld(kScrV + i), acc2 = mk(0.f, 0.f);
+    cf acc = vs.ld(i), acc2 = mk(0.f, 0.f);
 #pragma unroll
     for (int j = 0; j < B; ++j) {
       cf l = mk(0.f, 0.f);
 #pragma unroll
       for (int k = 0; k <= j; ++k) l = cfma_cj(M(j, k), row[k], l);  // row[k] conj(M[j][k])
-      scr.st(kScrL21 + i * B + j, l);
+      l21[j] = l;
       if (j & 1)
         acc2 = cfms(l, z1[j], acc2);
       else
         acc = cfms(l, z1[j], acc);
     }
-    scr.st(kScrV + i, acc + acc2);
+    rows.st_row(i, l21);
+    vs.st(i, acc + acc2);
+  }
+  rows.sync_st();
+  // ---- w = M^H z1, and the column norms of M (the first part of d for block 1)
+  cf w[B];
+#pragma unroll
+  for (int i = 0; i < B; ++i) {
+    cf acc = mk(0.f, 0.f);
+    float s1 = r1[i] * r1[i];
+#pragma unroll
+    for (int k = i; k < B; ++k) acc = cfma_cj(M(k, i), z1[k], acc);
+#pragma unroll
+    for (int k = i + 1; k < B; ++k) s1 += cabs2(M(k, i));
+    w[i] = acc;
+    d[i] = s1;
   }
   // ---- S = A22 - L21 L21^H
   cf s[B * (B + 1) / 2];
@@ -201,76 +222,70 @@ __device__ __forceinline__ SolveInfo solve16(GetA getA, RowA rowA, Scr scr, cons
 #pragma unroll 1
   for (int c = 0; c < B; ++c) {
     cf col[B];
-#pragma unroll
-    for (int i = 0; i < B; ++i) col[i] = scr.ld(kScrL21 + i * B + c);
+    rows.ld_col(c, col);
 #pragma unroll
     for (int i = 0; i < B; ++i)
 #pragma unroll
       for (int j = 0; j <= i; ++j) s[tri(i, j)] = cfms_cjb(col[i], col[j], s[tri(i, j)]);
   }
-  float r2[B];
-  si.ok = chol_packed<B>(s, r2, si.pmin, si.pmax, si.fin) && si.ok;
-  cf v[B], z2[B], x2[B];
-#pragma unroll
-  for (int i = 0; i < B; ++i) v[i] = scr.ld(kScrV + i);
-  fwd_packed<B>(s, r2, v, z2);
-  bwd_packed<B>(s, r2, z2, x2);
-  inv_packed<B>(s, r2);
-  auto Nn = [&](int i, int j) -> cf { return (i == j) ? mk(r2[i], 0.f) : s[tri(i, j)]; };
-  // ---- x1 = M^H (z1 - L21^H x2)
-  cf u[B];
-#pragma unroll
-  for (int j = 0; j < B; ++j) u[j] = z1[j];
-#pragma unroll
-  for (int i = 0; i < B; ++i) {
-#pragma unroll
-    for (int j = 0; j < B; ++j) {
-      // u_j -= conj(L21_ij) x2_i
-      const cf l = scr.ld(kScrL21 + i * B + j);
-      u[j].x = fmaf(-l.x, x2[i].x, u[j].x);
-      u[j].x = fmaf(-l.y, x2[i].y, u[j].x);
-      u[j].y = fmaf(-l.x, x2[i].y, u[j].y);
-      u[j].y = fmaf(l.y, x2[i].x, u[j].y);
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < B; ++i) {
-    cf acc = mk(0.f, 0.f);
-#pragma unroll
-    for (int k = i; k < B; ++k) acc = cfma_cj(M(k, i), u[k], acc);
-    x[i] = acc;
-    x[B + i] = x2[i];
-  }
-  // ---- diagonal of A^-1. Block 2: column norms of N. Block 1: column norms of M plus those
-  // of N T, T = L21 M (row i of T from row i of L21, written over it).
-#pragma unroll
-  for (int c = 0; c < B; ++c) {
-    float s2 = 0.f, s1 = r1[c] * r1[c];
-#pragma unroll
-    for (int i = c; i < B; ++i) s2 += cabs2(Nn(i, c));
-#pragma unroll
-    for (int i = c + 1; i < B; ++i) s1 += cabs2(M(i, c));
-    d[B + c] = s2;
-    d[c] = s1;
-  }
+  // ---- T = L21 M, row i of T from row i of L21, written over it (M is dead after this)
 #pragma unroll 1
   for (int i = 0; i < B; ++i) {
-    cf row[B];
-#pragma unroll
-    for (int k = 0; k < B; ++k) row[k] = scr.ld(kScrL21 + i * B + k);
+    cf row[B], trow[B];
+    rows.ld_row(i, row);
 #pragma unroll
     for (int c = 0; c < B; ++c) {
       cf acc = mk(0.f, 0.f);
 #pragma unroll
       for (int k = c; k < B; ++k) acc = cfma(row[k], M(k, c), acc);
-      scr.st(kScrL21 + i * B + c, acc);
+      trow[c] = acc;
     }
+    rows.st_row(i, trow);
+  }
+  rows.sync_st();
+  // ---- block 2: L22 = chol(S), z2 = L22^-1 v, x2 = L22^-H z2, N = L22^-1
+  float r2[B];
+  si.ok = chol_packed<B>(s, r2, si.pmin, si.pmax, si.fin) && si.ok;
+  cf v[B], z2[B], x2[B];
+#pragma unroll
+  for (int i = 0; i < B; ++i) v[i] = vs.ld(i);
+  fwd_packed<B>(s, r2, v, z2);
+  bwd_packed<B>(s, r2, z2, x2);
+  inv_packed<B>(s, r2);
+  auto Nn = [&](int i, int j) -> cf { return (i == j) ? mk(r2[i], 0.f) : s[tri(i, j)]; };
+  // ---- x1 = w - T^H x2
+#pragma unroll
+  for (int i = 0; i < B; ++i) {
+    cf row[B];
+    rows.ld_row(i, row);
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      // w_j -= conj(T_ij) x2_i
+      const cf t = row[j];
+      w[j].x = fmaf(-t.x, x2[i].x, w[j].x);
+      w[j].x = fmaf(-t.y, x2[i].y, w[j].x);
+      w[j].y = fmaf(-t.x, x2[i].y, w[j].y);
+      w[j].y = fmaf(t.y, x2[i].x, w[j].y);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < B; ++i) {
+    x[i] = w[i];
+    x[B + i] = x2[i];
+  }
+  // ---- diagonal of A^-1. Block 2: column norms of N. Block 1: those of M (above) plus those
+  // of N T.
+#pragma unroll
+  for (int c = 0; c < B; ++c) {
+    float s2 = 0.f;
+#pragma unroll
+    for (int i = c; i < B; ++i) s2 += cabs2(Nn(i, c));
+    d[B + c] = s2;
   }
 #pragma unroll 1
   for (int c = 0; c < B; ++c) {
     cf t[B];
-#pragma unroll
-    for (int i = 0; i < B; ++i) t[i] = scr.ld(kScrL21 + i * B + c);
+    rows.ld_col(c, t);
     float acc2 = 0.f;
 #pragma unroll
     for (int i = 0; i < B; ++i) {  // (N t)_i
