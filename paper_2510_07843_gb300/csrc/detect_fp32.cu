@@ -371,20 +371,23 @@ struct TmemRows {
 // Gram-block bytes of one (segment, data symbol): NTRI 4-tuples of complex values.
 constexpr uint32_t gram_block_bytes(int NL) { return (uint32_t)(NL * (NL + 1) / 2) * 32u; }
 
-// 9..16 layers with 128-RE CTAs keep the solver's L21/T matrices in tensor memory (128 columns
-// per CTA; this kernel issues no MMAs), which leaves shared memory to the Gram blocks and one
-// 8-vector per thread: three CTAs (12 warps) fit an SM where the shared-memory form fits two.
-// 64-RE CTAs keep the shared-memory form.
+// The single-job solve with 9..16 layers and 128-RE CTAs keeps the solver's L21/T matrices in
+// tensor memory (128 columns per CTA; this kernel issues no MMAs), which leaves shared memory to
+// the Gram blocks and one 8-vector per thread: three CTAs (12 warps) fit an SM where the
+// shared-memory form fits two. 64-RE CTAs keep the shared-memory form, and so does the batched
+// solve: its persistent CTAs would hold tensor memory on every SM for the whole launch, while
+// the other layer classes' tensor-core kernels, running next to it on forked streams, need 512
+// columns of an SM at once (measured: a mixed serving batch lost more time waiting for those
+// allocations than the faster solve gained).
 constexpr bool solve_uses_tmem(int NL, int W) { return NL == 16 && W == 128; }
 constexpr uint32_t kSolveTmemCols = 128;
 constexpr int kSolveCarveoutSlack = 2;  // percent above the exact need
-constexpr int solve_min_ctas(int NL, int W) { return solve_uses_tmem(NL, W) ? 3 : 1; }
+constexpr int solve_min_ctas(bool tm) { return tm ? 3 : 1; }
 
-// The solve kernel's CTA width W (REs per CTA) is a tile shape the autotuner picks: 128 or 64.
-constexpr size_t solve_scratch_bytes(int NL, int W = kSolveThreads) {
-  return NL != 16                  ? 0
-         : solve_uses_tmem(NL, W) ? (size_t)8 * W * sizeof(cf)
-                                  : (size_t)kScrSlots * W * sizeof(cf);
+// The solve kernel's CTA width W (REs per CTA) is a tile shape the autotuner picks: 128 or 64;
+// tm selects the tensor-memory form.
+constexpr size_t solve_scratch_bytes(int NL, int W, bool tm) {
+  return NL != 16 ? 0 : tm ? (size_t)8 * W * sizeof(cf) : (size_t)kScrSlots * W * sizeof(cf);
 }
 
 // 9..16 layers: after the solve, shared memory holds every thread's x and d in RE-major tables
@@ -397,8 +400,8 @@ constexpr size_t solve_stage_bytes(int W = kSolveThreads) {
 // 9..16 layers at least the epilogue's tables), then the mbarrier and the tensor-memory address
 // in the last 16 bytes, which the tables never reach.
 __host__ __device__ constexpr size_t solve_smem_bytes(int NL, int QM, int max_segs,
-                                                      int W = kSolveThreads) {
-  const size_t main = solve_scratch_bytes(NL, W) + (size_t)max_segs * gram_block_bytes(NL);
+                                                      int W = kSolveThreads, bool tm = false) {
+  const size_t main = solve_scratch_bytes(NL, W, tm) + (size_t)max_segs * gram_block_bytes(NL);
   const size_t stage = NL == 16 ? solve_stage_bytes(W) : 0;
   return (main > stage ? main : stage) + 16;
 }
@@ -478,10 +481,10 @@ __device__ __forceinline__ void demap_store_q(int qm, float* llr, size_t li, cf 
 // (512 B apart) would keep each warp waiting on the store path.
 // Work item (128 subcarriers from k0 = bx 128, data symbol jj, cell lc of the chunk starting at
 // cell0). The barrier `bar` is initialised and its phase `parity` is the one this item's copies
-// complete; `tmem` is the CTA's tensor-memory allocation when solve_uses_tmem(NL, W). QM = 0
+// complete; `tmem` is the CTA's tensor-memory allocation in the tensor-memory form TM. QM = 0
 // takes the modulation from g.qm. Returns false if the Gram-block copies did not land even after
 // a timeout's second wait (the barrier is then unusable for a later item).
-template <int NL, int QM, int W = kSolveThreads>
+template <int NL, int QM, int W = kSolveThreads, bool TM = false>
 __device__ __forceinline__ bool re_solve_body(
     const Geo& g, int cell0, int bx, int jj, int lc, uint64_t* bar, uint32_t parity, uint32_t tmem,
     const float4* __restrict__ ygg, const cf* __restrict__ bvec,
@@ -492,7 +495,7 @@ __device__ __forceinline__ bool re_solve_body(
   constexpr int NTRI = NL * (NL + 1) / 2;
   constexpr uint32_t kBlk = gram_block_bytes(NL);
   extern __shared__ __align__(128) unsigned char solve_smem[];
-  float4* ys = reinterpret_cast<float4*>(solve_smem + solve_scratch_bytes(NL, W));
+  float4* ys = reinterpret_cast<float4*>(solve_smem + solve_scratch_bytes(NL, W, TM));
   const int nl = g.n_layers, nds = g.n_dsym;
   const int qm = QM > 0 ? QM : g.qm;
   const int cell = cell0 + lc;
@@ -601,7 +604,7 @@ __device__ __forceinline__ bool re_solve_body(
         }
       };
       cf* sb = reinterpret_cast<cf*>(solve_smem) + threadIdx.x;
-      if constexpr (solve_uses_tmem(NL, W)) {
+      if constexpr (TM) {
         // the warp's lane quarter of the allocation: lane field 32 (warp mod 4) << 16
         const TmemRows rows{tmem + (((threadIdx.x >> 5) & 3u) << 21)};
         si = solve16(getA, rowA, SmemScratch<W>{sb}, rows, b, x, dd);
@@ -686,7 +689,7 @@ __device__ __forceinline__ bool re_solve_body(
   return true;
 }
 
-// The CTA's tensor memory for the solver (solve_uses_tmem): warp 0 allocates kSolveTmemCols
+// The CTA's tensor memory for the solver (the TM form): warp 0 allocates kSolveTmemCols
 // columns into *slot before the CTA's first barrier, and releases them after its last one.
 template <bool kTm>
 __device__ __forceinline__ uint32_t solve_tmem_acquire(uint32_t* slot) {
@@ -714,7 +717,7 @@ __device__ __forceinline__ void solve_tmem_release(uint32_t tmem) {
 }
 
 template <int NL, int QM, int W>
-__global__ void __launch_bounds__(W, solve_min_ctas(NL, W))
+__global__ void __launch_bounds__(W, solve_min_ctas(solve_uses_tmem(NL, W)))
     re_solve_fp32_kernel(Geo g, int cell0, int max_segs, const float4* __restrict__ ygg,
                          const cf* __restrict__ bvec, const float* __restrict__ sigma2,
                          const phy_c32* __restrict__ anchors, const phy_c32* __restrict__ Y,
@@ -722,15 +725,15 @@ __global__ void __launch_bounds__(W, solve_min_ctas(NL, W))
                          float* __restrict__ llr_out, uint8_t* __restrict__ flags_out,
                          const unsigned* __restrict__ prep_err) {
   extern __shared__ __align__(128) unsigned char solve_smem[];
-  unsigned char* top = solve_smem + solve_smem_bytes(NL, QM, max_segs, W);
+  constexpr bool kTm = solve_uses_tmem(NL, W);
+  unsigned char* top = solve_smem + solve_smem_bytes(NL, QM, max_segs, W, kTm);
   uint64_t* bar = reinterpret_cast<uint64_t*>(top - 16);
   if (threadIdx.x == 0) {
     tc::mbar_init(bar, 1);
     tc::mbar_fence_init();
   }
-  constexpr bool kTm = solve_uses_tmem(NL, W);
   const uint32_t tmem = solve_tmem_acquire<kTm>(reinterpret_cast<uint32_t*>(top - 8));
-  re_solve_body<NL, QM, W>(g, cell0, blockIdx.x, blockIdx.y, blockIdx.z, bar, 0, tmem, ygg, bvec,
+  re_solve_body<NL, QM, W, kTm>(g, cell0, blockIdx.x, blockIdx.y, blockIdx.z, bar, 0, tmem, ygg, bvec,
                            sigma2, anchors, Y, x_hat, sinr_out, llr_out, flags_out, prep_err);
   solve_tmem_release<kTm>(tmem);
 }
@@ -986,7 +989,7 @@ __global__ void __launch_bounds__(kPrepThreads)
 // jobs; one mbarrier per CTA counts every item's Gram-block copies, item i completing phase
 // i mod 2. The modulation is each job's own (run-time QM).
 template <int NL>
-__global__ void __launch_bounds__(kSolveThreads, solve_min_ctas(NL, kSolveThreads))
+__global__ void __launch_bounds__(kSolveThreads)
     re_solve_batch_kernel(const BatchTable* __restrict__ t, int smem_bytes) {
   extern __shared__ __align__(128) unsigned char solve_smem[];
   __shared__ Geo sg;
@@ -1000,9 +1003,7 @@ __global__ void __launch_bounds__(kSolveThreads, solve_min_ctas(NL, kSolveThread
     tc::mbar_fence_init();
   }
   batch_index_load(ix, t, kBatchSolve, cls);
-  constexpr bool kTm = solve_uses_tmem(NL, kSolveThreads);
-  const uint32_t tmem =
-      solve_tmem_acquire<kTm>(reinterpret_cast<uint32_t*>(solve_smem + smem_bytes - 8));
+  __syncthreads();
   uint32_t it = 0;
   for (int w = blockIdx.x; w < n; w += gridDim.x, ++it) {
     int local;
@@ -1013,12 +1014,11 @@ __global__ void __launch_bounds__(kSolveThreads, solve_min_ctas(NL, kSolveThread
     __syncthreads();
     const int nb = (sg.n_sc + kSolveThreads - 1) / kSolveThreads;
     const int bx = local % nb, jj = (local / nb) % sg.n_dsym, lc = local / (nb * sg.n_dsym);
-    const bool usable = re_solve_body<NL, 0>(sg, 0, bx, jj, lc, bar, it & 1, tmem, J.ygg, J.bvec,
+    const bool usable = re_solve_body<NL, 0>(sg, 0, bx, jj, lc, bar, it & 1, 0, J.ygg, J.bvec,
                                              J.sigma2, J.anchors, J.Y, J.x_hat, J.sinr, J.llr,
                                              J.flags, J.err);
     if (!__syncthreads_and(usable)) break;  // copies still in flight: the barrier is unusable
   }
-  solve_tmem_release<kTm>(tmem);
 }
 
 struct Sizes {
@@ -1079,7 +1079,7 @@ cudaError_t launch_solve_w(const Geo& g, int c0, int nc, const float4* ygg, cons
                            phy_c32* x_hat, float* sinr, float* llr, uint8_t* flags,
                            const unsigned* err, cudaStream_t st) {
   const int max_segs = max_segments_per_block(g, W);
-  const size_t smem = solve_smem_bytes(NL, QM, max_segs, W);
+  const size_t smem = solve_smem_bytes(NL, QM, max_segs, W, solve_uses_tmem(NL, W));
   static size_t configured_on[kMaxDevices] = {};
   size_t& configured = configured_on[current_device()];
   if (smem > configured) {
@@ -1088,7 +1088,7 @@ cudaError_t launch_solve_w(const Geo& g, int c0, int nc, const float4* ygg, cons
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(re_solve_fp32_kernel<NL, QM, W>,
                              cudaFuncAttributePreferredSharedMemoryCarveout,
-                             solve_carveout(smem, solve_min_ctas(NL, W)));
+                             solve_carveout(smem, solve_min_ctas(solve_uses_tmem(NL, W))));
     if (e != cudaSuccess) return e;
     configured = smem;
   }
@@ -1238,8 +1238,6 @@ BatchClassLaunch batch_class_launch() {
                        (int)b.smem_seg);
   cudaFuncSetAttribute(re_solve_batch_kernel<NL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)b.smem_solve);
-  cudaFuncSetAttribute(re_solve_batch_kernel<NL>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                       solve_carveout(b.smem_solve, solve_min_ctas(NL, kSolveThreads)));
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, seg_prep_batch_kernel<NL>, kPrepThreads,
                                                     b.smem_seg) != cudaSuccess || occ < 1)
     occ = 1;
