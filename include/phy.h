@@ -21,6 +21,13 @@
  *  - Arguments are validated on the host before anything is enqueued. A failed validation
  *    returns PHY_ERR_INVALID_ARG (bad sizes or pointers) or PHY_ERR_UNSUPPORTED (a valid but
  *    unimplemented shape) and enqueues nothing. A CUDA launch error returns PHY_ERR_CUDA.
+ *  - Some kernels use the SM's tensor memory (TMEM): the tensor-core segment kernels and the
+ *    denoiser's tensor-core forward pass for their accumulators, and the 9..16-layer solve of
+ *    phy_slot_run / phy_detect_stage (128-subcarrier CTAs) for per-RE scratch, each CTA
+ *    allocating at start and releasing before it ends. Another kernel that allocates tensor
+ *    memory and runs at the same time on another stream (the caller's, or this library's on
+ *    another stream) may wait for those columns. No kernel of this library waits for another
+ *    kernel while it holds tensor memory, so this can delay work but not deadlock it.
  *  - Numerical trouble is data, not an error: it is reported per RE in `flags`
  *    (bit 0: ill-conditioned Gram matrix, Cholesky pivot ratio below cfg.pivot_ratio_min or a
  *    non-positive pivot; bit 1: RE re-computed in FP64; bit 2: non-finite input). An RE whose

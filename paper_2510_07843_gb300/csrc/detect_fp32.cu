@@ -14,8 +14,9 @@
 //  seg_prep_fp32_kernel: one CTA per (segment, cell). Corners to shared memory, X (lower 4x4
 //    tiles), the four Y_gg' blocks per data symbol (lower triangle, 4-tuples) to the workspace,
 //    and the matched filter per symbol from a shared-memory Y tile (cp.async double buffer).
-//  re_solve_fp32_kernel: one thread per data RE, no barriers. Builds A from the 4-tuples,
-//    solves (solver.cuh), SINR, unbiasing, max-log LLRs, stores.
+//  re_solve_fp32_kernel: one thread per data RE. Builds A from the 4-tuples (bulk-copied to
+//    shared memory), solves (solver.cuh; with 9..16 layers the per-thread L21/T block in tensor
+//    memory), SINR, unbiasing, max-log LLRs, stores staged through shared memory.
 // The two kernels run per chunk of cells so that the intermediates stay small (L2-sized).
 #include <algorithm>
 #include <cstdlib>
