@@ -533,26 +533,37 @@ class BatchServer:
 
     def _take(self, waiting: "collections.deque", busy=frozenset()) -> List["MixedJob"]:
         """The arrival-order jobs that fit one lane: up to max_jobs and the arena's bytes. A job
-        that tracks its noise level waits (keeping its place) while a batch in flight, or an
-        earlier job of this batch, updates the same state: one cell's slots then update its
-        state in arrival order."""
+        that tracks its noise level waits (keeping its place) while an earlier job of this batch
+        updates the same state, or a batch in flight does (`busy`): one cell's slots then update
+        its state in arrival order. When every waiting job waits on a batch in flight, they form
+        a batch anyway, and run() starts it on the GPU after those batches (the lanes' streams
+        are chained) instead of waiting for them on the host."""
         batch, used, states, skipped = [], 0, set(busy), []
-        while waiting and len(batch) < self.max_jobs:
-            j = waiting[0]
-            st = j._addr[3]
-            if st is not None and st in states:
-                skipped.append(waiting.popleft())
-                continue
-            b = self.job_bytes(j.cfg)
-            if b > self.arena_bytes:
-                raise ValueError(f"job {j.job_id} needs {b} bytes, above the arena")
-            if used + b + _ALIGN > self.arena_bytes:
-                break
-            used += b
-            if st is not None:
-                states.add(st)
-            batch.append(waiting.popleft())
-        waiting.extendleft(reversed(skipped))
+
+        def fill():
+            nonlocal used
+            while waiting and len(batch) < self.max_jobs:
+                j = waiting[0]
+                st = j._addr[3]
+                if st is not None and st in states:
+                    skipped.append(waiting.popleft())
+                    continue
+                b = self.job_bytes(j.cfg)
+                if b > self.arena_bytes:
+                    raise ValueError(f"job {j.job_id} needs {b} bytes, above the arena")
+                if used + b + _ALIGN > self.arena_bytes:
+                    break
+                used += b
+                if st is not None:
+                    states.add(st)
+                batch.append(waiting.popleft())
+            waiting.extendleft(reversed(skipped))
+            skipped.clear()
+
+        fill()
+        if not batch and busy:  # all waiting on batches in flight: chain on the GPU
+            states.clear()
+            fill()
         return batch
 
     def run(self, jobs: Sequence["MixedJob"], realtime: bool = True,
@@ -605,17 +616,20 @@ class BatchServer:
                 retire(True)
             busy = frozenset(j._addr[3] for f in inflight for j in f[3] if j._addr[3] is not None)
             batch = self._take(waiting, busy)
-            if not batch:  # every waiting job waits for a state in flight
-                if not inflight:
-                    raise ValueError(f"job {waiting[0].job_id} does not fit a lane's arena")
-                retire(True)
-                continue
+            if not batch:
+                raise ValueError(f"job {waiting[0].job_id} does not fit a lane's arena")
+            # the latest batch in flight that updates each noise state this batch reads
+            last = {j._addr[3]: f[2] for f in inflight for j in f[3] if j._addr[3] is not None}
+            deps = {id(e): e for e in (last.get(j._addr[3]) for j in batch
+                                       if j._addr[3] is not None) if e is not None}
             li = free.pop(0)
             ln = self.lanes[li]
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             h0 = self.clock()
             ln.post(batch, self._layout)
             self.host_post.append(self.clock() - h0)
+            for e in deps.values():  # ordered on the GPU, not by the host
+                ln.stream.wait_event(e)
             e0.record(ln.stream)
             with torch.cuda.stream(ln.stream):
                 ln.graph.replay()

@@ -250,9 +250,11 @@ def test_noise_tracking_in_the_batch_equals_slot_run_track(dev):
 
 
 def test_batch_server_tracks_each_cells_noise_in_arrival_order(dev):
-    """Four cells, three slots each, every job tracking its cell's noise level: the server never
-    puts two slots of one cell in one batch or in two batches in flight, so each cell's state
-    follows its slots in arrival order; outputs and final states equal per-cell sequences of
+    """Four cells, three slots each, all arriving at once, every job tracking its cell's noise
+    level: the server never puts two slots of one cell in one batch, and a batch holding a
+    cell's later slot starts on the GPU only after the batch in flight with its earlier slot
+    (the lanes' streams are chained, the host does not wait), so each cell's state follows its
+    slots in arrival order; outputs and final states equal per-cell sequences of
     phy_slot_run_track."""
     import torch
     from paper_2510_07843_gb300 import phy, serve
