@@ -406,8 +406,10 @@ def main():
                     help="headline without the FP64 re-computation of flagged REs")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle timing")
     ap.add_argument("--llr", default="f32", choices=["f32", "f16"], help="LLR output format")
-    ap.add_argument("--streams", type=int, default=2,
-                    help="streams the timed steps alternate over (1: strictly serial)")
+    ap.add_argument("--streams", type=int, default=4,
+                    help="streams the pipelined steps rotate over (1: strictly serial)")
+    ap.add_argument("--serving-lanes", type=int, default=2,
+                    help="slot batches the serving run keeps in flight")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop latency run")
     ap.add_argument("--no-noise", action="store_true",
@@ -816,8 +818,9 @@ def time_variant(spec, precision, refactor, llr, args, slot, dev, world, fl_peak
 
     Serial pass: every step's stages bracketed by CUDA events on the launch stream (per-stage
     times, step latency p50/p99, per-kernel rooflines). Pipelined pass (the throughput): the
-    steps alternate over `args.streams` streams with their own buffers, so one step's solve
-    overlaps the next step's estimation and Gram kernels, as a continuous stream of slots runs.
+    steps rotate over `args.streams` streams (default four) with their own buffers, so one
+    step's solve overlaps the next steps' estimation and Gram kernels, as a continuous stream of
+    slots runs.
     Returns the variant's record and its buffers."""
     import torch
     from paper_2510_07843_gb300 import phy
@@ -1160,7 +1163,7 @@ def run_ours(args, spec, rank, world, local):
     serving = None
     if not args.no_serving:
         serving = serving_run(spec, args.precision, dev, buf, llr=args.llr,
-                              streams=args.streams)
+                              streams=args.serving_lanes)
 
     serving_mixed = None
     if not args.no_serving:
