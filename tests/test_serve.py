@@ -244,3 +244,37 @@ def test_batch_records_match_the_ctypes_jobs():
     spans.sort()
     assert all(b[0] >= a[1] for a, b in zip(spans, spans[1:])) and spans[-1][1] <= end
     assert ctypes.sizeof(phy.CJob) == phy.JOB_BYTES
+
+
+def test_batch_forming_defers_jobs_whose_noise_state_is_busy():
+    """BatchServer._take, the host logic that keeps one cell's noise-state updates in arrival
+    order: no two jobs of one state in a batch; jobs whose state a batch in flight updates wait
+    (keeping their places) while independent jobs go; and when every waiting job waits, they
+    form a batch anyway (run() then chains it on the GPU after the batches in flight)."""
+    import collections
+
+    class _Job:
+        def __init__(self, job_id, state):
+            self.job_id, self.cfg = job_id, None
+            self._addr = (0, 0, 0, state, 0.5, 0)
+
+    srv = serve.BatchServer.__new__(serve.BatchServer)  # the batch-forming state only
+    srv.max_jobs, srv.arena_bytes = 4, 1 << 30
+    srv.job_bytes = lambda cfg: 1 << 10
+
+    def take(states, busy=frozenset()):
+        waiting = collections.deque(_Job(i, s) for i, s in enumerate(states))
+        batch = srv._take(waiting, frozenset(busy))
+        return [j.job_id for j in batch], [j.job_id for j in waiting]
+
+    # within a batch: a state's second job waits, later independent jobs still join
+    assert take([7, 7, None, 8, 7]) == ([0, 2, 3], [1, 4])
+    # a state in flight: its jobs wait in place, the rest fill the batch (up to max_jobs)
+    assert take([7, None, 7, 8, 9, 10], busy={7}) == ([1, 3, 4, 5], [0, 2])
+    # every waiting job waits on a batch in flight: they form one batch, one job per state
+    assert take([7, 8, 7], busy={7, 8}) == ([0, 1], [2])
+    # nothing busy, nothing tracked: plain arrival order up to max_jobs
+    assert take([None] * 6) == ([0, 1, 2, 3], [4, 5])
+    # the arena bounds a batch (jobs' bytes plus one alignment pad): the rest stay waiting
+    srv.arena_bytes = 2 * (1 << 10) + serve._ALIGN
+    assert take([None] * 5) == ([0, 1], [2, 3, 4])
