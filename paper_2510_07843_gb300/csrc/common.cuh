@@ -161,15 +161,19 @@ __device__ __forceinline__ void pam_llr(float v, float scale, float* out) {
   }
 }
 
-// LLRs of one layer's QM bits (b0, b1, ... interleaving I and Q) from the unbiased symbol x~ and
-// effective noise s2eff. The axis grid is the NR normalisation sqrt(2 (4^H - 1) / 3).
+// LLRs of one layer's QM bits (b0, b1, ... interleaving I and Q) from the unbiased symbol x~,
+// given the scale 1 / (nrm2 s2eff) for effective noise s2eff, nrm2 = 2 (4^H - 1) / 3 the squared
+// NR grid normalisation (distances in grid units squared are nrm2 times the normalised ones).
+// With s2eff = e / mu and SINR = mu / e the scale is SINR / nrm2 (qam_inv_nrm2).
 template <int QM>
-__device__ __forceinline__ void qam_llr(cf xt, float s2eff, float* llr) {
+__device__ __forceinline__ constexpr float qam_inv_nrm2() {
+  return 3.f / (2.f * ((1 << QM) - 1));
+}
+template <int QM>
+__device__ __forceinline__ void qam_llr_scaled(cf xt, float scale, float* llr) {
   constexpr int H = QM / 2;
   constexpr float nrm2 = 2.f * ((1 << (2 * H)) - 1) / 3.f;  // squared normalisation
   const float a = sqrtf(nrm2);
-  // distances in grid units squared are nrm2 times the normalised ones
-  const float scale = 1.f / (nrm2 * s2eff);
   float li[H], lq[H];
   pam_llr<H>(xt.x * a, scale, li);
   pam_llr<H>(xt.y * a, scale, lq);
@@ -178,6 +182,12 @@ __device__ __forceinline__ void qam_llr(cf xt, float s2eff, float* llr) {
     llr[2 * i] = li[i];
     llr[2 * i + 1] = lq[i];
   }
+}
+// The same from the effective noise s2eff.
+template <int QM>
+__device__ __forceinline__ void qam_llr(cf xt, float s2eff, float* llr) {
+  constexpr float nrm2 = 2.f * ((1 << QM) - 1) / 3.f;
+  qam_llr_scaled<QM>(xt, 1.f / (nrm2 * s2eff), llr);
 }
 
 // An LLR pair to the output at element index idx (even): FP32, or binary16 rounded to nearest

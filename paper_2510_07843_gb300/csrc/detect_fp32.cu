@@ -442,14 +442,14 @@ __device__ __forceinline__ void store_llr_record(float* base, size_t idx, const 
   }
 }
 
-// LLRs of one layer (unbiased symbol xt, effective noise s2eff), or zeros when !ok, stored as
-// the record of layer index li.
+// LLRs of one layer (unbiased symbol xt; the layer's SINR gives the noise scale), or zeros when
+// !ok, stored as the record of layer index li.
 template <int QM>
-__device__ __forceinline__ void demap_store(float* llr, size_t li, cf xt, float s2eff, bool ok,
+__device__ __forceinline__ void demap_store(float* llr, size_t li, cf xt, float sinr, bool ok,
                                             bool f16) {
   float v[QM];
   if (ok) {
-    qam_llr<QM>(xt, s2eff, v);
+    qam_llr_scaled<QM>(xt, sinr * qam_inv_nrm2<QM>(), v);
   } else {
 #pragma unroll
     for (int q = 0; q < QM; ++q) v[q] = 0.f;
@@ -458,16 +458,16 @@ __device__ __forceinline__ void demap_store(float* llr, size_t li, cf xt, float 
 }
 // As demap_store for a compile-time QM, or for QM = 0 the run-time qm.
 template <int QM>
-__device__ __forceinline__ void demap_store_q(int qm, float* llr, size_t li, cf xt, float s2eff,
+__device__ __forceinline__ void demap_store_q(int qm, float* llr, size_t li, cf xt, float sinr,
                                               bool ok, bool f16) {
   if constexpr (QM > 0) {
-    demap_store<QM>(llr, li, xt, s2eff, ok, f16);
+    demap_store<QM>(llr, li, xt, sinr, ok, f16);
   } else {
     switch (qm) {
-      case 2: demap_store<2>(llr, li, xt, s2eff, ok, f16); break;
-      case 4: demap_store<4>(llr, li, xt, s2eff, ok, f16); break;
-      case 6: demap_store<6>(llr, li, xt, s2eff, ok, f16); break;
-      default: demap_store<8>(llr, li, xt, s2eff, ok, f16); break;
+      case 2: demap_store<2>(llr, li, xt, sinr, ok, f16); break;
+      case 4: demap_store<4>(llr, li, xt, sinr, ok, f16); break;
+      case 6: demap_store<6>(llr, li, xt, sinr, ok, f16); break;
+      default: demap_store<8>(llr, li, xt, sinr, ok, f16); break;
     }
   }
 }
@@ -666,7 +666,7 @@ __device__ __forceinline__ bool re_solve_body(
       const bool okr = oks[re] != 0;
       const LayerOut o = layer_stats(s2, ds[re * kXs + l]);
       const size_t li = (r0 + re) * nl + l;
-      if (llr_out) demap_store_q<QM>(qm, llr_out, li, o.inv_mu * xl, o.s2eff, okr, g.llr_f16);
+      if (llr_out) demap_store_q<QM>(qm, llr_out, li, o.inv_mu * xl, o.sinr, okr, g.llr_f16);
       if (sinr_out) sinr_out[li] = okr ? o.sinr : 0.f;
       if (x_hat) st(x_hat + li, okr ? xl : mk(0.f, 0.f));
     }
@@ -679,7 +679,7 @@ __device__ __forceinline__ bool re_solve_body(
       if (ok) {
         if (x_hat) st(x_hat + li, x[l]);
         if (sinr_out) sinr_out[li] = o.sinr;
-        if (llr_out) demap_store_q<QM>(qm, llr_out, li, o.inv_mu * x[l], o.s2eff, true, g.llr_f16);
+        if (llr_out) demap_store_q<QM>(qm, llr_out, li, o.inv_mu * x[l], o.sinr, true, g.llr_f16);
       } else {
         if (x_hat) st(x_hat + li, mk(0.f, 0.f));
         if (sinr_out) sinr_out[li] = 0.f;
@@ -913,7 +913,7 @@ __device__ __forceinline__ void direct_cta(const Geo& g, int k0, int t, int cell
     if (x_hat) st(x_hat + li, ok ? x[l] : mk(0.f, 0.f));
     if (sinr_out) sinr_out[li] = ok ? o.sinr : 0.f;
     if (llr_out)
-      demap_store_q<QM>(qm, llr_out, li, ok ? o.inv_mu * x[l] : mk(0.f, 0.f), o.s2eff, ok,
+      demap_store_q<QM>(qm, llr_out, li, ok ? o.inv_mu * x[l] : mk(0.f, 0.f), o.sinr, ok,
                         g.llr_f16);
   }
 }
